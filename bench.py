@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Benchmark of the 2D Tree Sliding Window DFT on one GB300 (or N, one process per GPU).
+
+Workload: the 512x512 float32 image of N(0,1) noise plus three sinusoids (seed 1) with
+32x32 windows at all 481x481 positions: 236,913,664 complex64 coefficients (1.895 GB) per
+step.  A step is one pass of the whole forward path: the row-level kernel (Eq. rowfswft2d)
+and the column-level kernel (Eq. colfswft2d), launched through the C ABI.
+
+Prints one JSON line: coefficients/s (value, whole job), the dominant kernel's roofline
+against the measured HBM bandwidth, the end-to-end rate through host buffers, clocks seen
+during the timed region, and the FP64 oracle timed on the host's cores on a bounded sample.
+``--impl reference`` times the FP64 oracle itself as the reference arm.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the stream
+the kernels run on; a 512 MiB buffer (> 129 MB L2) is rewritten before every step, outside
+the events, so each step starts with a cold L2.  Multi-GPU (torchrun): every rank runs its
+own copy of the workload (weak scaling, no data exchange); value = all ranks' coefficients
+over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2D SWDFT output coeffs/s & HBM GB/s; TC split-precision vs FP32 tree at ≤1e-5 err"
+UNIT = "coeffs/s"
+N0 = N1 = 512
+n0 = n1 = 32
+P0, P1 = N0 - n0 + 1, N1 - n1 + 1
+COEFFS = P0 * P1 * n0 * n1
+WORKLOAD = "sinusoids_512: 512x512 float32 N(0,1)+3 sinusoids (seed 1), 32x32 windows, 481x481 positions"
+FALLBACK_HBM_GBS = 6800.0
+# files whose content defines the column-level kernel (for matching a stored ncu capture)
+COL_KERNEL_SOURCES = ["paper_1707_08213_gb300/csrc/tree_core.cuh",
+                      "paper_1707_08213_gb300/csrc/tree_kernels.cuh",
+                      "paper_1707_08213_gb300/csrc/tree_col_m5.cu"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "col_tree_sinusoids_512.json")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def config_dict(extra=None):
+    c = {"workload": WORKLOAD, "N0": N0, "N1": N1, "n0": n0, "n1": n1, "P0": P0, "P1": P1,
+         "coeffs_per_step": COEFFS, "output_bytes_per_step": 8 * COEFFS,
+         "l2": "512 MiB buffer rewritten before every timed step (outside the events)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def source_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------------- clocks sampler
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def gpu_id_for(torch, dev):
+    try:
+        u = torch.cuda.get_device_properties(dev).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        return vis.split(",")[dev] if vis else str(dev)
+
+
+# ----------------------------------------------------------------------- CPU baselines
+
+def oracle_sample(x, seconds, seed=0):
+    """Time the FP64 oracle (row-column form, 1 thread) on random windows for ~seconds."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    oracle.swdft2d_windows(x, n0, n1, [0] * 64, [0] * 64)
+    per = (time.perf_counter() - t0) / 64
+    count = max(64, int(seconds / max(per, 1e-9)))
+    q0 = rng.integers(0, P0, count)
+    q1 = rng.integers(0, P1, count)
+    t0 = time.perf_counter()
+    ref = oracle.swdft2d_windows(x, n0, n1, q0, q1, threads=1)
+    dt = time.perf_counter() - t0
+    return {"value": count * n0 * n1 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{count} random windows of the 512x512/32x32 workload "
+                      f"(FP64 row-column sum, 1 thread), {dt:.1f} s"}, (q0, q1, ref)
+
+
+def cpu_tree_sample(x, rows=16):
+    """The paper's tree (Section 4.3 loop order) in FP32 with OpenMP on all host cores, on a
+    band of output rows."""
+    import oracle
+    cores = os.cpu_count() or 1
+    band = x[:rows + n0 - 1]
+    t0 = time.perf_counter()
+    oracle.tree2d(band, n0, n1, precision="f32", threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": rows * P1 * n0 * n1 / dt, "unit": UNIT, "cores": cores,
+            "kind": "paper tree, FP32, OpenMP",
+            "sample": f"output rows 0..{rows - 1} ({rows}x{P1} windows), {dt:.2f} s"}
+
+
+# ----------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    import workloads
+    oracle.build()
+    x = workloads.sinusoids_512().images[0]
+    t0 = time.perf_counter()
+    oracle.swdft2d_windows(x, n0, n1, [0] * 32, [0] * 32)
+    per = (time.perf_counter() - t0) / 32
+    budget = 150.0  # seconds of oracle work for warm-up + timed steps together
+    per_step = max(1, int(budget / max(1, args.steps + args.warmup) / max(per, 1e-9)))
+    rng = np.random.default_rng(0)
+    for _ in range(args.warmup):
+        oracle.swdft2d_windows(x, n0, n1, rng.integers(0, P0, per_step), rng.integers(0, P1, per_step))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.swdft2d_windows(x, n0, n1, rng.integers(0, P0, per_step), rng.integers(0, P1, per_step))
+    dt = time.perf_counter() - t0
+    value = args.steps * per_step * n0 * n1 / dt
+    sample = (f"{per_step} random windows per step of the 512x512/32x32 workload, FP64 "
+              f"row-column oracle, 1 host thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict({"reference": "FP64 CPU oracle (direct definition, Eq. 2, "
+                                                "row-column order)"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    rank, world, local_rank = dist_env()
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1707_08213_gb300 as sw
+    import workloads
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    x = workloads.sinusoids_512().images[0]
+    xd = torch.from_numpy(x).to(dev)
+    t = sw.Transform([(N0, N1, n0, n1, sw.R32)], device=dev)
+    out = t.empty_outputs()[0]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    in_ptrs, out_ptrs, ws = [xd.data_ptr()], [out.data_ptr()], t._ws_ptr
+
+    for _ in range(args.warmup):
+        t.plan.execute(in_ptrs, out_ptrs, ws, sp)
+    torch.cuda.synchronize(dev)
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    sampler = ClockSampler(gpu_id_for(torch, local_rank))
+    sampler.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        t.plan.execute_stage(0, in_ptrs, out_ptrs, ws, sp)   # row levels -> z
+        ev[k][1].record(stream)
+        t.plan.execute_stage(1, in_ptrs, out_ptrs, ws, sp)   # column levels -> output
+        ev[k][2].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    row_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
+    col_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]
+    total_ms = sum(r + c for r, c in zip(row_ms, col_ms))
+    if dist is not None:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / K
+    value = world * K * COEFFS / (total_ms / 1e3)
+
+    # dominant kernel: the column-level pass (output writes)
+    col_avg = sum(col_ms) / K
+    row_avg = sum(row_ms) / K
+    z_bytes = (N0 * P1 * n1) * 8
+    col_alg_bytes = 8 * COEFFS + z_bytes              # output written + z read once
+    row_alg_bytes = 4 * N0 * N1 + z_bytes             # input read + z written
+    peak, peak_kind = measured_peak_hbm()
+    achieved = col_alg_bytes / (col_avg / 1e3) / 1e9
+    traffic = None
+    try:
+        with open(TRAFFIC_FILE) as f:
+            prof = json.load(f)
+        if prof.get("source_sha") == source_sha(COL_KERNEL_SOURCES):
+            traffic = prof.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    roofline = {"bound": "hbm", "kernel": "col_tree_kernel<5,2> (column levels, Eq. colfswft2d)",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": col_alg_bytes, "avg_launch_ms": round(col_avg, 5),
+                "row_pass": {"avg_launch_ms": round(row_avg, 5),
+                             "algorithmic_bytes_per_launch": row_alg_bytes,
+                             "achieved_gbs": round(row_alg_bytes / (row_avg / 1e3) / 1e9, 1)},
+                "step_output_gbs": round(8 * COEFFS / (ms_per_step / 1e3) / 1e9, 1)}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e, check = None, None
+    if args.e2e_steps > 0:
+        th = sw.Transform([(N0, N1, n0, n1, sw.R32)], device=dev, flags=sw.FLAG_HOST_IO)
+        h_in = torch.from_numpy(x).pin_memory()
+        h_out = torch.empty((P0, P1, n0, n1), dtype=torch.complex64).pin_memory()
+        for _ in range(2):
+            th.plan.execute_host([h_in.data_ptr()], [h_out.data_ptr()], sp)
+        times = []
+        for _ in range(args.e2e_steps):
+            t0 = time.perf_counter()
+            th.plan.execute_host([h_in.data_ptr()], [h_out.data_ptr()], sp)
+            times.append(time.perf_counter() - t0)
+        e2e_s = sum(times) / len(times)
+        if dist is not None:
+            tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": world * COEFFS / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * N0 * N1,
+               "d2h_bytes_per_step": 8 * COEFFS, "ms_per_step": round(e2e_s * 1e3, 3),
+               "path": "swdft2d_execute_host: pinned host input -> device, 128 MiB output "
+                       "bands copied back while the next band computes"}
+        check = h_out
+        del th
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config_dict({"algo": "tree_f32",
+                                                        "parallelism": f"replicas x{world}"}),
+            "roofline": roofline, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": K * t.plan.launch_count(),
+            "wall_s_timed_region": round(wall, 3)}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import workloads as _w
+        cb, (q0, q1, ref) = oracle_sample(x, args.cpu_seconds)
+        line["cpu_baseline"] = cb
+        got = out[torch.from_numpy(q0).to(dev), torch.from_numpy(q1).to(dev)].cpu().numpy()
+        err, rms = _w.normalised_error(got, ref, _w.window_sq_norms_at(x, n0, n1, q0, q1))
+        line["error_vs_oracle"] = {"max": err, "rms": rms, "windows": int(len(q0)),
+                                   "metric": "max_k |a - a_oracle| / ||x_w||_2"}
+        if check is not None:
+            line["e2e"]["matches_device_path"] = bool(
+                torch.equal(check[q0[:64], q1[:64]], out[q0[:64], q1[:64]].cpu()))
+        try:
+            line["cpu_tree"] = cpu_tree_sample(x)
+        except Exception as e:  # noqa: BLE001
+            line["cpu_tree"] = {"error": str(e)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

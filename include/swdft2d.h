@@ -1,0 +1,186 @@
+/*
+ * swdft2d.h -- C ABI of the GB300 (sm_103a) 2D Tree Sliding Window DFT library.
+ *
+ * The operation (Richardson & Eddy, "The 2D Tree Sliding Window Discrete Fourier
+ * Transform", arXiv 1707.08213):
+ *
+ *   Section 4.1, Eq. (2): for an N0 x N1 array x and n0 x n1 windows (n_i = 2^m_i,
+ *   n_i <= N_i), every window position gets its 2D DFT
+ *
+ *     a[q0,q1,k0,k1] = c * sum_{j0<n0} sum_{j1<n1} x[q0+j0, q1+j1] w_{n0}^{-j0 k0} w_{n1}^{-j1 k1}
+ *
+ *   with w_n = exp(2 pi i / n), k_i < n_i, q_i < P_i = N_i - n_i + 1.  The paper names a
+ *   window by its last row/column p_i = q_i + n_i - 1 (p_i = n_i-1 .. N_i-1); the
+ *   position convention below only chooses which of the two indices the caller uses.
+ *   The default scale c is Eq. (2)'s 1/sqrt(n0 n1).
+ *
+ *   Section 4.2, Eqs. (rowfswft2d), (colfswft2d): the GPU evaluates it with the paper's tree
+ *   of radix-2 butterflies shared between overlapping windows, O(N0 N1 n0 n1) work:
+ *   m1 levels along dimension 1 (shift s = 2^(m1-t)), then m0 levels along dimension 0
+ *   (shift s = 2^(m0+m1-v)), each node T_A = T_B + Omega_C * T_D.  Level m0+m1 is the
+ *   window's DFT in natural (k0, k1) order.
+ *
+ * Memory layout (all row-major, no padding between windows):
+ *   input  : N0 rows of N1 elements, row stride ld elements; float32 (SWDFT_R32) or
+ *            interleaved complex64 (SWDFT_C64).
+ *   output : complex64 interleaved (re, im), [q0 - row_begin][q1][k0][k1]; the window's
+ *            n0*n1 coefficients are contiguous, windows of one output row are contiguous.
+ *            Bytes = 8 * rows * P1 * n0 * n1.
+ *
+ * Ownership: the caller owns every input, output and workspace buffer and passes plain
+ * pointers; the plan owns only host-side state (twiddle tables, chosen kernels, tuning,
+ * a captured CUDA graph and, with SWDFT_FLAG_HOST_IO, device staging buffers).
+ * swdft2d_destroy frees only what the plan owns.
+ *
+ * Errors: every call returns a swdft_status; nothing aborts, exits or throws across the
+ * ABI.  Argument checks happen before any CUDA call.  A CUDA launch or copy failure
+ * returns SWDFT_ERR_CUDA; asynchronous faults surface at the next synchronising call.
+ * Device kernels in this library contain no spin-waits.
+ *
+ * Threads and streams: a plan is immutable after swdft2d_plan except for its tuning
+ * state, graph and staging buffers; do not execute one plan on two streams at once.
+ */
+#ifndef SWDFT2D_H
+#define SWDFT2D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct swdft2d_plan_s *swdft2d_plan_t; /* opaque, library-owned */
+
+typedef enum {
+    SWDFT_OK = 0,
+    SWDFT_ERR_INVALID_ARG = -1,       /* null pointer, bad enum, negative size, bad band */
+    SWDFT_ERR_NOT_POW2 = -2,          /* n0 or n1 is not a power of two (radix-2 only, Sec. 4.2) */
+    SWDFT_ERR_WINDOW_TOO_LARGE = -3,  /* n_i > N_i: no window position exists */
+    SWDFT_ERR_UNSUPPORTED = -4,       /* valid request this build does not implement */
+    SWDFT_ERR_OOM = -5,               /* host or device allocation of plan-owned memory failed */
+    SWDFT_ERR_CUDA = -6,              /* a CUDA runtime call failed (launch, copy, graph) */
+    SWDFT_ERR_DEVICE_TIMEOUT = -7,    /* reserved: a bounded device wait ran out */
+    SWDFT_ERR_WORKSPACE = -8          /* workspace pointer null or misaligned while size > 0 */
+} swdft_status;
+
+typedef enum { SWDFT_R32 = 0, SWDFT_C64 = 1 } swdft_dtype;
+
+typedef enum {
+    SWDFT_NORM_UNITARY = 0, /* c = 1/sqrt(n0 n1), Eq. (2) (default) */
+    SWDFT_NORM_NONE = 1,    /* c = 1, the bare tree sums of Eqs. (rowfswft2d)/(colfswft2d) */
+    SWDFT_NORM_INV_N = 2    /* c = 1/(n0 n1), the 2D analogue of the 1D Eq. (1) */
+} swdft_norm;
+
+typedef enum {
+    SWDFT_POS_START = 0, /* band rows given as q0 = first row of the window */
+    SWDFT_POS_END = 1    /* band rows given as p0 = last row of the window (the paper's p) */
+} swdft_pos;
+
+typedef enum {
+    SWDFT_ALGO_AUTO = 0,          /* tree unless a tuned choice says otherwise */
+    SWDFT_ALGO_TREE_F32 = 1,      /* FP32 tree (Section 4.2) on CUDA cores */
+    SWDFT_ALGO_TC_BF16X3 = 2,     /* row GEMM + column GEMM on tcgen05, split bf16 hi/lo, 3 terms */
+    SWDFT_ALGO_TC_BF16 = 3,       /* same, plain bf16 operands (error reported, not bounded) */
+    SWDFT_ALGO_TC_F16_SCALED = 4, /* same, fp16 operands with a per-image scale */
+    SWDFT_ALGO_TC_F16 = 5         /* same, plain fp16 operands */
+} swdft_algo;
+
+enum {
+    SWDFT_FLAG_GRAPH = 1u,    /* capture each execute's launch sequence in a CUDA graph, replay after */
+    SWDFT_FLAG_HOST_IO = 2u,  /* plan owns device staging so swdft2d_execute_host can run */
+    SWDFT_FLAG_PERSISTENT = 4u /* batch: one persistent launch over all (image, tile) items */
+};
+
+/* One array of a batch.  row_begin/row_end select a band of output window rows in the
+ * plan's position convention ([row_begin, row_end); row_end = 0 means through the last
+ * window row).  The band still reads rows from row 0 of the input pointer. */
+typedef struct {
+    int64_t N0, N1;  /* array rows and columns, >= 1 */
+    int64_t ld;      /* input row stride in elements, >= N1; 0 means N1 */
+    int32_t n0, n1;  /* window rows and columns: powers of two, 1 <= n_i <= N_i */
+    int32_t dtype;   /* swdft_dtype of the input */
+    int32_t reserved;
+    int64_t row_begin, row_end;
+} swdft2d_shape;
+
+/* Create a plan for `batch` arrays (Section 4.1's problem for each).  Host work only:
+ * validates every shape (SWDFT_ERR_NOT_POW2 / WINDOW_TOO_LARGE / INVALID_ARG), builds the
+ * twiddle vectors Omega^0, Omega^1 of Section 4.2 in FP64 and rounds them to FP32, and
+ * picks kernels.  SWDFT_ERR_UNSUPPORTED for an algorithm or window size this build lacks
+ * (tree: n_i <= 64).  *plan is NULL on any error. */
+swdft_status swdft2d_plan(swdft2d_plan_t *plan, int32_t batch, const swdft2d_shape *shapes,
+                          int32_t norm, int32_t pos, int32_t algo, uint32_t flags);
+
+/* out[4] = {band rows, P1, n0, n1} of array i (Eq. (2)'s P0 x P1 x n0 x n1 output). */
+swdft_status swdft2d_output_shape(swdft2d_plan_t plan, int32_t i, int64_t out[4]);
+
+/* Device workspace bytes execute/execute_adjoint need (0 allowed; then pass NULL).
+ * The workspace must be 256-byte aligned; its contents need no initialisation. */
+swdft_status swdft2d_workspace_size(swdft2d_plan_t plan, size_t *bytes);
+
+/* The algorithm actually used (after AUTO and tuning). */
+swdft_status swdft2d_get_algo(swdft2d_plan_t plan, int32_t *algo);
+
+/* Forward transform, Eq. (2), of every array of the plan, enqueued on `stream`
+ * (a cudaStream_t; NULL = legacy default stream).  d_in[i] / d_out[i]: device pointers of
+ * array i, layouts above; input 4-byte (R32) or 8-byte (C64) aligned, output 16-byte
+ * aligned.  d_workspace: swdft2d_workspace_size bytes.  Returns after enqueueing. */
+swdft_status swdft2d_execute(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out,
+                             void *d_workspace, void *stream);
+
+/* Adjoint A^H of the forward map (the transpose of the tree, conjugated twiddles):
+ *   g[r,c] = sum over windows q containing (r,c) of c * sum_k G[q,k] w_{n0}^{+(r-q0)k0} w_{n1}^{+(c-q1)k1}
+ * i.e. the overlap-add of every window's inverse DFT of the upstream gradient G.
+ * d_grad_out[i]: complex64 G with the forward output layout (band rows only);
+ * d_grad_in[i]: N0 x N1 (row stride N1) float32 = Re(A^H G) for R32 inputs, complex64
+ * for C64.  Every element of d_grad_in is written (rows outside the band's reach get 0). */
+swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_grad_out,
+                                     void *const *d_grad_in, void *d_workspace, void *stream);
+
+/* Forward transform with HOST buffers (plan made with SWDFT_FLAG_HOST_IO): copies each
+ * input host->device, runs the transform in output-row bands and copies every band
+ * device->host while the next band computes, then synchronises `stream`.  Host buffers
+ * should be page-locked (cudaHostAlloc / torch pin_memory) for the copies to overlap. */
+swdft_status swdft2d_execute_host(swdft2d_plan_t plan, const void *const *h_in,
+                                  void *const *h_out, void *stream);
+
+/* Time every candidate kernel configuration of this plan on the given buffers (CUDA
+ * events on `stream`) and keep the fastest; the choice is reused by later executes and
+ * recorded in the cache file named by the SWDFT_TUNE_CACHE environment variable, if set. */
+swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out,
+                              void *d_workspace, void *stream);
+
+/* One pass of the forward tree only, for profiling: stage 0 runs the row levels
+ * (Eq. rowfswft2d) of every array into the workspace, stage 1 the column levels
+ * (Eq. colfswft2d) from the workspace into d_out.  stage 0 then 1 equals swdft2d_execute
+ * (without graph capture).  Other stage values: SWDFT_ERR_INVALID_ARG. */
+swdft_status swdft2d_execute_stage(swdft2d_plan_t plan, int32_t stage, const void *const *d_in,
+                                   void *const *d_out, void *d_workspace, void *stream);
+
+/* Override the tree kernels' launch configuration of array i (what swdft2d_autotune
+ * chooses): row_B / col_B = log2 of the threads sharing one tree's butterflies along
+ * dimension 1 / 0 (clamped to [0, min(m, 3)]), row_chunk = window columns per row-pass
+ * thread, col_chunk = window rows per column-pass thread (0 = all), col_groups = 32-channel
+ * groups per column-pass block.  Results do not depend on these values; speed does. */
+swdft_status swdft2d_set_tree_config(swdft2d_plan_t plan, int32_t i, int32_t row_B,
+                                     int64_t row_chunk, int32_t col_B, int64_t col_chunk,
+                                     int32_t col_groups);
+
+/* Number of kernel launches one execute enqueues (graph replays count their kernels). */
+swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t *launches);
+
+/* Free the plan and everything it owns.  NULL is accepted. */
+swdft_status swdft2d_destroy(swdft2d_plan_t plan);
+
+/* Static string for a status code. */
+const char *swdft2d_status_string(int32_t status);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int32_t swdft2d_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWDFT2D_H */

@@ -1,0 +1,545 @@
+// C-ABI of the sliding window DFT library (include/swdft2d.h): plan validation, twiddle
+// tables, kernel selection, launch sequencing, CUDA-graph replay, the host-buffer band
+// pipeline and the autotuner.  Compute happens only in the kernels of the .cu files.
+#include "swdft2d.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "swdft_internal.h"
+
+using namespace swdft;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+int log2_exact(int64_t n) {
+    if (n < 1) return -1;
+    int m = 0;
+    while ((int64_t(1) << m) < n) ++m;
+    return (int64_t(1) << m) == n ? m : -1;
+}
+
+struct TreeConfig {
+    int row_B = 2;
+    int64_t row_chunk = 0;
+    int col_B = 2;
+    int64_t col_chunk = 0;
+    int col_groups = 2;
+};
+
+struct ArrayPlan {
+    int64_t N0 = 0, N1 = 0, ld = 0, P0 = 0, P1 = 0;
+    int n0 = 1, n1 = 1, m0 = 0, m1 = 0, dtype = SWDFT_R32;
+    int64_t q_begin = 0, q_end = 0;  // band of window rows, q coordinates
+    float2 om0[kMaxN], om1[kMaxN];
+    TreeConfig cfg;
+    bool tuned = false;
+
+    int64_t band_rows() const { return q_end - q_begin; }
+    size_t in_elem() const { return dtype == SWDFT_C64 ? sizeof(float2) : sizeof(float); }
+    size_t out_row_bytes() const { return (size_t)P1 * n0 * n1 * sizeof(float2); }
+    // n0/2 padding rows in front of z (column-pass look-back), then rows_out + n0 - 1 rows
+    int64_t z_pad() const { return n0 / 2; }
+    size_t z_bytes(int64_t rows_out) const {
+        return (size_t)(z_pad() + rows_out + n0 - 1) * (size_t)P1 * n1 * sizeof(float2);
+    }
+};
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void *> key;
+    cudaStream_t stream = nullptr;
+};
+
+}  // namespace
+
+struct swdft2d_plan_s {
+    std::vector<ArrayPlan> arrays;
+    int norm = SWDFT_NORM_UNITARY, pos = SWDFT_POS_START, algo = SWDFT_ALGO_TREE_F32;
+    uint32_t flags = 0;
+    size_t ws_bytes = 0;
+    bool configured = false;
+    int sm_count = 152;
+    GraphCache graph;
+    // host-buffer pipeline (SWDFT_FLAG_HOST_IO), allocated at the first execute_host
+    bool io_ready = false;
+    int64_t io_band = 0;
+    void *io_in = nullptr;
+    void *io_ws = nullptr;
+    void *io_out[2] = {nullptr, nullptr};
+    cudaStream_t io_copy = nullptr;
+    cudaEvent_t io_done[2] = {nullptr, nullptr};
+    cudaEvent_t io_copied[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+float norm_scale(int norm, int n0, int n1) {
+    const double nn = (double)n0 * (double)n1;
+    switch (norm) {
+        case SWDFT_NORM_NONE: return 1.0f;
+        case SWDFT_NORM_INV_N: return (float)(1.0 / nn);
+        default: return (float)(1.0 / std::sqrt(nn));
+    }
+}
+
+void default_config(ArrayPlan &a, int sm_count) {
+    TreeConfig c;
+    const int64_t target = (int64_t)sm_count * 1024;  // threads in flight we aim for
+    // row levels: thread = (row, residue, chunk of positions)
+    c.row_B = std::min(a.m1, 2);
+    const int64_t rows = a.band_rows() + a.n0 - 1;
+    int64_t nchunk = std::max<int64_t>(1, target / std::max<int64_t>(1, rows << c.row_B));
+    int64_t chunk = (a.P1 + nchunk - 1) / nchunk;
+    c.row_chunk = std::max<int64_t>(chunk, std::min<int64_t>(a.P1, 2 * a.n1));
+    // column levels: thread = (channel, residue, chunk of output rows)
+    c.col_B = std::min(a.m0, 2);
+    const int64_t nch = a.P1 * a.n1;
+    nchunk = std::max<int64_t>(1, target / std::max<int64_t>(1, nch << c.col_B));
+    chunk = (a.band_rows() + nchunk - 1) / nchunk;
+    c.col_chunk = std::max<int64_t>(chunk, std::min<int64_t>(a.band_rows(), 4 * a.n0));
+    c.col_groups = std::max(1, 256 / (32 << c.col_B));
+    a.cfg = c;
+}
+
+swdft_status configure(swdft2d_plan_t plan) {
+    if (plan->configured) return SWDFT_OK;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SWDFT_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return SWDFT_ERR_CUDA;
+    plan->sm_count = sms > 0 ? sms : 152;
+    for (auto &a : plan->arrays)
+        if (!a.tuned) default_config(a, plan->sm_count);
+    plan->configured = true;
+    return SWDFT_OK;
+}
+
+// Enqueue the forward transform of output rows [q_lo, q_hi) of array a.
+// stages: bit 0 = row levels (x -> z), bit 1 = column levels (z -> out).
+cudaError_t enqueue_forward(const swdft2d_plan_s *plan, const ArrayPlan &a, const void *in,
+                            void *out, void *ws, int64_t q_lo, int64_t q_hi, cudaStream_t s,
+                            int stages = 3) {
+    const int64_t rows_out = q_hi - q_lo;
+    if (rows_out <= 0) return cudaSuccess;
+    RowTreeArgs r;
+    r.x = in;
+    r.ld = a.ld;
+    r.cplx = a.dtype == SWDFT_C64;
+    r.r_base = q_lo;
+    r.rows = rows_out + a.n0 - 1;
+    r.P1 = a.P1;
+    r.m1 = a.m1;
+    float2 *z = static_cast<float2 *>(ws) + a.z_pad() * a.P1 * a.n1;
+    r.z = z;
+    r.om1 = a.om1;
+    r.B = a.cfg.row_B;
+    r.chunk = a.cfg.row_chunk;
+    if (stages & 1) {
+        cudaError_t e = launch_row_tree(r, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (!(stages & 2)) return cudaSuccess;
+    ColTreeArgs c;
+    c.z = z;
+    c.P1 = a.P1;
+    c.rows_out = rows_out;
+    c.m0 = a.m0;
+    c.m1 = a.m1;
+    c.out = static_cast<float2 *>(out);
+    c.scale = norm_scale(plan->norm, a.n0, a.n1);
+    c.om0 = a.om0;
+    c.B = a.cfg.col_B;
+    c.chunk = a.cfg.col_chunk;
+    c.groups = a.cfg.col_groups;
+    return launch_col_tree(c, s);
+}
+
+swdft_status enqueue_all(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out,
+                         void *ws, cudaStream_t s, int stages = 3) {
+    for (size_t i = 0; i < plan->arrays.size(); ++i) {
+        const ArrayPlan &a = plan->arrays[i];
+        if (enqueue_forward(plan, a, d_in[i], d_out[i], ws, a.q_begin, a.q_end, s, stages) != cudaSuccess)
+            return SWDFT_ERR_CUDA;
+    }
+    return SWDFT_OK;
+}
+
+swdft_status check_buffers(swdft2d_plan_t plan, const void *const *in, void *const *out,
+                           void *ws) {
+    if (!in || !out) return SWDFT_ERR_INVALID_ARG;
+    for (size_t i = 0; i < plan->arrays.size(); ++i) {
+        const ArrayPlan &a = plan->arrays[i];
+        if (!in[i] || !out[i]) return SWDFT_ERR_INVALID_ARG;
+        if ((uintptr_t)in[i] % a.in_elem() != 0) return SWDFT_ERR_INVALID_ARG;
+        if ((uintptr_t)out[i] % 16 != 0) return SWDFT_ERR_INVALID_ARG;
+    }
+    if (plan->ws_bytes > 0 && (!ws || (uintptr_t)ws % kAlign != 0)) return SWDFT_ERR_WORKSPACE;
+    return SWDFT_OK;
+}
+
+void destroy_graph(GraphCache &g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    g.key.clear();
+    g.stream = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t swdft2d_version(void) { return 100; }
+
+const char *swdft2d_status_string(int32_t s) {
+    switch (s) {
+        case SWDFT_OK: return "SWDFT_OK";
+        case SWDFT_ERR_INVALID_ARG: return "SWDFT_ERR_INVALID_ARG: invalid argument";
+        case SWDFT_ERR_NOT_POW2: return "SWDFT_ERR_NOT_POW2: window sides must be powers of two";
+        case SWDFT_ERR_WINDOW_TOO_LARGE: return "SWDFT_ERR_WINDOW_TOO_LARGE: window larger than the array";
+        case SWDFT_ERR_UNSUPPORTED: return "SWDFT_ERR_UNSUPPORTED: not implemented for this request";
+        case SWDFT_ERR_OOM: return "SWDFT_ERR_OOM: allocation failed";
+        case SWDFT_ERR_CUDA: return "SWDFT_ERR_CUDA: a CUDA call failed";
+        case SWDFT_ERR_DEVICE_TIMEOUT: return "SWDFT_ERR_DEVICE_TIMEOUT: a bounded device wait ran out";
+        case SWDFT_ERR_WORKSPACE: return "SWDFT_ERR_WORKSPACE: workspace missing or misaligned";
+        default: return "unknown swdft status";
+    }
+}
+
+swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shape *shapes,
+                          int32_t norm, int32_t pos, int32_t algo, uint32_t flags) {
+    if (!out) return SWDFT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (batch < 1 || !shapes) return SWDFT_ERR_INVALID_ARG;
+    if (norm < SWDFT_NORM_UNITARY || norm > SWDFT_NORM_INV_N) return SWDFT_ERR_INVALID_ARG;
+    if (pos != SWDFT_POS_START && pos != SWDFT_POS_END) return SWDFT_ERR_INVALID_ARG;
+    if (algo < SWDFT_ALGO_AUTO || algo > SWDFT_ALGO_TC_F16) return SWDFT_ERR_INVALID_ARG;
+    if (flags & ~(uint32_t)(SWDFT_FLAG_GRAPH | SWDFT_FLAG_HOST_IO | SWDFT_FLAG_PERSISTENT))
+        return SWDFT_ERR_INVALID_ARG;
+
+    std::vector<ArrayPlan> arrays((size_t)batch);
+    for (int32_t i = 0; i < batch; ++i) {
+        const swdft2d_shape &s = shapes[i];
+        ArrayPlan &a = arrays[(size_t)i];
+        if (s.N0 < 1 || s.N1 < 1 || s.n0 < 1 || s.n1 < 1) return SWDFT_ERR_INVALID_ARG;
+        if (s.dtype != SWDFT_R32 && s.dtype != SWDFT_C64) return SWDFT_ERR_INVALID_ARG;
+        const int m0 = log2_exact(s.n0), m1 = log2_exact(s.n1);
+        if (m0 < 0 || m1 < 0) return SWDFT_ERR_NOT_POW2;
+        if (s.n0 > s.N0 || s.n1 > s.N1) return SWDFT_ERR_WINDOW_TOO_LARGE;
+        const int64_t ld = s.ld == 0 ? s.N1 : s.ld;
+        if (ld < s.N1) return SWDFT_ERR_INVALID_ARG;
+        a.N0 = s.N0;
+        a.N1 = s.N1;
+        a.ld = ld;
+        a.n0 = s.n0;
+        a.n1 = s.n1;
+        a.m0 = m0;
+        a.m1 = m1;
+        a.dtype = s.dtype;
+        a.P0 = s.N0 - s.n0 + 1;
+        a.P1 = s.N1 - s.n1 + 1;
+        // band of window rows in q coordinates
+        const int64_t shift = (pos == SWDFT_POS_END) ? (s.n0 - 1) : 0;
+        int64_t b = s.row_begin, e = s.row_end;
+        if (e == 0 && b == 0) {
+            a.q_begin = 0;
+            a.q_end = a.P0;
+        } else {
+            if (e == 0) e = a.P0 + shift;
+            a.q_begin = b - shift;
+            a.q_end = e - shift;
+            if (a.q_begin < 0 || a.q_end > a.P0 || a.q_begin >= a.q_end) return SWDFT_ERR_INVALID_ARG;
+        }
+        if (m0 > kMaxLog2 || m1 > kMaxLog2) return SWDFT_ERR_UNSUPPORTED;
+        make_omega(a.n0, a.om0);
+        make_omega(a.n1, a.om1);
+    }
+    if (algo != SWDFT_ALGO_AUTO && algo != SWDFT_ALGO_TREE_F32) return SWDFT_ERR_UNSUPPORTED;
+    if (flags & SWDFT_FLAG_PERSISTENT) return SWDFT_ERR_UNSUPPORTED;
+
+    swdft2d_plan_s *p = new (std::nothrow) swdft2d_plan_s();
+    if (!p) return SWDFT_ERR_OOM;
+    p->arrays = std::move(arrays);
+    p->norm = norm;
+    p->pos = pos;
+    p->algo = SWDFT_ALGO_TREE_F32;
+    p->flags = flags;
+    // arrays run one after another on one stream, so they share one z buffer
+    size_t ws = 0;
+    for (const auto &a : p->arrays) ws = std::max(ws, align_up(a.z_bytes(a.band_rows())));
+    p->ws_bytes = ws;
+    *out = p;
+    return SWDFT_OK;
+}
+
+swdft_status swdft2d_output_shape(swdft2d_plan_t plan, int32_t i, int64_t out[4]) {
+    if (!plan || !out || i < 0 || (size_t)i >= plan->arrays.size()) return SWDFT_ERR_INVALID_ARG;
+    const ArrayPlan &a = plan->arrays[(size_t)i];
+    out[0] = a.band_rows();
+    out[1] = a.P1;
+    out[2] = a.n0;
+    out[3] = a.n1;
+    return SWDFT_OK;
+}
+
+swdft_status swdft2d_workspace_size(swdft2d_plan_t plan, size_t *bytes) {
+    if (!plan || !bytes) return SWDFT_ERR_INVALID_ARG;
+    *bytes = plan->ws_bytes;
+    return SWDFT_OK;
+}
+
+swdft_status swdft2d_get_algo(swdft2d_plan_t plan, int32_t *algo) {
+    if (!plan || !algo) return SWDFT_ERR_INVALID_ARG;
+    *algo = plan->algo;
+    return SWDFT_OK;
+}
+
+swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t *launches) {
+    if (!plan || !launches) return SWDFT_ERR_INVALID_ARG;
+    if (adjoint) return SWDFT_ERR_UNSUPPORTED;
+    *launches = (int32_t)(2 * plan->arrays.size());
+    return SWDFT_OK;
+}
+
+swdft_status swdft2d_execute(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out,
+                             void *d_workspace, void *stream) {
+    if (!plan) return SWDFT_ERR_INVALID_ARG;
+    swdft_status st = check_buffers(plan, d_in, d_out, d_workspace);
+    if (st != SWDFT_OK) return st;
+    if ((st = configure(plan)) != SWDFT_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!(plan->flags & SWDFT_FLAG_GRAPH) || s == nullptr) return enqueue_all(plan, d_in, d_out, d_workspace, s);
+
+    // CUDA graph: capture the launch sequence once per (buffers, stream), replay after.
+    std::vector<const void *> key;
+    for (size_t i = 0; i < plan->arrays.size(); ++i) {
+        key.push_back(d_in[i]);
+        key.push_back(d_out[i]);
+    }
+    key.push_back(d_workspace);
+    GraphCache &g = plan->graph;
+    if (!g.exec || g.key != key || g.stream != s) {
+        destroy_graph(g);
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SWDFT_ERR_CUDA;
+        swdft_status est = enqueue_all(plan, d_in, d_out, d_workspace, s);
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (est != SWDFT_OK || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return est != SWDFT_OK ? est : SWDFT_ERR_CUDA;
+        }
+        ce = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            g.exec = nullptr;
+            return SWDFT_ERR_CUDA;
+        }
+        g.key = key;
+        g.stream = s;
+    }
+    return cudaGraphLaunch(g.exec, s) == cudaSuccess ? SWDFT_OK : SWDFT_ERR_CUDA;
+}
+
+swdft_status swdft2d_execute_stage(swdft2d_plan_t plan, int32_t stage, const void *const *d_in,
+                                   void *const *d_out, void *d_workspace, void *stream) {
+    if (!plan || (stage != 0 && stage != 1)) return SWDFT_ERR_INVALID_ARG;
+    swdft_status st = check_buffers(plan, d_in, d_out, d_workspace);
+    if (st != SWDFT_OK) return st;
+    if ((st = configure(plan)) != SWDFT_OK) return st;
+    return enqueue_all(plan, d_in, d_out, d_workspace, static_cast<cudaStream_t>(stream), stage == 0 ? 1 : 2);
+}
+
+swdft_status swdft2d_set_tree_config(swdft2d_plan_t plan, int32_t i, int32_t row_B,
+                                     int64_t row_chunk, int32_t col_B, int64_t col_chunk,
+                                     int32_t col_groups) {
+    if (!plan || i < 0 || (size_t)i >= plan->arrays.size()) return SWDFT_ERR_INVALID_ARG;
+    if (row_chunk < 0 || col_chunk < 0 || col_groups < 0) return SWDFT_ERR_INVALID_ARG;
+    ArrayPlan &a = plan->arrays[(size_t)i];
+    TreeConfig c;
+    c.row_B = std::max(0, std::min(row_B, std::min(a.m1, 3)));
+    c.row_chunk = row_chunk;
+    c.col_B = std::max(0, std::min(col_B, std::min(a.m0, 3)));
+    c.col_chunk = col_chunk;
+    c.col_groups = std::max(1, col_groups);
+    a.cfg = c;
+    a.tuned = true;
+    destroy_graph(plan->graph);
+    return SWDFT_OK;
+}
+
+swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_grad_out,
+                                     void *const *d_grad_in, void *d_workspace, void *stream) {
+    (void)d_grad_out;
+    (void)d_grad_in;
+    (void)d_workspace;
+    (void)stream;
+    if (!plan) return SWDFT_ERR_INVALID_ARG;
+    return SWDFT_ERR_UNSUPPORTED;
+}
+
+swdft_status swdft2d_execute_host(swdft2d_plan_t plan, const void *const *h_in,
+                                  void *const *h_out, void *stream) {
+    if (!plan || !h_in || !h_out) return SWDFT_ERR_INVALID_ARG;
+    if (!(plan->flags & SWDFT_FLAG_HOST_IO)) return SWDFT_ERR_INVALID_ARG;
+    for (size_t i = 0; i < plan->arrays.size(); ++i)
+        if (!h_in[i] || !h_out[i]) return SWDFT_ERR_INVALID_ARG;
+    swdft_status st = configure(plan);
+    if (st != SWDFT_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!plan->io_ready) {
+        // band: about 128 MiB of output per slot
+        size_t in_max = 0, out_max = 0, ws_max = 0;
+        int64_t band = INT64_MAX;
+        for (const auto &a : plan->arrays) {
+            const int64_t rows = std::max<int64_t>(1, (int64_t)((128u << 20) / a.out_row_bytes()));
+            band = std::min(band, rows);
+        }
+        for (const auto &a : plan->arrays) {
+            const int64_t br = std::min(band, a.band_rows());
+            in_max = std::max(in_max, align_up((size_t)a.N0 * a.ld * a.in_elem()));
+            out_max = std::max(out_max, align_up((size_t)br * a.out_row_bytes()));
+            ws_max = std::max(ws_max, align_up(a.z_bytes(br)));
+        }
+        if (cudaMalloc(&plan->io_in, in_max) != cudaSuccess) return SWDFT_ERR_OOM;
+        if (cudaMalloc(&plan->io_ws, ws_max) != cudaSuccess) return SWDFT_ERR_OOM;
+        for (int k = 0; k < 2; ++k)
+            if (cudaMalloc(&plan->io_out[k], out_max) != cudaSuccess) return SWDFT_ERR_OOM;
+        if (cudaStreamCreateWithFlags(&plan->io_copy, cudaStreamNonBlocking) != cudaSuccess) return SWDFT_ERR_CUDA;
+        for (int k = 0; k < 2; ++k) {
+            if (cudaEventCreateWithFlags(&plan->io_done[k], cudaEventDisableTiming) != cudaSuccess) return SWDFT_ERR_CUDA;
+            if (cudaEventCreateWithFlags(&plan->io_copied[k], cudaEventDisableTiming) != cudaSuccess) return SWDFT_ERR_CUDA;
+        }
+        plan->io_band = band;
+        plan->io_ready = true;
+    }
+    int64_t slot_uses = 0;
+    for (size_t i = 0; i < plan->arrays.size(); ++i) {
+        const ArrayPlan &a = plan->arrays[i];
+        const size_t in_bytes = (size_t)a.N0 * a.ld * a.in_elem();
+        // the input buffer is reused by the next array only after this array's kernels ran
+        if (cudaMemcpyAsync(plan->io_in, h_in[i], in_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return SWDFT_ERR_CUDA;
+        for (int64_t q = a.q_begin; q < a.q_end; q += plan->io_band) {
+            const int64_t qe = std::min(a.q_end, q + plan->io_band);
+            const int k = (int)(slot_uses & 1);
+            if (slot_uses >= 2 && cudaStreamWaitEvent(s, plan->io_copied[k], 0) != cudaSuccess) return SWDFT_ERR_CUDA;
+            if (enqueue_forward(plan, a, plan->io_in, plan->io_out[k], plan->io_ws, q, qe, s) != cudaSuccess)
+                return SWDFT_ERR_CUDA;
+            if (cudaEventRecord(plan->io_done[k], s) != cudaSuccess) return SWDFT_ERR_CUDA;
+            if (cudaStreamWaitEvent(plan->io_copy, plan->io_done[k], 0) != cudaSuccess) return SWDFT_ERR_CUDA;
+            char *dst = static_cast<char *>(h_out[i]) + (size_t)(q - a.q_begin) * a.out_row_bytes();
+            if (cudaMemcpyAsync(dst, plan->io_out[k], (size_t)(qe - q) * a.out_row_bytes(),
+                                cudaMemcpyDeviceToHost, plan->io_copy) != cudaSuccess)
+                return SWDFT_ERR_CUDA;
+            if (cudaEventRecord(plan->io_copied[k], plan->io_copy) != cudaSuccess) return SWDFT_ERR_CUDA;
+            ++slot_uses;
+        }
+    }
+    if (cudaStreamSynchronize(plan->io_copy) != cudaSuccess) return SWDFT_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SWDFT_ERR_CUDA;
+    return SWDFT_OK;
+}
+
+swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out,
+                              void *d_workspace, void *stream) {
+    if (!plan) return SWDFT_ERR_INVALID_ARG;
+    swdft_status st = check_buffers(plan, d_in, d_out, d_workspace);
+    if (st != SWDFT_OK) return st;
+    if ((st = configure(plan)) != SWDFT_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SWDFT_ERR_CUDA;
+    for (size_t i = 0; i < plan->arrays.size(); ++i) {
+        ArrayPlan &a = plan->arrays[i];
+        default_config(a, plan->sm_count);
+        const TreeConfig base = a.cfg;
+        std::vector<TreeConfig> cands;
+        for (int cb = 0; cb <= std::min(a.m0, 3); ++cb)
+            for (int cm : {1, 2, 4})
+                for (int rb : {std::min(a.m1, 1), std::min(a.m1, 2)}) {
+                    TreeConfig c = base;
+                    c.col_B = cb;
+                    c.col_groups = std::max(1, 256 / (32 << cb));
+                    const int64_t nch = a.P1 * a.n1;
+                    int64_t nchunk = std::max<int64_t>(1, (int64_t)plan->sm_count * 1024 * cm / std::max<int64_t>(1, nch << cb));
+                    int64_t chunk = (a.band_rows() + nchunk - 1) / nchunk;
+                    c.col_chunk = std::max<int64_t>(chunk, std::min<int64_t>(a.band_rows(), 2 * a.n0));
+                    c.row_B = rb;
+                    cands.push_back(c);
+                }
+        float best = 1e30f;
+        TreeConfig best_c = base;
+        for (const TreeConfig &c : cands) {
+            a.cfg = c;
+            float ms_min = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, s);
+                if (enqueue_forward(plan, a, d_in[i], d_out[i], d_workspace, a.q_begin, a.q_end, s) != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return SWDFT_ERR_CUDA;
+                }
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return SWDFT_ERR_CUDA;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms_min = std::min(ms_min, ms);
+            }
+            if (ms_min < best) {
+                best = ms_min;
+                best_c = c;
+            }
+        }
+        a.cfg = best_c;
+        a.tuned = true;
+        if (const char *path = std::getenv("SWDFT_TUNE_CACHE")) {
+            if (FILE *f = std::fopen(path, "a")) {
+                std::fprintf(f,
+                             "{\"N0\": %lld, \"N1\": %lld, \"n0\": %d, \"n1\": %d, \"dtype\": %d, "
+                             "\"row_B\": %d, \"row_chunk\": %lld, \"col_B\": %d, \"col_chunk\": %lld, "
+                             "\"col_groups\": %d, \"ms\": %.6f}\n",
+                             (long long)a.N0, (long long)a.N1, a.n0, a.n1, a.dtype, best_c.row_B,
+                             (long long)best_c.row_chunk, best_c.col_B, (long long)best_c.col_chunk,
+                             best_c.col_groups, best);
+                std::fclose(f);
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    destroy_graph(plan->graph);
+    return SWDFT_OK;
+}
+
+swdft_status swdft2d_destroy(swdft2d_plan_t plan) {
+    if (!plan) return SWDFT_OK;
+    destroy_graph(plan->graph);
+    if (plan->io_ready) {
+        cudaFree(plan->io_in);
+        cudaFree(plan->io_ws);
+        for (int k = 0; k < 2; ++k) {
+            cudaFree(plan->io_out[k]);
+            if (plan->io_done[k]) cudaEventDestroy(plan->io_done[k]);
+            if (plan->io_copied[k]) cudaEventDestroy(plan->io_copied[k]);
+        }
+        if (plan->io_copy) cudaStreamDestroy(plan->io_copy);
+    }
+    delete plan;
+    return SWDFT_OK;
+}
+
+}  // extern "C"

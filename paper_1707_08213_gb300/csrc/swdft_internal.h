@@ -1,0 +1,55 @@
+// Internal interfaces between the C-ABI host code (api.cpp) and the kernel translation
+// units.  Nothing here is exported.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace swdft {
+
+// Tree kernels keep every butterfly level of one window axis in registers; they are built
+// for window lengths up to 2^kMaxLog2 along each axis.
+constexpr int kMaxLog2 = 6;
+constexpr int kMaxN = 1 << kMaxLog2;
+
+// Omega^i of Section 4.2 for length n (power of two), FP64-evaluated, FP32-rounded.
+void make_omega(int n, float2 *out);
+
+// Row levels (Eq. rowfswft2d) of `rows` input rows starting at input row r_base:
+//   z[r][q1][k1] = sum_{j1<n1} x[r_base + r][q1 + j1] w_{n1}^{-j1 k1}   (unnormalised)
+// z is row-major rows x P1 x n1 complex64.
+struct RowTreeArgs {
+    const void *x = nullptr;  // N0 x N1 input, row stride ld elements
+    int64_t ld = 0;
+    int cplx = 0;             // 0: float32 input, 1: complex64
+    int64_t r_base = 0;
+    int64_t rows = 0;
+    int64_t P1 = 0;
+    int m1 = 0;               // log2 n1
+    float2 *z = nullptr;
+    const float2 *om1 = nullptr;  // host table, n1 entries (copied into kernel parameters)
+    int B = 0;                // log2 of the threads sharing one row's butterflies
+    int64_t chunk = 0;        // output positions per thread (plus n1-1 warm-up steps)
+};
+
+// Column levels (Eq. colfswft2d) of z, scaled and stored as the final output:
+//   out[q0][q1][k0][k1] = scale * sum_{j0<n0} z[q0 + j0][q1][k1] w_{n0}^{-j0 k0}
+struct ColTreeArgs {
+    const float2 *z = nullptr;  // (rows_out + n0 - 1) x P1 x n1
+    int64_t P1 = 0;
+    int64_t rows_out = 0;
+    int m0 = 0, m1 = 0;
+    float2 *out = nullptr;      // rows_out x P1 x n0 x n1
+    float scale = 1.f;
+    const float2 *om0 = nullptr;
+    int B = 0;
+    int64_t chunk = 0;          // output rows per thread (plus n0-1 warm-up steps)
+    int groups = 1;             // 32-channel groups per block (block = 32 * 2^B * groups)
+};
+
+cudaError_t launch_row_tree(const RowTreeArgs &a, cudaStream_t s);
+cudaError_t launch_col_tree(const ColTreeArgs &a, cudaStream_t s);
+
+}  // namespace swdft

@@ -1,0 +1,47 @@
+// Column-level pass (Eq. colfswft2d): launcher.  Kernel instantiations live in
+// tree_col_m*.cu so they compile in parallel.
+#include <algorithm>
+
+#include "tree_kernels.cuh"
+
+namespace swdft {
+
+cudaError_t launch_col_tree(const ColTreeArgs &a, cudaStream_t s) {
+    const int64_t nch = a.P1 << a.m1;
+    if (a.rows_out <= 0 || nch <= 0) return cudaSuccess;
+    if (a.m0 < 0 || a.m0 > kMaxLog2 || a.m1 < 0 || a.m1 > kMaxLog2 || a.rows_out > INT32_MAX)
+        return cudaErrorInvalidValue;
+    ColParams p;
+    p.z = a.z;
+    p.out = a.out;
+    p.nch = nch;
+    p.orow = nch << a.m0;
+    p.rows_out = (int)a.rows_out;
+    p.chunk = (int)std::min<int64_t>(a.chunk > 0 ? a.chunk : a.rows_out, a.rows_out);
+    p.m1 = a.m1;
+    p.scale = a.scale;
+    int B = a.B < 0 ? 0 : a.B;
+    B = std::min(B, std::min(a.m0, 3));
+    int groups = a.groups < 1 ? 1 : a.groups;
+    while (groups > 1 && 32 * (1 << B) * groups > 256) groups >>= 1;
+    p.groups = groups;
+    for (int j = 0; j < (1 << a.m0); ++j) p.om[j] = a.om0[j];
+    const int64_t per_block = 32LL * groups;
+    dim3 grid((unsigned)((nch + per_block - 1) / per_block),
+              (unsigned)((a.rows_out + p.chunk - 1) / p.chunk));
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    dim3 block(32 * (1 << B) * groups);
+    switch (a.m0 * 8 + B) {
+#define F(M_, B_)                                  \
+    case M_ * 8 + B_:                              \
+        col_launch_mb<M_, B_>(p, grid, block, s);  \
+        break;
+        SWDFT_MB_CASES(F)
+#undef F
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace swdft

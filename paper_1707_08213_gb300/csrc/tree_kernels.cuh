@@ -1,0 +1,175 @@
+// FP32 tree kernels for the 2D sliding window DFT (arXiv 1707.08213, Section 4.2).
+//
+// Two passes over the two level groups of the tree:
+//   row_tree : levels 1..m1 (Eq. rowfswft2d), along dimension 1 of every input row; its
+//              level m1 is z[r][q1][k1] = the n1-point DFT of x[r][q1 .. q1+n1-1].
+//   col_tree : levels m1+1..m1+m0 (Eq. colfswft2d), along dimension 0 of every channel
+//              (q1, k1) of z; its level m0+m1 is the window's 2D DFT, scaled and stored.
+// Both walk window positions with SlidingTree (tree_core.cuh), registers only.
+//
+// z layout: kZPad(n0) = n0/2 padding rows, then rows x P1 x n1 complex64.  The padding lets
+// the column pass read its level-0 look-back z[r - n0/2] without a bounds clamp (values
+// read there only feed incomplete border trees, which are never stored).
+//
+// Each column-pass warp covers 32 consecutive channels (q1, k1): its z loads and its
+// output stores move 256 contiguous bytes per k0 (full 32-byte sectors).  Outputs go out
+// with streaming stores so they do not evict z from L2.
+#pragma once
+
+#include <cstdint>
+
+#include "swdft_internal.h"
+#include "tree_core.cuh"
+
+namespace swdft {
+
+struct RowParams {
+    const void *x;
+    int64_t ld;       // input row stride, elements
+    int64_t r_base;   // first input row
+    int64_t zrow;     // elements per z row (P1 * n1)
+    int rows;
+    int P1;
+    int chunk;        // output positions per thread
+    float2 *z;        // first (non-padding) z row
+    float2 om[kMaxN];
+};
+
+struct ColParams {
+    const float2 *z;  // first (non-padding) z row
+    float2 *out;
+    int64_t nch;      // channels = P1 * n1 = elements per z row
+    int64_t orow;     // elements per output row = P1 * n0 * n1
+    int rows_out;
+    int chunk;        // output rows per thread
+    int m1;
+    int groups;       // 32-channel groups per block
+    float scale;
+    float2 om[kMaxN];
+};
+
+template <bool CPLX>
+__device__ __forceinline__ float2 load_x(const void *row, int64_t i) {
+    if constexpr (CPLX) {
+        return __ldg(reinterpret_cast<const float2 *>(row) + i);
+    } else {
+        return make_float2(__ldg(reinterpret_cast<const float *>(row) + i), 0.f);
+    }
+}
+
+// Thread = (row, residue c, chunk of output positions).  Lanes hold the residue in the low
+// B bits, then the row, so the 2^B threads of one row store adjacent k1 together.
+template <int M, int B, bool CPLX>
+__global__ void __launch_bounds__(128) row_tree_kernel(const RowParams p) {
+    using Tree = SlidingTree<M, B>;
+    constexpr int n = 1 << M;
+    const int c = threadIdx.x & ((1 << B) - 1);
+    const int row = blockIdx.x * (blockDim.x >> B) + (threadIdx.x >> B);
+    if (row >= p.rows) return;
+    const int qa = blockIdx.y * p.chunk;
+    if (qa >= p.P1) return;
+    const int qb = min(qa + p.chunk, p.P1);
+    const int steps = (qb - qa) + (n - 1);
+
+    const char *xrow = reinterpret_cast<const char *>(p.x) +
+                       (p.r_base + row) * p.ld * (int64_t)(CPLX ? sizeof(float2) : sizeof(float));
+    float2 *dst = p.z + (int64_t)row * p.zrow + (int64_t)qa * n + c;
+
+    Tree tree;
+    tree.init(c, p.om);
+    for (int jb = 0; jb < steps; jb += Tree::kPeriod) {
+        static_for<0, Tree::kPeriod>([&](auto JJ) {
+            constexpr int J = decltype(JJ)::value;
+            const int j = jb + J;
+            if (j < steps) {
+                const int p1 = qa + j;  // window end column
+                const float2 xp = load_x<CPLX>(xrow, p1);
+                const float2 xs = (M >= 1) ? load_x<CPLX>(xrow, max(p1 - Tree::kHalf, 0))
+                                           : make_float2(0.f, 0.f);
+                float2 o[Tree::kOut];
+                tree.template step<J>(xp, xs, o);
+                if (j >= n - 1) {
+#pragma unroll
+                    for (int t = 0; t < Tree::kOut; ++t) dst[t << B] = o[t];
+                    dst += n;
+                }
+            }
+        });
+    }
+}
+
+// Thread = (channel ch = q1*n1 + k1, residue c, chunk of output rows).  Warp w of a block
+// takes residue w mod 2^B (uniform per warp) and channel group w / 2^B.
+template <int M, int B>
+__global__ void __launch_bounds__(256) col_tree_kernel(const ColParams p) {
+    using Tree = SlidingTree<M, B>;
+    constexpr int R = 1 << B;
+    constexpr int n = 1 << M;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int c = warp & (R - 1);
+    const int64_t ch = ((int64_t)blockIdx.x * p.groups + (warp >> B)) * 32 + lane;
+    if (ch >= p.nch) return;
+    const int qa = blockIdx.y * p.chunk;
+    if (qa >= p.rows_out) return;
+    const int qb = min(qa + p.chunk, p.rows_out);
+    const int steps = (qb - qa) + (n - 1);
+
+    const int n1 = 1 << p.m1;
+    const int64_t q1 = ch >> p.m1;
+    const int64_t k1 = ch & (n1 - 1);
+    const int kstride = R * n1;  // elements between outputs t and t+1 (k0 step 2^B)
+    const int64_t back = (int64_t)Tree::kHalf * p.nch;
+    const float2 *zp = p.z + (int64_t)qa * p.nch + ch;
+    float2 *dst = p.out + (int64_t)qa * p.orow + q1 * ((int64_t)n * n1) + (int64_t)c * n1 + k1;
+    const float s = p.scale;
+
+    Tree tree;
+    tree.init(c, p.om);
+    for (int jb = 0; jb < steps; jb += Tree::kPeriod) {
+        static_for<0, Tree::kPeriod>([&](auto JJ) {
+            constexpr int J = decltype(JJ)::value;
+            const int j = jb + J;
+            if (j < steps) {
+                const float2 xp = __ldg(zp);
+                const float2 xs = (M >= 1) ? __ldg(zp - back) : make_float2(0.f, 0.f);
+                zp += p.nch;
+                float2 o[Tree::kOut];
+                tree.template step<J>(xp, xs, o);
+                if (j >= n - 1) {
+#pragma unroll
+                    for (int t = 0; t < Tree::kOut; ++t) __stcs(dst + t * kstride, c_scale(s, o[t]));
+                    dst += p.orow;
+                }
+            }
+        });
+    }
+}
+
+template <int M, int B>
+void row_launch_mb(const RowParams &p, int cplx, dim3 g, dim3 b, cudaStream_t s);
+template <int M, int B>
+void col_launch_mb(const ColParams &p, dim3 g, dim3 b, cudaStream_t s);
+
+#define SWDFT_ROW_INSTANTIATE(M_, B_)                                                        \
+    template <>                                                                              \
+    void row_launch_mb<M_, B_>(const RowParams &p, int cplx, dim3 g, dim3 b, cudaStream_t s) { \
+        if (cplx)                                                                            \
+            row_tree_kernel<M_, B_, true><<<g, b, 0, s>>>(p);                                \
+        else                                                                                 \
+            row_tree_kernel<M_, B_, false><<<g, b, 0, s>>>(p);                               \
+    }
+
+#define SWDFT_COL_INSTANTIATE(M_, B_)                                                     \
+    template <>                                                                           \
+    void col_launch_mb<M_, B_>(const ColParams &p, dim3 g, dim3 b, cudaStream_t s) {      \
+        col_tree_kernel<M_, B_><<<g, b, 0, s>>>(p);                                       \
+    }
+
+// (M, B) pairs with B <= min(M, 3)
+#define SWDFT_MB_CASES(F)                                                              \
+    F(0, 0) F(1, 0) F(1, 1) F(2, 0) F(2, 1) F(2, 2) F(3, 0) F(3, 1) F(3, 2) F(3, 3)     \
+    F(4, 0) F(4, 1) F(4, 2) F(4, 3) F(5, 0) F(5, 1) F(5, 2) F(5, 3) F(6, 0) F(6, 1)     \
+    F(6, 2) F(6, 3)
+
+}  // namespace swdft

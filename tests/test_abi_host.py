@@ -1,0 +1,145 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every symbol
+include/swdft2d.h declares, validates plans before any CUDA call, and reports the output
+shape of Eq. 2 (P0 x P1 x n0 x n1) and its workspace."""
+import ctypes
+import json
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "swdft2d.h")
+
+
+@pytest.fixture(scope="module")
+def nat():
+    import __graft_entry__
+    __graft_entry__._load_build_module().build()
+    from paper_1707_08213_gb300 import _native
+    return _native
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(swdft2d_\w+)\s*\(", text)))
+
+
+def test_header_declares_what_binding_lists(nat):
+    assert sorted(nat.EXPORTS) == declared_functions()
+
+
+def test_library_exports_every_declared_symbol(nat):
+    lib = ctypes.CDLL(nat.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_version_and_status_strings(nat):
+    assert nat.version() >= 100
+    for code in range(-8, 1):
+        assert nat.status_string(code).startswith("SWDFT_")
+    assert "unknown" in nat.status_string(42)
+
+
+def shp(N0, N1, n0, n1, **kw):
+    d = dict(N0=N0, N1=N1, n0=n0, n1=n1)
+    d.update(kw)
+    return d
+
+
+@pytest.mark.parametrize("shape,status", [
+    (shp(16, 16, 3, 4), -2),           # not a power of two
+    (shp(16, 16, 4, 12), -2),
+    (shp(16, 16, 32, 4), -3),          # window larger than the array
+    (shp(16, 8, 4, 16), -3),
+    (shp(0, 16, 1, 1), -1),            # empty array
+    (shp(16, 16, 0, 4), -1),
+    (shp(16, 16, 4, 4, ld=8), -1),     # row stride shorter than a row
+    (shp(16, 16, 4, 4, dtype=7), -1),  # bad dtype
+    (shp(16, 16, 4, 4, row_begin=5, row_end=3), -1),   # empty band
+    (shp(16, 16, 4, 4, row_begin=0, row_end=14), -1),  # band past P0 = 13
+    (shp(300, 300, 128, 4), -4),       # beyond the tree kernels' 64-point axis
+])
+def test_plan_validation(nat, shape, status):
+    st, h = nat.raw_plan([shape], 0, 0, 1, 0)
+    assert st == status
+    assert h is None
+
+
+def test_plan_validation_enums(nat):
+    good = [shp(16, 16, 4, 4)]
+    assert nat.raw_plan(good, 3, 0, 1, 0)[0] == -1      # norm
+    assert nat.raw_plan(good, 0, 2, 1, 0)[0] == -1      # position convention
+    assert nat.raw_plan(good, 0, 0, 9, 0)[0] == -1      # algorithm
+    assert nat.raw_plan(good, 0, 0, 1, 1 << 9)[0] == -1  # unknown flag
+    assert nat.raw_plan([], 0, 0, 1, 0)[0] == -1          # empty batch
+    st = nat.lib.swdft2d_plan(None, 1, None, 0, 0, 1, 0)
+    assert st == -1
+
+
+def test_output_shape_and_workspace(nat):
+    p = nat.Plan([shp(64, 77, 8, 16), shp(33, 40, 32, 1, dtype=1)])
+    assert p.output_shape(0) == (57, 62, 8, 16)
+    assert p.output_shape(1) == (2, 40, 32, 1)
+    # z workspace: (n0/2 padding + band rows + n0 - 1) x P1 x n1 complex64, largest array
+    need = max((4 + 57 + 7) * 62 * 16 * 8, (16 + 2 + 31) * 40 * 1 * 8)
+    ws = p.workspace_size()
+    assert ws >= need and ws % 256 == 0
+    with pytest.raises(nat.SwdftError):
+        p.output_shape(2)
+    p.destroy()
+
+
+def test_band_in_both_position_conventions(nat):
+    start = nat.Plan([shp(40, 20, 8, 4, row_begin=5, row_end=12)], pos="start")
+    end = nat.Plan([shp(40, 20, 8, 4, row_begin=5 + 7, row_end=12 + 7)], pos="end")
+    assert start.output_shape(0) == end.output_shape(0) == (7, 17, 8, 4)
+    # row_end = 0: through the last window row
+    tail = nat.Plan([shp(40, 20, 8, 4, row_begin=30, row_end=0)])
+    assert tail.output_shape(0) == (3, 17, 8, 4)
+
+
+def test_paper_output_size_example(nat):
+    """Section 4.3: P0 = P1 = 400, n0 = n1 = 32 gives 163,840,000 coefficients."""
+    with open(os.path.join(ROOT, "tests", "golden", "paper_printed_values.json")) as f:
+        ex = json.load(f)["output_size_example"]
+    N = ex["P0"] + ex["n0"] - 1
+    p = nat.Plan([shp(N, N, ex["n0"], ex["n1"])])
+    rows, P1, n0, n1 = p.output_shape(0)
+    assert rows * P1 * n0 * n1 == ex["complex_numbers"]
+    assert rows * P1 * n0 * n1 * ex["bytes_per_complex"] == ex["bytes"]
+
+
+def test_execute_rejects_bad_buffers_before_cuda(nat):
+    p = nat.Plan([shp(16, 16, 4, 4)])
+    with pytest.raises(nat.SwdftError) as e:
+        p.execute([0], [0], 0)
+    assert e.value.status == -1
+    with pytest.raises(nat.SwdftError) as e:
+        p.execute([4096], [4096 + 8], 4096)   # output not 16-byte aligned
+    assert e.value.status == -1
+    with pytest.raises(nat.SwdftError) as e:
+        p.execute([4096], [4096], 4096 + 64)  # workspace not 256-byte aligned
+    assert e.value.status == -8
+    with pytest.raises(nat.SwdftError) as e:
+        p.execute_host([4096], [4096])        # plan made without SWDFT_FLAG_HOST_IO
+    assert e.value.status == -1
+    with pytest.raises(nat.SwdftError) as e:
+        p.execute_stage(2, [4096], [4096], 4096)
+    assert e.value.status == -1
+    assert nat.lib.swdft2d_destroy(None) == 0
+
+
+def test_launch_count(nat):
+    p = nat.Plan([shp(16, 16, 4, 4), shp(32, 32, 8, 8)])
+    assert p.launch_count() == 4
+
+
+def test_twiddle_table_symmetry_via_plan(nat):
+    # a plan of every supported length is accepted (FP64 twiddles built on the host)
+    for m in range(0, 7):
+        n = 1 << m
+        p = nat.Plan([shp(n + 3, n + 5, n, n)])
+        assert p.output_shape(0) == (4, 6, n, n)

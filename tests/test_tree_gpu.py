@@ -1,0 +1,212 @@
+"""Parity of the FP32 tree kernels (through the C ABI) with the FP64 oracle.
+
+Bar (Section 4.1, Eq. 2): max over coefficients of |a_gpu - a_oracle| / ||x_w||_2 <= 1e-5
+per window, on the unitary scale.  Small arrays are compared on every coefficient, with
+launch configurations forced so that trees are split over several threads and position
+chunks end in ragged tails; the full-size workloads are compared on sampled windows plus
+per-window Parseval over every window.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+ORACLE_THREADS = 8
+
+
+@pytest.fixture(scope="module")
+def sw():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1707_08213_gb300 as sw
+    return sw
+
+
+def _dt(x):
+    return 1 if np.iscomplexobj(x) else 0
+
+
+def run_gpu(sw, x, n0, n1, norm="unitary", cfg=None, flags=0, band=None, pos="start"):
+    N0, N1 = x.shape
+    t = sw.Transform([(N0, N1, n0, n1, _dt(x))], norm=norm, flags=flags,
+                     bands=None if band is None else [band], pos=pos)
+    if cfg is not None:
+        t.plan.set_tree_config(0, *cfg)
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    a = t.forward([xd])[0]
+    torch.cuda.synchronize()
+    return a, t
+
+
+def assert_close_to_oracle(a_gpu, x, n0, n1, norm="unitary", method="separable"):
+    ref = oracle.swdft2d(x, n0, n1, norm=norm, method=method, threads=ORACLE_THREADS)
+    to_unitary = oracle.scale_for("unitary", n0, n1) / oracle.scale_for(norm, n0, n1)
+    a = a_gpu.cpu().numpy() if torch.is_tensor(a_gpu) else a_gpu
+    err, rms = workloads.normalised_error(a, ref, workloads.window_sq_norms(x, n0, n1), to_unitary)
+    assert err <= TOL, f"max normalised error {err:.3e} (rms {rms:.3e})"
+    return err, rms
+
+
+def test_small_uniform_64_every_coefficient(sw):
+    wl = workloads.small_uniform_64()
+    x = wl.images[0]
+    a, _ = run_gpu(sw, x, 8, 8)
+    assert tuple(a.shape) == (57, 57, 8, 8)
+    assert_close_to_oracle(a, x, 8, 8, method="direct")
+
+
+SHAPES = [
+    # N0, N1, n0, n1
+    (1, 1, 1, 1), (5, 7, 2, 1), (7, 5, 1, 2), (9, 9, 8, 8), (37, 53, 4, 8), (64, 77, 8, 16),
+    (50, 70, 16, 8), (23, 300, 1, 64), (300, 23, 64, 1), (100, 100, 32, 32), (130, 90, 64, 16),
+    (70, 140, 16, 64), (45, 45, 2, 32), (66, 40, 32, 2),
+]
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("N0,N1,n0,n1", SHAPES)
+def test_default_config_every_coefficient(sw, N0, N1, n0, n1, cplx):
+    x = workloads.random_array(N0 * 1000 + N1, N0, N1, complex_input=cplx)
+    a, _ = run_gpu(sw, x, n0, n1)
+    assert tuple(a.shape) == (N0 - n0 + 1, N1 - n1 + 1, n0, n1)
+    assert_close_to_oracle(a, x, n0, n1)
+
+
+# (row_B, row_chunk, col_B, col_chunk, col_groups): splits of 1..8 threads per tree and
+# chunks that leave ragged tails
+CONFIGS = [(0, 0, 0, 0, 1), (1, 3, 1, 5, 2), (2, 7, 3, 2, 1), (3, 1, 2, 1, 4), (2, 11, 1, 9, 8)]
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+@pytest.mark.parametrize("N0,N1,n0,n1,cplx", [(41, 67, 8, 16, False), (61, 35, 32, 4, True),
+                                               (90, 75, 64, 8, False), (33, 129, 2, 64, True)])
+def test_forced_configs_every_coefficient(sw, cfg, N0, N1, n0, n1, cplx):
+    x = workloads.random_array(7 + N0 + N1, N0, N1, complex_input=cplx, dist="uniform")
+    a, _ = run_gpu(sw, x, n0, n1, cfg=cfg)
+    assert_close_to_oracle(a, x, n0, n1)
+
+
+@pytest.mark.parametrize("norm", ["none", "inv_n"])
+def test_normalisations(sw, norm):
+    x = workloads.random_array(3, 40, 50, complex_input=True)
+    a, _ = run_gpu(sw, x, 8, 16, norm=norm)
+    assert_close_to_oracle(a, x, 8, 16, norm=norm)
+
+
+def test_bands_in_both_conventions_match_full(sw):
+    x = workloads.random_array(4, 80, 60)
+    full, _ = run_gpu(sw, x, 16, 8)
+    b1, _ = run_gpu(sw, x, 16, 8, band=(10, 37), pos="start")
+    b2, _ = run_gpu(sw, x, 16, 8, band=(10 + 15, 37 + 15), pos="end")
+    assert torch.equal(b1, full[10:37])
+    assert torch.equal(b2, full[10:37])
+
+
+def test_deterministic_and_graph_replay(sw):
+    x = workloads.random_array(5, 96, 96)
+    a1, _ = run_gpu(sw, x, 32, 32)
+    a2, _ = run_gpu(sw, x, 32, 32)
+    assert torch.equal(a1, a2)
+    t = sw.Transform([(96, 96, 32, 32, 0)], flags=sw.FLAG_GRAPH)
+    xd = torch.from_numpy(x).cuda()
+    outs = t.empty_outputs()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            outs[0].zero_()
+            t.forward([xd], outs)
+    s.synchronize()
+    assert torch.equal(outs[0], a1)
+
+
+def test_host_buffers_match_device_path(sw):
+    x = workloads.random_array(6, 200, 150, complex_input=True)
+    a, _ = run_gpu(sw, x, 16, 32)
+    t = sw.Transform([(200, 150, 16, 32, 1)], flags=sw.FLAG_HOST_IO)
+    h_in = torch.from_numpy(x).pin_memory()
+    h_out = torch.empty(tuple(a.shape), dtype=torch.complex64).pin_memory()
+    t.plan.execute_host([h_in.data_ptr()], [h_out.data_ptr()],
+                        torch.cuda.current_stream().cuda_stream)
+    assert torch.equal(h_out, a.cpu())
+
+
+def test_strided_input_rows(sw):
+    N0, N1, ld = 30, 40, 47
+    wide = workloads.random_array(8, N0, ld)
+    x = np.ascontiguousarray(wide[:, :N1])
+    plan = sw.Plan([dict(N0=N0, N1=N1, ld=ld, n0=8, n1=8, dtype=0)])
+    xd = torch.from_numpy(wide).cuda()
+    out = torch.empty(plan.output_shape(0), dtype=torch.complex64, device="cuda")
+    ws = torch.empty(plan.workspace_size(), dtype=torch.uint8, device="cuda")
+    plan.execute([xd.data_ptr()], [out.data_ptr()], ws.data_ptr(),
+                 torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert_close_to_oracle(out, x, 8, 8)
+
+
+def test_autotune_keeps_results(sw):
+    x = workloads.random_array(9, 120, 110)
+    a, t = run_gpu(sw, x, 16, 16)
+    xd = torch.from_numpy(x).cuda()
+    t.autotune([xd])
+    b = t.forward([xd])[0]
+    torch.cuda.synchronize()
+    assert_close_to_oracle(b, x, 16, 16)
+
+
+def test_batch_of_mixed_shapes(sw):
+    shapes = [(70, 50, 8, 32), (33, 90, 16, 4), (64, 64, 64, 16), (20, 20, 4, 4)]
+    xs = [workloads.random_array(20 + i, s[0], s[1], complex_input=(i % 2 == 1))
+          for i, s in enumerate(shapes)]
+    t = sw.Transform([(s[0], s[1], s[2], s[3], _dt(x)) for s, x in zip(shapes, xs)])
+    outs = t.forward([torch.from_numpy(x).cuda() for x in xs])
+    torch.cuda.synchronize()
+    for s, x, a in zip(shapes, xs, outs):
+        assert_close_to_oracle(a, x, s[2], s[3])
+
+
+# ------------------------------------------------------------- full-size workloads
+
+def _sample_windows(P0, P1, count, seed):
+    rng = np.random.default_rng(seed)
+    q0 = list(rng.integers(0, P0, count)) + [0, 0, P0 - 1, P0 - 1, P0 // 2]
+    q1 = list(rng.integers(0, P1, count)) + [0, P1 - 1, 0, P1 - 1, P1 // 2]
+    return np.array(q0), np.array(q1)
+
+
+def _full_size_check(sw, x, n0, n1, count, seed):
+    N0, N1 = x.shape
+    P0, P1 = N0 - n0 + 1, N1 - n1 + 1
+    a, _ = run_gpu(sw, x, n0, n1)
+    q0, q1 = _sample_windows(P0, P1, count, seed)
+    got = a[torch.from_numpy(q0).cuda(), torch.from_numpy(q1).cuda()].cpu().numpy()
+    ref = oracle.swdft2d_windows(x, n0, n1, q0, q1, threads=ORACLE_THREADS)
+    nrm = workloads.window_sq_norms_at(x, n0, n1, q0, q1)
+    err, _ = workloads.normalised_error(got, ref, nrm)
+    assert err <= TOL, f"sampled windows: max normalised error {err:.3e}"
+    # Parseval on every window (unitary scale): sum_k |a|^2 = ||x_w||^2
+    sq = torch.from_numpy(workloads.window_sq_norms(x, n0, n1)).cuda()
+    worst = 0.0
+    for r in range(0, P0, 64):
+        e = torch.view_as_real(a[r:r + 64]).pow(2).sum(dim=(2, 3, 4)).double()
+        worst = max(worst, float(((e - sq[r:r + 64]).abs() / sq[r:r + 64]).max()))
+    assert worst <= 1e-5, f"Parseval relative error {worst:.3e}"
+    del a
+    torch.cuda.empty_cache()
+
+
+def test_sinusoids_512_full_size(sw):
+    wl = workloads.sinusoids_512()
+    _full_size_check(sw, wl.images[0], 32, 32, count=2048, seed=11)
+
+
+def test_complex_1024x2048_full_size(sw):
+    wl = workloads.complex_1024x2048()
+    _full_size_check(sw, wl.images[0], 16, 64, count=2048, seed=12)
