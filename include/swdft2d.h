@@ -170,6 +170,24 @@ swdft_status swdft2d_set_tree_config(swdft2d_plan_t plan, int32_t i, int32_t row
 /* Number of kernel launches one execute enqueues (graph replays count their kernels). */
 swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t *launches);
 
+/* Forward transform without any allocation, for callers that may not call cudaMalloc
+ * (plug-ins handed only their input and output buffers, code running after a framework
+ * has claimed the device memory for its own pool, real-time paths where an allocation's
+ * latency or failure is not acceptable).  The paper has no counterpart; this is a service
+ * of this library.  It needs no plan and no workspace: the z rows between the row-level
+ * and column-level passes live in a fixed 32 MiB array of device memory inside the library
+ * (held on every GPU that loads it, until exit), and the output is produced in bands of
+ * window rows whose z fits there.  Arguments as in swdft2d_shape / swdft2d_execute
+ * (ld = 0 means N1); output layout as for swdft2d_execute with all P0 window rows.
+ * Errors: as swdft2d_plan for the shape; SWDFT_ERR_WORKSPACE when even a one-row band
+ * needs more than 32 MiB, i.e. (3*n0/2) * (N1-n1+1) * n1 * 8 bytes > 32 MiB.
+ * The first call on a device looks up the array's address there (do it before any stream
+ * capture).  All calls share the array and it keeps the last call's contents: calls that
+ * overlap on the GPU race and must be serialised by the caller. */
+swdft_status swdft2d_execute_static_scratch(const void *d_in, int64_t N0, int64_t N1, int64_t ld,
+                                            int32_t n0, int32_t n1, int32_t dtype, int32_t norm,
+                                            void *d_out, void *stream);
+
 /* Free the plan and everything it owns.  NULL is accepted. */
 swdft_status swdft2d_destroy(swdft2d_plan_t plan);
 

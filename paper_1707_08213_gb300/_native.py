@@ -36,7 +36,7 @@ EXPORTS = (
     "swdft2d_plan", "swdft2d_output_shape", "swdft2d_workspace_size", "swdft2d_get_algo",
     "swdft2d_execute", "swdft2d_execute_adjoint", "swdft2d_execute_host", "swdft2d_autotune",
     "swdft2d_launch_count", "swdft2d_destroy", "swdft2d_status_string", "swdft2d_version",
-    "swdft2d_execute_stage", "swdft2d_set_tree_config",
+    "swdft2d_execute_stage", "swdft2d_set_tree_config", "swdft2d_execute_static_scratch",
 )
 
 
@@ -72,6 +72,7 @@ def _load() -> ctypes.CDLL:
         "swdft2d_launch_count": ([P, i32, ctypes.POINTER(i32)], i32),
         "swdft2d_execute_stage": ([P, i32, PP, PP, P, P], i32),
         "swdft2d_set_tree_config": ([P, i32, i32, i64, i32, i64, i32], i32),
+        "swdft2d_execute_static_scratch": ([P, i64, i64, i64, i32, i32, i32, i32, P, P], i32),
         "swdft2d_destroy": ([P], i32),
         "swdft2d_status_string": ([i32], ctypes.c_char_p),
         "swdft2d_version": ([], i32),
