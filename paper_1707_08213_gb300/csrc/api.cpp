@@ -93,22 +93,29 @@ float norm_scale(int norm, int n0, int n1) {
     }
 }
 
+// Column pass: about eight chunks of window rows per channel group (measured best on the
+// 512x512/32x32 and 1024x2048/16x64 workloads: many small blocks balance the SMs better than
+// a few long ones), but never fewer than 2*n0 rows so warm-up stays under a third.
+int64_t col_chunk_for(const ArrayPlan &a, int nchunks) {
+    const int64_t rows = a.band_rows();
+    int64_t chunk = (rows + nchunks - 1) / nchunks;
+    return std::min(rows, std::max<int64_t>(chunk, 2 * a.n0));
+}
+
 void default_config(ArrayPlan &a, int sm_count) {
     TreeConfig c;
-    const int64_t target = (int64_t)sm_count * 1024;  // threads in flight we aim for
+    const int64_t target = (int64_t)sm_count * 1024;  // row-pass threads in flight we aim for
     // row levels: thread = (row, residue, chunk of positions)
     c.row_B = std::min(a.m1, 2);
     const int64_t rows = a.band_rows() + a.n0 - 1;
     int64_t nchunk = std::max<int64_t>(1, target / std::max<int64_t>(1, rows << c.row_B));
     int64_t chunk = (a.P1 + nchunk - 1) / nchunk;
     c.row_chunk = std::max<int64_t>(chunk, std::min<int64_t>(a.P1, 2 * a.n1));
-    // column levels: thread = (channel, residue, chunk of output rows)
-    c.col_B = std::min(a.m0, 2);
-    const int64_t nch = a.P1 * a.n1;
-    nchunk = std::max<int64_t>(1, target / std::max<int64_t>(1, nch << c.col_B));
-    chunk = (a.band_rows() + nchunk - 1) / nchunk;
-    c.col_chunk = std::max<int64_t>(chunk, std::min<int64_t>(a.band_rows(), 4 * a.n0));
-    c.col_groups = std::max(1, 256 / (32 << c.col_B));
+    // column levels: thread = (channel, residue, chunk of output rows); one 32-channel
+    // group per block (32 * 2^B threads)
+    c.col_B = a.m0 >= 6 ? 3 : std::min(a.m0, 2);
+    c.col_groups = 1;
+    c.col_chunk = col_chunk_for(a, 8);
     a.cfg = c;
 }
 
@@ -464,46 +471,68 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
         default_config(a, plan->sm_count);
         const TreeConfig base = a.cfg;
         std::vector<TreeConfig> cands;
-        for (int cb = 0; cb <= std::min(a.m0, 3); ++cb)
-            for (int cm : {1, 2, 4})
-                for (int rb : {std::min(a.m1, 1), std::min(a.m1, 2)}) {
+        for (int cb = std::max(0, std::min(a.m0, 3) - 2); cb <= std::min(a.m0, 3); ++cb)
+            for (int groups : {1, 2})
+                for (int nc : {4, 8, 12, 16}) {
+                    if (a.m0 >= 5 && cb < a.m0 - 3) continue;  // these spill registers
                     TreeConfig c = base;
                     c.col_B = cb;
-                    c.col_groups = std::max(1, 256 / (32 << cb));
-                    const int64_t nch = a.P1 * a.n1;
-                    int64_t nchunk = std::max<int64_t>(1, (int64_t)plan->sm_count * 1024 * cm / std::max<int64_t>(1, nch << cb));
-                    int64_t chunk = (a.band_rows() + nchunk - 1) / nchunk;
-                    c.col_chunk = std::max<int64_t>(chunk, std::min<int64_t>(a.band_rows(), 2 * a.n0));
-                    c.row_B = rb;
+                    c.col_groups = col_tree_clamp_groups(a.m0, cb, groups);
+                    c.col_chunk = col_chunk_for(a, nc);
                     cands.push_back(c);
                 }
-        float best = 1e30f;
-        TreeConfig best_c = base;
-        for (const TreeConfig &c : cands) {
+        for (int rb : {std::min(a.m1, 1), std::min(a.m1, 3)}) {
+            TreeConfig c = base;
+            c.row_B = rb;
+            cands.push_back(c);
+        }
+        // time one pass (stage 1 = row levels, 2 = column levels) of config c, best of 3
+        auto time_pass = [&](const TreeConfig &c, int stage, float *ms_out) -> bool {
             a.cfg = c;
             float ms_min = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 cudaEventRecord(e0, s);
-                if (enqueue_forward(plan, a, d_in[i], d_out[i], d_workspace, a.q_begin, a.q_end, s) != cudaSuccess) {
-                    cudaEventDestroy(e0);
-                    cudaEventDestroy(e1);
-                    return SWDFT_ERR_CUDA;
-                }
+                if (enqueue_forward(plan, a, d_in[i], d_out[i], d_workspace, a.q_begin, a.q_end, s,
+                                    stage) != cudaSuccess)
+                    return false;
                 cudaEventRecord(e1, s);
-                if (cudaEventSynchronize(e1) != cudaSuccess) {
-                    cudaEventDestroy(e0);
-                    cudaEventDestroy(e1);
-                    return SWDFT_ERR_CUDA;
-                }
+                if (cudaEventSynchronize(e1) != cudaSuccess) return false;
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
                 ms_min = std::min(ms_min, ms);
             }
-            if (ms_min < best) {
-                best = ms_min;
-                best_c = c;
+            *ms_out = ms_min;
+            return true;
+        };
+        TreeConfig best_c = base;
+        float best_col = 1e30f, best_row = 1e30f;
+        bool ok = time_pass(base, 1, &best_row);  // fills z for the column candidates
+        for (const TreeConfig &c : cands) {
+            float ms = 0.f;
+            if (ok && c.row_B == base.row_B) {
+                ok = time_pass(c, 2, &ms);
+                if (ok && ms < best_col) {
+                    best_col = ms;
+                    best_c.col_B = c.col_B;
+                    best_c.col_groups = c.col_groups;
+                    best_c.col_chunk = c.col_chunk;
+                }
+            }
+            if (ok && c.row_B != base.row_B) {
+                ok = time_pass(c, 1, &ms);
+                if (ok && ms < best_row) {
+                    best_row = ms;
+                    best_c.row_B = c.row_B;
+                }
             }
         }
+        if (!ok) {
+            a.cfg = base;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return SWDFT_ERR_CUDA;
+        }
+        const float best = best_row + best_col;
         a.cfg = best_c;
         a.tuned = true;
         if (const char *path = std::getenv("SWDFT_TUNE_CACHE")) {

@@ -50,6 +50,11 @@ struct ColTreeArgs {
 };
 
 cudaError_t launch_row_tree(const RowTreeArgs &a, cudaStream_t s);
+// Column-pass launch geometry: the B and groups a launch actually uses, and how many
+// blocks of that shape fit on one SM (occupancy API; 0 on error).
+int col_tree_clamp_B(int m0, int B);
+int col_tree_clamp_groups(int m0, int B, int groups);
+int col_tree_blocks_per_sm(int m0, int B, int groups);
 cudaError_t launch_col_tree(const ColTreeArgs &a, cudaStream_t s);
 
 }  // namespace swdft

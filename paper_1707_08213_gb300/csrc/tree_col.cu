@@ -6,6 +6,32 @@
 
 namespace swdft {
 
+int col_tree_clamp_B(int m0, int B) { return std::max(0, std::min(B, std::min(m0, 3))); }
+
+int col_tree_clamp_groups(int m0, int B, int groups) {
+    // at most 256 threads and a ring within the default 48 KB of dynamic shared memory
+    groups = std::max(1, groups);
+    while (groups > 1 && (32 * (1 << B) * groups > 256 ||
+                          sizeof(float2) * col_ring_rows(m0) * 32 * groups > 48 * 1024))
+        groups >>= 1;
+    return groups;
+}
+
+int col_tree_blocks_per_sm(int m0, int B, int groups) {
+    B = col_tree_clamp_B(m0, B);
+    groups = col_tree_clamp_groups(m0, B, groups);
+    const int threads = 32 * (1 << B) * groups;
+    switch (m0 * 8 + B) {
+#define F(M_, B_)      \
+    case M_ * 8 + B_:  \
+        return col_blocks_per_sm<M_, B_>(threads, groups);
+        SWDFT_MB_CASES(F)
+#undef F
+        default:
+            return 0;
+    }
+}
+
 cudaError_t launch_col_tree(const ColTreeArgs &a, cudaStream_t s) {
     const int64_t nch = a.P1 << a.m1;
     if (a.rows_out <= 0 || nch <= 0) return cudaSuccess;
@@ -20,10 +46,8 @@ cudaError_t launch_col_tree(const ColTreeArgs &a, cudaStream_t s) {
     p.chunk = (int)std::min<int64_t>(a.chunk > 0 ? a.chunk : a.rows_out, a.rows_out);
     p.m1 = a.m1;
     p.scale = a.scale;
-    int B = a.B < 0 ? 0 : a.B;
-    B = std::min(B, std::min(a.m0, 3));
-    int groups = a.groups < 1 ? 1 : a.groups;
-    while (groups > 1 && 32 * (1 << B) * groups > 256) groups >>= 1;
+    const int B = col_tree_clamp_B(a.m0, a.B);
+    const int groups = col_tree_clamp_groups(a.m0, B, a.groups);
     p.groups = groups;
     for (int j = 0; j < (1 << a.m0); ++j) p.om[j] = a.om0[j];
     const int64_t per_block = 32LL * groups;

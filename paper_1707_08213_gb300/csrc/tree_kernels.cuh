@@ -98,51 +98,99 @@ __global__ void __launch_bounds__(128) row_tree_kernel(const RowParams p) {
     }
 }
 
+// Rows of z staged in shared memory per column-pass block: a ring that holds the level-0
+// look-back (n/2 rows) plus two step groups (the group being computed and the one being
+// fetched), rounded up to a power of two.
+__host__ __device__ constexpr int col_ring_rows(int M) {
+    const int need = (M >= 1 ? (1 << (M - 1)) : 0) + 2 * tg_period(M);
+    int r = 1;
+    while (r < need) r <<= 1;
+    return r;
+}
+
+__device__ __forceinline__ void cp_async_8(void *smem, const void *gmem, bool valid) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(gmem),
+                 "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // Thread = (channel ch = q1*n1 + k1, residue c, chunk of output rows).  Warp w of a block
-// takes residue w mod 2^B (uniform per warp) and channel group w / 2^B.
+// takes residue w mod 2^B (uniform per warp) and channel group w / 2^B.  The block's z rows
+// arrive in a shared-memory ring by cp.async one step group ahead of use; all residue warps
+// read the same staged rows.  One __syncthreads per step group, no spin-waits.
 template <int M, int B>
-__global__ void __launch_bounds__(256) col_tree_kernel(const ColParams p) {
+__global__ void __launch_bounds__(256, 2) col_tree_kernel(const ColParams p) {
     using Tree = SlidingTree<M, B>;
     constexpr int R = 1 << B;
     constexpr int n = 1 << M;
+    constexpr int kP = Tree::kPeriod;
+    constexpr int kH = Tree::kHalf;
+    constexpr int RD = col_ring_rows(M);
+    extern __shared__ float2 ring[];  // RD x (32 * groups)
+
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int c = warp & (R - 1);
-    const int64_t ch = ((int64_t)blockIdx.x * p.groups + (warp >> B)) * 32 + lane;
-    if (ch >= p.nch) return;
+    const int CH = 32 * p.groups;                       // channels of this block
+    const int my = (warp >> B) * 32 + lane;             // this thread's channel in the block
+    const int64_t ch0 = (int64_t)blockIdx.x * CH;
+    const int64_t ch = ch0 + my;
     const int qa = blockIdx.y * p.chunk;
-    if (qa >= p.rows_out) return;
+    if (qa >= p.rows_out) return;                       // uniform per block
     const int qb = min(qa + p.chunk, p.rows_out);
     const int steps = (qb - qa) + (n - 1);
+    const int zr_end = qb + n - 1;                      // one past the last z row used
+    const bool active = ch < p.nch;
+
+    // stage z rows [r_lo, r_hi) of this block's channels into the ring
+    auto fetch = [&](int r_lo, int r_hi) {
+        r_hi = min(r_hi, zr_end);
+        const int total = (r_hi - r_lo) * CH;
+        for (int e = threadIdx.x; e < total; e += blockDim.x) {
+            const int rr = r_lo + e / CH;
+            const int cc = e - (e / CH) * CH;
+            const bool ok = ch0 + cc < p.nch;
+            const float2 *src = p.z + (int64_t)rr * p.nch + (ok ? ch0 + cc : 0);
+            cp_async_8(&ring[(rr & (RD - 1)) * CH + cc], src, ok);
+        }
+        cp_async_commit();
+    };
 
     const int n1 = 1 << p.m1;
     const int64_t q1 = ch >> p.m1;
     const int64_t k1 = ch & (n1 - 1);
     const int kstride = R * n1;  // elements between outputs t and t+1 (k0 step 2^B)
-    const int64_t back = (int64_t)Tree::kHalf * p.nch;
-    const float2 *zp = p.z + (int64_t)qa * p.nch + ch;
     float2 *dst = p.out + (int64_t)qa * p.orow + q1 * ((int64_t)n * n1) + (int64_t)c * n1 + k1;
     const float s = p.scale;
 
     Tree tree;
     tree.init(c, p.om);
-    for (int jb = 0; jb < steps; jb += Tree::kPeriod) {
-        static_for<0, Tree::kPeriod>([&](auto JJ) {
+    fetch(qa - kH, qa + kP);
+    cp_async_wait_all();
+    __syncthreads();
+    for (int jb = 0; jb < steps; jb += kP) {
+        if (jb + kP < steps) fetch(qa + jb + kP, qa + jb + 2 * kP);
+        static_for<0, kP>([&](auto JJ) {
             constexpr int J = decltype(JJ)::value;
             const int j = jb + J;
             if (j < steps) {
-                const float2 xp = __ldg(zp);
-                const float2 xs = (M >= 1) ? __ldg(zp - back) : make_float2(0.f, 0.f);
-                zp += p.nch;
+                const int zr = qa + j;  // z row = window end row, relative to the band
+                const float2 xp = ring[(zr & (RD - 1)) * CH + my];
+                const float2 xs = (M >= 1) ? ring[((zr - kH) & (RD - 1)) * CH + my] : make_float2(0.f, 0.f);
                 float2 o[Tree::kOut];
                 tree.template step<J>(xp, xs, o);
-                if (j >= n - 1) {
+                if (j >= n - 1 && active) {
 #pragma unroll
                     for (int t = 0; t < Tree::kOut; ++t) __stcs(dst + t * kstride, c_scale(s, o[t]));
                     dst += p.orow;
                 }
             }
         });
+        cp_async_wait_all();
+        __syncthreads();
     }
 }
 
@@ -150,6 +198,8 @@ template <int M, int B>
 void row_launch_mb(const RowParams &p, int cplx, dim3 g, dim3 b, cudaStream_t s);
 template <int M, int B>
 void col_launch_mb(const ColParams &p, dim3 g, dim3 b, cudaStream_t s);
+template <int M, int B>
+int col_blocks_per_sm(int threads, int groups);
 
 #define SWDFT_ROW_INSTANTIATE(M_, B_)                                                        \
     template <>                                                                              \
@@ -163,7 +213,17 @@ void col_launch_mb(const ColParams &p, dim3 g, dim3 b, cudaStream_t s);
 #define SWDFT_COL_INSTANTIATE(M_, B_)                                                     \
     template <>                                                                           \
     void col_launch_mb<M_, B_>(const ColParams &p, dim3 g, dim3 b, cudaStream_t s) {      \
-        col_tree_kernel<M_, B_><<<g, b, 0, s>>>(p);                                       \
+        const size_t smem = sizeof(float2) * col_ring_rows(M_) * 32 * p.groups;          \
+        col_tree_kernel<M_, B_><<<g, b, smem, s>>>(p);                                    \
+    }                                                                                     \
+    template <>                                                                           \
+    int col_blocks_per_sm<M_, B_>(int threads, int groups) {                              \
+        int nb = 0;                                                                       \
+        const size_t smem = sizeof(float2) * col_ring_rows(M_) * 32 * groups;             \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_tree_kernel<M_, B_>,   \
+                                                          threads, smem) != cudaSuccess)  \
+            return 0;                                                                     \
+        return nb;                                                                        \
     }
 
 // (M, B) pairs with B <= min(M, 3)
