@@ -1,0 +1,73 @@
+// Adjoint passes (transposed tree): launchers.  Instantiations live in adj_m*.cu.
+#include <algorithm>
+
+#include "adjoint_kernels.cuh"
+#include "tree_kernels.cuh"
+
+namespace swdft {
+
+cudaError_t launch_adj_col(const AdjColArgs &a, cudaStream_t s) {
+    const int64_t nch = a.P1 << a.m1;
+    const int64_t zrows = a.rows_out + (int64_t(1) << a.m0) - 1;
+    if (a.rows_out <= 0 || nch <= 0) return cudaSuccess;
+    if (a.m0 < 0 || a.m0 > kMaxLog2 || a.m1 < 0 || a.m1 > kMaxLog2 || zrows > INT32_MAX)
+        return cudaErrorInvalidValue;
+    AdjColParams p;
+    p.G = a.G;
+    p.gz = a.gz;
+    p.nch = nch;
+    p.rows_out = (int)a.rows_out;
+    p.zrows = (int)zrows;
+    p.chunk = (int)std::min<int64_t>(a.chunk > 0 ? a.chunk : zrows, zrows);
+    p.m1 = a.m1;
+    p.scale = a.scale;
+    for (int j = 0; j < (1 << a.m0); ++j) p.om[j] = a.om0[j];
+    const int B = std::max(0, std::min(a.B, std::min(a.m0, 3)));
+    const int threads = 128;
+    const int64_t per_block = threads >> B;
+    dim3 grid((unsigned)((nch + per_block - 1) / per_block), (unsigned)((zrows + p.chunk - 1) / p.chunk));
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    switch (a.m0 * 8 + B) {
+#define F(M_, B_)                                              \
+    case M_ * 8 + B_:                                          \
+        adj_col_launch_mb<M_, B_>(p, grid, dim3(threads), s);  \
+        break;
+        SWDFT_MB_CASES(F)
+#undef F
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_row(const AdjRowArgs &a, cudaStream_t s) {
+    if (a.zrows <= 0 || a.N1 <= 0) return cudaSuccess;
+    if (a.m1 < 0 || a.m1 > kMaxLog2 || a.zrows > INT32_MAX || a.N1 > INT32_MAX) return cudaErrorInvalidValue;
+    AdjRowParams p;
+    p.gz = a.gz;
+    p.gx = a.gx;
+    p.ld_out = a.ld_out;
+    p.zrows = (int)a.zrows;
+    p.N1 = (int)a.N1;
+    p.P1 = (int)(a.N1 - (int64_t(1) << a.m1) + 1);
+    p.chunk = (int)std::min<int64_t>(a.chunk > 0 ? a.chunk : a.N1, a.N1);
+    for (int j = 0; j < (1 << a.m1); ++j) p.om[j] = a.om1[j];
+    const int B = std::max(0, std::min(a.B, std::min(a.m1, 3)));
+    const int threads = 128;
+    const int64_t per_block = threads >> B;
+    dim3 grid((unsigned)((a.zrows + per_block - 1) / per_block), (unsigned)((a.N1 + p.chunk - 1) / p.chunk));
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    switch (a.m1 * 8 + B) {
+#define F(M_, B_)                                                       \
+    case M_ * 8 + B_:                                                   \
+        adj_row_launch_mb<M_, B_>(p, a.cplx, grid, dim3(threads), s);   \
+        break;
+        SWDFT_MB_CASES(F)
+#undef F
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace swdft

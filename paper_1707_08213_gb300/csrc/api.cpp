@@ -313,7 +313,7 @@ swdft_status swdft2d_get_algo(swdft2d_plan_t plan, int32_t *algo) {
 
 swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t *launches) {
     if (!plan || !launches) return SWDFT_ERR_INVALID_ARG;
-    if (adjoint) return SWDFT_ERR_UNSUPPORTED;
+    (void)adjoint;  // forward: row + column pass; adjoint: column + row adjoint pass
     *launches = (int32_t)(2 * plan->arrays.size());
     return SWDFT_OK;
 }
@@ -386,12 +386,57 @@ swdft_status swdft2d_set_tree_config(swdft2d_plan_t plan, int32_t i, int32_t row
 
 swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_grad_out,
                                      void *const *d_grad_in, void *d_workspace, void *stream) {
-    (void)d_grad_out;
-    (void)d_grad_in;
-    (void)d_workspace;
-    (void)stream;
-    if (!plan) return SWDFT_ERR_INVALID_ARG;
-    return SWDFT_ERR_UNSUPPORTED;
+    if (!plan || !d_grad_out || !d_grad_in) return SWDFT_ERR_INVALID_ARG;
+    for (size_t i = 0; i < plan->arrays.size(); ++i) {
+        const ArrayPlan &a = plan->arrays[i];
+        if (!d_grad_out[i] || !d_grad_in[i]) return SWDFT_ERR_INVALID_ARG;
+        if ((uintptr_t)d_grad_out[i] % sizeof(float2) != 0) return SWDFT_ERR_INVALID_ARG;
+        if ((uintptr_t)d_grad_in[i] % a.in_elem() != 0) return SWDFT_ERR_INVALID_ARG;
+    }
+    if (plan->ws_bytes > 0 && (!d_workspace || (uintptr_t)d_workspace % kAlign != 0)) return SWDFT_ERR_WORKSPACE;
+    swdft_status st = configure(plan);
+    if (st != SWDFT_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (size_t i = 0; i < plan->arrays.size(); ++i) {
+        const ArrayPlan &a = plan->arrays[i];
+        const int64_t zrows = a.band_rows() + a.n0 - 1;
+        const size_t row_bytes = (size_t)a.N1 * a.in_elem();
+        char *gx = static_cast<char *>(d_grad_in[i]);
+        // rows no window of the band touches get a zero gradient
+        if (a.q_begin > 0 && cudaMemsetAsync(gx, 0, (size_t)a.q_begin * row_bytes, s) != cudaSuccess)
+            return SWDFT_ERR_CUDA;
+        const int64_t tail = a.N0 - (a.q_begin + zrows);
+        if (tail > 0 && cudaMemsetAsync(gx + (size_t)(a.q_begin + zrows) * row_bytes, 0,
+                                        (size_t)tail * row_bytes, s) != cudaSuccess)
+            return SWDFT_ERR_CUDA;
+        AdjColArgs c;
+        c.G = static_cast<const float2 *>(d_grad_out[i]);
+        c.gz = static_cast<float2 *>(d_workspace);
+        c.P1 = a.P1;
+        c.rows_out = a.band_rows();
+        c.m0 = a.m0;
+        c.m1 = a.m1;
+        c.scale = norm_scale(plan->norm, a.n0, a.n1);
+        c.om0 = a.om0;
+        c.B = a.m0 <= 4 ? std::min(a.m0, 1) : a.m0 - 3;
+        c.chunk = std::min(zrows, std::max<int64_t>((zrows + 7) / 8, 2 * a.n0));
+        if (launch_adj_col(c, s) != cudaSuccess) return SWDFT_ERR_CUDA;
+        AdjRowArgs r;
+        r.gz = static_cast<const float2 *>(d_workspace);
+        r.gx = gx + (size_t)a.q_begin * row_bytes;
+        r.ld_out = a.N1;
+        r.cplx = a.dtype == SWDFT_C64;
+        r.zrows = zrows;
+        r.N1 = a.N1;
+        r.m1 = a.m1;
+        r.om1 = a.om1;
+        r.B = a.m1 >= 6 ? 3 : std::min(a.m1, 2);
+        const int64_t target = (int64_t)plan->sm_count * 1024;
+        const int64_t nchunk = std::max<int64_t>(1, target / std::max<int64_t>(1, zrows << r.B));
+        r.chunk = std::min<int64_t>(a.N1, std::max<int64_t>((a.N1 + nchunk - 1) / nchunk, 2 * a.n1));
+        if (launch_adj_row(r, s) != cudaSuccess) return SWDFT_ERR_CUDA;
+    }
+    return SWDFT_OK;
 }
 
 swdft_status swdft2d_execute_host(swdft2d_plan_t plan, const void *const *h_in,

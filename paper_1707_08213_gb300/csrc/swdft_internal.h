@@ -57,4 +57,34 @@ int col_tree_clamp_groups(int m0, int B, int groups);
 int col_tree_blocks_per_sm(int m0, int B, int groups);
 cudaError_t launch_col_tree(const ColTreeArgs &a, cudaStream_t s);
 
+// Adjoint of the column levels: gz[r][q1][k1] = scale * sum_{j0,k0} G[r-j0][q1][k0][k1] w_{n0}^{+j0 k0}
+// for the rows_out + n0 - 1 z rows of a band (G holds rows_out window rows).
+struct AdjColArgs {
+    const float2 *G = nullptr;
+    float2 *gz = nullptr;
+    int64_t P1 = 0, rows_out = 0;
+    int m0 = 0, m1 = 0;
+    float scale = 1.f;
+    const float2 *om0 = nullptr;
+    int B = 0;
+    int64_t chunk = 0;  // gz rows per thread (plus n0-1 warm-up steps)
+};
+
+// Adjoint of the row levels: gx[r][p1] = sum_{j1,k1} gz[r][p1-j1][k1] w_{n1}^{+j1 k1}
+// (real part stored for float32 inputs), for zrows rows of N1 columns.
+struct AdjRowArgs {
+    const float2 *gz = nullptr;
+    void *gx = nullptr;
+    int64_t ld_out = 0;
+    int cplx = 0;
+    int64_t zrows = 0, N1 = 0;
+    int m1 = 0;
+    const float2 *om1 = nullptr;
+    int B = 0;
+    int64_t chunk = 0;  // output columns per thread (plus n1-1 warm-up steps)
+};
+
+cudaError_t launch_adj_col(const AdjColArgs &a, cudaStream_t s);
+cudaError_t launch_adj_row(const AdjRowArgs &a, cudaStream_t s);
+
 }  // namespace swdft

@@ -1,0 +1,157 @@
+"""Parity of the hand-written adjoint kernels (transposed tree, through the C ABI and
+torch.autograd) with the FP64 oracle's explicit adjoint A^H, the dot-product identity, and
+central finite differences of an FP64 loss.
+
+Bar: max over pixels of |g_gpu - g_oracle| / sqrt(sum over windows w containing the pixel of
+||G_w||^2) <= 1e-5 (the adjoint's analogue of the forward's window-norm metric).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sw():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1707_08213_gb300 as sw
+    return sw
+
+
+def _G(seed, P0, P1, n0, n1):
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((P0, P1, n0, n1)) + 1j * rng.standard_normal((P0, P1, n0, n1))
+            ).astype(np.complex64)
+
+
+def gpu_adjoint(sw, G, N0, N1, cplx, norm="unitary", band=None, pos="start"):
+    n0, n1 = G.shape[2], G.shape[3]
+    t = sw.Transform([(N0, N1, n0, n1, 1 if cplx else 0)], norm=norm,
+                     bands=None if band is None else [band], pos=pos)
+    g = t.adjoint([torch.from_numpy(G).cuda()])[0]
+    torch.cuda.synchronize()
+    return g.cpu().numpy()
+
+
+SHAPES = [(1, 1, 1, 1), (9, 9, 8, 8), (37, 53, 4, 8), (64, 77, 8, 16), (23, 300, 1, 64),
+          (300, 23, 64, 1), (100, 100, 32, 32), (130, 90, 64, 16), (45, 45, 2, 32), (50, 70, 16, 8)]
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("N0,N1,n0,n1", SHAPES)
+def test_adjoint_matches_oracle(sw, N0, N1, n0, n1, cplx):
+    P0, P1 = N0 - n0 + 1, N1 - n1 + 1
+    G = _G(N0 + 3 * N1, P0, P1, n0, n1)
+    g = gpu_adjoint(sw, G, N0, N1, cplx)
+    ref = oracle.swdft2d_adjoint(G, N0, N1)
+    if not cplx:
+        ref = ref.real
+    assert g.shape == (N0, N1)
+    err = workloads.adjoint_error(g, ref, workloads.adjoint_pixel_norms(G, N0, N1))
+    assert err <= TOL, f"adjoint max normalised error {err:.3e}"
+
+
+@pytest.mark.parametrize("norm", ["none", "inv_n"])
+def test_adjoint_normalisations(sw, norm):
+    N0, N1, n0, n1 = 40, 50, 8, 16
+    G = _G(5, N0 - n0 + 1, N1 - n1 + 1, n0, n1)
+    g = gpu_adjoint(sw, G, N0, N1, True, norm=norm)
+    ref = oracle.swdft2d_adjoint(G, N0, N1, norm=norm)
+    scale = oracle.scale_for("unitary", n0, n1) / oracle.scale_for(norm, n0, n1)
+    err = workloads.adjoint_error(g * scale, ref * scale, workloads.adjoint_pixel_norms(G, N0, N1))
+    assert err <= TOL
+
+
+def test_adjoint_of_band_zeroes_untouched_rows(sw):
+    N0, N1, n0, n1 = 60, 40, 8, 4
+    P0, P1 = N0 - n0 + 1, N1 - n1 + 1
+    G = _G(6, P0, P1, n0, n1)
+    Gb = np.zeros_like(G)
+    Gb[10:30] = G[10:30]
+    g = gpu_adjoint(sw, np.ascontiguousarray(G[10:30]), N0, N1, False, band=(10, 30))
+    ref = oracle.swdft2d_adjoint(Gb, N0, N1).real
+    err = workloads.adjoint_error(g, ref, workloads.adjoint_pixel_norms(Gb, N0, N1))
+    assert err <= TOL
+    assert np.all(g[:10] == 0) and np.all(g[30 + n0 - 1:] == 0)
+
+
+def test_dot_product_identity_full_size(sw):
+    """<A x, G> = <x, A^H G> on the 8 x 256x256, 16x16-window differentiation workload."""
+    xs, w, (n0, n1) = workloads.adjoint_batch_8()
+    N0, N1 = xs.shape[1:]
+    t = sw.Transform([(N0, N1, n0, n1, 0)] * len(xs))
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    a = t.forward(xd)
+    rng = np.random.default_rng(44)
+    Gs = [torch.from_numpy(_G(100 + i, N0 - n0 + 1, N1 - n1 + 1, n0, n1)).cuda() for i in range(len(xs))]
+    g = t.adjoint(Gs)
+    torch.cuda.synchronize()
+    lhs = sum(torch.vdot(ai.flatten().to(torch.complex128), Gi.flatten().to(torch.complex128))
+              for ai, Gi in zip(a, Gs))
+    rhs = sum(torch.vdot(xi.flatten().to(torch.complex128), gi.flatten().to(torch.complex128))
+              for xi, gi in zip(xd, g))
+    # x is real: <x, A^H G> uses Re(A^H G), so compare real parts
+    assert abs(lhs.real - rhs.real) <= 1e-5 * abs(lhs.real) + 1e-3, (lhs, rhs)
+
+
+def test_autograd_gradient_full_size_against_oracle(sw):
+    """loss = sum w |A x|^2 per image of the 8-image batch; torch's grad via the adjoint
+    kernel vs the oracle's explicit adjoint (image 0 in full, sampled pixels of the rest)."""
+    xs, w, (n0, n1) = workloads.adjoint_batch_8()
+    N0, N1 = xs.shape[1:]
+    wd = torch.from_numpy(w).cuda()
+    rng = np.random.default_rng(45)
+    for i, x in enumerate(xs):
+        xd = torch.from_numpy(x).cuda().requires_grad_(True)
+        a = sw.SWDFT2dFunction.apply(xd, n0, n1)
+        loss = (wd * a.abs() ** 2).sum()
+        loss.backward()
+        g = xd.grad.cpu().numpy()
+        a_np = a.detach().cpu().numpy()
+        Gup = 2 * w * a_np                                  # torch's gradient w.r.t. a
+        if i == 0:
+            ref = oracle.swdft2d_adjoint(Gup, N0, N1).real
+            err = workloads.adjoint_error(g, ref, workloads.adjoint_pixel_norms(Gup, N0, N1))
+        else:
+            rs = rng.integers(0, N0, 256)
+            cs = rng.integers(0, N1, 256)
+            ref = oracle.swdft2d_adjoint_pixels(Gup, N0, N1, rs, cs, threads=8).real
+            err = workloads.adjoint_error(g[rs, cs], ref,
+                                          workloads.adjoint_pixel_norms(Gup, N0, N1)[rs, cs])
+        assert err <= TOL, f"image {i}: {err:.3e}"
+
+
+@pytest.mark.parametrize("n", [4, 8, 16])
+def test_autograd_gradient_matches_fp64_finite_differences(sw, n):
+    """The 16x16 top-left crop of image 0 with n x n windows; mask = the first P0 x P1 x n x n
+    entries of the workload's mask; central differences (h = 1e-6) of the FP64 oracle loss."""
+    xs, w_full, _ = workloads.adjoint_batch_8()
+    x = np.ascontiguousarray(xs[0, :16, :16])
+    P = 16 - n + 1
+    w = np.ascontiguousarray(w_full[:P, :P, :n, :n]).astype(np.float64)
+    xd = torch.from_numpy(x).cuda().requires_grad_(True)
+    a = sw.SWDFT2dFunction.apply(xd, n, n)
+    loss = (torch.from_numpy(w).cuda().float() * a.abs() ** 2).sum()
+    loss.backward()
+    g = xd.grad.cpu().numpy().astype(np.float64)
+
+    def L(v):
+        return float(np.sum(w * np.abs(oracle.swdft2d(v, n, n)) ** 2))
+
+    x64 = x.astype(np.float64)
+    h = 1e-6
+    fd = np.empty_like(x64)
+    for r in range(16):
+        for c in range(16):
+            e = np.zeros_like(x64)
+            e[r, c] = h
+            fd[r, c] = (L(x64 + e) - L(x64 - e)) / (2 * h)
+    scale = np.abs(fd).max()
+    assert np.abs(g - fd).max() <= 1e-5 * scale + 1e-6, (np.abs(g - fd).max(), scale)

@@ -184,3 +184,30 @@ def normalised_error(a: np.ndarray, ref: np.ndarray, sq_norms: np.ndarray,
     safe = np.where(nrm > 0, nrm, 1.0)
     rel = np.where(nrm > 0, flat / safe, flat)
     return float(rel.max(initial=0.0)), float(math.sqrt(np.mean(rel ** 2)) if rel.size else 0.0)
+
+
+def adjoint_pixel_norms(G: np.ndarray, N0: int, N1: int) -> np.ndarray:
+    """sqrt(sum over windows w containing pixel (r,c) of ||G_w||_2^2), shape (N0, N1).
+
+    With the unitary scale, each window adds at most ||G_w||_2 to |(A^H G)[r,c]|, so this is
+    the natural per-pixel scale of an adjoint's error (the analogue of ||x_w||_2 forward).
+    """
+    Gs = np.asarray(G)
+    P0, P1, n0, n1 = Gs.shape
+    e = np.sum(np.abs(Gs.astype(np.complex128)) ** 2, axis=(2, 3))
+    S = np.zeros((P0 + 1, P1 + 1))
+    S[1:, 1:] = np.cumsum(np.cumsum(e, axis=0), axis=1)
+    r = np.arange(N0)
+    c = np.arange(N1)
+    r_lo = np.clip(r - n0 + 1, 0, P0)[:, None]
+    r_hi = np.clip(r + 1, 0, P0)[:, None]
+    c_lo = np.clip(c - n1 + 1, 0, P1)[None, :]
+    c_hi = np.clip(c + 1, 0, P1)[None, :]
+    box = S[r_hi, c_hi] - S[r_lo, c_hi] - S[r_hi, c_lo] + S[r_lo, c_lo]
+    return np.sqrt(np.clip(box, 0.0, None))
+
+
+def adjoint_error(g: np.ndarray, ref: np.ndarray, pixel_norms: np.ndarray) -> float:
+    """max over pixels of |g - ref| / pixel norm (absolute where the norm is 0)."""
+    d = np.abs(np.asarray(g, dtype=np.complex128) - np.asarray(ref, dtype=np.complex128))
+    return float(np.max(np.where(pixel_norms > 0, d / np.where(pixel_norms > 0, pixel_norms, 1), d)))
