@@ -21,7 +21,7 @@ cudaError_t launch_adj_col(const AdjColArgs &a, cudaStream_t s) {
     p.chunk = (int)std::min<int64_t>(a.chunk > 0 ? a.chunk : zrows, zrows);
     p.m1 = a.m1;
     p.scale = a.scale;
-    for (int j = 0; j < (1 << a.m0); ++j) p.om[j] = a.om0[j];
+    for (int j = 0; j < kMaxN; ++j) p.om64[j] = a.om64[j];
     const int B = std::max(0, std::min(a.B, std::min(a.m0, 3)));
     const int threads = 128;
     const int64_t per_block = threads >> B;
@@ -51,7 +51,7 @@ cudaError_t launch_adj_row(const AdjRowArgs &a, cudaStream_t s) {
     p.N1 = (int)a.N1;
     p.P1 = (int)(a.N1 - (int64_t(1) << a.m1) + 1);
     p.chunk = (int)std::min<int64_t>(a.chunk > 0 ? a.chunk : a.N1, a.N1);
-    for (int j = 0; j < (1 << a.m1); ++j) p.om[j] = a.om1[j];
+    for (int j = 0; j < kMaxN; ++j) p.om64[j] = a.om64[j];
     const int B = std::max(0, std::min(a.B, std::min(a.m1, 3)));
     const int threads = 128;
     const int64_t per_block = threads >> B;

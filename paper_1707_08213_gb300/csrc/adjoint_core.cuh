@@ -43,18 +43,20 @@ struct SlidingTreeAdjoint {
     float2 ring[kRing > 0 ? kRing : 1];
     float2 tw[kTw > 0 ? kTw : 1];  // conjugated twiddles, same indexing as SlidingTree
 
-    __device__ __forceinline__ void init(int c, const float2 *om) {
+    // om64[j] = w_64^{-j}; conj(W_v^i) = conj(om64[i * 2^(6-v)])
+    __device__ __forceinline__ void init(int c, const float2 *om64) {
+        static_assert(M <= 6, "twiddle table covers windows up to 64");
         const int cb = c & ((1 << B) - 1);
 #pragma unroll
         for (int v = 1; v <= M; ++v) {
             const int base = tg_twoff(B, v);
             if (v <= B) {
-                const float2 w = om[(c & ((1 << v) - 1)) << (M - v)];
+                const float2 w = om64[(c & ((1 << v) - 1)) << (6 - v)];
                 tw[base] = make_float2(w.x, -w.y);
             } else {
 #pragma unroll
                 for (int t = 0; t < tg_held(B, v - 1); ++t) {
-                    const float2 w = om[(cb + (t << B)) << (M - v)];
+                    const float2 w = om64[(cb + (t << B)) << (6 - v)];
                     tw[base + t] = make_float2(w.x, -w.y);
                 }
             }

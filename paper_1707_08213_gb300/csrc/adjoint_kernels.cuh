@@ -30,7 +30,7 @@ struct AdjColParams {
     int chunk;         // gz rows per thread (plus n0 - 1 warm-up steps)
     int m1;
     float scale;
-    float2 om[kMaxN];
+    float2 om64[kMaxN];  // w_64^{-j}: every power-of-two length's twiddles
 };
 
 struct AdjRowParams {
@@ -40,7 +40,7 @@ struct AdjRowParams {
     int zrows;
     int N1, P1;
     int chunk;         // output columns per thread (plus n1 - 1 warm-up steps)
-    float2 om[kMaxN];
+    float2 om64[kMaxN];  // w_64^{-j}: every power-of-two length's twiddles
 };
 
 template <int R>
@@ -54,7 +54,7 @@ __device__ __forceinline__ float2 reduce_residues(float2 v) {
 }
 
 template <int M, int B>
-__global__ void __launch_bounds__(128) adj_col_kernel(const AdjColParams p) {
+__global__ void __launch_bounds__(128) adj_col_kernel(const __grid_constant__ AdjColParams p) {
     using Tree = SlidingTreeAdjoint<M, B>;
     constexpr int R = 1 << B;
     constexpr int n = 1 << M;
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(128) adj_col_kernel(const AdjColParams p) {
     const float s = p.scale;
 
     Tree tree;
-    tree.init(c, p.om);
+    tree.init(c, p.om64);
     for (int jb = 0; jb < steps; jb += Tree::kPeriod) {
         static_for<0, Tree::kPeriod>([&](auto JJ) {
             constexpr int J = decltype(JJ)::value;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(128) adj_col_kernel(const AdjColParams p) {
 }
 
 template <int M, int B, bool CPLX>
-__global__ void __launch_bounds__(128) adj_row_kernel(const AdjRowParams p) {
+__global__ void __launch_bounds__(128) adj_row_kernel(const __grid_constant__ AdjRowParams p) {
     using Tree = SlidingTreeAdjoint<M, B>;
     constexpr int R = 1 << B;
     constexpr int n = 1 << M;
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(128) adj_row_kernel(const AdjRowParams p) {
     const float2 *zrow = p.gz + (int64_t)(active ? row : 0) * p.P1 * n + c;
 
     Tree tree;
-    tree.init(c, p.om);
+    tree.init(c, p.om64);
     for (int jb = 0; jb < steps; jb += Tree::kPeriod) {
         static_for<0, Tree::kPeriod>([&](auto JJ) {
             constexpr int J = decltype(JJ)::value;

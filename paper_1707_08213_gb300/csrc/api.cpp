@@ -41,7 +41,6 @@ struct ArrayPlan {
     int64_t N0 = 0, N1 = 0, ld = 0, P0 = 0, P1 = 0;
     int n0 = 1, n1 = 1, m0 = 0, m1 = 0, dtype = SWDFT_R32;
     int64_t q_begin = 0, q_end = 0;  // band of window rows, q coordinates
-    float2 om0[kMaxN], om1[kMaxN];
     TreeConfig cfg;
     bool tuned = false;
 
@@ -68,9 +67,21 @@ struct swdft2d_plan_s {
     int norm = SWDFT_NORM_UNITARY, pos = SWDFT_POS_START, algo = SWDFT_ALGO_TREE_F32;
     uint32_t flags = 0;
     size_t ws_bytes = 0;
+    // Omega of length 64 (FP64-evaluated, FP32-rounded): Omega^i of Section 4.2 for every
+    // n_i = 2^m_i <= 64 is its strided view, Omega^i[j] = om64[j * 64 / n_i], bit for bit.
+    float2 om64[kMaxN];
     bool configured = false;
     int sm_count = 152;
     GraphCache graph;
+    // persistent batch (SWDFT_FLAG_PERSISTENT): per-array z offsets in the workspace, the
+    // tile descriptors (pinned staging + device copy, allocated at the first execute)
+    std::vector<size_t> z_off;
+    BatchImage *desc_host = nullptr;
+    BatchImage *desc_dev = nullptr;    // used by direct executes
+    BatchImage *desc_graph = nullptr;  // owned by the captured graph (fixed buffers)
+    cudaEvent_t desc_uploaded = nullptr;
+    int64_t row_items = 0, col_items = 0;
+    int64_t row_slots = 0, col_slots = 0;
     // host-buffer pipeline (SWDFT_FLAG_HOST_IO), allocated at the first execute_host
     bool io_ready = false;
     int64_t io_band = 0;
@@ -128,7 +139,83 @@ swdft_status configure(swdft2d_plan_t plan) {
     plan->sm_count = sms > 0 ? sms : 152;
     for (auto &a : plan->arrays)
         if (!a.tuned) default_config(a, plan->sm_count);
+    if (plan->flags & SWDFT_FLAG_PERSISTENT) {
+        const size_t bytes = sizeof(BatchImage) * plan->arrays.size();
+        if (cudaHostAlloc((void **)&plan->desc_host, bytes, cudaHostAllocDefault) != cudaSuccess) return SWDFT_ERR_OOM;
+        if (cudaMalloc((void **)&plan->desc_dev, bytes) != cudaSuccess) return SWDFT_ERR_OOM;
+        if (cudaMalloc((void **)&plan->desc_graph, bytes) != cudaSuccess) return SWDFT_ERR_OOM;
+        if (cudaEventCreateWithFlags(&plan->desc_uploaded, cudaEventDisableTiming) != cudaSuccess) return SWDFT_ERR_CUDA;
+        int row_bps = 0, col_bps = 0;
+        if (batch_blocks_per_sm(&row_bps, &col_bps) != cudaSuccess) return SWDFT_ERR_CUDA;
+        plan->row_slots = (int64_t)plan->sm_count * std::max(1, row_bps);
+        plan->col_slots = (int64_t)plan->sm_count * std::max(1, col_bps);
+    }
     plan->configured = true;
+    return SWDFT_OK;
+}
+
+// Fill the pinned batch descriptors for these buffers.  The caller makes sure no pending
+// copy still reads them.
+void fill_batch(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out, void *ws) {
+    int64_t row_items = 0, col_items = 0;
+    for (size_t i = 0; i < plan->arrays.size(); ++i) {
+        const ArrayPlan &a = plan->arrays[i];
+        BatchImage d;
+        std::memset(&d, 0, sizeof(d));
+        float2 *z = reinterpret_cast<float2 *>(static_cast<char *>(ws) + plan->z_off[i]) + a.z_pad() * a.P1 * a.n1;
+        const int64_t zrows = a.band_rows() + a.n0 - 1;
+        const int rowB = batch_row_B(a.m1);
+        d.row.x = static_cast<const char *>(d_in[i]);
+        d.row.ld = a.ld;
+        d.row.r_base = a.q_begin;
+        d.row.zrow = a.P1 * a.n1;
+        d.row.rows = (int)zrows;
+        d.row.P1 = (int)a.P1;
+        d.row.chunk = (int)std::min<int64_t>(a.P1, std::max<int64_t>(1, a.cfg.row_chunk));
+        d.row.z = z;
+        const int colB = batch_col_B(a.m0);
+        d.col.z = z;
+        d.col.out = static_cast<float2 *>(d_out[i]);
+        d.col.nch = a.P1 * a.n1;
+        d.col.orow = a.P1 * a.n1 * a.n0;
+        d.col.rows_out = (int)a.band_rows();
+        d.col.chunk = (int)std::min<int64_t>(a.band_rows(), std::max<int64_t>(1, a.cfg.col_chunk));
+        d.col.m1 = a.m1;
+        d.col.groups = batch_col_groups(a.m0);
+        d.col.scale = norm_scale(plan->norm, a.n0, a.n1);
+        d.m0 = a.m0;
+        d.m1 = a.m1;
+        d.cplx = a.dtype == SWDFT_C64;
+        const int rows_per_block = 256 >> rowB;
+        d.row_blocks = (int)((zrows + rows_per_block - 1) / rows_per_block);
+        d.row_chunks = (int)((a.P1 + d.row.chunk - 1) / d.row.chunk);
+        const int64_t ch_per_block = 32LL * d.col.groups;
+        d.col_blocks = (int)((d.col.nch + ch_per_block - 1) / ch_per_block);
+        d.col_chunks = (int)((a.band_rows() + d.col.chunk - 1) / d.col.chunk);
+        (void)colB;
+        d.row_item0 = row_items;
+        d.col_item0 = col_items;
+        row_items += (int64_t)d.row_blocks * d.row_chunks;
+        col_items += (int64_t)d.col_blocks * d.col_chunks;
+        plan->desc_host[i] = d;
+    }
+    plan->row_items = row_items;
+    plan->col_items = col_items;
+}
+
+// Direct (non-graph) persistent execute: refill the staging once its previous upload ran,
+// upload it on the stream and launch the two persistent passes.
+swdft_status enqueue_batch(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out,
+                           void *ws, cudaStream_t s) {
+    if (cudaEventSynchronize(plan->desc_uploaded) != cudaSuccess) return SWDFT_ERR_CUDA;
+    fill_batch(plan, d_in, d_out, ws);
+    if (cudaMemcpyAsync(plan->desc_dev, plan->desc_host, sizeof(BatchImage) * plan->arrays.size(),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return SWDFT_ERR_CUDA;
+    if (cudaEventRecord(plan->desc_uploaded, s) != cudaSuccess) return SWDFT_ERR_CUDA;
+    if (launch_batch_tree(plan->desc_dev, (int)plan->arrays.size(), plan->row_items, plan->col_items,
+                          plan->om64, plan->row_slots, plan->col_slots, s) != cudaSuccess)
+        return SWDFT_ERR_CUDA;
     return SWDFT_OK;
 }
 
@@ -149,7 +236,7 @@ cudaError_t enqueue_forward(const swdft2d_plan_s *plan, const ArrayPlan &a, cons
     r.m1 = a.m1;
     float2 *z = static_cast<float2 *>(ws) + a.z_pad() * a.P1 * a.n1;
     r.z = z;
-    r.om1 = a.om1;
+    r.om64 = plan->om64;
     r.B = a.cfg.row_B;
     r.chunk = a.cfg.row_chunk;
     if (stages & 1) {
@@ -165,7 +252,7 @@ cudaError_t enqueue_forward(const swdft2d_plan_s *plan, const ArrayPlan &a, cons
     c.m1 = a.m1;
     c.out = static_cast<float2 *>(out);
     c.scale = norm_scale(plan->norm, a.n0, a.n1);
-    c.om0 = a.om0;
+    c.om64 = plan->om64;
     c.B = a.cfg.col_B;
     c.chunk = a.cfg.col_chunk;
     c.groups = a.cfg.col_groups;
@@ -268,11 +355,8 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
             if (a.q_begin < 0 || a.q_end > a.P0 || a.q_begin >= a.q_end) return SWDFT_ERR_INVALID_ARG;
         }
         if (m0 > kMaxLog2 || m1 > kMaxLog2) return SWDFT_ERR_UNSUPPORTED;
-        make_omega(a.n0, a.om0);
-        make_omega(a.n1, a.om1);
     }
     if (algo != SWDFT_ALGO_AUTO && algo != SWDFT_ALGO_TREE_F32) return SWDFT_ERR_UNSUPPORTED;
-    if (flags & SWDFT_FLAG_PERSISTENT) return SWDFT_ERR_UNSUPPORTED;
 
     swdft2d_plan_s *p = new (std::nothrow) swdft2d_plan_s();
     if (!p) return SWDFT_ERR_OOM;
@@ -281,9 +365,18 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
     p->pos = pos;
     p->algo = SWDFT_ALGO_TREE_F32;
     p->flags = flags;
-    // arrays run one after another on one stream, so they share one z buffer
+    make_omega(kMaxN, p->om64);
     size_t ws = 0;
-    for (const auto &a : p->arrays) ws = std::max(ws, align_up(a.z_bytes(a.band_rows())));
+    if (flags & SWDFT_FLAG_PERSISTENT) {
+        // one launch covers every array, so each array has its own z region
+        for (const auto &a : p->arrays) {
+            p->z_off.push_back(ws);
+            ws += align_up(a.z_bytes(a.band_rows()));
+        }
+    } else {
+        // arrays run one after another on one stream, so they share one z buffer
+        for (const auto &a : p->arrays) ws = std::max(ws, align_up(a.z_bytes(a.band_rows())));
+    }
     p->ws_bytes = ws;
     *out = p;
     return SWDFT_OK;
@@ -313,8 +406,9 @@ swdft_status swdft2d_get_algo(swdft2d_plan_t plan, int32_t *algo) {
 
 swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t *launches) {
     if (!plan || !launches) return SWDFT_ERR_INVALID_ARG;
-    (void)adjoint;  // forward: row + column pass; adjoint: column + row adjoint pass
-    *launches = (int32_t)(2 * plan->arrays.size());
+    // forward: row + column pass per array, or the two persistent passes for the whole batch;
+    // adjoint: column + row adjoint pass per array
+    *launches = (!adjoint && (plan->flags & SWDFT_FLAG_PERSISTENT)) ? 2 : (int32_t)(2 * plan->arrays.size());
     return SWDFT_OK;
 }
 
@@ -325,7 +419,19 @@ swdft_status swdft2d_execute(swdft2d_plan_t plan, const void *const *d_in, void 
     if (st != SWDFT_OK) return st;
     if ((st = configure(plan)) != SWDFT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (!(plan->flags & SWDFT_FLAG_GRAPH) || s == nullptr) return enqueue_all(plan, d_in, d_out, d_workspace, s);
+    const bool persistent = (plan->flags & SWDFT_FLAG_PERSISTENT) != 0;
+    if (!(plan->flags & SWDFT_FLAG_GRAPH) || s == nullptr)
+        return persistent ? enqueue_batch(plan, d_in, d_out, d_workspace, s)
+                          : enqueue_all(plan, d_in, d_out, d_workspace, s);
+    // inside a graph only kernel launches are recorded; a persistent plan's descriptors for
+    // these buffers go to the graph's own device buffer before capture
+    auto enqueue = [&]() {
+        if (!persistent) return enqueue_all(plan, d_in, d_out, d_workspace, s);
+        return launch_batch_tree(plan->desc_graph, (int)plan->arrays.size(), plan->row_items,
+                                 plan->col_items, plan->om64, plan->row_slots, plan->col_slots, s) == cudaSuccess
+                   ? SWDFT_OK
+                   : SWDFT_ERR_CUDA;
+    };
 
     // CUDA graph: capture the launch sequence once per (buffers, stream), replay after.
     std::vector<const void *> key;
@@ -337,9 +443,18 @@ swdft_status swdft2d_execute(swdft2d_plan_t plan, const void *const *d_in, void 
     GraphCache &g = plan->graph;
     if (!g.exec || g.key != key || g.stream != s) {
         destroy_graph(g);
+        if (persistent) {
+            // an earlier graph of this plan may still be reading the descriptors on any
+            // stream: re-capture is rare, so wait for the whole device
+            if (cudaDeviceSynchronize() != cudaSuccess) return SWDFT_ERR_CUDA;
+            fill_batch(plan, d_in, d_out, d_workspace);
+            if (cudaMemcpy(plan->desc_graph, plan->desc_host, sizeof(BatchImage) * plan->arrays.size(),
+                           cudaMemcpyHostToDevice) != cudaSuccess)
+                return SWDFT_ERR_CUDA;
+        }
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SWDFT_ERR_CUDA;
-        swdft_status est = enqueue_all(plan, d_in, d_out, d_workspace, s);
+        swdft_status est = enqueue();
         cudaError_t ce = cudaStreamEndCapture(s, &graph);
         if (est != SWDFT_OK || ce != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -417,7 +532,7 @@ swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_g
         c.m0 = a.m0;
         c.m1 = a.m1;
         c.scale = norm_scale(plan->norm, a.n0, a.n1);
-        c.om0 = a.om0;
+        c.om64 = plan->om64;
         c.B = a.m0 <= 4 ? std::min(a.m0, 1) : a.m0 - 3;
         c.chunk = std::min(zrows, std::max<int64_t>((zrows + 7) / 8, 2 * a.n0));
         if (launch_adj_col(c, s) != cudaSuccess) return SWDFT_ERR_CUDA;
@@ -429,7 +544,7 @@ swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_g
         r.zrows = zrows;
         r.N1 = a.N1;
         r.m1 = a.m1;
-        r.om1 = a.om1;
+        r.om64 = plan->om64;
         r.B = a.m1 >= 6 ? 3 : std::min(a.m1, 2);
         const int64_t target = (int64_t)plan->sm_count * 1024;
         const int64_t nchunk = std::max<int64_t>(1, target / std::max<int64_t>(1, zrows << r.B));
@@ -602,6 +717,13 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
 swdft_status swdft2d_destroy(swdft2d_plan_t plan) {
     if (!plan) return SWDFT_OK;
     destroy_graph(plan->graph);
+    if (plan->desc_uploaded) {
+        cudaEventSynchronize(plan->desc_uploaded);
+        cudaEventDestroy(plan->desc_uploaded);
+    }
+    if (plan->desc_host) cudaFreeHost(plan->desc_host);
+    if (plan->desc_dev) cudaFree(plan->desc_dev);
+    if (plan->desc_graph) cudaFree(plan->desc_graph);
     if (plan->io_ready) {
         cudaFree(plan->io_in);
         cudaFree(plan->io_ws);

@@ -88,9 +88,8 @@ extern "C" swdft_status swdft2d_execute_static_scratch(const void *d_in, int64_t
     swdft_status st = scratch_address(&scratch);
     if (st != SWDFT_OK) return st;
 
-    float2 om0[kMaxN], om1[kMaxN];
-    make_omega(n0, om0);
-    make_omega(n1, om1);
+    float2 om64[kMaxN];
+    make_omega(kMaxN, om64);
     const double nn = (double)n0 * (double)n1;
     const float scale = norm == SWDFT_NORM_NONE ? 1.0f
                         : norm == SWDFT_NORM_INV_N ? (float)(1.0 / nn) : (float)(1.0 / std::sqrt(nn));
@@ -109,7 +108,7 @@ extern "C" swdft_status swdft2d_execute_static_scratch(const void *d_in, int64_t
         r.P1 = P1;
         r.m1 = m1;
         r.z = z;
-        r.om1 = om1;
+        r.om64 = om64;
         r.B = std::min(m1, 2);
         r.chunk = P1;
         if (launch_row_tree(r, s) != cudaSuccess) return SWDFT_ERR_CUDA;
@@ -121,7 +120,7 @@ extern "C" swdft_status swdft2d_execute_static_scratch(const void *d_in, int64_t
         c.m1 = m1;
         c.out = static_cast<float2 *>(d_out) + (size_t)q * out_row;
         c.scale = scale;
-        c.om0 = om0;
+        c.om64 = om64;
         c.B = std::min(m0, 2);
         c.chunk = rows_out;
         c.groups = 2;

@@ -17,6 +17,55 @@ constexpr int kMaxN = 1 << kMaxLog2;
 // Omega^i of Section 4.2 for length n (power of two), FP64-evaluated, FP32-rounded.
 void make_omega(int n, float2 *out);
 
+// Geometry of one row-level pass (see RowTreeArgs): z[r][q1][k1] for `rows` input rows.
+struct RowGeom {
+    const void *x;
+    int64_t ld;       // input row stride, elements
+    int64_t r_base;   // first input row
+    int64_t zrow;     // elements per z row (P1 * n1)
+    int rows;
+    int P1;
+    int chunk;        // window columns per thread
+    float2 *z;        // first (non-padding) z row
+};
+
+// Geometry of one column-level pass (see ColTreeArgs).
+struct ColGeom {
+    const float2 *z;  // first (non-padding) z row
+    float2 *out;
+    int64_t nch;      // channels = P1 * n1 = elements per z row
+    int64_t orow;     // elements per output row = P1 * n0 * n1
+    int rows_out;
+    int chunk;        // window rows per thread
+    int m1;
+    int groups;       // 32-channel groups per block
+    float scale;
+};
+
+// One array of a persistent batch launch.  Work items are numbered image by image:
+// row items [row_item0, row_item0 + row_blocks * row_chunks) and likewise for columns.
+struct BatchImage {
+    RowGeom row;
+    ColGeom col;
+    int m0, m1, cplx;
+    int row_blocks, row_chunks;  // row pass: blocks of (256 >> B) rows x chunks of columns
+    int col_blocks, col_chunks;  // column pass: blocks of 32 * groups channels x row chunks
+    int64_t row_item0, col_item0;
+};
+
+// Persistent launch over every (image, tile) of a batch: one pass over all row tiles, then
+// one over all column tiles (stream order separates them).  d_images: device copy of the
+// descriptors; each pass runs min(items, slots) blocks, slots = SMs x resident blocks
+// (batch_blocks_per_sm).  No other CUDA call than the two launches (capturable).
+cudaError_t launch_batch_tree(const BatchImage *d_images, int nimg, int64_t row_items,
+                              int64_t col_items, const float2 *om64, int64_t row_slots,
+                              int64_t col_slots, cudaStream_t s);
+cudaError_t batch_blocks_per_sm(int *row_bps, int *col_bps);
+// Launch choices the batch kernels use for a window side of 2^m.
+int batch_row_B(int m1);
+int batch_col_B(int m0);
+int batch_col_groups(int m0);
+
 // Row levels (Eq. rowfswft2d) of `rows` input rows starting at input row r_base:
 //   z[r][q1][k1] = sum_{j1<n1} x[r_base + r][q1 + j1] w_{n1}^{-j1 k1}   (unnormalised)
 // z is row-major rows x P1 x n1 complex64.
@@ -29,7 +78,7 @@ struct RowTreeArgs {
     int64_t P1 = 0;
     int m1 = 0;               // log2 n1
     float2 *z = nullptr;
-    const float2 *om1 = nullptr;  // host table, n1 entries (copied into kernel parameters)
+    const float2 *om64 = nullptr;  // host table w_64^{-j}, 64 entries (copied into kernel parameters)
     int B = 0;                // log2 of the threads sharing one row's butterflies
     int64_t chunk = 0;        // output positions per thread (plus n1-1 warm-up steps)
 };
@@ -43,7 +92,7 @@ struct ColTreeArgs {
     int m0 = 0, m1 = 0;
     float2 *out = nullptr;      // rows_out x P1 x n0 x n1
     float scale = 1.f;
-    const float2 *om0 = nullptr;
+    const float2 *om64 = nullptr;  // host table w_64^{-j}, 64 entries
     int B = 0;
     int64_t chunk = 0;          // output rows per thread (plus n0-1 warm-up steps)
     int groups = 1;             // 32-channel groups per block (block = 32 * 2^B * groups)
@@ -65,7 +114,7 @@ struct AdjColArgs {
     int64_t P1 = 0, rows_out = 0;
     int m0 = 0, m1 = 0;
     float scale = 1.f;
-    const float2 *om0 = nullptr;
+    const float2 *om64 = nullptr;  // host table w_64^{-j}, 64 entries
     int B = 0;
     int64_t chunk = 0;  // gz rows per thread (plus n0-1 warm-up steps)
 };
@@ -79,7 +128,7 @@ struct AdjRowArgs {
     int cplx = 0;
     int64_t zrows = 0, N1 = 0;
     int m1 = 0;
-    const float2 *om1 = nullptr;
+    const float2 *om64 = nullptr;  // host table w_64^{-j}, 64 entries
     int B = 0;
     int64_t chunk = 0;  // output columns per thread (plus n1-1 warm-up steps)
 };

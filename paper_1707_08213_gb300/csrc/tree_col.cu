@@ -38,21 +38,21 @@ cudaError_t launch_col_tree(const ColTreeArgs &a, cudaStream_t s) {
     if (a.m0 < 0 || a.m0 > kMaxLog2 || a.m1 < 0 || a.m1 > kMaxLog2 || a.rows_out > INT32_MAX)
         return cudaErrorInvalidValue;
     ColParams p;
-    p.z = a.z;
-    p.out = a.out;
-    p.nch = nch;
-    p.orow = nch << a.m0;
-    p.rows_out = (int)a.rows_out;
-    p.chunk = (int)std::min<int64_t>(a.chunk > 0 ? a.chunk : a.rows_out, a.rows_out);
-    p.m1 = a.m1;
-    p.scale = a.scale;
+    p.g.z = a.z;
+    p.g.out = a.out;
+    p.g.nch = nch;
+    p.g.orow = nch << a.m0;
+    p.g.rows_out = (int)a.rows_out;
+    p.g.chunk = (int)std::min<int64_t>(a.chunk > 0 ? a.chunk : a.rows_out, a.rows_out);
+    p.g.m1 = a.m1;
+    p.g.scale = a.scale;
     const int B = col_tree_clamp_B(a.m0, a.B);
     const int groups = col_tree_clamp_groups(a.m0, B, a.groups);
-    p.groups = groups;
-    for (int j = 0; j < (1 << a.m0); ++j) p.om[j] = a.om0[j];
+    p.g.groups = groups;
+    for (int j = 0; j < kMaxN; ++j) p.om.w[j] = a.om64[j];
     const int64_t per_block = 32LL * groups;
     dim3 grid((unsigned)((nch + per_block - 1) / per_block),
-              (unsigned)((a.rows_out + p.chunk - 1) / p.chunk));
+              (unsigned)((a.rows_out + p.g.chunk - 1) / p.g.chunk));
     if (grid.y > 65535) return cudaErrorInvalidValue;
     dim3 block(32 * (1 << B) * groups);
     switch (a.m0 * 8 + B) {

@@ -75,18 +75,20 @@ struct SlidingTree {
     float2 ring[kRing > 0 ? kRing : 1];
     float2 tw[kTw > 0 ? kTw : 1];
 
-    // c: this thread's residue (< 2^B); om: Omega of length 2^M, om[j] = w_{2^M}^{-j}.
-    __device__ __forceinline__ void init(int c, const float2 *om) {
+    // c: this thread's residue (< 2^B); om64: Omega of length 64, om64[j] = w_64^{-j}.
+    // W_v^i = w_{2^v}^{-i} = om64[i * 2^(6-v)], the same FP32 value as Omega^(2^M)[i * s_v].
+    __device__ __forceinline__ void init(int c, const float2 *om64) {
+        static_assert(M <= 6, "twiddle table covers windows up to 64");
         const int cb = c & ((1 << B) - 1);
 #pragma unroll
         for (int v = 1; v <= M; ++v) {
             const int base = tg_twoff(B, v);
             if (v <= B) {
                 const int i = c & ((1 << v) - 1);
-                tw[base] = om[i << (M - v)];
+                tw[base] = om64[i << (6 - v)];
             } else {
 #pragma unroll
-                for (int t = 0; t < tg_held(B, v - 1); ++t) tw[base + t] = om[(cb + (t << B)) << (M - v)];
+                for (int t = 0; t < tg_held(B, v - 1); ++t) tw[base + t] = om64[(cb + (t << B)) << (6 - v)];
             }
         }
 #pragma unroll

@@ -23,29 +23,19 @@
 
 namespace swdft {
 
+// w_64^{-j}, j < 64: the twiddles of every power-of-two length (kernel parameter).
+struct Omega64 {
+    float2 w[kMaxN];
+};
+
 struct RowParams {
-    const void *x;
-    int64_t ld;       // input row stride, elements
-    int64_t r_base;   // first input row
-    int64_t zrow;     // elements per z row (P1 * n1)
-    int rows;
-    int P1;
-    int chunk;        // output positions per thread
-    float2 *z;        // first (non-padding) z row
-    float2 om[kMaxN];
+    RowGeom g;
+    Omega64 om;
 };
 
 struct ColParams {
-    const float2 *z;  // first (non-padding) z row
-    float2 *out;
-    int64_t nch;      // channels = P1 * n1 = elements per z row
-    int64_t orow;     // elements per output row = P1 * n0 * n1
-    int rows_out;
-    int chunk;        // output rows per thread
-    int m1;
-    int groups;       // 32-channel groups per block
-    float scale;
-    float2 om[kMaxN];
+    ColGeom g;
+    Omega64 om;
 };
 
 template <bool CPLX>
@@ -57,16 +47,19 @@ __device__ __forceinline__ float2 load_x(const void *row, int64_t i) {
     }
 }
 
-// Thread = (row, residue c, chunk of output positions).  Lanes hold the residue in the low
-// B bits, then the row, so the 2^B threads of one row store adjacent k1 together.
+// Row pass, one block tile.  Thread = (row, residue c, chunk of window columns).  Lanes hold
+// the residue in the low B bits, then the row, so the 2^B threads of one row store adjacent
+// k1 together.  Tile (row_block, chunk_idx) covers rows row_block * (threads >> B) ... of the
+// pass and window columns [chunk_idx * chunk, ...).
 template <int M, int B, bool CPLX>
-__global__ void __launch_bounds__(128) row_tree_kernel(const RowParams p) {
+__device__ __forceinline__ void row_tile(const RowGeom &p, int row_block, int chunk_idx,
+                                         const float2 *om64) {
     using Tree = SlidingTree<M, B>;
     constexpr int n = 1 << M;
     const int c = threadIdx.x & ((1 << B) - 1);
-    const int row = blockIdx.x * (blockDim.x >> B) + (threadIdx.x >> B);
+    const int row = row_block * (blockDim.x >> B) + (threadIdx.x >> B);
     if (row >= p.rows) return;
-    const int qa = blockIdx.y * p.chunk;
+    const int qa = chunk_idx * p.chunk;
     if (qa >= p.P1) return;
     const int qb = min(qa + p.chunk, p.P1);
     const int steps = (qb - qa) + (n - 1);
@@ -76,7 +69,7 @@ __global__ void __launch_bounds__(128) row_tree_kernel(const RowParams p) {
     float2 *dst = p.z + (int64_t)row * p.zrow + (int64_t)qa * n + c;
 
     Tree tree;
-    tree.init(c, p.om);
+    tree.init(c, om64);
     for (int jb = 0; jb < steps; jb += Tree::kPeriod) {
         static_for<0, Tree::kPeriod>([&](auto JJ) {
             constexpr int J = decltype(JJ)::value;
@@ -98,6 +91,11 @@ __global__ void __launch_bounds__(128) row_tree_kernel(const RowParams p) {
     }
 }
 
+template <int M, int B, bool CPLX>
+__global__ void __launch_bounds__(128) row_tree_kernel(const __grid_constant__ RowParams p) {
+    row_tile<M, B, CPLX>(p.g, blockIdx.x, blockIdx.y, p.om.w);
+}
+
 // Rows of z staged in shared memory per column-pass block: a ring that holds the level-0
 // look-back (n/2 rows) plus two step groups (the group being computed and the one being
 // fetched), rounded up to a power of two.
@@ -117,35 +115,36 @@ __device__ __forceinline__ void cp_async_8(void *smem, const void *gmem, bool va
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// Thread = (channel ch = q1*n1 + k1, residue c, chunk of output rows).  Warp w of a block
-// takes residue w mod 2^B (uniform per warp) and channel group w / 2^B.  The block's z rows
-// arrive in a shared-memory ring by cp.async one step group ahead of use; all residue warps
-// read the same staged rows.  One __syncthreads per step group, no spin-waits.
+// Column pass, one block tile.  Thread = (channel ch = q1*n1 + k1, residue c, chunk of
+// window rows).  Warp w of a block takes residue w mod 2^B (uniform per warp) and channel
+// group w / 2^B.  The tile's z rows arrive in a shared-memory ring by cp.async one step group
+// ahead of use; all residue warps read the same staged rows.  One __syncthreads per step
+// group, no spin-waits; the tile ends with a barrier, so the ring is free for the next tile.
 template <int M, int B>
-__global__ void __launch_bounds__(256, 2) col_tree_kernel(const ColParams p) {
+__device__ __forceinline__ void col_tile(const ColGeom &p, int64_t ch_block, int chunk_idx,
+                                         const float2 *om64, float2 *ring) {
     using Tree = SlidingTree<M, B>;
     constexpr int R = 1 << B;
     constexpr int n = 1 << M;
     constexpr int kP = Tree::kPeriod;
     constexpr int kH = Tree::kHalf;
     constexpr int RD = col_ring_rows(M);
-    extern __shared__ float2 ring[];  // RD x (32 * groups)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int c = warp & (R - 1);
-    const int CH = 32 * p.groups;                       // channels of this block
-    const int my = (warp >> B) * 32 + lane;             // this thread's channel in the block
-    const int64_t ch0 = (int64_t)blockIdx.x * CH;
+    const int CH = 32 * p.groups;                       // channels of this tile
+    const int my = (warp >> B) * 32 + lane;             // this thread's channel in the tile
+    const int64_t ch0 = ch_block * CH;
     const int64_t ch = ch0 + my;
-    const int qa = blockIdx.y * p.chunk;
+    const int qa = chunk_idx * p.chunk;
     if (qa >= p.rows_out) return;                       // uniform per block
     const int qb = min(qa + p.chunk, p.rows_out);
     const int steps = (qb - qa) + (n - 1);
     const int zr_end = qb + n - 1;                      // one past the last z row used
     const bool active = ch < p.nch;
 
-    // stage z rows [r_lo, r_hi) of this block's channels into the ring
+    // stage z rows [r_lo, r_hi) of this tile's channels into the ring
     auto fetch = [&](int r_lo, int r_hi) {
         r_hi = min(r_hi, zr_end);
         const int total = (r_hi - r_lo) * CH;
@@ -167,7 +166,7 @@ __global__ void __launch_bounds__(256, 2) col_tree_kernel(const ColParams p) {
     const float s = p.scale;
 
     Tree tree;
-    tree.init(c, p.om);
+    tree.init(c, om64);
     fetch(qa - kH, qa + kP);
     cp_async_wait_all();
     __syncthreads();
@@ -195,6 +194,12 @@ __global__ void __launch_bounds__(256, 2) col_tree_kernel(const ColParams p) {
 }
 
 template <int M, int B>
+__global__ void __launch_bounds__(256, 2) col_tree_kernel(const __grid_constant__ ColParams p) {
+    extern __shared__ float2 ring[];  // col_ring_rows(M) x (32 * groups)
+    col_tile<M, B>(p.g, blockIdx.x, blockIdx.y, p.om.w, ring);
+}
+
+template <int M, int B>
 void row_launch_mb(const RowParams &p, int cplx, dim3 g, dim3 b, cudaStream_t s);
 template <int M, int B>
 void col_launch_mb(const ColParams &p, dim3 g, dim3 b, cudaStream_t s);
@@ -213,7 +218,7 @@ int col_blocks_per_sm(int threads, int groups);
 #define SWDFT_COL_INSTANTIATE(M_, B_)                                                     \
     template <>                                                                           \
     void col_launch_mb<M_, B_>(const ColParams &p, dim3 g, dim3 b, cudaStream_t s) {      \
-        const size_t smem = sizeof(float2) * col_ring_rows(M_) * 32 * p.groups;          \
+        const size_t smem = sizeof(float2) * col_ring_rows(M_) * 32 * p.g.groups;          \
         col_tree_kernel<M_, B_><<<g, b, smem, s>>>(p);                                    \
     }                                                                                     \
     template <>                                                                           \

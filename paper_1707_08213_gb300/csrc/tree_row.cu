@@ -11,21 +11,21 @@ cudaError_t launch_row_tree(const RowTreeArgs &a, cudaStream_t s) {
     if (a.rows <= 0 || a.P1 <= 0) return cudaSuccess;
     if (a.m1 < 0 || a.m1 > kMaxLog2 || a.rows > INT32_MAX || a.P1 > INT32_MAX) return cudaErrorInvalidValue;
     RowParams p;
-    p.x = a.x;
-    p.ld = a.ld;
-    p.r_base = a.r_base;
-    p.zrow = a.P1 << a.m1;
-    p.rows = (int)a.rows;
-    p.P1 = (int)a.P1;
-    p.chunk = (int)std::min<int64_t>(a.chunk > 0 ? a.chunk : a.P1, a.P1);
-    p.z = a.z;
-    for (int j = 0; j < (1 << a.m1); ++j) p.om[j] = a.om1[j];
+    p.g.x = a.x;
+    p.g.ld = a.ld;
+    p.g.r_base = a.r_base;
+    p.g.zrow = a.P1 << a.m1;
+    p.g.rows = (int)a.rows;
+    p.g.P1 = (int)a.P1;
+    p.g.chunk = (int)std::min<int64_t>(a.chunk > 0 ? a.chunk : a.P1, a.P1);
+    p.g.z = a.z;
+    for (int j = 0; j < kMaxN; ++j) p.om.w[j] = a.om64[j];
     int B = a.B < 0 ? 0 : a.B;
     B = std::min(B, std::min(a.m1, 3));
     const int threads = 128;
     const int rows_per_block = threads >> B;
     dim3 grid((unsigned)((a.rows + rows_per_block - 1) / rows_per_block),
-              (unsigned)((a.P1 + p.chunk - 1) / p.chunk));
+              (unsigned)((a.P1 + p.g.chunk - 1) / p.g.chunk));
     if (grid.y > 65535) return cudaErrorInvalidValue;
     dim3 block(threads);
     switch (a.m1 * 8 + B) {
