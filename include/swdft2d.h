@@ -108,7 +108,8 @@ typedef struct {
  * validates every shape (SWDFT_ERR_NOT_POW2 / WINDOW_TOO_LARGE / INVALID_ARG), builds the
  * twiddle vectors Omega^0, Omega^1 of Section 4.2 in FP64 and rounds them to FP32, and
  * picks kernels.  SWDFT_ERR_UNSUPPORTED for an algorithm or window size this build lacks
- * (tree: n_i <= 64).  *plan is NULL on any error. */
+ * (tree: n_i <= 64; tensor-core forms: 16 <= n0 <= 64, 8 <= n1 <= 64, no persistent batch).
+ * *plan is NULL on any error. */
 swdft_status swdft2d_plan(swdft2d_plan_t *plan, int32_t batch, const swdft2d_shape *shapes,
                           int32_t norm, int32_t pos, int32_t algo, uint32_t flags);
 
@@ -187,6 +188,12 @@ swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t 
 swdft_status swdft2d_execute_static_scratch(const void *d_in, int64_t N0, int64_t N1, int64_t ld,
                                             int32_t n0, int32_t n1, int32_t dtype, int32_t norm,
                                             void *d_out, void *stream);
+
+/* Device-side health of the current device: SWDFT_ERR_DEVICE_TIMEOUT if, since the last
+ * call, a tensor-core kernel gave up on one of its bounded waits (its outputs are then
+ * incomplete); SWDFT_OK otherwise.  Reads and resets the library's device status word
+ * (synchronous copy).  SWDFT_ERR_CUDA if the read fails. */
+swdft_status swdft2d_check_device(void);
 
 /* Free the plan and everything it owns.  NULL is accepted. */
 swdft_status swdft2d_destroy(swdft2d_plan_t plan);

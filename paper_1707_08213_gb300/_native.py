@@ -37,6 +37,7 @@ EXPORTS = (
     "swdft2d_execute", "swdft2d_execute_adjoint", "swdft2d_execute_host", "swdft2d_autotune",
     "swdft2d_launch_count", "swdft2d_destroy", "swdft2d_status_string", "swdft2d_version",
     "swdft2d_execute_stage", "swdft2d_set_tree_config", "swdft2d_execute_static_scratch",
+    "swdft2d_check_device",
 )
 
 
@@ -73,6 +74,7 @@ def _load() -> ctypes.CDLL:
         "swdft2d_execute_stage": ([P, i32, PP, PP, P, P], i32),
         "swdft2d_set_tree_config": ([P, i32, i32, i64, i32, i64, i32], i32),
         "swdft2d_execute_static_scratch": ([P, i64, i64, i64, i32, i32, i32, i32, P, P], i32),
+        "swdft2d_check_device": ([], i32),
         "swdft2d_destroy": ([P], i32),
         "swdft2d_status_string": ([i32], ctypes.c_char_p),
         "swdft2d_version": ([], i32),
@@ -190,6 +192,11 @@ class Plan:
             self.destroy()
         except Exception:
             pass
+
+
+def check_device() -> int:
+    """SWDFT_OK, or ERR_DEVICE_TIMEOUT if a bounded device wait gave up since the last call."""
+    return int(lib.swdft2d_check_device())
 
 
 def version() -> int:

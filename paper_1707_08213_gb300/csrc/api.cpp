@@ -43,6 +43,8 @@ struct ArrayPlan {
     int64_t q_begin = 0, q_end = 0;  // band of window rows, q coordinates
     TreeConfig cfg;
     bool tuned = false;
+    int algo = SWDFT_ALGO_TREE_F32;  // per array: tree or one of the tensor-core forms
+    int64_t tc_chunk = 48;           // window rows per tensor-core CTA
 
     int64_t band_rows() const { return q_end - q_begin; }
     size_t in_elem() const { return dtype == SWDFT_C64 ? sizeof(float2) : sizeof(float); }
@@ -51,6 +53,17 @@ struct ArrayPlan {
     int64_t z_pad() const { return n0 / 2; }
     size_t z_bytes(int64_t rows_out) const {
         return (size_t)(z_pad() + rows_out + n0 - 1) * (size_t)P1 * n1 * sizeof(float2);
+    }
+    // tensor-core forms: 16-bit operand planes of z after the z buffer, then a max-abs word
+    bool tc_eligible() const { return m0 >= 4 && m0 <= 6 && m1 >= 3 && m1 <= 6; }
+    static int tc_terms(int algo) { return algo == SWDFT_ALGO_TC_BF16X3 ? 3 : 1; }
+    size_t planes_bytes(int64_t rows_out, int algo) const {
+        return (size_t)tc_terms(algo) * 2 * (size_t)(rows_out + n0 - 1) * (size_t)P1 * n1 * 2;
+    }
+    size_t ws_bytes_for(int64_t rows_out, int algo) const {
+        size_t b = align_up(z_bytes(rows_out));
+        if (algo >= SWDFT_ALGO_TC_BF16X3) b += align_up(planes_bytes(rows_out, algo)) + kAlign;
+        return b;
     }
 };
 
@@ -244,6 +257,30 @@ cudaError_t enqueue_forward(const swdft2d_plan_s *plan, const ArrayPlan &a, cons
         if (e != cudaSuccess) return e;
     }
     if (!(stages & 2)) return cudaSuccess;
+    if (a.algo >= SWDFT_ALGO_TC_BF16X3) {
+        const int terms = ArrayPlan::tc_terms(a.algo);
+        const bool f16 = a.algo == SWDFT_ALGO_TC_F16 || a.algo == SWDFT_ALGO_TC_F16_SCALED;
+        char *planes = static_cast<char *>(ws) + align_up(a.z_bytes(rows_out));
+        float *amax = reinterpret_cast<float *>(planes + align_up(a.planes_bytes(rows_out, a.algo)));
+        const bool scaled = a.algo == SWDFT_ALGO_TC_F16_SCALED;
+        cudaError_t e = launch_z_to_planes(z, planes, (rows_out + a.n0 - 1) * a.P1 * a.n1, terms, f16,
+                                           scaled ? amax : nullptr, s);
+        if (e != cudaSuccess) return e;
+        TcColArgs t;
+        t.planes = planes;
+        t.terms = terms;
+        t.f16 = f16;
+        t.amax = scaled ? amax : nullptr;
+        t.P1 = a.P1;
+        t.rows_out = rows_out;
+        t.m0 = a.m0;
+        t.m1 = a.m1;
+        t.out = static_cast<float2 *>(out);
+        t.scale = norm_scale(plan->norm, a.n0, a.n1);
+        t.om64 = plan->om64;
+        t.chunk = a.tc_chunk;
+        return launch_tc_col(t, s);
+    }
     ColTreeArgs c;
     c.z = z;
     c.P1 = a.P1;
@@ -355,15 +392,17 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
             if (a.q_begin < 0 || a.q_end > a.P0 || a.q_begin >= a.q_end) return SWDFT_ERR_INVALID_ARG;
         }
         if (m0 > kMaxLog2 || m1 > kMaxLog2) return SWDFT_ERR_UNSUPPORTED;
+        a.algo = (algo == SWDFT_ALGO_AUTO) ? SWDFT_ALGO_TREE_F32 : algo;
+        if (a.algo >= SWDFT_ALGO_TC_BF16X3 && !a.tc_eligible()) return SWDFT_ERR_UNSUPPORTED;
     }
-    if (algo != SWDFT_ALGO_AUTO && algo != SWDFT_ALGO_TREE_F32) return SWDFT_ERR_UNSUPPORTED;
+    if (algo >= SWDFT_ALGO_TC_BF16X3 && (flags & SWDFT_FLAG_PERSISTENT)) return SWDFT_ERR_UNSUPPORTED;
 
     swdft2d_plan_s *p = new (std::nothrow) swdft2d_plan_s();
     if (!p) return SWDFT_ERR_OOM;
     p->arrays = std::move(arrays);
     p->norm = norm;
     p->pos = pos;
-    p->algo = SWDFT_ALGO_TREE_F32;
+    p->algo = (algo == SWDFT_ALGO_AUTO) ? SWDFT_ALGO_TREE_F32 : algo;
     p->flags = flags;
     make_omega(kMaxN, p->om64);
     size_t ws = 0;
@@ -375,7 +414,7 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
         }
     } else {
         // arrays run one after another on one stream, so they share one z buffer
-        for (const auto &a : p->arrays) ws = std::max(ws, align_up(a.z_bytes(a.band_rows())));
+        for (const auto &a : p->arrays) ws = std::max(ws, align_up(a.ws_bytes_for(a.band_rows(), a.algo)));
     }
     p->ws_bytes = ws;
     *out = p;
@@ -575,7 +614,7 @@ swdft_status swdft2d_execute_host(swdft2d_plan_t plan, const void *const *h_in,
             const int64_t br = std::min(band, a.band_rows());
             in_max = std::max(in_max, align_up((size_t)a.N0 * a.ld * a.in_elem()));
             out_max = std::max(out_max, align_up((size_t)br * a.out_row_bytes()));
-            ws_max = std::max(ws_max, align_up(a.z_bytes(br)));
+            ws_max = std::max(ws_max, align_up(a.ws_bytes_for(br, a.algo)));
         }
         if (cudaMalloc(&plan->io_in, in_max) != cudaSuccess) return SWDFT_ERR_OOM;
         if (cudaMalloc(&plan->io_ws, ws_max) != cudaSuccess) return SWDFT_ERR_OOM;
@@ -712,6 +751,12 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
     cudaEventDestroy(e1);
     destroy_graph(plan->graph);
     return SWDFT_OK;
+}
+
+swdft_status swdft2d_check_device(void) {
+    int status = 0;
+    if (tc_status(&status, true) != cudaSuccess) return SWDFT_ERR_CUDA;
+    return status ? SWDFT_ERR_DEVICE_TIMEOUT : SWDFT_OK;
 }
 
 swdft_status swdft2d_destroy(swdft2d_plan_t plan) {

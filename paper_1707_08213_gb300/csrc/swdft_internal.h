@@ -53,6 +53,30 @@ struct BatchImage {
     int64_t row_item0, col_item0;
 };
 
+// Tensor-core column levels: out[q0][q1][k0][k1] = scale * sum_j0 z[q0+j0][ch] F0[j0][k0]
+// from 16-bit operand planes of z ([plane][rows_out + n0 - 1][P1*n1]; planes Re hi, Im hi,
+// Re lo, Im lo for terms = 3, Re, Im for terms = 1).  n0, n1 in [8, 64].
+struct TcColArgs {
+    void *planes = nullptr;
+    int terms = 3;
+    bool f16 = false;
+    const float *amax = nullptr;  // per-image fp16 scaling (see launch_z_to_planes)
+    int64_t P1 = 0, rows_out = 0;
+    int m0 = 0, m1 = 0;
+    float2 *out = nullptr;
+    float scale = 1.f;
+    const float2 *om64 = nullptr;
+    int64_t chunk = 0;  // window rows per CTA
+};
+cudaError_t launch_tc_col(const TcColArgs &a, cudaStream_t s);
+// z (n complex64) -> operand planes; amax (device float, or null) enables the per-image
+// power-of-two fp16 scale, computed on the device from max |Re|, |Im|.
+cudaError_t launch_z_to_planes(const float2 *z, void *planes, int64_t n, int terms, bool f16, float *amax,
+                               cudaStream_t s);
+size_t tc_col_smem_bytes(int m0, int terms, int chunk);
+// Device error word of the tensor-core kernels (1 = a bounded wait timed out).
+cudaError_t tc_status(int *status, bool reset);
+
 // Persistent launch over every (image, tile) of a batch: one pass over all row tiles, then
 // one over all column tiles (stream order separates them).  d_images: device copy of the
 // descriptors; each pass runs min(items, slots) blocks, slots = SMs x resident blocks

@@ -1,0 +1,383 @@
+// Dense-contraction form of the 2D sliding window DFT on tcgen05 tensor cores.
+//
+// The row-column factorisation of Section 4.2 writes every window's 2D DFT as a row DFT
+// followed by a column DFT.  Here the column DFT is a matrix product against the n0-point
+// DFT matrix F0[j0][k0] = w_{n0}^{-j0 k0}, one product per window row q0 and block of 128
+// channels (channel = (q1, k1), the columns of z):
+//
+//     a[q0][ch][k0] = c * sum_{j0} z[q0 + j0][ch] * F0[j0][k0]
+//
+// realified as D (128 x 2n0) = A (128 x 2n0) * B (2n0 x 2n0) with A = [Re z | Im z] and
+// B = [[C, -S], [S, C]] (C = cos, S = sin of 2 pi j0 k0 / n0).  A is MN-major in shared
+// memory: channels are contiguous in z, and the n0 rows a window needs are consecutive
+// 16-byte rows of the staged tile, so sliding the window by one row moves the descriptor
+// start by 16 bytes -- every window row of the CTA's chunk reuses one TMA-loaded tile.
+//
+// Precision: operands are bf16 (or fp16) with fp32 accumulation in TMEM.  The 3-term split
+// keeps v = hi + lo (hi = bf16(v), lo = bf16(v - hi)) for both z and F0 and accumulates
+// hi*hi + hi*lo + lo*hi, dropping only lo*lo (~2^-16 relative per product).
+//
+// One CTA = 128 threads = the 128 TMEM lanes = 128 channels.  Thread 0 issues the TMA loads
+// and the UMMAs; every wait on an mbarrier is bounded and a time-out sets an error word and
+// skips ahead to the TMEM release.  The epilogue reads D with tcgen05.ld and each thread
+// stores its channel's n0 coefficients: for fixed k0 a warp writes 32 consecutive channels
+// (256 contiguous bytes), the same pattern as the tree kernel.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "sm100_ptx.cuh"
+#include "swdft_internal.h"
+
+namespace swdft {
+
+__device__ int g_tc_status;  // 0 = ok; 1 = an mbarrier wait timed out
+
+constexpr int TC_CH = 128;      // channels per CTA = UMMA M = TMEM lanes
+constexpr int TC_THREADS = 128;
+constexpr uint32_t TC_MAX_POLLS = 4000;  // x up to ~1 ms per poll
+
+struct TcColParams {
+    CUtensorMap planes[4];  // z operand planes: Re hi, Im hi, Re lo, Im lo (2D [rows][nch])
+    float2 *out;
+    int64_t nch;            // channels = P1 * n1
+    int64_t orow;           // output elements per window row
+    int rows_out;           // window rows
+    int chunk;              // window rows per CTA
+    int rz;                 // staged rows per plane (chunk + n0 - 1, rounded up to 8)
+    int m1;
+    float scale;
+    const float *amax;      // per-image fp16 scaling: max |Re|,|Im| of z (null: no scaling)
+    float2 om64[kMaxN];
+};
+
+// Power-of-two scale that brings the largest |value| of an array to [2^13, 2^14): fp16 then
+// keeps its full 11-bit precision without overflow (max 65504).
+__device__ __forceinline__ float fp16_prescale(const float *amax) {
+    if (!amax) return 1.f;
+    const float m = *amax;
+    if (!(m > 0.f) || !isfinite(m)) return 1.f;
+    int e;
+    frexpf(m, &e);              // m = f * 2^e, f in [0.5, 1)
+    return ldexpf(1.f, 14 - e);
+}
+
+__global__ void __launch_bounds__(256) amax_kernel(const float2 *__restrict__ z, int64_t n, float *amax) {
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = z[i];
+        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(amax), __float_as_int(m));
+}
+
+template <bool F16>
+__device__ __forceinline__ uint16_t to_bits(float v) {
+    if constexpr (F16) {
+        __half h = __float2half_rn(v);
+        return *reinterpret_cast<uint16_t *>(&h);
+    } else {
+        __nv_bfloat16 h = __float2bfloat16_rn(v);
+        return *reinterpret_cast<uint16_t *>(&h);
+    }
+}
+template <bool F16>
+__device__ __forceinline__ float from_bits(uint16_t b) {
+    if constexpr (F16) {
+        return __half2float(*reinterpret_cast<__half *>(&b));
+    } else {
+        return __bfloat162float(*reinterpret_cast<__nv_bfloat16 *>(&b));
+    }
+}
+
+// z (complex64, rows x nch) -> operand planes (16-bit, [plane][rows][nch]).
+// terms = 3: Re hi, Im hi, Re lo, Im lo; terms = 1: Re, Im.  With amax (per-image fp16
+// scaling) values are first multiplied by the power of two fp16_prescale(amax).
+template <bool F16>
+__global__ void __launch_bounds__(256) z_to_planes_kernel(const float2 *__restrict__ z, uint16_t *__restrict__ planes,
+                                                          int64_t n, int terms, const float *amax) {
+    const float prescale = fp16_prescale(amax);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = z[i];
+        const float re = v.x * prescale, im = v.y * prescale;
+        const uint16_t rh = to_bits<F16>(re), ih = to_bits<F16>(im);
+        planes[i] = rh;
+        planes[n + i] = ih;
+        if (terms == 3) {
+            planes[2 * n + i] = to_bits<F16>(re - from_bits<F16>(rh));
+            planes[3 * n + i] = to_bits<F16>(im - from_bits<F16>(ih));
+        }
+    }
+}
+
+// Byte offset of element (n, k) in a K-major, no-swizzle operand of K columns: 8x8 core
+// matrices of 128 bytes, K-adjacent core matrices 128 B apart, 8-row groups K*16 B apart.
+__device__ __forceinline__ uint32_t kmajor_off(int n, int k, int K) {
+    return (uint32_t)(((n >> 3) * (K >> 3) + (k >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2);
+}
+
+template <int M0, int TERMS, bool F16>
+__global__ void __launch_bounds__(TC_THREADS) tc_col_kernel(const __grid_constant__ TcColParams p) {
+    constexpr int n0 = 1 << M0;
+    constexpr int K = 2 * n0;   // realified contraction length
+    constexpr int N = 2 * n0;   // realified output columns (Re k0 | Im k0)
+    constexpr int KS = K / 16;  // UMMA k-steps per term
+    constexpr int NB = TERMS == 3 ? 2 : 1;       // B tiles (hi, lo)
+    constexpr int NP = TERMS == 3 ? 4 : 2;       // A planes
+    constexpr uint32_t TMEM_COLS = (2 * N) < 32 ? 32 : 2 * N;  // two accumulator buffers
+    constexpr uint32_t B_BYTES = N * K * 2;
+    constexpr uint32_t IDESC = umma_idesc_f16(TC_CH, N, !F16, /*a_mn=*/true, /*b_mn=*/false);
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned base (the launch requests 1 KB of slack)
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int rz = p.rz;
+    const uint32_t plane_bytes = (uint32_t)(16 * rz * 16);  // 16 chunks x rz rows x 16 B
+    unsigned char *sB = smem;                              // NB x B_BYTES
+    unsigned char *sA = smem + NB * B_BYTES;               // NP x plane_bytes
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sA + NP * plane_bytes);  // load, mma
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int64_t ch0 = (int64_t)blockIdx.x * TC_CH;
+    const int qa = blockIdx.y * p.chunk;
+    if (qa >= p.rows_out) return;  // uniform per block
+    const int qb = min(qa + p.chunk, p.rows_out);
+
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, TMEM_COLS);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_barrier_init();
+    }
+    // B = realified F0 (K-major): rows n (Re k0 | Im k0), columns k (Re j0 | Im j0)
+    for (int e = tid; e < N * K; e += TC_THREADS) {
+        const int n = e / K, k = e - (e / K) * K;
+        const int k0 = n & (n0 - 1), j0 = k & (n0 - 1);
+        const float2 w = p.om64[((j0 * k0) & (n0 - 1)) << (6 - M0)];  // (C, -S)
+        const bool out_im = n >= n0, in_im = k >= n0;
+        const float v = (out_im == in_im) ? w.x : (in_im ? -w.y : w.y);
+        const uint16_t hi = to_bits<F16>(v);
+        const uint32_t off = kmajor_off(n, k, K);
+        *reinterpret_cast<uint16_t *>(sB + off) = hi;
+        if (NB == 2) *reinterpret_cast<uint16_t *>(sB + B_BYTES + off) = to_bits<F16>(v - from_bits<F16>(hi));
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    bool ok = true;
+    if (tid == 0) {
+        mbar_expect_tx(&bars[0], NP * plane_bytes);
+        for (int pl = 0; pl < NP; ++pl)
+            for (int c = 0; c < 16; ++c)
+                tma_load_2d(sA + pl * plane_bytes + c * rz * 16, &p.planes[pl], &bars[0], (int)(ch0 + 8 * c), qa);
+    }
+    ok = __syncthreads_and(mbar_wait(&bars[0], 0, TC_MAX_POLLS));  // block-uniform
+
+    const int n1 = 1 << p.m1;
+    const int64_t ch = ch0 + warp * 32 + lane;
+    const bool active = ch < p.nch;
+    const int64_t q1 = ch >> p.m1, k1 = ch & (n1 - 1);
+    float2 *dst = p.out + (int64_t)qa * p.orow + q1 * ((int64_t)n0 * n1) + k1;
+    const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
+    static_assert(n0 >= 16, "each 16-row k-step must lie in one plane");
+    const uint32_t a_lbo = 128u;  // K-group stride of A: consecutive 16-byte rows
+    const uint32_t a_sbo = (uint32_t)rz * 16u;
+    const uint32_t b_lbo = 128u, b_sbo = (uint32_t)(K / 8) * 128u;
+    const float out_scale = p.scale / fp16_prescale(p.amax);
+
+    for (int q0 = qa; q0 < qb && ok; ++q0) {
+        const int i = q0 - qa;
+        const uint32_t d_tmem = tmem + (uint32_t)((i & 1) * N);
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int t = 0; t < TERMS; ++t) {
+                const int a_set = (t == 2) ? 1 : 0;  // A lo only in the third term
+                const int b_set = (t == 1) ? 1 : 0;  // B lo only in the second term
+#pragma unroll
+                for (int ks = 0; ks < KS; ++ks) {
+                    const int kk = ks * 16;
+                    const int part = kk / n0;  // 0: Re rows, 1: Im rows
+                    const int row = i + kk % n0;
+                    const uint32_t a_addr = sA0 + (uint32_t)((2 * a_set + part) * plane_bytes + row * 16);
+                    const uint32_t b_addr = sB0 + (uint32_t)(b_set * B_BYTES + ks * 2 * 128);
+                    umma_f16(d_tmem, smem_desc(a_addr, a_lbo, a_sbo), smem_desc(b_addr, b_lbo, b_sbo), IDESC,
+                             (t | ks) != 0);
+                }
+            }
+            umma_commit(&bars[1]);
+        }
+        const bool done = mbar_wait(&bars[1], (uint32_t)(i & 1), TC_MAX_POLLS);
+        tc_fence_after();
+        // epilogue: this thread's TMEM lane = its channel; columns [0, n0) Re, [n0, 2n0) Im
+        const uint32_t lane_addr = d_tmem + ((uint32_t)(warp * 32) << 16);
+        float acc[N];
+#pragma unroll
+        for (int c = 0; c < N; c += 16) {
+            float v[16];
+            tmem_ld_16(lane_addr + c, v);
+            tmem_ld_wait();
+#pragma unroll
+            for (int u = 0; u < 16; ++u) acc[c + u] = v[u];
+        }
+        tc_fence_before();
+        // every lane has read this buffer before it is written again; the vote keeps the
+        // loop exit block-uniform
+        ok = __syncthreads_and(done);
+        if (active && ok) {
+#pragma unroll
+            for (int k0 = 0; k0 < n0; ++k0)
+                __stcs(dst + (int64_t)k0 * n1, make_float2(out_scale * acc[k0], out_scale * acc[n0 + k0]));
+        }
+        dst += p.orow;
+    }
+    if (!ok) {
+        // a wait timed out: record it, give in-flight copies and products a last bounded
+        // chance to land, then release TMEM
+        if (tid == 0) atomicExch(&g_tc_status, 1);
+        mbar_wait(&bars[0], 0, 64);
+        mbar_wait(&bars[1], 0, 64);
+        mbar_wait(&bars[1], 1, 64);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+size_t tc_col_smem_bytes(int m0, int terms, int chunk) {
+    const int n0 = 1 << m0;
+    const int rz = ((chunk + n0 - 1) + 7) / 8 * 8;
+    const int nb = terms == 3 ? 2 : 1, np = terms == 3 ? 4 : 2;
+    // + barriers, + 1 KB alignment slack, + 8 KB guard band after the staged tiles
+    return (size_t)nb * (2 * n0) * (2 * n0) * 2 + (size_t)np * 16 * rz * 16 + 64 + 1024 + 8192;
+}
+
+int tc_col_max_chunk(int m0) { return 256 - (1 << m0) + 1 - 7; }
+
+cudaError_t launch_z_to_planes(const float2 *z, void *planes, int64_t n, int terms, bool f16, float *amax,
+                               cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>((n + threads - 1) / threads, 152 * 16);
+    if (amax) {
+        cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(float), s);
+        if (e != cudaSuccess) return e;
+        amax_kernel<<<(unsigned)blocks, threads, 0, s>>>(z, n, amax);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (f16)
+        z_to_planes_kernel<true><<<(unsigned)blocks, threads, 0, s>>>(z, (uint16_t *)planes, n, terms, amax);
+    else
+        z_to_planes_kernel<false><<<(unsigned)blocks, threads, 0, s>>>(z, (uint16_t *)planes, n, terms, amax);
+    return cudaGetLastError();
+}
+
+template <int M0, int TERMS, bool F16>
+static cudaError_t launch_tc_col_t(const TcColParams &p, dim3 grid, size_t smem, cudaStream_t s) {
+    auto k = tc_col_kernel<M0, TERMS, F16>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, TC_THREADS, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_col(const TcColArgs &a, cudaStream_t s) {
+    if (a.rows_out <= 0) return cudaSuccess;
+    if (a.m0 < 4 || a.m0 > kMaxLog2 || a.m1 < 3 || a.m1 > kMaxLog2) return cudaErrorInvalidValue;
+    if (a.terms != 1 && a.terms != 3) return cudaErrorInvalidValue;
+    const int n0 = 1 << a.m0;
+    const int64_t nch = a.P1 << a.m1;
+    const int64_t zrows = a.rows_out + n0 - 1;
+    const int chunk = (int)std::min<int64_t>(std::min<int64_t>(a.chunk > 0 ? a.chunk : 64, a.rows_out),
+                                             tc_col_max_chunk(a.m0));
+    const int rz = ((chunk + n0 - 1) + 7) / 8 * 8;
+    if (nch % 8 != 0 || zrows > INT32_MAX || (uintptr_t)a.planes % 16 != 0) return cudaErrorInvalidValue;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    TcColParams p;
+    std::memset(&p, 0, sizeof(p));
+    const int np = a.terms == 3 ? 4 : 2;
+    for (int pl = 0; pl < np; ++pl) {
+        cuuint64_t dims[2] = {(cuuint64_t)nch, (cuuint64_t)zrows};
+        cuuint64_t strides[1] = {(cuuint64_t)nch * 2};
+        cuuint32_t box[2] = {8, (cuuint32_t)rz};
+        cuuint32_t estr[2] = {1, 1};
+        void *base = static_cast<char *>(a.planes) + (size_t)pl * nch * zrows * 2;
+        CUresult r = enc(&p.planes[pl], a.f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                         base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    p.out = a.out;
+    p.nch = nch;
+    p.orow = nch << a.m0;
+    p.rows_out = (int)a.rows_out;
+    p.chunk = chunk;
+    p.rz = rz;
+    p.m1 = a.m1;
+    p.scale = a.scale;
+    p.amax = a.amax;
+    for (int j = 0; j < kMaxN; ++j) p.om64[j] = a.om64[j];
+    const size_t smem = tc_col_smem_bytes(a.m0, a.terms, chunk);
+    dim3 grid((unsigned)((nch + TC_CH - 1) / TC_CH), (unsigned)((a.rows_out + chunk - 1) / chunk));
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+#define TC_CASE(M_)                                                                                 \
+    case M_:                                                                                        \
+        if (a.f16) return launch_tc_col_t<M_, 1, true>(p, grid, smem, s);                           \
+        return a.terms == 3 ? launch_tc_col_t<M_, 3, false>(p, grid, smem, s)                       \
+                            : launch_tc_col_t<M_, 1, false>(p, grid, smem, s);
+    switch (a.m0) {
+        TC_CASE(4)
+        TC_CASE(5)
+        TC_CASE(6)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef TC_CASE
+}
+
+cudaError_t tc_status(int *status, bool reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(status, g_tc_status, sizeof(int));
+    if (e == cudaSuccess && reset) {
+        const int zero = 0;
+        e = cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(int));
+    }
+    return e;
+}
+
+}  // namespace swdft
