@@ -198,46 +198,53 @@ __global__ void __launch_bounds__(TC_THREADS) tc_col_kernel(const __grid_constan
     const uint32_t b_lbo = 128u, b_sbo = (uint32_t)(K / 8) * 128u;
     const float out_scale = p.scale / fp16_prescale(p.amax);
 
-    for (int q0 = qa; q0 < qb && ok; ++q0) {
-        const int i = q0 - qa;
+    // issue all UMMAs of window row i into TMEM buffer i & 1, then commit
+    auto issue = [&](int i) {
         const uint32_t d_tmem = tmem + (uint32_t)((i & 1) * N);
-        if (tid == 0) {
-            tc_fence_after();
-#pragma unroll
-            for (int t = 0; t < TERMS; ++t) {
-                const int a_set = (t == 2) ? 1 : 0;  // A lo only in the third term
-                const int b_set = (t == 1) ? 1 : 0;  // B lo only in the second term
-#pragma unroll
-                for (int ks = 0; ks < KS; ++ks) {
-                    const int kk = ks * 16;
-                    const int part = kk / n0;  // 0: Re rows, 1: Im rows
-                    const int row = i + kk % n0;
-                    const uint32_t a_addr = sA0 + (uint32_t)((2 * a_set + part) * plane_bytes + row * 16);
-                    const uint32_t b_addr = sB0 + (uint32_t)(b_set * B_BYTES + ks * 2 * 128);
-                    umma_f16(d_tmem, smem_desc(a_addr, a_lbo, a_sbo), smem_desc(b_addr, b_lbo, b_sbo), IDESC,
-                             (t | ks) != 0);
-                }
-            }
-            umma_commit(&bars[1]);
-        }
-        const bool done = mbar_wait(&bars[1], (uint32_t)(i & 1), TC_MAX_POLLS);
         tc_fence_after();
+#pragma unroll
+        for (int t = 0; t < TERMS; ++t) {
+            const int a_set = (t == 2) ? 1 : 0;  // A lo only in the third term
+            const int b_set = (t == 1) ? 1 : 0;  // B lo only in the second term
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks) {
+                const int kk = ks * 16;
+                const int part = kk / n0;  // 0: Re rows, 1: Im rows
+                const int row = i + kk % n0;
+                const uint32_t a_addr = sA0 + (uint32_t)((2 * a_set + part) * plane_bytes + row * 16);
+                const uint32_t b_addr = sB0 + (uint32_t)(b_set * B_BYTES + ks * 2 * 128);
+                umma_f16(d_tmem, smem_desc(a_addr, a_lbo, a_sbo), smem_desc(b_addr, b_lbo, b_sbo), IDESC,
+                         (t | ks) != 0);
+            }
+        }
+        umma_commit(&bars[1]);
+    };
+
+    // Pipeline: the products of row i+1 run in the other TMEM buffer while row i's epilogue
+    // drains.  Row i+1 is issued only after every thread has seen row i's phase complete (the
+    // barrier below), so no waiter ever falls two phases behind the parity it waits for; its
+    // buffer (i+1)&1 was last read in iteration i-1, before that same barrier.
+    const int L = qb - qa;
+    if (tid == 0 && ok) issue(0);
+    for (int i = 0; i < L && ok; ++i) {
+        const bool done = mbar_wait(&bars[1], (uint32_t)(i & 1), TC_MAX_POLLS);
+        tc_fence_before();              // orders the previous iteration's TMEM loads
+        ok = __syncthreads_and(done);   // block-uniform
+        if (!ok) break;
+        tc_fence_after();
+        if (tid == 0 && i + 1 < L) issue(i + 1);
         // epilogue: this thread's TMEM lane = its channel; columns [0, n0) Re, [n0, 2n0) Im
-        const uint32_t lane_addr = d_tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t lane_addr = tmem + (uint32_t)((i & 1) * N) + ((uint32_t)(warp * 32) << 16);
         float acc[N];
 #pragma unroll
         for (int c = 0; c < N; c += 16) {
             float v[16];
             tmem_ld_16(lane_addr + c, v);
-            tmem_ld_wait();
+            tmem_ld_wait();  // the loaded registers are valid only after the wait
 #pragma unroll
             for (int u = 0; u < 16; ++u) acc[c + u] = v[u];
         }
-        tc_fence_before();
-        // every lane has read this buffer before it is written again; the vote keeps the
-        // loop exit block-uniform
-        ok = __syncthreads_and(done);
-        if (active && ok) {
+        if (active) {
 #pragma unroll
             for (int k0 = 0; k0 < n0; ++k0)
                 __stcs(dst + (int64_t)k0 * n1, make_float2(out_scale * acc[k0], out_scale * acc[n0 + k0]));
