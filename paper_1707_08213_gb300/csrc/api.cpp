@@ -61,9 +61,9 @@ struct ArrayPlan {
         return (size_t)tc_terms(algo) * 2 * (size_t)(rows_out + n0 - 1) * (size_t)P1 * n1 * 2;
     }
     size_t ws_bytes_for(int64_t rows_out, int algo) const {
-        size_t b = align_up(z_bytes(rows_out));
-        if (algo >= SWDFT_ALGO_TC_BF16X3) b += align_up(planes_bytes(rows_out, algo)) + kAlign;
-        return b;
+        // tree: z (complex64); tensor-core forms: z as operand planes, then a max-abs word
+        if (algo >= SWDFT_ALGO_TC_BF16X3) return align_up(planes_bytes(rows_out, algo)) + kAlign;
+        return align_up(z_bytes(rows_out));
     }
 };
 
@@ -239,6 +239,47 @@ cudaError_t enqueue_forward(const swdft2d_plan_s *plan, const ArrayPlan &a, cons
                             int stages = 3) {
     const int64_t rows_out = q_hi - q_lo;
     if (rows_out <= 0) return cudaSuccess;
+    if (a.algo >= SWDFT_ALGO_TC_BF16X3) {
+        // tensor-core form: row DFT (tcgen05) -> operand planes -> column DFT (tcgen05)
+        const int terms = ArrayPlan::tc_terms(a.algo);
+        const bool f16 = a.algo == SWDFT_ALGO_TC_F16 || a.algo == SWDFT_ALGO_TC_F16_SCALED;
+        const bool scaled = a.algo == SWDFT_ALGO_TC_F16_SCALED;
+        char *planes = static_cast<char *>(ws);
+        float *amax = reinterpret_cast<float *>(planes + align_up(a.planes_bytes(rows_out, a.algo)));
+        if (stages & 1) {
+            TcRowArgs tr;
+            tr.x = static_cast<const char *>(in) + (size_t)q_lo * a.ld * a.in_elem();
+            tr.ld = a.ld;
+            tr.cplx = a.dtype == SWDFT_C64;
+            tr.N1 = a.N1;
+            tr.P1 = a.P1;
+            tr.zrows = rows_out + a.n0 - 1;
+            tr.m1 = a.m1;
+            tr.planes = planes;
+            tr.terms = terms;
+            tr.f16 = f16;
+            tr.amax = scaled ? amax : nullptr;
+            tr.om64 = plan->om64;
+            cudaError_t e = launch_tc_row(tr, s);
+            if (e != cudaSuccess) return e;
+        }
+        if (!(stages & 2)) return cudaSuccess;
+        TcColArgs t;
+        t.planes = planes;
+        t.terms = terms;
+        t.f16 = f16;
+        t.amax = scaled ? amax : nullptr;
+        t.amax_mult = (float)a.n1;
+        t.P1 = a.P1;
+        t.rows_out = rows_out;
+        t.m0 = a.m0;
+        t.m1 = a.m1;
+        t.out = static_cast<float2 *>(out);
+        t.scale = norm_scale(plan->norm, a.n0, a.n1);
+        t.om64 = plan->om64;
+        t.chunk = a.tc_chunk;
+        return launch_tc_col(t, s);
+    }
     RowTreeArgs r;
     r.x = in;
     r.ld = a.ld;
@@ -257,30 +298,6 @@ cudaError_t enqueue_forward(const swdft2d_plan_s *plan, const ArrayPlan &a, cons
         if (e != cudaSuccess) return e;
     }
     if (!(stages & 2)) return cudaSuccess;
-    if (a.algo >= SWDFT_ALGO_TC_BF16X3) {
-        const int terms = ArrayPlan::tc_terms(a.algo);
-        const bool f16 = a.algo == SWDFT_ALGO_TC_F16 || a.algo == SWDFT_ALGO_TC_F16_SCALED;
-        char *planes = static_cast<char *>(ws) + align_up(a.z_bytes(rows_out));
-        float *amax = reinterpret_cast<float *>(planes + align_up(a.planes_bytes(rows_out, a.algo)));
-        const bool scaled = a.algo == SWDFT_ALGO_TC_F16_SCALED;
-        cudaError_t e = launch_z_to_planes(z, planes, (rows_out + a.n0 - 1) * a.P1 * a.n1, terms, f16,
-                                           scaled ? amax : nullptr, s);
-        if (e != cudaSuccess) return e;
-        TcColArgs t;
-        t.planes = planes;
-        t.terms = terms;
-        t.f16 = f16;
-        t.amax = scaled ? amax : nullptr;
-        t.P1 = a.P1;
-        t.rows_out = rows_out;
-        t.m0 = a.m0;
-        t.m1 = a.m1;
-        t.out = static_cast<float2 *>(out);
-        t.scale = norm_scale(plan->norm, a.n0, a.n1);
-        t.om64 = plan->om64;
-        t.chunk = a.tc_chunk;
-        return launch_tc_col(t, s);
-    }
     ColTreeArgs c;
     c.z = z;
     c.P1 = a.P1;

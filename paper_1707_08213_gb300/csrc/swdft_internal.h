@@ -55,12 +55,13 @@ struct BatchImage {
 
 // Tensor-core column levels: out[q0][q1][k0][k1] = scale * sum_j0 z[q0+j0][ch] F0[j0][k0]
 // from 16-bit operand planes of z ([plane][rows_out + n0 - 1][P1*n1]; planes Re hi, Im hi,
-// Re lo, Im lo for terms = 3, Re, Im for terms = 1).  n0, n1 in [8, 64].
+// Re lo, Im lo for terms = 3, Re, Im for terms = 1).  16 <= n0 <= 64, 8 <= n1 <= 64.
 struct TcColArgs {
     void *planes = nullptr;
     int terms = 3;
     bool f16 = false;
-    const float *amax = nullptr;  // per-image fp16 scaling (see launch_z_to_planes)
+    const float *amax = nullptr;  // per-image fp16 scaling: amax * amax_mult bounds |z|
+    float amax_mult = 1.f;
     int64_t P1 = 0, rows_out = 0;
     int m0 = 0, m1 = 0;
     float2 *out = nullptr;
@@ -69,11 +70,25 @@ struct TcColArgs {
     int64_t chunk = 0;  // window rows per CTA
 };
 cudaError_t launch_tc_col(const TcColArgs &a, cudaStream_t s);
-// z (n complex64) -> operand planes; amax (device float, or null) enables the per-image
-// power-of-two fp16 scale, computed on the device from max |Re|, |Im|.
-cudaError_t launch_z_to_planes(const float2 *z, void *planes, int64_t n, int terms, bool f16, float *amax,
-                               cudaStream_t s);
 size_t tc_col_smem_bytes(int m0, int terms, int chunk);
+
+// Tensor-core row levels: writes z[r][q1][k1] = sum_j1 x[r][q1+j1] F1[j1][k1] for the band's
+// zrows input rows directly as the column pass's operand planes.  With amax (fp16 forms with
+// the per-image scale) the kernel first stores max |x| there and scales by the power of two
+// that fits n1 * max|x| below 2^14.
+struct TcRowArgs {
+    const void *x = nullptr;  // first input row of the band
+    int64_t ld = 0;
+    int cplx = 0;
+    int64_t N1 = 0, P1 = 0, zrows = 0;
+    int m1 = 0;
+    void *planes = nullptr;
+    int terms = 3;
+    bool f16 = false;
+    float *amax = nullptr;
+    const float2 *om64 = nullptr;
+};
+cudaError_t launch_tc_row(const TcRowArgs &a, cudaStream_t s);
 // Device error word of the tensor-core kernels (1 = a bounded wait timed out).
 cudaError_t tc_status(int *status, bool reset);
 

@@ -50,26 +50,35 @@ struct TcColParams {
     int rz;                 // staged rows per plane (chunk + n0 - 1, rounded up to 8)
     int m1;
     float scale;
-    const float *amax;      // per-image fp16 scaling: max |Re|,|Im| of z (null: no scaling)
+    const float *amax;      // per-image fp16 scaling: amax * amax_mult bounds |z| (null: none)
+    float amax_mult;
     float2 om64[kMaxN];
 };
 
-// Power-of-two scale that brings the largest |value| of an array to [2^13, 2^14): fp16 then
-// keeps its full 11-bit precision without overflow (max 65504).
-__device__ __forceinline__ float fp16_prescale(const float *amax) {
+// Power-of-two scale that brings a bound on the largest |value| of z, amax * mult, to
+// [2^13, 2^14): fp16 then keeps its full 11-bit precision without overflow (max 65504).
+__device__ __forceinline__ float fp16_prescale(const float *amax, float mult = 1.f) {
     if (!amax) return 1.f;
-    const float m = *amax;
+    const float m = *amax * mult;
     if (!(m > 0.f) || !isfinite(m)) return 1.f;
     int e;
     frexpf(m, &e);              // m = f * 2^e, f in [0.5, 1)
     return ldexpf(1.f, 14 - e);
 }
 
-__global__ void __launch_bounds__(256) amax_kernel(const float2 *__restrict__ z, int64_t n, float *amax) {
+// max |Re|, |Im| over rows x cols of a strided float32 (cplx = 0) or complex64 array
+__global__ void __launch_bounds__(256) amax_x_kernel(const void *__restrict__ x, int64_t ld, int64_t rows,
+                                                     int64_t cols, int cplx, float *amax) {
     float m = 0.f;
+    const int64_t n = rows * cols;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float2 v = z[i];
-        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+        const int64_t r = i / cols, c = i - (i / cols) * cols;
+        if (cplx) {
+            const float2 v = reinterpret_cast<const float2 *>(x)[r * ld + c];
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+        } else {
+            m = fmaxf(m, fabsf(reinterpret_cast<const float *>(x)[r * ld + c]));
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
@@ -92,26 +101,6 @@ __device__ __forceinline__ float from_bits(uint16_t b) {
         return __half2float(*reinterpret_cast<__half *>(&b));
     } else {
         return __bfloat162float(*reinterpret_cast<__nv_bfloat16 *>(&b));
-    }
-}
-
-// z (complex64, rows x nch) -> operand planes (16-bit, [plane][rows][nch]).
-// terms = 3: Re hi, Im hi, Re lo, Im lo; terms = 1: Re, Im.  With amax (per-image fp16
-// scaling) values are first multiplied by the power of two fp16_prescale(amax).
-template <bool F16>
-__global__ void __launch_bounds__(256) z_to_planes_kernel(const float2 *__restrict__ z, uint16_t *__restrict__ planes,
-                                                          int64_t n, int terms, const float *amax) {
-    const float prescale = fp16_prescale(amax);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float2 v = z[i];
-        const float re = v.x * prescale, im = v.y * prescale;
-        const uint16_t rh = to_bits<F16>(re), ih = to_bits<F16>(im);
-        planes[i] = rh;
-        planes[n + i] = ih;
-        if (terms == 3) {
-            planes[2 * n + i] = to_bits<F16>(re - from_bits<F16>(rh));
-            planes[3 * n + i] = to_bits<F16>(im - from_bits<F16>(ih));
-        }
     }
 }
 
@@ -196,7 +185,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_col_kernel(const __grid_constan
     const uint32_t a_lbo = 128u;  // K-group stride of A: consecutive 16-byte rows
     const uint32_t a_sbo = (uint32_t)rz * 16u;
     const uint32_t b_lbo = 128u, b_sbo = (uint32_t)(K / 8) * 128u;
-    const float out_scale = p.scale / fp16_prescale(p.amax);
+    const float out_scale = p.scale / fp16_prescale(p.amax, p.amax_mult);
 
     // issue all UMMAs of window row i into TMEM buffer i & 1, then commit
     auto issue = [&](int i) {
@@ -267,6 +256,212 @@ __global__ void __launch_bounds__(TC_THREADS) tc_col_kernel(const __grid_constan
     }
 }
 
+
+// ------------------------------------------------------------------ row DFT on tcgen05
+//
+// z[r][q1][k1] = sum_j1 x[r][q1 + j1] F1[j1][k1], one product per input row and 128 window
+// positions: D (128 x 2n1) = A (128 x K) * B (K x 2n1), A[m][k] = x[r][q1_0 + m + k] (Re x,
+// then Im x for complex input; K padded with zeros to a multiple of 16), B = realified F1.
+// A is a Hankel matrix -- consecutive positions shift by one element, which no descriptor
+// can express -- so each row's A is written to shared memory (K-major) from the staged input
+// rows.  The epilogue writes z directly as the column pass's operand planes.
+
+constexpr int TCR_ROWS = 8;  // input rows per CTA
+
+struct TcRowParams {
+    const void *x;       // first input row of the band
+    int64_t ld;          // input row stride, elements
+    int N1, P1, zrows;
+    uint16_t *planes;    // [plane][zrows][P1 * n1]
+    int64_t plane_elems; // zrows * P1 * n1
+    const float *amax;   // per-image fp16 scaling (max |x|; |z| <= n1 * max |x|), or null
+    float2 om64[kMaxN];
+};
+
+__host__ __device__ constexpr int tcr_K(int M1, bool cplx) {
+    return ((cplx ? 2 : 1) << M1) < 16 ? 16 : ((cplx ? 2 : 1) << M1);
+}
+
+size_t tc_row_smem_bytes(int m1, bool cplx, int terms) {
+    const int n1 = 1 << m1, K = tcr_K(m1, cplx), N = 2 * n1, nb = terms == 3 ? 2 : 1;
+    const int W = TC_CH + n1;  // staged columns per row (n1 - 1 look-ahead, rounded)
+    return (size_t)TCR_ROWS * W * (cplx ? 2 : 1) * 4 + (size_t)nb * N * K * 2 + (size_t)nb * TC_CH * K * 2 + 64 +
+           1024 + 8192;
+}
+
+template <int M1, bool CPLX, int TERMS, bool F16>
+__global__ void __launch_bounds__(TC_THREADS) tc_row_kernel(const __grid_constant__ TcRowParams p) {
+    constexpr int n1 = 1 << M1;
+    constexpr int K = tcr_K(M1, CPLX);
+    constexpr int N = 2 * n1;
+    constexpr int KS = K / 16;
+    constexpr int NB = TERMS == 3 ? 2 : 1;
+    constexpr int W = TC_CH + n1;
+    constexpr uint32_t TMEM_COLS = N < 32 ? 32 : N;
+    constexpr uint32_t B_BYTES = N * K * 2, A_BYTES = TC_CH * K * 2;
+    constexpr uint32_t IDESC = umma_idesc_f16(TC_CH, N, !F16, /*a_mn=*/false, /*b_mn=*/false);
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    unsigned char *sB = smem;                                   // NB x B_BYTES
+    unsigned char *sA = sB + NB * B_BYTES;                      // NB x A_BYTES
+    float *sx = reinterpret_cast<float *>(sA + NB * A_BYTES);   // TCR_ROWS x W (x2 complex)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sx + TCR_ROWS * W * (CPLX ? 2 : 1));
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int q1_0 = blockIdx.x * TC_CH;
+    const int r0 = blockIdx.y * TCR_ROWS;
+    if (r0 >= p.zrows) return;  // uniform per block
+    const int nrows = min(TCR_ROWS, p.zrows - r0);
+    const float pre = F16 ? fp16_prescale(p.amax, (float)n1) : 1.f;
+
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, TMEM_COLS);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_barrier_init();
+    }
+    // B = realified F1 (K-major): rows n (Re k1 | Im k1), columns k (Re j1 | Im j1 | zero pad)
+    for (int e = tid; e < N * K; e += TC_THREADS) {
+        const int n = e / K, k = e - (e / K) * K;
+        const int k1 = n & (n1 - 1);
+        const bool in_im = CPLX && k >= n1 && k < 2 * n1;
+        const bool pad = CPLX ? (k >= 2 * n1) : (k >= n1);
+        const int j1 = k & (n1 - 1);
+        const float2 w = p.om64[((j1 * k1) & (n1 - 1)) << (6 - M1)];  // (C, -S)
+        const bool out_im = n >= n1;
+        const float v = pad ? 0.f : ((out_im == in_im) ? w.x : (in_im ? -w.y : w.y));
+        const uint16_t hi = to_bits<F16>(v);
+        const uint32_t off = kmajor_off(n, k, K);
+        *reinterpret_cast<uint16_t *>(sB + off) = hi;
+        if (NB == 2) *reinterpret_cast<uint16_t *>(sB + B_BYTES + off) = to_bits<F16>(v - from_bits<F16>(hi));
+    }
+    // stage the CTA's input rows (columns q1_0 .. q1_0 + W - 1; zero beyond the array)
+    for (int e = tid; e < nrows * W; e += TC_THREADS) {
+        const int rr = e / W, c = e - (e / W) * W;
+        const int col = q1_0 + c;
+        if (CPLX) {
+            float2 v = make_float2(0.f, 0.f);
+            if (col < p.N1) v = reinterpret_cast<const float2 *>(p.x)[(int64_t)(r0 + rr) * p.ld + col];
+            sx[(rr * W + c) * 2] = v.x * pre;
+            sx[(rr * W + c) * 2 + 1] = v.y * pre;
+        } else {
+            float v = 0.f;
+            if (col < p.N1) v = reinterpret_cast<const float *>(p.x)[(int64_t)(r0 + rr) * p.ld + col];
+            sx[rr * W + c] = v * pre;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
+    const uint32_t lbo = 128u, sbo = (uint32_t)(K / 8) * 128u;  // K-major, both operands
+
+    const int m = tid;                  // this thread's position in the tile = its TMEM lane
+    const int pos = q1_0 + m;
+    const int64_t nch = (int64_t)p.P1 * n1;
+    bool ok = true;
+    for (int rr = 0; rr < nrows && ok; ++rr) {
+        // A row m: x[pos + k] (Re, then Im), 8 elements (one 16-byte chunk) at a time
+#pragma unroll
+        for (int g = 0; g < K / 8; ++g) {
+            uint16_t hv[8], lv[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int k = 8 * g + e;
+                float v = 0.f;
+                if (CPLX) {
+                    if (k < n1) v = sx[(rr * W + m + k) * 2];
+                    else if (k < 2 * n1) v = sx[(rr * W + m + k - n1) * 2 + 1];
+                } else if (k < n1) {
+                    v = sx[rr * W + m + k];
+                }
+                hv[e] = to_bits<F16>(v);
+                lv[e] = to_bits<F16>(v - from_bits<F16>(hv[e]));
+            }
+            const uint32_t off = (uint32_t)((m >> 3) * (K / 8) + g) * 128u + (uint32_t)(m & 7) * 16u;
+            uint4 h4, l4;
+            h4.x = hv[0] | ((uint32_t)hv[1] << 16); h4.y = hv[2] | ((uint32_t)hv[3] << 16);
+            h4.z = hv[4] | ((uint32_t)hv[5] << 16); h4.w = hv[6] | ((uint32_t)hv[7] << 16);
+            *reinterpret_cast<uint4 *>(sA + off) = h4;
+            if (NB == 2) {
+                l4.x = lv[0] | ((uint32_t)lv[1] << 16); l4.y = lv[2] | ((uint32_t)lv[3] << 16);
+                l4.z = lv[4] | ((uint32_t)lv[5] << 16); l4.w = lv[6] | ((uint32_t)lv[7] << 16);
+                *reinterpret_cast<uint4 *>(sA + A_BYTES + off) = l4;
+            }
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int t = 0; t < TERMS; ++t) {
+                const int a_set = (t == 2) ? 1 : 0, b_set = (t == 1) ? 1 : 0;
+#pragma unroll
+                for (int ks = 0; ks < KS; ++ks)
+                    umma_f16(tmem, smem_desc(sA0 + a_set * A_BYTES + ks * 256, lbo, sbo),
+                             smem_desc(sB0 + b_set * B_BYTES + ks * 256, lbo, sbo), IDESC, (t | ks) != 0);
+            }
+            umma_commit(bar);
+        }
+        const bool done = mbar_wait(bar, (uint32_t)(rr & 1), TC_MAX_POLLS);
+        tc_fence_after();
+        float acc[N];
+#pragma unroll
+        for (int c = 0; c < N; c += 16) {
+            float v[16];
+            tmem_ld_16(tmem + ((uint32_t)(warp * 32) << 16) + c, v);
+            tmem_ld_wait();
+#pragma unroll
+            for (int u = 0; u < 16; ++u) acc[c + u] = v[u];
+        }
+        tc_fence_before();
+        ok = __syncthreads_and(done);  // A and TMEM are free for the next row
+        if (ok && pos < p.P1) {
+            // z for this position: acc[k1] = Re, acc[n1 + k1] = Im -> operand planes
+            const int64_t base = (int64_t)(r0 + rr) * nch + (int64_t)pos * n1;
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
+#pragma unroll
+                for (int g = 0; g < n1 / 8; ++g) {
+                    uint16_t hv[8], lv[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const float v = acc[part * n1 + 8 * g + e];
+                        hv[e] = to_bits<F16>(v);
+                        lv[e] = to_bits<F16>(v - from_bits<F16>(hv[e]));
+                    }
+                    uint4 h4, l4;
+                    h4.x = hv[0] | ((uint32_t)hv[1] << 16); h4.y = hv[2] | ((uint32_t)hv[3] << 16);
+                    h4.z = hv[4] | ((uint32_t)hv[5] << 16); h4.w = hv[6] | ((uint32_t)hv[7] << 16);
+                    *reinterpret_cast<uint4 *>(p.planes + part * p.plane_elems + base + 8 * g) = h4;
+                    if (TERMS == 3) {
+                        l4.x = lv[0] | ((uint32_t)lv[1] << 16); l4.y = lv[2] | ((uint32_t)lv[3] << 16);
+                        l4.z = lv[4] | ((uint32_t)lv[5] << 16); l4.w = lv[6] | ((uint32_t)lv[7] << 16);
+                        *reinterpret_cast<uint4 *>(p.planes + (2 + part) * p.plane_elems + base + 8 * g) = l4;
+                    }
+                }
+            }
+        }
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(&g_tc_status, 1);
+        mbar_wait(bar, 0, 64);
+        mbar_wait(bar, 1, 64);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
 // ------------------------------------------------------------------ host side
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -295,24 +490,6 @@ size_t tc_col_smem_bytes(int m0, int terms, int chunk) {
 }
 
 int tc_col_max_chunk(int m0) { return 256 - (1 << m0) + 1 - 7; }
-
-cudaError_t launch_z_to_planes(const float2 *z, void *planes, int64_t n, int terms, bool f16, float *amax,
-                               cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    const int threads = 256;
-    const int64_t blocks = std::min<int64_t>((n + threads - 1) / threads, 152 * 16);
-    if (amax) {
-        cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(float), s);
-        if (e != cudaSuccess) return e;
-        amax_kernel<<<(unsigned)blocks, threads, 0, s>>>(z, n, amax);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    if (f16)
-        z_to_planes_kernel<true><<<(unsigned)blocks, threads, 0, s>>>(z, (uint16_t *)planes, n, terms, amax);
-    else
-        z_to_planes_kernel<false><<<(unsigned)blocks, threads, 0, s>>>(z, (uint16_t *)planes, n, terms, amax);
-    return cudaGetLastError();
-}
 
 template <int M0, int TERMS, bool F16>
 static cudaError_t launch_tc_col_t(const TcColParams &p, dim3 grid, size_t smem, cudaStream_t s) {
@@ -359,6 +536,7 @@ cudaError_t launch_tc_col(const TcColArgs &a, cudaStream_t s) {
     p.m1 = a.m1;
     p.scale = a.scale;
     p.amax = a.amax;
+    p.amax_mult = a.amax_mult;
     for (int j = 0; j < kMaxN; ++j) p.om64[j] = a.om64[j];
     const size_t smem = tc_col_smem_bytes(a.m0, a.terms, chunk);
     dim3 grid((unsigned)((nch + TC_CH - 1) / TC_CH), (unsigned)((a.rows_out + chunk - 1) / chunk));
@@ -376,6 +554,63 @@ cudaError_t launch_tc_col(const TcColArgs &a, cudaStream_t s) {
             return cudaErrorInvalidValue;
     }
 #undef TC_CASE
+}
+
+
+template <int M1, bool CPLX, int TERMS, bool F16>
+static cudaError_t launch_tc_row_t(const TcRowParams &p, dim3 grid, size_t smem, cudaStream_t s) {
+    auto k = tc_row_kernel<M1, CPLX, TERMS, F16>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, TC_THREADS, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int M1>
+static cudaError_t launch_tc_row_m(const TcRowParams &p, bool cplx, int terms, bool f16, dim3 grid, size_t smem,
+                                   cudaStream_t s) {
+    if (f16) return cplx ? launch_tc_row_t<M1, true, 1, true>(p, grid, smem, s)
+                         : launch_tc_row_t<M1, false, 1, true>(p, grid, smem, s);
+    if (terms == 3) return cplx ? launch_tc_row_t<M1, true, 3, false>(p, grid, smem, s)
+                                : launch_tc_row_t<M1, false, 3, false>(p, grid, smem, s);
+    return cplx ? launch_tc_row_t<M1, true, 1, false>(p, grid, smem, s)
+                : launch_tc_row_t<M1, false, 1, false>(p, grid, smem, s);
+}
+
+cudaError_t launch_tc_row(const TcRowArgs &a, cudaStream_t s) {
+    if (a.zrows <= 0 || a.P1 <= 0) return cudaSuccess;
+    if (a.m1 < 3 || a.m1 > kMaxLog2 || (a.terms != 1 && a.terms != 3)) return cudaErrorInvalidValue;
+    if (a.zrows > INT32_MAX || a.N1 > INT32_MAX || (uintptr_t)a.planes % 16 != 0) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (a.amax) {
+        if ((e = cudaMemsetAsync(a.amax, 0, sizeof(float), s)) != cudaSuccess) return e;
+        const int64_t n = a.zrows * a.N1;
+        const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 8);
+        amax_x_kernel<<<(unsigned)blocks, 256, 0, s>>>(a.x, a.ld, a.zrows, a.N1, a.cplx, a.amax);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    TcRowParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.x = a.x;
+    p.ld = a.ld;
+    p.N1 = (int)a.N1;
+    p.P1 = (int)a.P1;
+    p.zrows = (int)a.zrows;
+    p.planes = static_cast<uint16_t *>(a.planes);
+    p.plane_elems = a.zrows * (a.P1 << a.m1);
+    p.amax = a.amax;
+    for (int j = 0; j < kMaxN; ++j) p.om64[j] = a.om64[j];
+    const size_t smem = tc_row_smem_bytes(a.m1, a.cplx != 0, a.terms);
+    dim3 grid((unsigned)((a.P1 + TC_CH - 1) / TC_CH), (unsigned)((a.zrows + TCR_ROWS - 1) / TCR_ROWS));
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    const bool cplx = a.cplx != 0;
+    switch (a.m1) {
+        case 3: return launch_tc_row_m<3>(p, cplx, a.terms, a.f16, grid, smem, s);
+        case 4: return launch_tc_row_m<4>(p, cplx, a.terms, a.f16, grid, smem, s);
+        case 5: return launch_tc_row_m<5>(p, cplx, a.terms, a.f16, grid, smem, s);
+        case 6: return launch_tc_row_m<6>(p, cplx, a.terms, a.f16, grid, smem, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t tc_status(int *status, bool reset) {
