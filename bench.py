@@ -46,6 +46,10 @@ COL_KERNEL_SOURCES = ["paper_1707_08213_gb300/csrc/tree_core.cuh",
                       "paper_1707_08213_gb300/csrc/tree_kernels.cuh",
                       "paper_1707_08213_gb300/csrc/tree_col_m5.cu"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "col_tree_sinusoids_512.json")
+TC_PROFILE_FILE = os.path.join(ROOT, "profiles", "tc_col_sinusoids_512.json")
+TC_KERNEL_SOURCES = ["paper_1707_08213_gb300/csrc/tc_kernels.cu",
+                     "paper_1707_08213_gb300/csrc/sm100_ptx.cuh"]
+TC_ALGOS = ("tc_bf16x3", "tc_bf16", "tc_f16_scaled")
 
 
 def parse_args():
@@ -57,6 +61,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the tensor-core, batch and adjoint side measurements")
     return ap.parse_args()
 
 
@@ -233,6 +239,119 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------------- side measurements
+
+def time_forward(torch, t, xd, out, flush, steps):
+    """Median ms of one forward (both passes) on the current stream, L2 flushed before each."""
+    sp = torch.cuda.current_stream().cuda_stream
+    for _ in range(3):
+        t.plan.execute([xd.data_ptr()], [out.data_ptr()], t._ws_ptr, sp)
+    ts = []
+    for _ in range(steps):
+        flush.fill_(3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        t.plan.execute([xd.data_ptr()], [out.data_ptr()], t._ws_ptr, sp)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def tc_comparison(torch, sw, xd, out, flush, tree_ms):
+    """Tensor-core forms on the same workload and GPU, timed like the tree."""
+    res = {"tree_f32": {"ms_per_step": round(tree_ms, 5), "value": COEFFS / (tree_ms / 1e3)}}
+    for algo in TC_ALGOS:
+        try:
+            t = sw.Transform([(N0, N1, n0, n1, sw.R32)], algo=algo)
+            ms = time_forward(torch, t, xd, out, flush, 50)
+            res[algo] = {"ms_per_step": round(ms, 5), "value": COEFFS / (ms / 1e3),
+                         "vs_tree": round(tree_ms / ms, 4),
+                         "device_status": sw._native.check_device()}
+            del t
+        except Exception as e:  # noqa: BLE001
+            res[algo] = {"error": str(e)}
+    try:
+        with open(TC_PROFILE_FILE) as f:
+            prof = json.load(f)
+        if prof.get("source_sha") == source_sha(TC_KERNEL_SOURCES):
+            res["tensor_pipe_active_pct"] = prof.get("tensor_pipe_active_pct")
+            res["tensor_pipe_source"] = prof.get("command")
+    except Exception:
+        pass
+    return res
+
+
+def batch_measurement(torch, sw):
+    """The 256-image uneven batch (1.8e10 coefficients) through one persistent launch pair
+    replayed from a CUDA graph, and through per-array launches replayed from a graph."""
+    import workloads
+    wl = workloads.uneven_batch_256()
+    shapes = [(x.shape[0], x.shape[1], a, b, 0) for x, (a, b) in zip(wl.images, wl.windows)]
+    coeffs = workloads.uneven_batch_output_coeffs()
+    xd = [torch.from_numpy(x).cuda() for x in wl.images]
+    res = {"workload": "uneven_batch_256: 256 f32 images, sides {128..1024}, windows from "
+                       "{4x4,8x8,16x16,32x32,8x32,64x16} (seed 3)",
+           "coeffs_per_step": coeffs, "output_bytes_per_step": 8 * coeffs}
+    outs = None
+    s = torch.cuda.Stream()
+    for name, flags in (("persistent_graph", sw.FLAG_PERSISTENT | sw.FLAG_GRAPH),
+                        ("per_array_graph", sw.FLAG_GRAPH)):
+        t = sw.Transform(shapes, flags=flags)
+        if outs is None:
+            outs = t.empty_outputs()
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                t.forward(xd, outs)
+            ts = []
+            for _ in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                t.forward(xd, outs)
+                e1.record(s)
+                s.synchronize()
+                ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        res[name] = {"ms_per_step": round(ms, 4), "value": coeffs / (ms / 1e3),
+                     "output_gbs": round(8 * coeffs / (ms / 1e3) / 1e9, 1),
+                     "launches": t.plan.launch_count()}
+        del t
+    del outs, xd
+    torch.cuda.empty_cache()
+    return res
+
+
+def adjoint_measurement(torch, sw):
+    """8 x 256x256, 16x16 windows: forward and the hand-written adjoint (A^H) per step."""
+    import workloads
+    xs, w, (a0, a1) = workloads.adjoint_batch_8()
+    M0, M1 = xs.shape[1:]
+    t = sw.Transform([(M0, M1, a0, a1, 0)] * len(xs))
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    a = t.forward(xd)
+    g = t.adjoint(a)
+    coeffs = sum(o.numel() for o in a)
+    res = {"workload": "adjoint_batch_8: 8 x 256x256 f32, 16x16 windows", "coeffs_per_step": coeffs}
+    for name, fn in (("forward", lambda: t.forward(xd, a)), ("adjoint", lambda: t.adjoint(a, g))):
+        for _ in range(3):
+            fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        res[name] = {"ms_per_step": round(ms, 4), "value": coeffs / (ms / 1e3),
+                     "gbs_of_coefficients": round(8 * coeffs / (ms / 1e3) / 1e9, 1)}
+    del t, xd, a, g
+    torch.cuda.empty_cache()
+    return res
+
+
 # ----------------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -295,12 +414,14 @@ def run_ours(args):
     ms_per_step = total_ms / K
     value = world * K * COEFFS / (total_ms / 1e3)
 
-    # dominant kernel: the column-level pass (output writes)
+    # dominant kernel: the column-level pass (output writes); with the fused form the
+    # single kernel reads x and writes the output, and stage 0 launches nothing
+    fused = t.plan.launch_count() == 1
     col_avg = sum(col_ms) / K
     row_avg = sum(row_ms) / K
     z_bytes = (N0 * P1 * n1) * 8
-    col_alg_bytes = 8 * COEFFS + z_bytes              # output written + z read once
-    row_alg_bytes = 4 * N0 * N1 + z_bytes             # input read + z written
+    col_alg_bytes = 8 * COEFFS + (4 * N0 * N1 if fused else z_bytes)
+    row_alg_bytes = 0 if fused else 4 * N0 * N1 + z_bytes
     peak, peak_kind = measured_peak_hbm()
     achieved = col_alg_bytes / (col_avg / 1e3) / 1e9
     traffic = None
@@ -311,18 +432,33 @@ def run_ours(args):
             traffic = prof.get("dram_bytes_per_launch")
     except Exception:
         pass
-    roofline = {"bound": "hbm", "kernel": "col_tree_kernel<5,2> (column levels, Eq. colfswft2d)",
+    kname = ("fused_tree_kernel<5,2,5,false> (row levels in the column tile + column levels)"
+             if fused else "col_tree_kernel<5,2> (column levels, Eq. colfswft2d)")
+    roofline = {"bound": "hbm", "kernel": kname,
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": col_alg_bytes, "avg_launch_ms": round(col_avg, 5),
-                "row_pass": {"avg_launch_ms": round(row_avg, 5),
-                             "algorithmic_bytes_per_launch": row_alg_bytes,
-                             "achieved_gbs": round(row_alg_bytes / (row_avg / 1e3) / 1e9, 1)},
+                "row_pass": None if fused else {
+                    "avg_launch_ms": round(row_avg, 5), "algorithmic_bytes_per_launch": row_alg_bytes,
+                    "achieved_gbs": round(row_alg_bytes / (row_avg / 1e3) / 1e9, 1)},
                 "step_output_gbs": round(8 * COEFFS / (ms_per_step / 1e3) / 1e9, 1)}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    extra = {}
+    if not args.no_extra:
+        try:
+            extra["tensor_core"] = tc_comparison(torch, sw, xd, out, flush, ms_per_step)
+        except Exception as e:  # noqa: BLE001
+            extra["tensor_core"] = {"error": str(e)}
+        for key, fn in (("batch", batch_measurement), ("adjoint", adjoint_measurement)):
+            try:
+                extra[key] = fn(torch, sw)
+            except Exception as e:  # noqa: BLE001
+                extra[key] = {"error": str(e)}
+                torch.cuda.empty_cache()
+
     e2e, check = None, None
     if args.e2e_steps > 0:
         th = sw.Transform([(N0, N1, n0, n1, sw.R32)], device=dev, flags=sw.FLAG_HOST_IO)
@@ -355,6 +491,7 @@ def run_ours(args):
             "roofline": roofline, "e2e": e2e, "clocks": clocks,
             "gpu_launches": K * t.plan.launch_count(),
             "wall_s_timed_region": round(wall, 3)}
+    line.update(extra)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import workloads as _w
@@ -364,6 +501,20 @@ def run_ours(args):
         err, rms = _w.normalised_error(got, ref, _w.window_sq_norms_at(x, n0, n1, q0, q1))
         line["error_vs_oracle"] = {"max": err, "rms": rms, "windows": int(len(q0)),
                                    "metric": "max_k |a - a_oracle| / ||x_w||_2"}
+        if "tensor_core" in line:
+            sq = _w.window_sq_norms_at(x, n0, n1, q0, q1)
+            for algo in TC_ALGOS:
+                ent = line["tensor_core"].get(algo)
+                if not isinstance(ent, dict) or "error" in ent:
+                    continue
+                tt = sw.Transform([(N0, N1, n0, n1, sw.R32)], algo=algo)
+                o = tt.forward([xd])[0]
+                got_tc = o[torch.from_numpy(q0).to(dev), torch.from_numpy(q1).to(dev)].cpu().numpy()
+                e_tc, r_tc = _w.normalised_error(got_tc, ref, sq)
+                ent["error_vs_oracle"] = {"max": e_tc, "rms": r_tc, "windows": int(len(q0))}
+                ent["meets_1e-5"] = bool(e_tc <= 1e-5)
+                del tt, o
+            torch.cuda.empty_cache()
         if check is not None:
             line["e2e"]["matches_device_path"] = bool(
                 torch.equal(check[q0[:64], q1[:64]], out[q0[:64], q1[:64]].cpu()))

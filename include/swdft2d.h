@@ -163,10 +163,12 @@ swdft_status swdft2d_execute_stage(swdft2d_plan_t plan, int32_t stage, const voi
  * chooses): row_B / col_B = log2 of the threads sharing one tree's butterflies along
  * dimension 1 / 0 (clamped to [0, min(m, 3)]), row_chunk = window columns per row-pass
  * thread, col_chunk = window rows per column-pass thread (0 = all), col_groups = 32-channel
- * groups per column-pass block.  Results do not depend on these values; speed does. */
+ * groups per column-pass block, fused = 1: evaluate the row levels inside the column
+ * kernel (one launch, z never written to HBM; windows with n1 <= 32 only), 0: two passes,
+ * -1: the library's default.  Results do not depend on these values; speed does. */
 swdft_status swdft2d_set_tree_config(swdft2d_plan_t plan, int32_t i, int32_t row_B,
                                      int64_t row_chunk, int32_t col_B, int64_t col_chunk,
-                                     int32_t col_groups);
+                                     int32_t col_groups, int32_t fused);
 
 /* Number of kernel launches one execute enqueues (graph replays count their kernels). */
 swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t *launches);

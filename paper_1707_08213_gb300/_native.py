@@ -72,7 +72,7 @@ def _load() -> ctypes.CDLL:
         "swdft2d_autotune": ([P, PP, PP, P, P], i32),
         "swdft2d_launch_count": ([P, i32, ctypes.POINTER(i32)], i32),
         "swdft2d_execute_stage": ([P, i32, PP, PP, P, P], i32),
-        "swdft2d_set_tree_config": ([P, i32, i32, i64, i32, i64, i32], i32),
+        "swdft2d_set_tree_config": ([P, i32, i32, i64, i32, i64, i32, i32], i32),
         "swdft2d_execute_static_scratch": ([P, i64, i64, i64, i32, i32, i32, i32, P, P], i32),
         "swdft2d_check_device": ([], i32),
         "swdft2d_destroy": ([P], i32),
@@ -161,9 +161,9 @@ class Plan:
                                          ctypes.c_void_p(stream or None)), "swdft2d_execute_stage")
 
     def set_tree_config(self, i: int, row_B: int, row_chunk: int, col_B: int, col_chunk: int,
-                        col_groups: int):
+                        col_groups: int, fused: int = -1):
         _check(lib.swdft2d_set_tree_config(self.handle, int(i), int(row_B), int(row_chunk),
-                                           int(col_B), int(col_chunk), int(col_groups)),
+                                           int(col_B), int(col_chunk), int(col_groups), int(fused)),
                "swdft2d_set_tree_config")
 
     def execute_adjoint(self, gout_ptrs, gin_ptrs, ws_ptr: int, stream: int = 0):

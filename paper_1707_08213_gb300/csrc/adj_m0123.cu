@@ -3,8 +3,9 @@
 
 namespace swdft {
 
-#define F(M_, B_) SWDFT_ADJ_INSTANTIATE(M_, B_)
-F(0, 0) F(1, 0) F(1, 1) F(2, 0) F(2, 1) F(2, 2) F(3, 0) F(3, 1) F(3, 2) F(3, 3)
-#undef F
+SWDFT_ADJ_INSTANTIATE(0)
+SWDFT_ADJ_INSTANTIATE(1)
+SWDFT_ADJ_INSTANTIATE(2)
+SWDFT_ADJ_INSTANTIATE(3)
 
 }  // namespace swdft

@@ -3,8 +3,6 @@
 
 namespace swdft {
 
-#define F(M_, B_) SWDFT_ADJ_INSTANTIATE(M_, B_)
-F(4, 0) F(4, 1) F(4, 2) F(4, 3)
-#undef F
+SWDFT_ADJ_INSTANTIATE(4)
 
 }  // namespace swdft

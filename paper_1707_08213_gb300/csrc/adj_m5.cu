@@ -3,8 +3,6 @@
 
 namespace swdft {
 
-#define F(M_, B_) SWDFT_ADJ_INSTANTIATE(M_, B_)
-F(5, 0) F(5, 1) F(5, 2) F(5, 3)
-#undef F
+SWDFT_ADJ_INSTANTIATE(5)
 
 }  // namespace swdft

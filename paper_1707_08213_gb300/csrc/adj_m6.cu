@@ -3,8 +3,6 @@
 
 namespace swdft {
 
-#define F(M_, B_) SWDFT_ADJ_INSTANTIATE(M_, B_)
-F(6, 0) F(6, 1) F(6, 2) F(6, 3)
-#undef F
+SWDFT_ADJ_INSTANTIATE(6)
 
 }  // namespace swdft

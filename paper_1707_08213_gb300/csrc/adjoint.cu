@@ -22,17 +22,17 @@ cudaError_t launch_adj_col(const AdjColArgs &a, cudaStream_t s) {
     p.m1 = a.m1;
     p.scale = a.scale;
     for (int j = 0; j < kMaxN; ++j) p.om64[j] = a.om64[j];
-    const int B = std::max(0, std::min(a.B, std::min(a.m0, 3)));
+    const int B = adj_col_B(a.m0);  // the one split built per window side
     const int threads = 128;
     const int64_t per_block = threads >> B;
     dim3 grid((unsigned)((nch + per_block - 1) / per_block), (unsigned)((zrows + p.chunk - 1) / p.chunk));
     if (grid.y > 65535) return cudaErrorInvalidValue;
-    switch (a.m0 * 8 + B) {
-#define F(M_, B_)                                              \
-    case M_ * 8 + B_:                                          \
-        adj_col_launch_mb<M_, B_>(p, grid, dim3(threads), s);  \
+    switch (a.m0) {
+#define F(M_)                                                                \
+    case M_:                                                                 \
+        adj_col_launch_mb<M_, adj_col_B(M_)>(p, grid, dim3(threads), s);     \
         break;
-        SWDFT_MB_CASES(F)
+        F(0) F(1) F(2) F(3) F(4) F(5) F(6)
 #undef F
         default:
             return cudaErrorInvalidValue;
@@ -52,17 +52,17 @@ cudaError_t launch_adj_row(const AdjRowArgs &a, cudaStream_t s) {
     p.P1 = (int)(a.N1 - (int64_t(1) << a.m1) + 1);
     p.chunk = (int)std::min<int64_t>(a.chunk > 0 ? a.chunk : a.N1, a.N1);
     for (int j = 0; j < kMaxN; ++j) p.om64[j] = a.om64[j];
-    const int B = std::max(0, std::min(a.B, std::min(a.m1, 3)));
+    const int B = adj_row_B(a.m1);  // the one split built per window side
     const int threads = 128;
     const int64_t per_block = threads >> B;
     dim3 grid((unsigned)((a.zrows + per_block - 1) / per_block), (unsigned)((a.N1 + p.chunk - 1) / p.chunk));
     if (grid.y > 65535) return cudaErrorInvalidValue;
-    switch (a.m1 * 8 + B) {
-#define F(M_, B_)                                                       \
-    case M_ * 8 + B_:                                                   \
-        adj_row_launch_mb<M_, B_>(p, a.cplx, grid, dim3(threads), s);   \
+    switch (a.m1) {
+#define F(M_)                                                                         \
+    case M_:                                                                          \
+        adj_row_launch_mb<M_, adj_row_B(M_)>(p, a.cplx, grid, dim3(threads), s);      \
         break;
-        SWDFT_MB_CASES(F)
+        F(0) F(1) F(2) F(3) F(4) F(5) F(6)
 #undef F
         default:
             return cudaErrorInvalidValue;

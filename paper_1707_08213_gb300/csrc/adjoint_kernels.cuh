@@ -153,18 +153,23 @@ void adj_col_launch_mb(const AdjColParams &p, dim3 g, dim3 b, cudaStream_t s);
 template <int M, int B>
 void adj_row_launch_mb(const AdjRowParams &p, int cplx, dim3 g, dim3 b, cudaStream_t s);
 
-#define SWDFT_ADJ_INSTANTIATE(M_, B_)                                                            \
+// The residue split each adjoint pass uses for a window side 2^M (registers without spills).
+__host__ __device__ constexpr int adj_col_B(int M) { return M <= 4 ? (M < 1 ? M : 1) : M - 3; }
+__host__ __device__ constexpr int adj_row_B(int M) { return M >= 6 ? 3 : (M < 2 ? M : 2); }
+
+#define SWDFT_ADJ_INSTANTIATE(M_)                                                                 \
     template <>                                                                                  \
-    void adj_col_launch_mb<M_, B_>(const AdjColParams &p, dim3 g, dim3 b, cudaStream_t s) {      \
-        adj_col_kernel<M_, B_><<<g, b, 0, s>>>(p);                                               \
+    void adj_col_launch_mb<M_, adj_col_B(M_)>(const AdjColParams &p, dim3 g, dim3 b,             \
+                                              cudaStream_t s) {                                  \
+        adj_col_kernel<M_, adj_col_B(M_)><<<g, b, 0, s>>>(p);                                    \
     }                                                                                            \
     template <>                                                                                  \
-    void adj_row_launch_mb<M_, B_>(const AdjRowParams &p, int cplx, dim3 g, dim3 b,              \
-                                   cudaStream_t s) {                                             \
+    void adj_row_launch_mb<M_, adj_row_B(M_)>(const AdjRowParams &p, int cplx, dim3 g, dim3 b,   \
+                                              cudaStream_t s) {                                  \
         if (cplx)                                                                                \
-            adj_row_kernel<M_, B_, true><<<g, b, 0, s>>>(p);                                     \
+            adj_row_kernel<M_, adj_row_B(M_), true><<<g, b, 0, s>>>(p);                          \
         else                                                                                     \
-            adj_row_kernel<M_, B_, false><<<g, b, 0, s>>>(p);                                    \
+            adj_row_kernel<M_, adj_row_B(M_), false><<<g, b, 0, s>>>(p);                         \
     }
 
 }  // namespace swdft

@@ -30,6 +30,7 @@ int log2_exact(int64_t n) {
 }
 
 struct TreeConfig {
+    bool fused = false;  // n1 <= 32: row levels inside the column kernel (no z in HBM)
     int row_B = 2;
     int64_t row_chunk = 0;
     int col_B = 2;
@@ -128,18 +129,21 @@ int64_t col_chunk_for(const ArrayPlan &a, int nchunks) {
 
 void default_config(ArrayPlan &a, int sm_count) {
     TreeConfig c;
-    const int64_t target = (int64_t)sm_count * 1024;  // row-pass threads in flight we aim for
-    // row levels: thread = (row, residue, chunk of positions)
-    c.row_B = std::min(a.m1, 2);
+    // row levels: thread = (row, residue, chunk of window columns).  About 64K threads in
+    // flight (measured best on the 512x512/32x32 and 1024x2048/16x64 workloads: B = 3 with
+    // 16-32 column chunks, B = 2 with 128-column chunks), chunks no shorter than n1/2.
+    (void)sm_count;
+    c.row_B = a.m1 >= 6 ? 2 : std::min(a.m1, 3);
     const int64_t rows = a.band_rows() + a.n0 - 1;
-    int64_t nchunk = std::max<int64_t>(1, target / std::max<int64_t>(1, rows << c.row_B));
-    int64_t chunk = (a.P1 + nchunk - 1) / nchunk;
-    c.row_chunk = std::max<int64_t>(chunk, std::min<int64_t>(a.P1, 2 * a.n1));
+    const int64_t nchunk = std::max<int64_t>(1, (64LL << 10) / std::max<int64_t>(1, rows << c.row_B));
+    const int64_t chunk = (a.P1 + nchunk - 1) / nchunk;
+    c.row_chunk = std::min<int64_t>(a.P1, std::max<int64_t>(chunk, std::max(1, a.n1 / 2)));
     // column levels: thread = (channel, residue, chunk of output rows); one 32-channel
     // group per block (32 * 2^B threads)
     c.col_B = a.m0 >= 6 ? 3 : std::min(a.m0, 2);
     c.col_groups = 1;
     c.col_chunk = col_chunk_for(a, 8);
+    c.fused = false;
     a.cfg = c;
 }
 
@@ -279,6 +283,24 @@ cudaError_t enqueue_forward(const swdft2d_plan_s *plan, const ArrayPlan &a, cons
         t.om64 = plan->om64;
         t.chunk = a.tc_chunk;
         return launch_tc_col(t, s);
+    }
+    if (a.cfg.fused && a.m1 <= 5) {
+        // one launch: row levels inside the column tile; stage 0 has nothing to do
+        if (!(stages & 2)) return cudaSuccess;
+        FusedTreeArgs f;
+        f.x = static_cast<const char *>(in) + (size_t)q_lo * a.ld * a.in_elem();
+        f.ld = a.ld;
+        f.cplx = a.dtype == SWDFT_C64;
+        f.P1 = a.P1;
+        f.rows_out = rows_out;
+        f.m0 = a.m0;
+        f.m1 = a.m1;
+        f.out = static_cast<float2 *>(out);
+        f.scale = norm_scale(plan->norm, a.n0, a.n1);
+        f.om64 = plan->om64;
+        f.chunk = a.cfg.col_chunk;
+        f.groups = a.cfg.col_groups;
+        return launch_fused_tree(f, s);
     }
     RowTreeArgs r;
     r.x = in;
@@ -464,7 +486,13 @@ swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t 
     if (!plan || !launches) return SWDFT_ERR_INVALID_ARG;
     // forward: row + column pass per array, or the two persistent passes for the whole batch;
     // adjoint: column + row adjoint pass per array
-    *launches = (!adjoint && (plan->flags & SWDFT_FLAG_PERSISTENT)) ? 2 : (int32_t)(2 * plan->arrays.size());
+    if (!adjoint && (plan->flags & SWDFT_FLAG_PERSISTENT)) {
+        *launches = 2;
+        return SWDFT_OK;
+    }
+    int32_t n = 0;
+    for (const auto &a : plan->arrays) n += (!adjoint && a.cfg.fused && a.m1 <= 5) ? 1 : 2;
+    *launches = n;
     return SWDFT_OK;
 }
 
@@ -539,11 +567,18 @@ swdft_status swdft2d_execute_stage(swdft2d_plan_t plan, int32_t stage, const voi
 
 swdft_status swdft2d_set_tree_config(swdft2d_plan_t plan, int32_t i, int32_t row_B,
                                      int64_t row_chunk, int32_t col_B, int64_t col_chunk,
-                                     int32_t col_groups) {
+                                     int32_t col_groups, int32_t fused) {
     if (!plan || i < 0 || (size_t)i >= plan->arrays.size()) return SWDFT_ERR_INVALID_ARG;
-    if (row_chunk < 0 || col_chunk < 0 || col_groups < 0) return SWDFT_ERR_INVALID_ARG;
+    if (row_chunk < 0 || col_chunk < 0 || col_groups < 0 || fused < -1 || fused > 1) return SWDFT_ERR_INVALID_ARG;
     ArrayPlan &a = plan->arrays[(size_t)i];
     TreeConfig c;
+    if (fused == -1) {
+        ArrayPlan tmp = a;
+        default_config(tmp, plan->sm_count);
+        c.fused = tmp.cfg.fused;
+    } else {
+        c.fused = fused == 1 && a.m1 <= 5;
+    }
     c.row_B = std::max(0, std::min(row_B, std::min(a.m1, 3)));
     c.row_chunk = row_chunk;
     c.col_B = std::max(0, std::min(col_B, std::min(a.m0, 3)));
@@ -589,7 +624,7 @@ swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_g
         c.m1 = a.m1;
         c.scale = norm_scale(plan->norm, a.n0, a.n1);
         c.om64 = plan->om64;
-        c.B = a.m0 <= 4 ? std::min(a.m0, 1) : a.m0 - 3;
+        c.B = 0;  // the launcher uses the one split built per window side
         c.chunk = std::min(zrows, std::max<int64_t>((zrows + 7) / 8, 2 * a.n0));
         if (launch_adj_col(c, s) != cudaSuccess) return SWDFT_ERR_CUDA;
         AdjRowArgs r;
@@ -601,9 +636,9 @@ swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_g
         r.N1 = a.N1;
         r.m1 = a.m1;
         r.om64 = plan->om64;
-        r.B = a.m1 >= 6 ? 3 : std::min(a.m1, 2);
+        r.B = 0;  // the launcher uses the one split built per window side
         const int64_t target = (int64_t)plan->sm_count * 1024;
-        const int64_t nchunk = std::max<int64_t>(1, target / std::max<int64_t>(1, zrows << r.B));
+        const int64_t nchunk = std::max<int64_t>(1, target / std::max<int64_t>(1, zrows << (a.m1 >= 6 ? 3 : std::min(a.m1, 2))));
         r.chunk = std::min<int64_t>(a.N1, std::max<int64_t>((a.N1 + nchunk - 1) / nchunk, 2 * a.n1));
         if (launch_adj_row(r, s) != cudaSuccess) return SWDFT_ERR_CUDA;
     }
@@ -742,24 +777,40 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
                 }
             }
         }
+        // fused form (n1 <= 32): one kernel, timed as a whole against the two passes
+        float best = best_row + best_col;
+        if (ok && a.m1 <= 5) {
+            for (int nc : {4, 8, 16}) {
+                TreeConfig c = best_c;
+                c.fused = true;
+                c.col_groups = 1;
+                c.col_chunk = col_chunk_for(a, nc);
+                float ms = 0.f;
+                ok = time_pass(c, 2, &ms);
+                if (!ok) break;
+                if (ms < best) {
+                    best = ms;
+                    best_c = c;
+                }
+            }
+        }
         if (!ok) {
             a.cfg = base;
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             return SWDFT_ERR_CUDA;
         }
-        const float best = best_row + best_col;
         a.cfg = best_c;
         a.tuned = true;
         if (const char *path = std::getenv("SWDFT_TUNE_CACHE")) {
             if (FILE *f = std::fopen(path, "a")) {
                 std::fprintf(f,
                              "{\"N0\": %lld, \"N1\": %lld, \"n0\": %d, \"n1\": %d, \"dtype\": %d, "
-                             "\"row_B\": %d, \"row_chunk\": %lld, \"col_B\": %d, \"col_chunk\": %lld, "
-                             "\"col_groups\": %d, \"ms\": %.6f}\n",
-                             (long long)a.N0, (long long)a.N1, a.n0, a.n1, a.dtype, best_c.row_B,
-                             (long long)best_c.row_chunk, best_c.col_B, (long long)best_c.col_chunk,
-                             best_c.col_groups, best);
+                             "\"fused\": %d, \"row_B\": %d, \"row_chunk\": %lld, \"col_B\": %d, "
+                             "\"col_chunk\": %lld, \"col_groups\": %d, \"ms\": %.6f}\n",
+                             (long long)a.N0, (long long)a.N1, a.n0, a.n1, a.dtype, (int)best_c.fused,
+                             best_c.row_B, (long long)best_c.row_chunk, best_c.col_B,
+                             (long long)best_c.col_chunk, best_c.col_groups, best);
                 std::fclose(f);
             }
         }

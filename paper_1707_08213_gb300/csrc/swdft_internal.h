@@ -145,6 +145,22 @@ int col_tree_clamp_groups(int m0, int B, int groups);
 int col_tree_blocks_per_sm(int m0, int B, int groups);
 cudaError_t launch_col_tree(const ColTreeArgs &a, cudaStream_t s);
 
+// Fused tree, n1 <= 32: one kernel evaluates the row levels of each z row inside the column
+// tile (a warp per 32 channels) and the column levels as col_tree does; z never reaches HBM.
+struct FusedTreeArgs {
+    const void *x = nullptr;  // first input row of the band
+    int64_t ld = 0;
+    int cplx = 0;
+    int64_t P1 = 0, rows_out = 0;
+    int m0 = 0, m1 = 0;
+    float2 *out = nullptr;
+    float scale = 1.f;
+    const float2 *om64 = nullptr;
+    int64_t chunk = 0;
+    int groups = 1;
+};
+cudaError_t launch_fused_tree(const FusedTreeArgs &a, cudaStream_t s);
+
 // Adjoint of the column levels: gz[r][q1][k1] = scale * sum_{j0,k0} G[r-j0][q1][k0][k1] w_{n0}^{+j0 k0}
 // for the rows_out + n0 - 1 z rows of a band (G holds rows_out window rows).
 struct AdjColArgs {

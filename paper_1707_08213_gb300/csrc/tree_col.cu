@@ -6,7 +6,7 @@
 
 namespace swdft {
 
-int col_tree_clamp_B(int m0, int B) { return std::max(0, std::min(B, std::min(m0, 3))); }
+int col_tree_clamp_B(int m0, int B) { return clamp_split(m0, B); }
 
 int col_tree_clamp_groups(int m0, int B, int groups) {
     // at most 256 threads and a ring within the default 48 KB of dynamic shared memory
@@ -64,6 +64,46 @@ cudaError_t launch_col_tree(const ColTreeArgs &a, cudaStream_t s) {
 #undef F
         default:
             return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int fused_col_B(int m0) { return m0 >= 6 ? 3 : std::min(m0, 2); }
+
+cudaError_t launch_fused_tree(const FusedTreeArgs &a, cudaStream_t s) {
+    const int64_t nch = a.P1 << a.m1;
+    if (a.rows_out <= 0 || nch <= 0) return cudaSuccess;
+    if (a.m0 < 0 || a.m0 > kMaxLog2 || a.m1 < 0 || a.m1 > 5 || a.rows_out > INT32_MAX || a.P1 > INT32_MAX)
+        return cudaErrorInvalidValue;
+    FusedParams p;
+    p.g.z = nullptr;
+    p.g.out = a.out;
+    p.g.nch = nch;
+    p.g.orow = nch << a.m0;
+    p.g.rows_out = (int)a.rows_out;
+    p.g.chunk = (int)std::min<int64_t>(a.chunk > 0 ? a.chunk : a.rows_out, a.rows_out);
+    p.g.m1 = a.m1;
+    p.g.scale = a.scale;
+    const int B = fused_col_B(a.m0);
+    p.g.groups = col_tree_clamp_groups(a.m0, B, a.groups);
+    p.x = a.x;
+    p.ld = a.ld;
+    p.zrows = (int)(a.rows_out + (int64_t(1) << a.m0) - 1);
+    p.P1 = (int)a.P1;
+    for (int j = 0; j < kMaxN; ++j) p.om.w[j] = a.om64[j];
+    const int64_t per_block = 32LL * p.g.groups;
+    dim3 grid((unsigned)((nch + per_block - 1) / per_block), (unsigned)((a.rows_out + p.g.chunk - 1) / p.g.chunk));
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    dim3 block(32 * (1 << B) * p.g.groups);
+    switch (a.m0) {
+        case 0: fused_launch_mb<0, 0>(p, a.m1, a.cplx, grid, block, s); break;
+        case 1: fused_launch_mb<1, 1>(p, a.m1, a.cplx, grid, block, s); break;
+        case 2: fused_launch_mb<2, 2>(p, a.m1, a.cplx, grid, block, s); break;
+        case 3: fused_launch_mb<3, 2>(p, a.m1, a.cplx, grid, block, s); break;
+        case 4: fused_launch_mb<4, 2>(p, a.m1, a.cplx, grid, block, s); break;
+        case 5: fused_launch_mb<5, 2>(p, a.m1, a.cplx, grid, block, s); break;
+        case 6: fused_launch_mb<6, 3>(p, a.m1, a.cplx, grid, block, s); break;
+        default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }

@@ -4,7 +4,7 @@
 namespace swdft {
 
 #define F(M_, B_) SWDFT_COL_INSTANTIATE(M_, B_)
-F(6, 0) F(6, 1) F(6, 2) F(6, 3)
+F(6, 2) F(6, 3)
 #undef F
 
 }  // namespace swdft

@@ -115,14 +115,98 @@ __device__ __forceinline__ void cp_async_8(void *smem, const void *gmem, bool va
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// z rows for a column tile come from one of two stages:
+//  * ZStageLoad  : cp.async copies of z rows written by the row pass (two-pass form);
+//  * ZStageRowDft: the row levels of Eq. rowfswft2d evaluated in the tile itself (fused
+//                  form, n1 <= 32): z never goes to HBM.
+// fetch(ring, r_lo, r_hi, CH, ch0, RD) fills ring rows r_lo..r_hi-1; wait() completes it.
+struct ZStageLoad {
+    const float2 *z;
+    int64_t nch;
+    __device__ __forceinline__ void fetch(float2 *ring, int r_lo, int r_hi, int CH, int64_t ch0, int RD) {
+        const int total = (r_hi - r_lo) * CH;
+        for (int e = threadIdx.x; e < total; e += blockDim.x) {
+            const int rr = r_lo + e / CH;
+            const int cc = e - (e / CH) * CH;
+            const bool ok = ch0 + cc < nch;
+            const float2 *src = z + (int64_t)rr * nch + (ok ? ch0 + cc : 0);
+            cp_async_8(&ring[(rr & (RD - 1)) * CH + cc], src, ok);
+        }
+        cp_async_commit();
+    }
+    __device__ __forceinline__ void wait() { cp_async_wait_all(); }
+};
+
+// Row levels of one z row for 32 channels, by one warp.  Channels are (q1, k1) with k1
+// fastest, so the warp covers 32 >> M1 window columns q1.  Level t of the tree under the
+// window ending at column p needs level t-1 at p and p - s_t (s_t = 2^(M1-t)); for one
+// window that is 2^(M1-t) positions x 2^t nodes = n1 values per level, one per lane:
+// lane (i, d) holds node i at position p - d.  Each level is two shuffles and one node
+// evaluation T = T_{t-1}(p - d - s_t) + W_t^i T_{t-1}(p - d) per lane; level M1 leaves node
+// k1 = lane on lane k1, in natural order.
+template <int M1, bool CPLX>
+struct ZStageRowDft {
+    const void *x;      // first input row of the band
+    int64_t ld;
+    int zrows;          // z rows that exist (band rows + n0 - 1)
+    int P1;
+    float2 w[M1 > 0 ? M1 : 1];  // this lane's twiddle per level
+
+    __device__ __forceinline__ void init(const float2 *om64) {
+        const int l = threadIdx.x & ((1 << M1) - 1);
+#pragma unroll
+        for (int t = 1; t <= M1; ++t) {
+            const int i = l >> (M1 - t);
+            w[t - 1] = om64[i << (6 - t)];
+        }
+    }
+
+    __device__ __forceinline__ float2 row_dft(int r, int64_t ch0) const {
+        const int lane = threadIdx.x & 31;
+        const int l = lane & ((1 << M1) - 1);
+        const int base = lane - l;
+        const int64_t q1 = (ch0 >> M1) + (lane >> M1);
+        float2 v = make_float2(0.f, 0.f);
+        if (r >= 0 && r < zrows && q1 < P1) {
+            const int64_t col = q1 + (1 << M1) - 1 - l;  // level 0 on lane d: x at p - d
+            if constexpr (CPLX)
+                v = __ldg(reinterpret_cast<const float2 *>(x) + (int64_t)r * ld + col);
+            else
+                v = make_float2(__ldg(reinterpret_cast<const float *>(x) + (int64_t)r * ld + col), 0.f);
+        }
+#pragma unroll
+        for (int t = 1; t <= M1; ++t) {
+            const int i = l >> (M1 - t), d = l & ((1 << (M1 - t)) - 1);
+            const int src = base + ((i & ((1 << (t - 1)) - 1)) << (M1 - t + 1)) + d;  // node i mod 2^(t-1), offset d
+            const float cx = __shfl_sync(0xffffffffu, v.x, src);
+            const float cy = __shfl_sync(0xffffffffu, v.y, src);
+            const float sx = __shfl_sync(0xffffffffu, v.x, src + (1 << (M1 - t)));  // offset d + s_t
+            const float sy = __shfl_sync(0xffffffffu, v.y, src + (1 << (M1 - t)));
+            v = c_add(make_float2(sx, sy), c_mul(w[t - 1], make_float2(cx, cy)));
+        }
+        return v;
+    }
+
+    __device__ __forceinline__ void fetch(float2 *ring, int r_lo, int r_hi, int CH, int64_t ch0, int RD) {
+        const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+        const int groups = CH >> 5;
+        for (int e = warp; e < (r_hi - r_lo) * groups; e += nwarp) {
+            const int rr = r_lo + e / groups, g = e - (e / groups) * groups;
+            ring[(rr & (RD - 1)) * CH + g * 32 + (threadIdx.x & 31)] = row_dft(rr, ch0 + g * 32);
+        }
+    }
+    __device__ __forceinline__ void wait() {}
+};
+
 // Column pass, one block tile.  Thread = (channel ch = q1*n1 + k1, residue c, chunk of
 // window rows).  Warp w of a block takes residue w mod 2^B (uniform per warp) and channel
-// group w / 2^B.  The tile's z rows arrive in a shared-memory ring by cp.async one step group
-// ahead of use; all residue warps read the same staged rows.  One __syncthreads per step
-// group, no spin-waits; the tile ends with a barrier, so the ring is free for the next tile.
-template <int M, int B>
-__device__ __forceinline__ void col_tile(const ColGeom &p, int64_t ch_block, int chunk_idx,
-                                         const float2 *om64, float2 *ring) {
+// group w / 2^B.  The tile's z rows reach a shared-memory ring one step group ahead of use
+// (copied or computed by the stage); all residue warps read the same staged rows.  One
+// __syncthreads per step group, no spin-waits; the tile ends with a barrier, so the ring is
+// free for the next tile.
+template <int M, int B, class Stage>
+__device__ __forceinline__ void col_tile_impl(const ColGeom &p, int64_t ch_block, int chunk_idx,
+                                              const float2 *om64, float2 *ring, Stage &stage) {
     using Tree = SlidingTree<M, B>;
     constexpr int R = 1 << B;
     constexpr int n = 1 << M;
@@ -144,20 +228,6 @@ __device__ __forceinline__ void col_tile(const ColGeom &p, int64_t ch_block, int
     const int zr_end = qb + n - 1;                      // one past the last z row used
     const bool active = ch < p.nch;
 
-    // stage z rows [r_lo, r_hi) of this tile's channels into the ring
-    auto fetch = [&](int r_lo, int r_hi) {
-        r_hi = min(r_hi, zr_end);
-        const int total = (r_hi - r_lo) * CH;
-        for (int e = threadIdx.x; e < total; e += blockDim.x) {
-            const int rr = r_lo + e / CH;
-            const int cc = e - (e / CH) * CH;
-            const bool ok = ch0 + cc < p.nch;
-            const float2 *src = p.z + (int64_t)rr * p.nch + (ok ? ch0 + cc : 0);
-            cp_async_8(&ring[(rr & (RD - 1)) * CH + cc], src, ok);
-        }
-        cp_async_commit();
-    };
-
     const int n1 = 1 << p.m1;
     const int64_t q1 = ch >> p.m1;
     const int64_t k1 = ch & (n1 - 1);
@@ -167,11 +237,11 @@ __device__ __forceinline__ void col_tile(const ColGeom &p, int64_t ch_block, int
 
     Tree tree;
     tree.init(c, om64);
-    fetch(qa - kH, qa + kP);
-    cp_async_wait_all();
+    stage.fetch(ring, qa - kH, min(qa + kP, zr_end), CH, ch0, RD);
+    stage.wait();
     __syncthreads();
     for (int jb = 0; jb < steps; jb += kP) {
-        if (jb + kP < steps) fetch(qa + jb + kP, qa + jb + 2 * kP);
+        if (jb + kP < steps) stage.fetch(ring, qa + jb + kP, min(qa + jb + 2 * kP, zr_end), CH, ch0, RD);
         static_for<0, kP>([&](auto JJ) {
             constexpr int J = decltype(JJ)::value;
             const int j = jb + J;
@@ -188,9 +258,16 @@ __device__ __forceinline__ void col_tile(const ColGeom &p, int64_t ch_block, int
                 }
             }
         });
-        cp_async_wait_all();
+        stage.wait();
         __syncthreads();
     }
+}
+
+template <int M, int B>
+__device__ __forceinline__ void col_tile(const ColGeom &p, int64_t ch_block, int chunk_idx,
+                                         const float2 *om64, float2 *ring) {
+    ZStageLoad stage{p.z, p.nch};
+    col_tile_impl<M, B>(p, ch_block, chunk_idx, om64, ring, stage);
 }
 
 template <int M, int B>
@@ -199,8 +276,31 @@ __global__ void __launch_bounds__(256, 2) col_tree_kernel(const __grid_constant_
     col_tile<M, B>(p.g, blockIdx.x, blockIdx.y, p.om.w, ring);
 }
 
+// Fused form: both level groups in one kernel, x in, window DFTs out.
+struct FusedParams {
+    ColGeom g;          // g.z unused
+    const void *x;      // first input row of the band
+    int64_t ld;
+    int zrows, P1;
+    Omega64 om;
+};
+
+template <int M0, int B, int M1, bool CPLX>
+__global__ void __launch_bounds__(256, 2) fused_tree_kernel(const __grid_constant__ FusedParams p) {
+    extern __shared__ float2 ring[];
+    ZStageRowDft<M1, CPLX> stage;
+    stage.x = p.x;
+    stage.ld = p.ld;
+    stage.zrows = p.zrows;
+    stage.P1 = p.P1;
+    stage.init(p.om.w);
+    col_tile_impl<M0, B>(p.g, blockIdx.x, blockIdx.y, p.om.w, ring, stage);
+}
+
 template <int M, int B>
 void row_launch_mb(const RowParams &p, int cplx, dim3 g, dim3 b, cudaStream_t s);
+template <int M0, int B>
+void fused_launch_mb(const FusedParams &p, int m1, int cplx, dim3 g, dim3 b, cudaStream_t s);
 template <int M, int B>
 void col_launch_mb(const ColParams &p, dim3 g, dim3 b, cudaStream_t s);
 template <int M, int B>
@@ -231,10 +331,36 @@ int col_blocks_per_sm(int threads, int groups);
         return nb;                                                                        \
     }
 
-// (M, B) pairs with B <= min(M, 3)
+#define SWDFT_FUSED_INSTANTIATE(M_, B_)                                                          \
+    template <>                                                                                  \
+    void fused_launch_mb<M_, B_>(const FusedParams &p, int m1, int cplx, dim3 g, dim3 b,         \
+                                 cudaStream_t s) {                                               \
+        const size_t smem = sizeof(float2) * col_ring_rows(M_) * 32 * p.g.groups;               \
+        switch (m1 * 2 + cplx) {                                                                 \
+            case 0: fused_tree_kernel<M_, B_, 0, false><<<g, b, smem, s>>>(p); break;            \
+            case 1: fused_tree_kernel<M_, B_, 0, true><<<g, b, smem, s>>>(p); break;             \
+            case 2: fused_tree_kernel<M_, B_, 1, false><<<g, b, smem, s>>>(p); break;            \
+            case 3: fused_tree_kernel<M_, B_, 1, true><<<g, b, smem, s>>>(p); break;             \
+            case 4: fused_tree_kernel<M_, B_, 2, false><<<g, b, smem, s>>>(p); break;            \
+            case 5: fused_tree_kernel<M_, B_, 2, true><<<g, b, smem, s>>>(p); break;             \
+            case 6: fused_tree_kernel<M_, B_, 3, false><<<g, b, smem, s>>>(p); break;            \
+            case 7: fused_tree_kernel<M_, B_, 3, true><<<g, b, smem, s>>>(p); break;             \
+            case 8: fused_tree_kernel<M_, B_, 4, false><<<g, b, smem, s>>>(p); break;            \
+            case 9: fused_tree_kernel<M_, B_, 4, true><<<g, b, smem, s>>>(p); break;             \
+            case 10: fused_tree_kernel<M_, B_, 5, false><<<g, b, smem, s>>>(p); break;           \
+            case 11: fused_tree_kernel<M_, B_, 5, true><<<g, b, smem, s>>>(p); break;            \
+            default: break;                                                                      \
+        }                                                                                        \
+    }
+
+// (M, B) pairs built: B <= min(M, 3), and B >= 2 for 64-point trees (fewer threads per tree
+// would need more registers than there are; launchers raise B to 2 there)
 #define SWDFT_MB_CASES(F)                                                              \
     F(0, 0) F(1, 0) F(1, 1) F(2, 0) F(2, 1) F(2, 2) F(3, 0) F(3, 1) F(3, 2) F(3, 3)     \
-    F(4, 0) F(4, 1) F(4, 2) F(4, 3) F(5, 0) F(5, 1) F(5, 2) F(5, 3) F(6, 0) F(6, 1)     \
-    F(6, 2) F(6, 3)
+    F(4, 0) F(4, 1) F(4, 2) F(4, 3) F(5, 0) F(5, 1) F(5, 2) F(5, 3) F(6, 2) F(6, 3)
+
+__host__ __device__ constexpr int clamp_split(int M, int B) {
+    return B < 0 ? 0 : (B > M ? M : (B > 3 ? 3 : (M >= 6 && B < 2 ? 2 : B)));
+}
 
 }  // namespace swdft

@@ -20,8 +20,7 @@ cudaError_t launch_row_tree(const RowTreeArgs &a, cudaStream_t s) {
     p.g.chunk = (int)std::min<int64_t>(a.chunk > 0 ? a.chunk : a.P1, a.P1);
     p.g.z = a.z;
     for (int j = 0; j < kMaxN; ++j) p.om.w[j] = a.om64[j];
-    int B = a.B < 0 ? 0 : a.B;
-    B = std::min(B, std::min(a.m1, 3));
+    const int B = clamp_split(a.m1, a.B);
     const int threads = 128;
     const int rows_per_block = threads >> B;
     dim3 grid((unsigned)((a.rows + rows_per_block - 1) / rows_per_block),

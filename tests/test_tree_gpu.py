@@ -79,9 +79,9 @@ def test_default_config_every_coefficient(sw, N0, N1, n0, n1, cplx):
     assert_close_to_oracle(a, x, n0, n1)
 
 
-# (row_B, row_chunk, col_B, col_chunk, col_groups): splits of 1..8 threads per tree and
-# chunks that leave ragged tails
-CONFIGS = [(0, 0, 0, 0, 1), (1, 3, 1, 5, 2), (2, 7, 3, 2, 1), (3, 1, 2, 1, 4), (2, 11, 1, 9, 8)]
+# (row_B, row_chunk, col_B, col_chunk, col_groups, fused): splits of 1..8 threads per tree,
+# chunks that leave ragged tails, two-pass and fused forms
+CONFIGS = [(0, 0, 0, 0, 1, 0), (1, 3, 1, 5, 2, 0), (2, 7, 3, 2, 1, 0), (3, 1, 2, 1, 4, 1), (2, 11, 1, 9, 8, 1)]
 
 
 @pytest.mark.parametrize("cfg", CONFIGS)
@@ -210,3 +210,21 @@ def test_sinusoids_512_full_size(sw):
 def test_complex_1024x2048_full_size(sw):
     wl = workloads.complex_1024x2048()
     _full_size_check(sw, wl.images[0], 16, 64, count=2048, seed=12)
+
+
+FUSED_SHAPES = [(41, 67, 8, 16, False), (61, 35, 32, 4, True), (90, 75, 64, 8, False),
+                (70, 100, 16, 32, True), (100, 100, 32, 32, False), (23, 50, 1, 32, False),
+                (50, 23, 32, 1, True), (9, 9, 8, 8, False)]
+
+
+@pytest.mark.parametrize("chunk", [0, 5])
+@pytest.mark.parametrize("N0,N1,n0,n1,cplx", FUSED_SHAPES)
+def test_fused_tree_matches_oracle_and_two_pass(sw, N0, N1, n0, n1, cplx, chunk):
+    """Row levels evaluated inside the column kernel: the same node arithmetic as the
+    two-pass tree, so results are bit-identical to it and within tolerance of the oracle."""
+    x = workloads.random_array(300 + N0 + N1, N0, N1, complex_input=cplx)
+    two, _ = run_gpu(sw, x, n0, n1, cfg=(2, 0, 2, chunk, 1, 0))
+    fused, t = run_gpu(sw, x, n0, n1, cfg=(2, 0, 2, chunk, 1, 1))
+    assert t.plan.launch_count() == 1
+    assert torch.equal(two, fused)
+    assert_close_to_oracle(fused, x, n0, n1)
