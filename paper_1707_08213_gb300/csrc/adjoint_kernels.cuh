@@ -77,24 +77,34 @@ __global__ void __launch_bounds__(128) adj_col_kernel(const __grid_constant__ Ad
     const int kstride = R * n1;
     const float s = p.scale;
 
+    // G for step j: the window ending at z row p_hi - j (zeros where none ends there)
+    auto load_g = [&](int j, float2 (&u)[Tree::kIn]) {
+        const int q0 = p_hi - j - (n - 1);
+        if (active && j < steps && q0 >= 0 && q0 < p.rows_out) {
+            const float2 *g = gbase + (int64_t)q0 * grow;
+#pragma unroll
+            for (int t = 0; t < Tree::kIn; ++t) u[t] = __ldcs(g + t * kstride);
+        } else {
+#pragma unroll
+            for (int t = 0; t < Tree::kIn; ++t) u[t] = make_float2(0.f, 0.f);
+        }
+    };
+
     Tree tree;
     tree.init(c, p.om64);
+    // software pipeline: the loads of step j+1 are in flight while step j computes
+    float2 nxt[Tree::kIn];
+    load_g(0, nxt);
     for (int jb = 0; jb < steps; jb += Tree::kPeriod) {
         static_for<0, Tree::kPeriod>([&](auto JJ) {
             constexpr int J = decltype(JJ)::value;
             const int j = jb + J;
             if (j < steps) {
-                const int r = p_hi - j;        // z row (window end row) of this step
-                const int q0 = r - (n - 1);    // the window ending here
+                const int r = p_hi - j;  // z row (window end row) of this step
                 float2 u[Tree::kIn];
-                if (active && q0 >= 0 && q0 < p.rows_out) {
-                    const float2 *g = gbase + (int64_t)q0 * grow;
 #pragma unroll
-                    for (int t = 0; t < Tree::kIn; ++t) u[t] = c_scale(s, __ldcs(g + t * kstride));
-                } else {
-#pragma unroll
-                    for (int t = 0; t < Tree::kIn; ++t) u[t] = make_float2(0.f, 0.f);
-                }
+                for (int t = 0; t < Tree::kIn; ++t) u[t] = c_scale(s, nxt[t]);
+                load_g(j + 1, nxt);
                 const float2 y = reduce_residues<R>(tree.template step<J>(u));
                 if (c == 0 && active && r < rb) p.gz[(int64_t)r * p.nch + ch] = y;
             }

@@ -87,6 +87,13 @@ struct swdft2d_plan_s {
     bool configured = false;
     int sm_count = 152;
     GraphCache graph;
+    // several arrays (not persistent): up to kConc of them run concurrently on plan-owned
+    // streams forked from and joined back to the caller's stream, one workspace slot each
+    int conc = 1;
+    size_t slot_bytes = 0;
+    cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // persistent batch (SWDFT_FLAG_PERSISTENT): per-array z offsets in the workspace, the
     // tile descriptors (pinned staging + device copy, allocated at the first execute)
     std::vector<size_t> z_off;
@@ -156,6 +163,13 @@ swdft_status configure(swdft2d_plan_t plan) {
     plan->sm_count = sms > 0 ? sms : 152;
     for (auto &a : plan->arrays)
         if (!a.tuned) default_config(a, plan->sm_count);
+    if (plan->conc > 1) {
+        if (cudaEventCreateWithFlags(&plan->fork_ev, cudaEventDisableTiming) != cudaSuccess) return SWDFT_ERR_CUDA;
+        for (int k = 0; k < plan->conc; ++k) {
+            if (cudaStreamCreateWithFlags(&plan->side[k], cudaStreamNonBlocking) != cudaSuccess) return SWDFT_ERR_CUDA;
+            if (cudaEventCreateWithFlags(&plan->join_ev[k], cudaEventDisableTiming) != cudaSuccess) return SWDFT_ERR_CUDA;
+        }
+    }
     if (plan->flags & SWDFT_FLAG_PERSISTENT) {
         const size_t bytes = sizeof(BatchImage) * plan->arrays.size();
         if (cudaHostAlloc((void **)&plan->desc_host, bytes, cudaHostAllocDefault) != cudaSuccess) return SWDFT_ERR_OOM;
@@ -335,14 +349,39 @@ cudaError_t enqueue_forward(const swdft2d_plan_s *plan, const ArrayPlan &a, cons
     return launch_col_tree(c, s);
 }
 
+// Run body(i, stream, workspace slot) for every array: on the caller's stream when the plan
+// has one array, else forked over the plan's side streams and joined back to s.
+template <class Body>
+swdft_status for_each_array(swdft2d_plan_t plan, void *ws, cudaStream_t s, Body body) {
+    const size_t n = plan->arrays.size();
+    if (plan->conc <= 1) {
+        for (size_t i = 0; i < n; ++i)
+            if (body(i, s, ws) != cudaSuccess) return SWDFT_ERR_CUDA;
+        return SWDFT_OK;
+    }
+    if (cudaEventRecord(plan->fork_ev, s) != cudaSuccess) return SWDFT_ERR_CUDA;
+    for (int k = 0; k < plan->conc; ++k)
+        if (cudaStreamWaitEvent(plan->side[k], plan->fork_ev, 0) != cudaSuccess) return SWDFT_ERR_CUDA;
+    swdft_status st = SWDFT_OK;
+    for (size_t i = 0; i < n && st == SWDFT_OK; ++i) {
+        const int k = (int)(i % plan->conc);
+        void *slot = static_cast<char *>(ws) + (size_t)k * plan->slot_bytes;
+        if (body(i, plan->side[k], slot) != cudaSuccess) st = SWDFT_ERR_CUDA;
+    }
+    // always join every side stream back (a capture must end with all streams joined)
+    for (int k = 0; k < plan->conc; ++k) {
+        if (cudaEventRecord(plan->join_ev[k], plan->side[k]) != cudaSuccess) st = SWDFT_ERR_CUDA;
+        if (cudaStreamWaitEvent(s, plan->join_ev[k], 0) != cudaSuccess) st = SWDFT_ERR_CUDA;
+    }
+    return st;
+}
+
 swdft_status enqueue_all(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out,
                          void *ws, cudaStream_t s, int stages = 3) {
-    for (size_t i = 0; i < plan->arrays.size(); ++i) {
+    return for_each_array(plan, ws, s, [&](size_t i, cudaStream_t st, void *slot) {
         const ArrayPlan &a = plan->arrays[i];
-        if (enqueue_forward(plan, a, d_in[i], d_out[i], ws, a.q_begin, a.q_end, s, stages) != cudaSuccess)
-            return SWDFT_ERR_CUDA;
-    }
-    return SWDFT_OK;
+        return enqueue_forward(plan, a, d_in[i], d_out[i], slot, a.q_begin, a.q_end, st, stages);
+    });
 }
 
 swdft_status check_buffers(swdft2d_plan_t plan, const void *const *in, void *const *out,
@@ -452,8 +491,11 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
             ws += align_up(a.z_bytes(a.band_rows()));
         }
     } else {
-        // arrays run one after another on one stream, so they share one z buffer
+        // up to four arrays run at once (plan-owned streams), each with its own z slot
         for (const auto &a : p->arrays) ws = std::max(ws, align_up(a.ws_bytes_for(a.band_rows(), a.algo)));
+        p->conc = (int)std::min<size_t>(4, p->arrays.size());
+        p->slot_bytes = ws;
+        ws *= (size_t)p->conc;
     }
     p->ws_bytes = ws;
     *out = p;
@@ -602,22 +644,22 @@ swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_g
     if (plan->ws_bytes > 0 && (!d_workspace || (uintptr_t)d_workspace % kAlign != 0)) return SWDFT_ERR_WORKSPACE;
     swdft_status st = configure(plan);
     if (st != SWDFT_OK) return st;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    for (size_t i = 0; i < plan->arrays.size(); ++i) {
+    cudaStream_t s0 = static_cast<cudaStream_t>(stream);
+    return for_each_array(plan, d_workspace, s0, [&](size_t i, cudaStream_t s, void *slot) -> cudaError_t {
         const ArrayPlan &a = plan->arrays[i];
         const int64_t zrows = a.band_rows() + a.n0 - 1;
         const size_t row_bytes = (size_t)a.N1 * a.in_elem();
         char *gx = static_cast<char *>(d_grad_in[i]);
+        cudaError_t e;
         // rows no window of the band touches get a zero gradient
-        if (a.q_begin > 0 && cudaMemsetAsync(gx, 0, (size_t)a.q_begin * row_bytes, s) != cudaSuccess)
-            return SWDFT_ERR_CUDA;
+        if (a.q_begin > 0 && (e = cudaMemsetAsync(gx, 0, (size_t)a.q_begin * row_bytes, s)) != cudaSuccess) return e;
         const int64_t tail = a.N0 - (a.q_begin + zrows);
-        if (tail > 0 && cudaMemsetAsync(gx + (size_t)(a.q_begin + zrows) * row_bytes, 0,
-                                        (size_t)tail * row_bytes, s) != cudaSuccess)
-            return SWDFT_ERR_CUDA;
+        if (tail > 0 && (e = cudaMemsetAsync(gx + (size_t)(a.q_begin + zrows) * row_bytes, 0,
+                                             (size_t)tail * row_bytes, s)) != cudaSuccess)
+            return e;
         AdjColArgs c;
         c.G = static_cast<const float2 *>(d_grad_out[i]);
-        c.gz = static_cast<float2 *>(d_workspace);
+        c.gz = static_cast<float2 *>(slot);
         c.P1 = a.P1;
         c.rows_out = a.band_rows();
         c.m0 = a.m0;
@@ -626,9 +668,9 @@ swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_g
         c.om64 = plan->om64;
         c.B = 0;  // the launcher uses the one split built per window side
         c.chunk = std::min(zrows, std::max<int64_t>((zrows + 7) / 8, 2 * a.n0));
-        if (launch_adj_col(c, s) != cudaSuccess) return SWDFT_ERR_CUDA;
+        if ((e = launch_adj_col(c, s)) != cudaSuccess) return e;
         AdjRowArgs r;
-        r.gz = static_cast<const float2 *>(d_workspace);
+        r.gz = static_cast<const float2 *>(slot);
         r.gx = gx + (size_t)a.q_begin * row_bytes;
         r.ld_out = a.N1;
         r.cplx = a.dtype == SWDFT_C64;
@@ -640,9 +682,8 @@ swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_g
         const int64_t target = (int64_t)plan->sm_count * 1024;
         const int64_t nchunk = std::max<int64_t>(1, target / std::max<int64_t>(1, zrows << (a.m1 >= 6 ? 3 : std::min(a.m1, 2))));
         r.chunk = std::min<int64_t>(a.N1, std::max<int64_t>((a.N1 + nchunk - 1) / nchunk, 2 * a.n1));
-        if (launch_adj_row(r, s) != cudaSuccess) return SWDFT_ERR_CUDA;
-    }
-    return SWDFT_OK;
+        return launch_adj_row(r, s);
+    });
 }
 
 swdft_status swdft2d_execute_host(swdft2d_plan_t plan, const void *const *h_in,
@@ -835,6 +876,11 @@ swdft_status swdft2d_destroy(swdft2d_plan_t plan) {
         cudaEventDestroy(plan->desc_uploaded);
     }
     if (plan->desc_host) cudaFreeHost(plan->desc_host);
+    for (int k = 0; k < 4; ++k) {
+        if (plan->side[k]) cudaStreamDestroy(plan->side[k]);
+        if (plan->join_ev[k]) cudaEventDestroy(plan->join_ev[k]);
+    }
+    if (plan->fork_ev) cudaEventDestroy(plan->fork_ev);
     if (plan->desc_dev) cudaFree(plan->desc_dev);
     if (plan->desc_graph) cudaFree(plan->desc_graph);
     if (plan->io_ready) {
