@@ -97,12 +97,18 @@ struct swdft2d_plan_s {
     // persistent batch (SWDFT_FLAG_PERSISTENT): per-array z offsets in the workspace, the
     // tile descriptors (pinned staging + device copy, allocated at the first execute)
     std::vector<size_t> z_off;
-    BatchImage *desc_host = nullptr;
-    BatchImage *desc_dev = nullptr;    // used by direct executes
-    BatchImage *desc_graph = nullptr;  // owned by the captured graph (fixed buffers)
+    // descriptor buffers: BatchImage[n], then the row-group entries, then the column-group
+    // entries (each group contiguous); pinned staging, a direct-execute copy, a graph copy
+    unsigned char *desc_host = nullptr;
+    unsigned char *desc_dev = nullptr;
+    unsigned char *desc_graph = nullptr;
+    size_t desc_bytes = 0;
     cudaEvent_t desc_uploaded = nullptr;
-    int64_t row_items = 0, col_items = 0;
-    int64_t row_slots = 0, col_slots = 0;
+    // per window exponent m: entries [off, off + n) of the group, its tile count, grid slots
+    int row_off[kMaxLog2 + 1] = {}, row_n[kMaxLog2 + 1] = {};
+    int col_off[kMaxLog2 + 1] = {}, col_n[kMaxLog2 + 1] = {};
+    int64_t row_items[kMaxLog2 + 1] = {}, col_items[kMaxLog2 + 1] = {};
+    int64_t row_slots[kMaxLog2 + 1] = {}, col_slots[kMaxLog2 + 1] = {};
     // host-buffer pipeline (SWDFT_FLAG_HOST_IO), allocated at the first execute_host
     bool io_ready = false;
     int64_t io_band = 0;
@@ -171,15 +177,19 @@ swdft_status configure(swdft2d_plan_t plan) {
         }
     }
     if (plan->flags & SWDFT_FLAG_PERSISTENT) {
-        const size_t bytes = sizeof(BatchImage) * plan->arrays.size();
-        if (cudaHostAlloc((void **)&plan->desc_host, bytes, cudaHostAllocDefault) != cudaSuccess) return SWDFT_ERR_OOM;
-        if (cudaMalloc((void **)&plan->desc_dev, bytes) != cudaSuccess) return SWDFT_ERR_OOM;
-        if (cudaMalloc((void **)&plan->desc_graph, bytes) != cudaSuccess) return SWDFT_ERR_OOM;
+        const size_t n = plan->arrays.size();
+        plan->desc_bytes = sizeof(BatchImage) * n + 2 * sizeof(BatchClassEntry) * n;
+        if (cudaHostAlloc((void **)&plan->desc_host, plan->desc_bytes, cudaHostAllocDefault) != cudaSuccess)
+            return SWDFT_ERR_OOM;
+        if (cudaMalloc((void **)&plan->desc_dev, plan->desc_bytes) != cudaSuccess) return SWDFT_ERR_OOM;
+        if (cudaMalloc((void **)&plan->desc_graph, plan->desc_bytes) != cudaSuccess) return SWDFT_ERR_OOM;
         if (cudaEventCreateWithFlags(&plan->desc_uploaded, cudaEventDisableTiming) != cudaSuccess) return SWDFT_ERR_CUDA;
-        int row_bps = 0, col_bps = 0;
-        if (batch_blocks_per_sm(&row_bps, &col_bps) != cudaSuccess) return SWDFT_ERR_CUDA;
-        plan->row_slots = (int64_t)plan->sm_count * std::max(1, row_bps);
-        plan->col_slots = (int64_t)plan->sm_count * std::max(1, col_bps);
+        for (int m = 0; m <= kMaxLog2; ++m) {
+            int row_bps = 0, col_bps = 0;
+            if (batch_blocks_per_sm(m, &row_bps, &col_bps) != cudaSuccess) return SWDFT_ERR_CUDA;
+            plan->row_slots[m] = (int64_t)plan->sm_count * std::max(1, row_bps);
+            plan->col_slots[m] = (int64_t)plan->sm_count * std::max(1, col_bps);
+        }
     }
     plan->configured = true;
     return SWDFT_OK;
@@ -188,14 +198,16 @@ swdft_status configure(swdft2d_plan_t plan) {
 // Fill the pinned batch descriptors for these buffers.  The caller makes sure no pending
 // copy still reads them.
 void fill_batch(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out, void *ws) {
-    int64_t row_items = 0, col_items = 0;
-    for (size_t i = 0; i < plan->arrays.size(); ++i) {
+    const size_t n = plan->arrays.size();
+    BatchImage *imgs = reinterpret_cast<BatchImage *>(plan->desc_host);
+    BatchClassEntry *row_ent = reinterpret_cast<BatchClassEntry *>(imgs + n);
+    BatchClassEntry *col_ent = row_ent + n;
+    for (size_t i = 0; i < n; ++i) {
         const ArrayPlan &a = plan->arrays[i];
         BatchImage d;
         std::memset(&d, 0, sizeof(d));
         float2 *z = reinterpret_cast<float2 *>(static_cast<char *>(ws) + plan->z_off[i]) + a.z_pad() * a.P1 * a.n1;
         const int64_t zrows = a.band_rows() + a.n0 - 1;
-        const int rowB = batch_row_B(a.m1);
         d.row.x = static_cast<const char *>(d_in[i]);
         d.row.ld = a.ld;
         d.row.r_base = a.q_begin;
@@ -204,7 +216,6 @@ void fill_batch(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out
         d.row.P1 = (int)a.P1;
         d.row.chunk = (int)std::min<int64_t>(a.P1, std::max<int64_t>(1, a.cfg.row_chunk));
         d.row.z = z;
-        const int colB = batch_col_B(a.m0);
         d.col.z = z;
         d.col.out = static_cast<float2 *>(d_out[i]);
         d.col.nch = a.P1 * a.n1;
@@ -217,21 +228,78 @@ void fill_batch(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out
         d.m0 = a.m0;
         d.m1 = a.m1;
         d.cplx = a.dtype == SWDFT_C64;
-        const int rows_per_block = 256 >> rowB;
+        const int rows_per_block = 128 >> batch_row_B(a.m1);
         d.row_blocks = (int)((zrows + rows_per_block - 1) / rows_per_block);
         d.row_chunks = (int)((a.P1 + d.row.chunk - 1) / d.row.chunk);
         const int64_t ch_per_block = 32LL * d.col.groups;
         d.col_blocks = (int)((d.col.nch + ch_per_block - 1) / ch_per_block);
         d.col_chunks = (int)((a.band_rows() + d.col.chunk - 1) / d.col.chunk);
-        (void)colB;
-        d.row_item0 = row_items;
-        d.col_item0 = col_items;
-        row_items += (int64_t)d.row_blocks * d.row_chunks;
-        col_items += (int64_t)d.col_blocks * d.col_chunks;
-        plan->desc_host[i] = d;
+        imgs[i] = d;
     }
-    plan->row_items = row_items;
-    plan->col_items = col_items;
+    // group the arrays by window exponent, in array order within a group
+    int pos = 0;
+    for (int m = 0; m <= kMaxLog2; ++m) {
+        plan->row_off[m] = pos;
+        int64_t items = 0;
+        for (size_t i = 0; i < n; ++i)
+            if (imgs[i].m1 == m) {
+                row_ent[pos].item0 = items;
+                row_ent[pos].img = (int)i;
+                row_ent[pos].pad = 0;
+                items += (int64_t)imgs[i].row_blocks * imgs[i].row_chunks;
+                ++pos;
+            }
+        plan->row_n[m] = pos - plan->row_off[m];
+        plan->row_items[m] = items;
+    }
+    pos = 0;
+    for (int m = 0; m <= kMaxLog2; ++m) {
+        plan->col_off[m] = pos;
+        int64_t items = 0;
+        for (size_t i = 0; i < n; ++i)
+            if (imgs[i].m0 == m) {
+                col_ent[pos].item0 = items;
+                col_ent[pos].img = (int)i;
+                col_ent[pos].pad = 0;
+                items += (int64_t)imgs[i].col_blocks * imgs[i].col_chunks;
+                ++pos;
+            }
+        plan->col_n[m] = pos - plan->col_off[m];
+        plan->col_items[m] = items;
+    }
+}
+
+// Launch every row group, join, then every column group, join: groups run concurrently on
+// the plan's side streams.  Only event records/waits and kernel launches (capturable).
+swdft_status launch_batch(swdft2d_plan_t plan, const unsigned char *desc, cudaStream_t s) {
+    const size_t n = plan->arrays.size();
+    const BatchImage *imgs = reinterpret_cast<const BatchImage *>(desc);
+    const BatchClassEntry *row_ent = reinterpret_cast<const BatchClassEntry *>(imgs + n);
+    const BatchClassEntry *col_ent = row_ent + n;
+    for (int phase = 0; phase < 2; ++phase) {
+        const bool col = phase == 1;
+        if (cudaEventRecord(plan->fork_ev, s) != cudaSuccess) return SWDFT_ERR_CUDA;
+        for (int k = 0; k < plan->conc; ++k)
+            if (cudaStreamWaitEvent(plan->side[k], plan->fork_ev, 0) != cudaSuccess) return SWDFT_ERR_CUDA;
+        swdft_status st = SWDFT_OK;
+        int k = 0;
+        for (int m = 0; m <= kMaxLog2 && st == SWDFT_OK; ++m) {
+            const int cnt = col ? plan->col_n[m] : plan->row_n[m];
+            if (cnt == 0) continue;
+            const BatchClassEntry *ent = col ? col_ent + plan->col_off[m] : row_ent + plan->row_off[m];
+            if (launch_batch_class(col, m, imgs, ent, cnt, col ? plan->col_items[m] : plan->row_items[m],
+                                   plan->om64, col ? plan->col_slots[m] : plan->row_slots[m],
+                                   plan->side[k % plan->conc]) != cudaSuccess)
+                st = SWDFT_ERR_CUDA;
+            ++k;
+        }
+        for (int j = 0; j < plan->conc; ++j) {
+            if (cudaEventRecord(plan->join_ev[j], plan->side[j]) != cudaSuccess) st = SWDFT_ERR_CUDA;
+            if (cudaStreamWaitEvent(s, plan->join_ev[j], 0) != cudaSuccess) st = SWDFT_ERR_CUDA;
+        }
+        if (st != SWDFT_OK) return st;
+    }
+    return SWDFT_OK;
 }
 
 // Direct (non-graph) persistent execute: refill the staging once its previous upload ran,
@@ -240,14 +308,10 @@ swdft_status enqueue_batch(swdft2d_plan_t plan, const void *const *d_in, void *c
                            void *ws, cudaStream_t s) {
     if (cudaEventSynchronize(plan->desc_uploaded) != cudaSuccess) return SWDFT_ERR_CUDA;
     fill_batch(plan, d_in, d_out, ws);
-    if (cudaMemcpyAsync(plan->desc_dev, plan->desc_host, sizeof(BatchImage) * plan->arrays.size(),
-                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+    if (cudaMemcpyAsync(plan->desc_dev, plan->desc_host, plan->desc_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return SWDFT_ERR_CUDA;
     if (cudaEventRecord(plan->desc_uploaded, s) != cudaSuccess) return SWDFT_ERR_CUDA;
-    if (launch_batch_tree(plan->desc_dev, (int)plan->arrays.size(), plan->row_items, plan->col_items,
-                          plan->om64, plan->row_slots, plan->col_slots, s) != cudaSuccess)
-        return SWDFT_ERR_CUDA;
-    return SWDFT_OK;
+    return launch_batch(plan, plan->desc_dev, s);
 }
 
 // Enqueue the forward transform of output rows [q_lo, q_hi) of array a.
@@ -485,11 +549,13 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
     make_omega(kMaxN, p->om64);
     size_t ws = 0;
     if (flags & SWDFT_FLAG_PERSISTENT) {
-        // one launch covers every array, so each array has its own z region
+        // one launch covers every array, so each array has its own z region; the window
+        // groups' kernels run on up to four side streams
         for (const auto &a : p->arrays) {
             p->z_off.push_back(ws);
             ws += align_up(a.z_bytes(a.band_rows()));
         }
+        p->conc = 4;
     } else {
         // up to four arrays run at once (plan-owned streams), each with its own z slot
         for (const auto &a : p->arrays) ws = std::max(ws, align_up(a.ws_bytes_for(a.band_rows(), a.algo)));
@@ -529,7 +595,15 @@ swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t 
     // forward: row + column pass per array, or the two persistent passes for the whole batch;
     // adjoint: column + row adjoint pass per array
     if (!adjoint && (plan->flags & SWDFT_FLAG_PERSISTENT)) {
-        *launches = 2;
+        // one persistent kernel per row-window group and per column-window group
+        bool r[kMaxLog2 + 1] = {}, c[kMaxLog2 + 1] = {};
+        for (const auto &a : plan->arrays) {
+            r[a.m1] = true;
+            c[a.m0] = true;
+        }
+        int32_t k = 0;
+        for (int m = 0; m <= kMaxLog2; ++m) k += (int)r[m] + (int)c[m];
+        *launches = k;
         return SWDFT_OK;
     }
     int32_t n = 0;
@@ -553,10 +627,7 @@ swdft_status swdft2d_execute(swdft2d_plan_t plan, const void *const *d_in, void 
     // these buffers go to the graph's own device buffer before capture
     auto enqueue = [&]() {
         if (!persistent) return enqueue_all(plan, d_in, d_out, d_workspace, s);
-        return launch_batch_tree(plan->desc_graph, (int)plan->arrays.size(), plan->row_items,
-                                 plan->col_items, plan->om64, plan->row_slots, plan->col_slots, s) == cudaSuccess
-                   ? SWDFT_OK
-                   : SWDFT_ERR_CUDA;
+        return launch_batch(plan, plan->desc_graph, s);
     };
 
     // CUDA graph: capture the launch sequence once per (buffers, stream), replay after.
@@ -574,8 +645,7 @@ swdft_status swdft2d_execute(swdft2d_plan_t plan, const void *const *d_in, void 
             // stream: re-capture is rare, so wait for the whole device
             if (cudaDeviceSynchronize() != cudaSuccess) return SWDFT_ERR_CUDA;
             fill_batch(plan, d_in, d_out, d_workspace);
-            if (cudaMemcpy(plan->desc_graph, plan->desc_host, sizeof(BatchImage) * plan->arrays.size(),
-                           cudaMemcpyHostToDevice) != cudaSuccess)
+            if (cudaMemcpy(plan->desc_graph, plan->desc_host, plan->desc_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
                 return SWDFT_ERR_CUDA;
         }
         cudaGraph_t graph = nullptr;

@@ -42,15 +42,14 @@ struct ColGeom {
     float scale;
 };
 
-// One array of a persistent batch launch.  Work items are numbered image by image:
-// row items [row_item0, row_item0 + row_blocks * row_chunks) and likewise for columns.
+// One array of a persistent batch launch: its geometry and how its row and column passes
+// are cut into block tiles (row tiles = row_blocks x row_chunks, column tiles likewise).
 struct BatchImage {
     RowGeom row;
     ColGeom col;
     int m0, m1, cplx;
-    int row_blocks, row_chunks;  // row pass: blocks of (256 >> B) rows x chunks of columns
+    int row_blocks, row_chunks;  // row pass: blocks of (128 >> B) rows x chunks of columns
     int col_blocks, col_chunks;  // column pass: blocks of 32 * groups channels x row chunks
-    int64_t row_item0, col_item0;
 };
 
 // Tensor-core column levels: out[q0][q1][k0][k1] = scale * sum_j0 z[q0+j0][ch] F0[j0][k0]
@@ -92,14 +91,19 @@ cudaError_t launch_tc_row(const TcRowArgs &a, cudaStream_t s);
 // Device error word of the tensor-core kernels (1 = a bounded wait timed out).
 cudaError_t tc_status(int *status, bool reset);
 
-// Persistent launch over every (image, tile) of a batch: one pass over all row tiles, then
-// one over all column tiles (stream order separates them).  d_images: device copy of the
-// descriptors; each pass runs min(items, slots) blocks, slots = SMs x resident blocks
-// (batch_blocks_per_sm).  No other CUDA call than the two launches (capturable).
-cudaError_t launch_batch_tree(const BatchImage *d_images, int nimg, int64_t row_items,
-                              int64_t col_items, const float2 *om64, int64_t row_slots,
-                              int64_t col_slots, cudaStream_t s);
-cudaError_t batch_blocks_per_sm(int *row_bps, int *col_bps);
+// One array of a window-exponent group in a persistent batch launch: item0 = the group's
+// first tile of this array (tiles are numbered array by array within the group).
+struct BatchClassEntry {
+    int64_t item0;
+    int img;
+    int pad;
+};
+// Persistent launch over every tile of one group (col = false: row tiles of the arrays with
+// n1 = 2^m; true: column tiles of those with n0 = 2^m).  grid = min(items, slots), slots =
+// SMs x resident blocks (batch_blocks_per_sm).  No CUDA call besides the launch (capturable).
+cudaError_t launch_batch_class(bool col, int m, const BatchImage *d_images, const BatchClassEntry *ent, int nent,
+                               int64_t nitems, const float2 *om64, int64_t slots, cudaStream_t s);
+cudaError_t batch_blocks_per_sm(int m, int *row_bps, int *col_bps);
 // Launch choices the batch kernels use for a window side of 2^m.
 int batch_row_B(int m1);
 int batch_col_B(int m0);
