@@ -12,6 +12,9 @@ Contents (plain C in ``swdft2d_oracle.c`` / ``swdft2d_tree_ref.c``, loaded throu
 * :func:`swdft2d_adjoint` / :func:`swdft2d_adjoint_pixels` -- the explicit adjoint A^H.
 * :func:`tree2d` -- the paper's tree (Section 4.2 equations, Section 4.3 loop order) in
   FP64 or FP32, with the node-operation count of Eq. windowops and level dumps.
+* :func:`swdftkd` / :func:`swdftkd_windows` -- the k-dimensional transform of Section 4.4
+  (k <= 4) by its definition, direct or axis by axis (``swdftkd_oracle.c``).
+* :func:`treekd` -- the tree of Eq. kdfswft in FP64, with its node-operation count.
 
 Arrays are numpy; outputs are complex128 with layout [q0][q1][k0][k1], where window q
 covers rows q0..q0+n0-1 and columns q1..q1+n1-1 (the paper's window end p = q + n - 1).
@@ -29,7 +32,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["swdft2d_oracle.c", "swdft2d_tree_ref.c"]
+_SOURCES = ["swdft2d_oracle.c", "swdft2d_tree_ref.c", "swdftkd_oracle.c"]
 _lib = None
 
 NORMS = ("unitary", "none", "inv_n")
@@ -69,9 +72,12 @@ def _load():
     lib.swo_swdft2d_adjoint_pixels.argtypes = [P, i64, i64, i32, i32, d, i64, P, P, i32, P]
     lib.swt_tree2d_f64.argtypes = [P, i64, i64, i32, i32, d, P, P, i32, P, i32]
     lib.swt_tree2d_f32.argtypes = [P, i64, i64, i32, i32, ctypes.c_float, P, P, i32, P, i32]
+    lib.swo_swdftkd.argtypes = [P, i32, P, P, d, i32, i32, P]
+    lib.swo_swdftkd_windows.argtypes = [P, i32, P, P, d, i32, i64, P, i32, P]
+    lib.swt_treekd_f64.argtypes = [P, i32, P, P, d, P, P]
     for f in ("swo_swdft2d", "swo_swdft2d_windows", "swo_swdft2d_adjoint",
               "swo_swdft2d_adjoint_pixels", "swt_tree2d_f64", "swt_tree2d_f32",
-              "swo_openmp_available"):
+              "swo_openmp_available", "swo_swdftkd", "swo_swdftkd_windows", "swt_treekd_f64"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -198,3 +204,60 @@ def tree2d(x, n0: int, n1: int, norm: str = "unitary", precision: str = "f64",
             None if dump is None else _ptr(dump), threads)
     _check(rc, "tree2d")
     return out, int(ops.value), dump
+
+
+# ------------------------------------------------------------------ k dimensions (Section 4.4)
+
+MAX_DIMS = 4
+
+
+def scale_for_kd(norm: str, n: Sequence[int]) -> float:
+    """Eq. 2's scale in k dimensions: 1/sqrt(prod n) ("unitary"), 1, or 1/prod n."""
+    nn = int(np.prod(n))
+    return {"unitary": 1.0 / math.sqrt(nn), "none": 1.0, "inv_n": 1.0 / nn}[norm]
+
+
+def _kd_args(x, n):
+    xs = _as_c128(x)
+    K = xs.ndim
+    if K < 1 or K > MAX_DIMS or len(n) != K:
+        raise ValueError("need 1..4 dimensions and one window length per dimension")
+    N = np.ascontiguousarray(xs.shape, dtype=np.int64)
+    nw = np.ascontiguousarray(n, dtype=np.int32)
+    if np.any(nw < 1) or np.any(nw > N):
+        raise ValueError("window larger than the array")
+    return xs, K, N, nw
+
+
+def swdftkd(x, n: Sequence[int], norm: str = "unitary", method: str = "direct",
+            threads: int = 1) -> np.ndarray:
+    """All windows of a k-dimensional array: (P_0..P_{k-1}, n_0..n_{k-1}) complex128."""
+    xs, K, N, nw = _kd_args(x, n)
+    P = tuple(int(a - b + 1) for a, b in zip(N, nw))
+    out = np.empty(P + tuple(int(v) for v in nw), dtype=np.complex128)
+    _check(_load().swo_swdftkd(_ptr(xs), K, _ptr(N), _ptr(nw), scale_for_kd(norm, nw),
+                               _METHODS[method], threads, _ptr(out)), "swdftkd")
+    return out
+
+
+def swdftkd_windows(x, n: Sequence[int], qs, norm: str = "unitary", method: str = "separable",
+                    threads: int = 1) -> np.ndarray:
+    """Selected windows, qs of shape (count, k) first samples -> (count, n_0..) complex128."""
+    xs, K, N, nw = _kd_args(x, n)
+    q = np.ascontiguousarray(qs, dtype=np.int64).reshape(-1, K)
+    out = np.empty((q.shape[0],) + tuple(int(v) for v in nw), dtype=np.complex128)
+    _check(_load().swo_swdftkd_windows(_ptr(xs), K, _ptr(N), _ptr(nw), scale_for_kd(norm, nw),
+                                       _METHODS[method], q.shape[0], _ptr(q), threads,
+                                       _ptr(out)), "swdftkd_windows")
+    return out
+
+
+def treekd(x, n: Sequence[int], norm: str = "unitary"):
+    """The tree of Eq. kdfswft in FP64.  Returns (out, opcount) like :func:`swdftkd`."""
+    xs, K, N, nw = _kd_args(x, n)
+    P = tuple(int(a - b + 1) for a, b in zip(N, nw))
+    out = np.empty(P + tuple(int(v) for v in nw), dtype=np.complex128)
+    ops = ctypes.c_int64(0)
+    _check(_load().swt_treekd_f64(_ptr(xs), K, _ptr(N), _ptr(nw), scale_for_kd(norm, nw),
+                                  _ptr(out), ctypes.byref(ops)), "treekd")
+    return out, int(ops.value)
