@@ -355,6 +355,43 @@ def adjoint_measurement(torch, sw):
     return res
 
 
+def volume_measurement(torch, sw):
+    """128^3 float32, 8x8x8 windows: the k-dimensional transform (k = 3) per step."""
+    import workloads
+    x, n = workloads.volume_128()
+    t = sw.TransformKD(x.shape, n, dtype=sw.R32)
+    xd = torch.from_numpy(x).cuda()
+    out = t.empty_output()
+    coeffs = out.numel()
+    N, P = x.shape, out.shape[:3]
+    # bytes each pass must move at least: x in; z after dimension 2's levels and z after
+    # dimension 1's levels each written once and read once; the output written once
+    z2 = 8 * N[0] * N[1] * P[2] * n[2]
+    z1 = 8 * N[0] * P[1] * n[1] * P[2] * n[2]
+    floor = 4 * x.size + 2 * (z2 + z1) + 8 * coeffs
+    for _ in range(3):
+        t.forward(xd, out)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    steps = 10
+    e0.record()
+    for _ in range(steps):
+        t.forward(xd, out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    res = {"workload": "volume_128: 128^3 f32 N(0,1) (seed 5), 8x8x8 windows, 121^3 positions",
+           "coeffs_per_step": coeffs, "launches": t.plan.launch_count(),
+           "l2": "output 7.26 GB per step, larger than L2",
+           "ms_per_step": round(ms, 4), "value": coeffs / (ms / 1e3),
+           "output_gbs": round(8 * coeffs / (ms / 1e3) / 1e9, 1),
+           "traffic_floor_bytes": floor,
+           "traffic_floor_gbs": round(floor / (ms / 1e3) / 1e9, 1)}
+    del t, xd, out
+    torch.cuda.empty_cache()
+    return res
+
+
 # ----------------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -455,7 +492,8 @@ def run_ours(args):
             extra["tensor_core"] = tc_comparison(torch, sw, xd, flush, ms_per_step)
         except Exception as e:  # noqa: BLE001
             extra["tensor_core"] = {"error": str(e)}
-        for key, fn in (("batch", batch_measurement), ("adjoint", adjoint_measurement)):
+        for key, fn in (("batch", batch_measurement), ("adjoint", adjoint_measurement),
+                        ("volume", volume_measurement)):
             try:
                 extra[key] = fn(torch, sw)
             except Exception as e:  # noqa: BLE001

@@ -9,7 +9,8 @@ C ABI of ``include/swdft2d.h``.  PyTorch supplies device memory and streams only
     a = sw.swdft2d(x_cuda, 32, 32)        # (P0, P1, n0, n1) complex64
 
 Output layout is [q0][q1][k0][k1] with q_i the window's first row/column; the default
-scale is Eq. 2's 1/sqrt(n0 n1).
+scale is Eq. 2's 1/sqrt(n0 n1).  ``TransformKD`` / ``swdftkd`` give the k-dimensional
+transform of Section 4.4 (k <= 4) through ``include/swdftkd.h``.
 """
 from __future__ import annotations
 
@@ -19,10 +20,11 @@ import torch
 
 from . import _native
 from ._native import (ALGOS, C64, FLAG_GRAPH, FLAG_HOST_IO, FLAG_PERSISTENT, NORMS, R32, Plan,
-                      SwdftError, status_string, version)
+                      PlanKD, SwdftError, status_string, version)
 
 __all__ = ["swdft2d", "swdft2d_adjoint", "Transform", "Plan", "SwdftError", "SWDFT2dFunction",
-           "status_string", "version", "FLAG_GRAPH", "FLAG_HOST_IO", "FLAG_PERSISTENT"]
+           "status_string", "version", "FLAG_GRAPH", "FLAG_HOST_IO", "FLAG_PERSISTENT",
+           "TransformKD", "PlanKD", "swdftkd"]
 
 
 def _dtype_code(x: torch.Tensor) -> int:
@@ -143,3 +145,49 @@ class SWDFT2dFunction(torch.autograd.Function):
     def backward(ctx, grad):
         N0, N1, cplx, n0, n1, norm = ctx.shape
         return swdft2d_adjoint(grad, N0, N1, complex_input=cplx, norm=norm), None, None, None
+
+
+class TransformKD:
+    """A k-dimensional plan (Section 4.4, k <= 4) plus its workspace on one CUDA device."""
+
+    def __init__(self, N: Sequence[int], n: Sequence[int], dtype: int = R32,
+                 norm: str = "unitary", device=None):
+        self.plan = PlanKD(N, n, dtype=dtype, norm=norm)
+        self.N, self.n, self.dtype = tuple(int(v) for v in N), tuple(int(v) for v in n), dtype
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        ws = self.plan.workspace_size()
+        self.workspace = torch.empty(max(ws, 1), dtype=torch.uint8, device=self.device)
+        self._ws_ptr = self.workspace.data_ptr() if ws > 0 else 0
+
+    def output_shape(self):
+        return self.plan.output_shape()
+
+    def empty_output(self):
+        return torch.empty(self.output_shape(), dtype=torch.complex64, device=self.device)
+
+    def forward(self, x: torch.Tensor, out: torch.Tensor = None) -> torch.Tensor:
+        if not x.is_cuda or x.device != self.device or tuple(x.shape) != self.N \
+                or _dtype_code(x) != self.dtype or not x.is_contiguous():
+            raise ValueError("input does not match the planned shape/dtype/device or is not contiguous")
+        out = self.empty_output() if out is None else out
+        if tuple(out.shape) != self.output_shape() or out.dtype != torch.complex64 \
+                or not out.is_contiguous() or out.device != self.device:
+            raise ValueError("output must be a contiguous complex64 tensor of the output shape")
+        self.plan.execute(x.data_ptr(), out.data_ptr(), self._ws_ptr, _stream_ptr(self.device))
+        return out
+
+
+_CACHE_KD: Dict[tuple, TransformKD] = {}
+
+
+def swdftkd(x: torch.Tensor, n: Sequence[int], norm: str = "unitary") -> torch.Tensor:
+    """k-dimensional sliding window DFT of one CUDA array (k = x.dim() <= 4)
+    -> (P_0, .., P_{k-1}, n_0, .., n_{k-1}) complex64."""
+    x = x.contiguous()
+    key = (x.device, tuple(x.shape), x.dtype, tuple(n), norm)
+    t = _CACHE_KD.get(key)
+    if t is None:
+        t = TransformKD(tuple(x.shape), n, dtype=_dtype_code(x), norm=norm, device=x.device)
+        _CACHE_KD[key] = t
+    return t.forward(x)

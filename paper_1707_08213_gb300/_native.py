@@ -1,4 +1,5 @@
-"""ctypes binding of the C ABI in include/swdft2d.h (argument marshalling only).
+"""ctypes binding of the C ABI in include/swdft2d.h and include/swdftkd.h (argument
+marshalling only).
 
 Every step of the transform runs in the CUDA library ``_lib/libswdft2d.so``; this module
 only converts Python values to the plain pointers and sizes the ABI takes.  There is no
@@ -31,14 +32,17 @@ ALGOS = {"auto": 0, "tree": 1, "tc_bf16x3": 2, "tc_bf16": 3, "tc_f16_scaled": 4,
 ALGO_NAMES = {v: k for k, v in ALGOS.items()}
 FLAG_GRAPH, FLAG_HOST_IO, FLAG_PERSISTENT = 1, 2, 4
 
-# every symbol include/swdft2d.h declares
+# every symbol include/swdft2d.h and include/swdftkd.h declare
 EXPORTS = (
     "swdft2d_plan", "swdft2d_output_shape", "swdft2d_workspace_size", "swdft2d_get_algo",
     "swdft2d_execute", "swdft2d_execute_adjoint", "swdft2d_execute_host", "swdft2d_autotune",
     "swdft2d_launch_count", "swdft2d_destroy", "swdft2d_status_string", "swdft2d_version",
     "swdft2d_execute_stage", "swdft2d_set_tree_config", "swdft2d_execute_static_scratch",
     "swdft2d_check_device",
+    "swdftkd_plan", "swdftkd_output_shape", "swdftkd_workspace_size", "swdftkd_launch_count",
+    "swdftkd_execute", "swdftkd_destroy",
 )
+KD_MAX_DIMS = 4
 
 
 class SwdftError(RuntimeError):
@@ -52,6 +56,11 @@ class Shape(ctypes.Structure):
                 ("n0", ctypes.c_int32), ("n1", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("row_begin", ctypes.c_int64),
                 ("row_end", ctypes.c_int64)]
+
+
+class ShapeKD(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("N", ctypes.c_int64 * KD_MAX_DIMS), ("n", ctypes.c_int32 * KD_MAX_DIMS)]
 
 
 def _load() -> ctypes.CDLL:
@@ -78,6 +87,12 @@ def _load() -> ctypes.CDLL:
         "swdft2d_destroy": ([P], i32),
         "swdft2d_status_string": ([i32], ctypes.c_char_p),
         "swdft2d_version": ([], i32),
+        "swdftkd_plan": ([ctypes.POINTER(P), ctypes.POINTER(ShapeKD), i32, u32], i32),
+        "swdftkd_output_shape": ([P, ctypes.POINTER(i64)], i32),
+        "swdftkd_workspace_size": ([P, ctypes.POINTER(ctypes.c_size_t)], i32),
+        "swdftkd_launch_count": ([P, ctypes.POINTER(i32)], i32),
+        "swdftkd_execute": ([P, P, P, P, P], i32),
+        "swdftkd_destroy": ([P], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -213,3 +228,67 @@ def raw_plan(shapes: Sequence[dict], norm: int, pos: int, algo: int, flags: int)
     h = ctypes.c_void_p()
     st = lib.swdft2d_plan(ctypes.byref(h), len(shapes), arr, norm, pos, algo, flags)
     return st, (h if h.value else None)
+
+
+def raw_plan_kd(N: Sequence[int], n: Sequence[int], dtype: int = R32, norm: int = 0,
+                flags: int = 0, k: Optional[int] = None):
+    """Call swdftkd_plan with raw values; returns (status, handle or None)."""
+    sh = ShapeKD()
+    sh.k = len(N) if k is None else int(k)
+    sh.dtype = int(dtype)
+    for d in range(min(len(N), KD_MAX_DIMS)):
+        sh.N[d] = int(N[d])
+        sh.n[d] = int(n[d])
+    h = ctypes.c_void_p()
+    st = lib.swdftkd_plan(ctypes.byref(h), ctypes.byref(sh), int(norm), int(flags))
+    return st, (h if h.value else None)
+
+
+class PlanKD:
+    """Owns one swdftkd plan (Section 4.4: the k-dimensional transform, k <= 4)."""
+
+    def __init__(self, N: Sequence[int], n: Sequence[int], dtype: int = R32,
+                 norm: str = "unitary"):
+        if len(N) != len(n) or not 1 <= len(N) <= KD_MAX_DIMS:
+            raise ValueError("need 1..4 dimensions and one window length per dimension")
+        st, h = raw_plan_kd(N, n, dtype, NORMS[norm])
+        _check(st, "swdftkd_plan")
+        self._h = h
+        self.k = len(N)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("plan destroyed")
+        return self._h
+
+    def output_shape(self):
+        out = (ctypes.c_int64 * (2 * KD_MAX_DIMS))()
+        _check(lib.swdftkd_output_shape(self.handle, out), "swdftkd_output_shape")
+        return tuple(int(v) for v in out[:2 * self.k])
+
+    def workspace_size(self) -> int:
+        v = ctypes.c_size_t()
+        _check(lib.swdftkd_workspace_size(self.handle, ctypes.byref(v)), "swdftkd_workspace_size")
+        return int(v.value)
+
+    def launch_count(self) -> int:
+        v = ctypes.c_int32()
+        _check(lib.swdftkd_launch_count(self.handle, ctypes.byref(v)), "swdftkd_launch_count")
+        return int(v.value)
+
+    def execute(self, in_ptr: int, out_ptr: int, ws_ptr: int, stream: int = 0):
+        _check(lib.swdftkd_execute(self.handle, ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
+                                   ctypes.c_void_p(ws_ptr or None), ctypes.c_void_p(stream or None)),
+               "swdftkd_execute")
+
+    def destroy(self):
+        if self._h is not None and self._h.value:
+            lib.swdftkd_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -37,9 +37,11 @@ struct ColGeom {
     int64_t orow;     // elements per output row = P1 * n0 * n1
     int rows_out;
     int chunk;        // window rows per thread
-    int m1;
+    int m1;           // log2 of the coefficients per window column (n1; prod n_e in kD)
     int groups;       // 32-channel groups per block
     float scale;
+    int64_t zslice;   // elements between slices of z / of the output (grid z, kD passes)
+    int64_t oslice;
 };
 
 // One array of a persistent batch launch: its geometry and how its row and column passes
@@ -128,6 +130,10 @@ struct RowTreeArgs {
 
 // Column levels (Eq. colfswft2d) of z, scaled and stored as the final output:
 //   out[q0][q1][k0][k1] = scale * sum_{j0<n0} z[q0 + j0][q1][k1] w_{n0}^{-j0 k0}
+// The same pass serves each earlier dimension of a k-dimensional transform (Eq. kdfswft):
+// there q1 runs over the window positions of all later dimensions, k1 over their
+// coefficients (m1 = the sum of their log2 lengths), and `slices` independent stacks of
+// z rows (the positions of all earlier dimensions) are processed by one launch.
 struct ColTreeArgs {
     const float2 *z = nullptr;  // (rows_out + n0 - 1) x P1 x n1
     int64_t P1 = 0;
@@ -139,7 +145,12 @@ struct ColTreeArgs {
     int B = 0;
     int64_t chunk = 0;          // output rows per thread (plus n0-1 warm-up steps)
     int groups = 1;             // 32-channel groups per block (block = 32 * 2^B * groups)
+    int64_t slices = 1;         // stacks of z rows; slice s reads z + s*z_slice and
+    int64_t z_slice = 0;        // writes out + s*out_slice (elements).  Rows before a
+    int64_t out_slice = 0;      // slice's first row must be readable (padding / previous slice).
 };
+// Largest m1 a column pass accepts (coefficient blocks of up to 2^18 per window column).
+constexpr int kMaxInnerLog2 = 18;
 
 cudaError_t launch_row_tree(const RowTreeArgs &a, cudaStream_t s);
 // Column-pass launch geometry: the B and groups a launch actually uses, and how many

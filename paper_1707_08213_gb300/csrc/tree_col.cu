@@ -33,10 +33,10 @@ int col_tree_blocks_per_sm(int m0, int B, int groups) {
 }
 
 cudaError_t launch_col_tree(const ColTreeArgs &a, cudaStream_t s) {
+    if (a.P1 < 0 || a.m1 < 0 || a.m1 > kMaxInnerLog2 || a.P1 > (INT64_MAX >> kMaxInnerLog2)) return cudaErrorInvalidValue;
     const int64_t nch = a.P1 << a.m1;
-    if (a.rows_out <= 0 || nch <= 0) return cudaSuccess;
-    if (a.m0 < 0 || a.m0 > kMaxLog2 || a.m1 < 0 || a.m1 > kMaxLog2 || a.rows_out > INT32_MAX)
-        return cudaErrorInvalidValue;
+    if (a.rows_out <= 0 || nch <= 0 || a.slices <= 0) return cudaSuccess;
+    if (a.m0 < 0 || a.m0 > kMaxLog2 || a.rows_out > INT32_MAX) return cudaErrorInvalidValue;
     ColParams p;
     p.g.z = a.z;
     p.g.out = a.out;
@@ -46,26 +46,38 @@ cudaError_t launch_col_tree(const ColTreeArgs &a, cudaStream_t s) {
     p.g.chunk = (int)std::min<int64_t>(a.chunk > 0 ? a.chunk : a.rows_out, a.rows_out);
     p.g.m1 = a.m1;
     p.g.scale = a.scale;
+    p.g.zslice = a.z_slice;
+    p.g.oslice = a.out_slice;
     const int B = col_tree_clamp_B(a.m0, a.B);
     const int groups = col_tree_clamp_groups(a.m0, B, a.groups);
     p.g.groups = groups;
     for (int j = 0; j < kMaxN; ++j) p.om.w[j] = a.om64[j];
     const int64_t per_block = 32LL * groups;
-    dim3 grid((unsigned)((nch + per_block - 1) / per_block),
-              (unsigned)((a.rows_out + p.g.chunk - 1) / p.g.chunk));
-    if (grid.y > 65535) return cudaErrorInvalidValue;
+    const int64_t gx = (nch + per_block - 1) / per_block;
+    const int64_t gy = (a.rows_out + p.g.chunk - 1) / p.g.chunk;
+    if (gy > 65535 || gx > INT32_MAX) return cudaErrorInvalidValue;
     dim3 block(32 * (1 << B) * groups);
-    switch (a.m0 * 8 + B) {
+    // slices beyond the grid's z limit go out as further launches with shifted bases
+    constexpr int64_t kMaxZ = 65535;
+    for (int64_t s0 = 0; s0 < a.slices; s0 += kMaxZ) {
+        const int64_t ns = std::min(kMaxZ, a.slices - s0);
+        p.g.z = a.z + s0 * a.z_slice;
+        p.g.out = a.out + s0 * a.out_slice;
+        dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)ns);
+        switch (a.m0 * 8 + B) {
 #define F(M_, B_)                                  \
     case M_ * 8 + B_:                              \
         col_launch_mb<M_, B_>(p, grid, block, s);  \
         break;
-        SWDFT_MB_CASES(F)
+            SWDFT_MB_CASES(F)
 #undef F
-        default:
-            return cudaErrorInvalidValue;
+            default:
+                return cudaErrorInvalidValue;
+        }
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 int fused_col_B(int m0) { return m0 >= 6 ? 3 : std::min(m0, 2); }
@@ -84,6 +96,8 @@ cudaError_t launch_fused_tree(const FusedTreeArgs &a, cudaStream_t s) {
     p.g.chunk = (int)std::min<int64_t>(a.chunk > 0 ? a.chunk : a.rows_out, a.rows_out);
     p.g.m1 = a.m1;
     p.g.scale = a.scale;
+    p.g.zslice = 0;
+    p.g.oslice = 0;
     const int B = fused_col_B(a.m0);
     p.g.groups = col_tree_clamp_groups(a.m0, B, a.groups);
     p.x = a.x;

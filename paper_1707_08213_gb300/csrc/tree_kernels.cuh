@@ -206,7 +206,8 @@ struct ZStageRowDft {
 // free for the next tile.
 template <int M, int B, class Stage>
 __device__ __forceinline__ void col_tile_impl(const ColGeom &p, int64_t ch_block, int chunk_idx,
-                                              const float2 *om64, float2 *ring, Stage &stage) {
+                                              const float2 *om64, float2 *ring, Stage &stage,
+                                              int64_t slice = 0) {
     using Tree = SlidingTree<M, B>;
     constexpr int R = 1 << B;
     constexpr int n = 1 << M;
@@ -232,7 +233,8 @@ __device__ __forceinline__ void col_tile_impl(const ColGeom &p, int64_t ch_block
     const int64_t q1 = ch >> p.m1;
     const int64_t k1 = ch & (n1 - 1);
     const int kstride = R * n1;  // elements between outputs t and t+1 (k0 step 2^B)
-    float2 *dst = p.out + (int64_t)qa * p.orow + q1 * ((int64_t)n * n1) + (int64_t)c * n1 + k1;
+    float2 *dst = p.out + slice * p.oslice + (int64_t)qa * p.orow + q1 * ((int64_t)n * n1) +
+                  (int64_t)c * n1 + k1;
     const float s = p.scale;
 
     Tree tree;
@@ -265,15 +267,16 @@ __device__ __forceinline__ void col_tile_impl(const ColGeom &p, int64_t ch_block
 
 template <int M, int B>
 __device__ __forceinline__ void col_tile(const ColGeom &p, int64_t ch_block, int chunk_idx,
-                                         const float2 *om64, float2 *ring) {
-    ZStageLoad stage{p.z, p.nch};
-    col_tile_impl<M, B>(p, ch_block, chunk_idx, om64, ring, stage);
+                                         const float2 *om64, float2 *ring, int64_t slice = 0) {
+    ZStageLoad stage{p.z + slice * p.zslice, p.nch};
+    col_tile_impl<M, B>(p, ch_block, chunk_idx, om64, ring, stage, slice);
 }
 
+// grid: x = 32-channel groups, y = chunks of window rows, z = slices (kD passes; 1 in 2D)
 template <int M, int B>
 __global__ void __launch_bounds__(256, 2) col_tree_kernel(const __grid_constant__ ColParams p) {
     extern __shared__ float2 ring[];  // col_ring_rows(M) x (32 * groups)
-    col_tile<M, B>(p.g, blockIdx.x, blockIdx.y, p.om.w, ring);
+    col_tile<M, B>(p.g, blockIdx.x, blockIdx.y, p.om.w, ring, blockIdx.z);
 }
 
 // Fused form: both level groups in one kernel, x in, window DFTs out.

@@ -1,5 +1,5 @@
 """Host-side checks of the C ABI (no GPU needed): the library loads, exports every symbol
-include/swdft2d.h declares, validates plans before any CUDA call, and reports the output
+include/*.h declare, validates plans before any CUDA call, and reports the output
 shape of Eq. 2 (P0 x P1 x n0 x n1) and its workspace."""
 import ctypes
 import json
@@ -9,7 +9,8 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "swdft2d.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if h.endswith(".h")]
 
 
 @pytest.fixture(scope="module")
@@ -21,9 +22,11 @@ def nat():
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(swdft2d_\w+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(swdft(?:2d|kd)_\w+)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_what_binding_lists(nat):
@@ -143,3 +146,42 @@ def test_twiddle_table_symmetry_via_plan(nat):
         n = 1 << m
         p = nat.Plan([shp(n + 3, n + 5, n, n)])
         assert p.output_shape(0) == (4, 6, n, n)
+
+
+# ------------------------------------------------------------------ k dimensions (swdftkd.h)
+
+@pytest.mark.parametrize("N,n,kw,status", [
+    ((), (), dict(k=0), -1),                          # no dimension
+    ((4,) * 5, (1,) * 5, dict(k=5), -1),              # more than four
+    ((8, 0, 8), (2, 1, 2), {}, -1),                   # empty extent
+    ((8, 8, 8), (2, 0, 2), {}, -1),                   # empty window
+    ((8, 8, 8), (2, 3, 2), {}, -2),                   # not a power of two
+    ((8, 8, 8), (2, 16, 2), {}, -3),                  # window larger than the array
+    ((200, 8, 8), (128, 2, 2), {}, -4),               # beyond the 64-point axis
+    ((8, 8, 8), (2, 2, 2), dict(dtype=7), -1),        # bad dtype
+    ((8, 8, 8), (2, 2, 2), dict(norm=3), -1),         # bad normalisation
+    ((8, 8, 8), (2, 2, 2), dict(flags=1), -4),        # no flags for kD plans
+])
+def test_kd_plan_validation(nat, N, n, kw, status):
+    st, h = nat.raw_plan_kd(N, n, **kw)
+    assert st == status
+    assert h is None
+
+
+def test_kd_output_shape_workspace_and_launches(nat):
+    N, n = (20, 24, 28), (4, 8, 2)
+    p = nat.PlanKD(N, n)
+    P = tuple(a - b + 1 for a, b in zip(N, n))
+    assert p.output_shape() == P + n
+    # z after the last dimension's levels: N0*N1 rows of P2*n2, with n1/2 look-back rows in
+    # front; after dimension 1's levels: N0 rows of P1*n1*P2*n2 with n0/2 rows in front
+    r = lambda b: (b + 255) // 256 * 256
+    c2 = P[2] * n[2]
+    c1 = P[1] * n[1] * c2
+    assert p.workspace_size() == r(8 * (n[1] // 2 + N[0] * N[1]) * c2) + r(8 * (n[0] // 2 + N[0]) * c1)
+    assert p.launch_count() == 3
+    assert nat.PlanKD((5, 6, 7, 8), (2, 2, 4, 8)).launch_count() == 4
+    # one and two dimensions run the 2D plan (two passes)
+    assert nat.PlanKD((30,), (8,)).output_shape() == (23, 8)
+    assert nat.PlanKD((30, 20), (8, 4)).output_shape() == (23, 17, 8, 4)
+    assert nat.PlanKD((30, 20), (8, 4)).launch_count() == 2

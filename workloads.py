@@ -18,6 +18,8 @@ hot path is specified on, each named for what it is:
                            seed 3; window per image from six shapes
 ``adjoint_batch_8``        8x256x256 float32 N(0,1), seed 4; 16x16 windows; loss mask
                            w ~ U[0,1) over (position, k0, k1) drawn after the images
+``volume_128``             128x128x128 float32 N(0,1), seed 5; 8x8x8 windows (the
+                           k-dimensional transform of Section 4.4, k = 3)
 =========================  ===========================================================
 """
 from __future__ import annotations
@@ -68,6 +70,27 @@ def random_array(seed: int, N0: int, N1: int, complex_input: bool = False,
         v = _real(rng, (2, N0, N1), dist)
         return (v[0] + 1j * v[1]).astype(np.complex64)
     return _real(rng, (N0, N1), dist).astype(np.float32)
+
+
+def random_array_kd(seed: int, shape, complex_input: bool = False,
+                    dist: str = "normal") -> np.ndarray:
+    """Seeded array of any rank (complex: real and imaginary parts as one (2, *shape) draw)."""
+    rng = np.random.default_rng(seed)
+    shape = tuple(int(v) for v in shape)
+    if complex_input:
+        v = _real(rng, (2,) + shape, dist)
+        return (v[0] + 1j * v[1]).astype(np.complex64)
+    return _real(rng, shape, dist).astype(np.float32)
+
+
+VOLUME_SHAPE = (128, 128, 128)
+VOLUME_WINDOW = (8, 8, 8)
+
+
+def volume_128() -> Tuple[np.ndarray, Tuple[int, int, int]]:
+    """128x128x128 float32 N(0,1) (seed 5) and its 8x8x8 window: 121^3 positions x 512
+    coefficients = 9.07e8 complex64 outputs (7.26 GB)."""
+    return random_array_kd(5, VOLUME_SHAPE), VOLUME_WINDOW
 
 
 def small_uniform_64() -> Workload:
@@ -167,6 +190,28 @@ def window_sq_norms(x: np.ndarray, n0: int, n1: int) -> np.ndarray:
 def window_sq_norms_at(x: np.ndarray, n0: int, n1: int, q0s, q1s) -> np.ndarray:
     xs = np.asarray(x, dtype=np.complex128)
     return np.array([np.sum(np.abs(xs[a:a + n0, b:b + n1]) ** 2) for a, b in zip(q0s, q1s)])
+
+
+def window_sq_norms_kd(x: np.ndarray, n) -> np.ndarray:
+    """||x_w||_2^2 for every window of a k-dimensional array (shape P_0..P_{k-1}), float64,
+    by a sliding sum along each axis in turn."""
+    a = np.abs(np.asarray(x, dtype=np.complex128)) ** 2
+    for ax, w in enumerate(n):
+        c = np.cumsum(a, axis=ax)
+        zero = np.zeros_like(np.take(c, [0], axis=ax))
+        c = np.concatenate([zero, c], axis=ax)
+        L = a.shape[ax] - w + 1
+        a = np.take(c, range(w, w + L), axis=ax) - np.take(c, range(0, L), axis=ax)
+    return a.clip(min=0.0)
+
+
+def window_sq_norms_kd_at(x: np.ndarray, n, qs) -> np.ndarray:
+    xs = np.asarray(x, dtype=np.complex128)
+    out = []
+    for q in np.asarray(qs).reshape(-1, xs.ndim):
+        sl = tuple(slice(int(a), int(a) + int(b)) for a, b in zip(q, n))
+        out.append(np.sum(np.abs(xs[sl]) ** 2))
+    return np.array(out)
 
 
 def normalised_error(a: np.ndarray, ref: np.ndarray, sq_norms: np.ndarray,
