@@ -96,11 +96,17 @@ __global__ void __launch_bounds__(128) row_tree_kernel(const __grid_constant__ R
     row_tile<M, B, CPLX>(p.g, blockIdx.x, blockIdx.y, p.om.w);
 }
 
+// Rows of z a column-pass block stages per step group: the tree's unroll period
+// (2^(M-2) steps) or 8, whichever is larger.  Short trees (n0 <= 16) would otherwise reach a
+// block barrier every one to four rows with as little fetched ahead; a group of several
+// periods keeps each FIFO slot a compile-time register, since every FIFO depth divides it.
+__host__ __device__ constexpr int col_group(int M) { return tg_period(M) > 8 ? tg_period(M) : 8; }
+
 // Rows of z staged in shared memory per column-pass block: a ring that holds the level-0
 // look-back (n/2 rows) plus two step groups (the group being computed and the one being
 // fetched), rounded up to a power of two.
 __host__ __device__ constexpr int col_ring_rows(int M) {
-    const int need = (M >= 1 ? (1 << (M - 1)) : 0) + 2 * tg_period(M);
+    const int need = (M >= 1 ? (1 << (M - 1)) : 0) + 2 * col_group(M);
     int r = 1;
     while (r < need) r <<= 1;
     return r;
@@ -211,7 +217,7 @@ __device__ __forceinline__ void col_tile_impl(const ColGeom &p, int64_t ch_block
     using Tree = SlidingTree<M, B>;
     constexpr int R = 1 << B;
     constexpr int n = 1 << M;
-    constexpr int kP = Tree::kPeriod;
+    constexpr int kP = col_group(M);  // steps per staged group, a multiple of Tree::kPeriod
     constexpr int kH = Tree::kHalf;
     constexpr int RD = col_ring_rows(M);
 
