@@ -35,7 +35,8 @@
  * Errors: every call returns a swdft_status; nothing aborts, exits or throws across the
  * ABI.  Argument checks happen before any CUDA call.  A CUDA launch or copy failure
  * returns SWDFT_ERR_CUDA; asynchronous faults surface at the next synchronising call.
- * Device kernels in this library contain no spin-waits.
+ * The only device-side waits are the tensor-core kernels' mbarrier waits; each gives up
+ * after a bounded number of polls and records it (see swdft2d_check_device).
  *
  * Threads and streams: a plan is immutable after swdft2d_plan except for its tuning
  * state, graph and staging buffers; do not execute one plan on two streams at once.
