@@ -392,6 +392,46 @@ def volume_measurement(torch, sw):
     return res
 
 
+def stream_measurement(torch, sw):
+    """Streaming form: 4096 rows of a 512-wide float32 array (seed 7), 32x32 windows, pushed
+    1, 32 or 256 rows at a time; each push emits the window rows it completes."""
+    import workloads
+    N0, N1, a0, a1 = 4096, 512, 32, 32
+    x = torch.from_numpy(workloads.random_array(7, N0, N1)).cuda()
+    P1 = N1 - a1 + 1
+    res = {"workload": "4096 x 512 float32 N(0,1) (seed 7) pushed in pieces, 32x32 windows"}
+    for R in (1, 32, 256):
+        st = sw.SlidingStream(N1, a0, a1, max_rows=R)
+        out = torch.empty((R, P1, a0, a1), dtype=torch.complex64, device=x.device)
+
+        def run():
+            st.reset()
+            rows = 0
+            for r in range(0, N0, R):
+                seen = min(r, a0 - 1)
+                nout = max(0, seen + R - (a0 - 1))
+                st.push(x[r:r + R], out[:nout])
+                rows += nout
+            return rows
+        run()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        wrows = run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        pushes = N0 // R
+        coeffs = wrows * P1 * a0 * a1
+        res[f"rows_per_push_{R}"] = {"pushes": pushes, "us_per_push": round(1e3 * ms / pushes, 2),
+                                     "coeffs_per_s": coeffs / (ms / 1e3),
+                                     "output_gbs": round(8 * coeffs / (ms / 1e3) / 1e9, 1)}
+        del st, out
+    torch.cuda.empty_cache()
+    return res
+
+
 # ----------------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -493,7 +533,7 @@ def run_ours(args):
         except Exception as e:  # noqa: BLE001
             extra["tensor_core"] = {"error": str(e)}
         for key, fn in (("batch", batch_measurement), ("adjoint", adjoint_measurement),
-                        ("volume", volume_measurement)):
+                        ("volume", volume_measurement), ("stream", stream_measurement)):
             try:
                 extra[key] = fn(torch, sw)
             except Exception as e:  # noqa: BLE001

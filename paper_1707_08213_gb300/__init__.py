@@ -10,7 +10,8 @@ C ABI of ``include/swdft2d.h``.  PyTorch supplies device memory and streams only
 
 Output layout is [q0][q1][k0][k1] with q_i the window's first row/column; the default
 scale is Eq. 2's 1/sqrt(n0 n1).  ``TransformKD`` / ``swdftkd`` give the k-dimensional
-transform of Section 4.4 (k <= 4) through ``include/swdftkd.h``.
+transform of Section 4.4 (k <= 4) through ``include/swdftkd.h``; ``SlidingStream`` the
+streaming form (rows pushed over time, ``include/swdftstream.h``).
 """
 from __future__ import annotations
 
@@ -20,11 +21,11 @@ import torch
 
 from . import _native
 from ._native import (ALGOS, C64, FLAG_GRAPH, FLAG_HOST_IO, FLAG_PERSISTENT, NORMS, R32, Plan,
-                      PlanKD, SwdftError, status_string, version)
+                      PlanKD, StreamPlan, SwdftError, status_string, version)
 
 __all__ = ["swdft2d", "swdft2d_adjoint", "Transform", "Plan", "SwdftError", "SWDFT2dFunction",
            "status_string", "version", "FLAG_GRAPH", "FLAG_HOST_IO", "FLAG_PERSISTENT",
-           "TransformKD", "PlanKD", "swdftkd"]
+           "TransformKD", "PlanKD", "swdftkd", "SlidingStream", "StreamPlan"]
 
 
 def _dtype_code(x: torch.Tensor) -> int:
@@ -191,3 +192,40 @@ def swdftkd(x: torch.Tensor, n: Sequence[int], norm: str = "unitary") -> torch.T
         t = TransformKD(tuple(x.shape), n, dtype=_dtype_code(x), norm=norm, device=x.device)
         _CACHE_KD[key] = t
     return t.forward(x)
+
+
+class SlidingStream:
+    """Rows of an N1-wide array pushed over time; each push returns the window rows they
+    complete, (rows, P1, n0, n1) complex64, identical to the same rows of one transform of
+    everything pushed so far (Section 4.3's real-time order)."""
+
+    def __init__(self, N1: int, n0: int, n1: int, dtype: int = R32, norm: str = "unitary",
+                 max_rows: int = 64, device=None):
+        self.plan = StreamPlan(N1, n0, n1, dtype=dtype, norm=norm, max_rows=max_rows)
+        self.N1, self.n0, self.n1, self.dtype, self.max_rows = N1, n0, n1, dtype, max_rows
+        self.P1 = N1 - n1 + 1
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        self.state = torch.empty(max(self.plan.state_size(), 1), dtype=torch.uint8, device=self.device)
+
+    def push(self, rows: torch.Tensor, out: torch.Tensor = None):
+        """rows: (R, N1) float32 / complex64 on the stream's device.  Returns (q0 of the first
+        window row, tensor (rows_out, P1, n0, n1))."""
+        if rows.dim() != 2 or rows.shape[1] != self.N1 or _dtype_code(rows) != self.dtype \
+                or not rows.is_cuda or rows.device != self.device or rows.stride(1) != 1:
+            raise ValueError("rows must be (R, N1) on the stream's device with the planned dtype")
+        R = int(rows.shape[0])
+        seen = self.plan.rows_seen()
+        hist = min(seen, self.n0 - 1)
+        nout = max(0, hist + R - (self.n0 - 1))
+        if out is None:
+            out = torch.empty((nout, self.P1, self.n0, self.n1), dtype=torch.complex64, device=self.device)
+        elif tuple(out.shape) != (nout, self.P1, self.n0, self.n1) or not out.is_contiguous():
+            raise ValueError("out must be a contiguous (rows_out, P1, n0, n1) complex64 tensor")
+        n, first = self.plan.push(rows.data_ptr(), R, rows.stride(0), out.data_ptr() if nout else 0,
+                                  self.state.data_ptr(), _stream_ptr(self.device))
+        assert n == nout
+        return first, out
+
+    def reset(self):
+        self.plan.reset()

@@ -1,5 +1,5 @@
-"""ctypes binding of the C ABI in include/swdft2d.h and include/swdftkd.h (argument
-marshalling only).
+"""ctypes binding of the C ABI in include/swdft2d.h, include/swdftkd.h and
+include/swdftstream.h (argument marshalling only).
 
 Every step of the transform runs in the CUDA library ``_lib/libswdft2d.so``; this module
 only converts Python values to the plain pointers and sizes the ABI takes.  There is no
@@ -32,7 +32,7 @@ ALGOS = {"auto": 0, "tree": 1, "tc_bf16x3": 2, "tc_bf16": 3, "tc_f16_scaled": 4,
 ALGO_NAMES = {v: k for k, v in ALGOS.items()}
 FLAG_GRAPH, FLAG_HOST_IO, FLAG_PERSISTENT = 1, 2, 4
 
-# every symbol include/swdft2d.h and include/swdftkd.h declare
+# every symbol include/*.h declare
 EXPORTS = (
     "swdft2d_plan", "swdft2d_output_shape", "swdft2d_workspace_size", "swdft2d_get_algo",
     "swdft2d_execute", "swdft2d_execute_adjoint", "swdft2d_execute_host", "swdft2d_autotune",
@@ -41,6 +41,8 @@ EXPORTS = (
     "swdft2d_check_device",
     "swdftkd_plan", "swdftkd_output_shape", "swdftkd_workspace_size", "swdftkd_launch_count",
     "swdftkd_execute", "swdftkd_destroy",
+    "swdft2d_stream_create", "swdft2d_stream_state_size", "swdft2d_stream_push",
+    "swdft2d_stream_rows_seen", "swdft2d_stream_reset", "swdft2d_stream_destroy",
 )
 KD_MAX_DIMS = 4
 
@@ -93,6 +95,12 @@ def _load() -> ctypes.CDLL:
         "swdftkd_launch_count": ([P, ctypes.POINTER(i32)], i32),
         "swdftkd_execute": ([P, P, P, P, P], i32),
         "swdftkd_destroy": ([P], i32),
+        "swdft2d_stream_create": ([ctypes.POINTER(P), i64, i32, i32, i32, i32, i64], i32),
+        "swdft2d_stream_state_size": ([P, ctypes.POINTER(ctypes.c_size_t)], i32),
+        "swdft2d_stream_push": ([P, P, i64, i64, P, P, ctypes.POINTER(i64), ctypes.POINTER(i64), P], i32),
+        "swdft2d_stream_rows_seen": ([P, ctypes.POINTER(i64)], i32),
+        "swdft2d_stream_reset": ([P], i32),
+        "swdft2d_stream_destroy": ([P], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -285,6 +293,63 @@ class PlanKD:
     def destroy(self):
         if self._h is not None and self._h.value:
             lib.swdftkd_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def raw_stream(N1: int, n0: int, n1: int, dtype: int = R32, norm: int = 0, max_rows: int = 1):
+    """Call swdft2d_stream_create with raw values; returns (status, handle or None)."""
+    h = ctypes.c_void_p()
+    st = lib.swdft2d_stream_create(ctypes.byref(h), int(N1), int(n0), int(n1), int(dtype),
+                                   int(norm), int(max_rows))
+    return st, (h if h.value else None)
+
+
+class StreamPlan:
+    """Owns one swdft2d_stream object (rows pushed over time, windows emitted as completed)."""
+
+    def __init__(self, N1: int, n0: int, n1: int, dtype: int = R32, norm: str = "unitary",
+                 max_rows: int = 1):
+        st, h = raw_stream(N1, n0, n1, dtype, NORMS[norm], max_rows)
+        _check(st, "swdft2d_stream_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("stream destroyed")
+        return self._h
+
+    def state_size(self) -> int:
+        v = ctypes.c_size_t()
+        _check(lib.swdft2d_stream_state_size(self.handle, ctypes.byref(v)), "swdft2d_stream_state_size")
+        return int(v.value)
+
+    def push(self, rows_ptr: int, nrows: int, ld: int, out_ptr: int, state_ptr: int, stream: int = 0):
+        """Returns (window rows written, index q0 of the first)."""
+        n, first = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.swdft2d_stream_push(self.handle, ctypes.c_void_p(rows_ptr or None), int(nrows), int(ld),
+                                       ctypes.c_void_p(out_ptr or None), ctypes.c_void_p(state_ptr or None),
+                                       ctypes.byref(n), ctypes.byref(first), ctypes.c_void_p(stream or None)),
+               "swdft2d_stream_push")
+        return int(n.value), int(first.value)
+
+    def rows_seen(self) -> int:
+        v = ctypes.c_int64()
+        _check(lib.swdft2d_stream_rows_seen(self.handle, ctypes.byref(v)), "swdft2d_stream_rows_seen")
+        return int(v.value)
+
+    def reset(self):
+        _check(lib.swdft2d_stream_reset(self.handle), "swdft2d_stream_reset")
+
+    def destroy(self):
+        if self._h is not None and self._h.value:
+            lib.swdft2d_stream_destroy(self._h)
         self._h = None
 
     def __del__(self):

@@ -185,3 +185,34 @@ def test_kd_output_shape_workspace_and_launches(nat):
     assert nat.PlanKD((30,), (8,)).output_shape() == (23, 8)
     assert nat.PlanKD((30, 20), (8, 4)).output_shape() == (23, 17, 8, 4)
     assert nat.PlanKD((30, 20), (8, 4)).launch_count() == 2
+
+
+
+# ------------------------------------------------------------------ streaming (swdftstream.h)
+
+@pytest.mark.parametrize("args,status", [
+    ((0, 4, 4, 0, 0, 1), -1),      # empty row
+    ((16, 3, 4, 0, 0, 1), -2),     # not a power of two
+    ((16, 4, 32, 0, 0, 1), -3),    # window wider than the row
+    ((300, 128, 4, 0, 0, 1), -4),  # beyond the 64-point axis
+    ((16, 4, 4, 5, 0, 1), -1),     # bad dtype
+    ((16, 4, 4, 0, 9, 1), -1),     # bad normalisation
+    ((16, 4, 4, 0, 0, 0), -1),     # no rows per push
+])
+def test_stream_validation(nat, args, status):
+    st, h = nat.raw_stream(*args)
+    assert st == status
+    assert h is None
+
+
+def test_stream_state_and_push_bookkeeping(nat):
+    s = nat.StreamPlan(40, 8, 4, max_rows=5)
+    # n0/2 look-back rows + 2(n0-1) + max_rows kept rows of P1*n1 complex64
+    assert s.state_size() == (4 + 14 + 5) * 37 * 4 * 8
+    # pushes of zero rows enqueue nothing and need no pointers
+    assert s.push(0, 0, 0, 0, 0) == (0, 0)
+    assert s.rows_seen() == 0
+    with pytest.raises(nat.SwdftError):
+        s.push(0, 6, 0, 0, 0)      # more rows than max_rows
+    with pytest.raises(nat.SwdftError):
+        s.push(0, 2, 20, 0, 0)     # row stride shorter than a row
