@@ -19,6 +19,9 @@ using namespace swdft;
 namespace {
 
 constexpr size_t kAlign = 256;
+// arrays of one plan that run at once on plan-owned streams (per-array launches and the
+// adjoint); each has its own workspace slot
+constexpr int kConc = 4;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -61,10 +64,22 @@ struct ArrayPlan {
     size_t planes_bytes(int64_t rows_out, int algo) const {
         return (size_t)tc_terms(algo) * 2 * (size_t)(rows_out + n0 - 1) * (size_t)P1 * n1 * 2;
     }
+    // adjoint: window rows per adj_col chunk (about eight chunks, none shorter than 2*n0:
+    // chunks read disjoint rows of G, and each costs n0-1 drain steps and n0-1 side rows),
+    // gz where the forward pass keeps z, then the chunks' side rows
+    int64_t adj_chunk(int64_t rows_out) const {
+        return std::min(rows_out, std::max<int64_t>((rows_out + 7) / 8, 2 * n0));
+    }
+    size_t adj_side_bytes(int64_t rows_out) const {
+        return (size_t)adj_side_elems(rows_out, m0, P1, m1, adj_chunk(rows_out)) * sizeof(float2);
+    }
+    size_t adj_bytes(int64_t rows_out) const { return align_up(z_bytes(rows_out)) + align_up(adj_side_bytes(rows_out)); }
     size_t ws_bytes_for(int64_t rows_out, int algo) const {
-        // tree: z (complex64); tensor-core forms: z as operand planes, then a max-abs word
-        if (algo >= SWDFT_ALGO_TC_BF16X3) return align_up(planes_bytes(rows_out, algo)) + kAlign;
-        return align_up(z_bytes(rows_out));
+        // tree: z (complex64); tensor-core forms: z as operand planes, then a max-abs word;
+        // either way at least what the adjoint needs
+        const size_t fwd = algo >= SWDFT_ALGO_TC_BF16X3 ? align_up(planes_bytes(rows_out, algo)) + kAlign
+                                                        : align_up(z_bytes(rows_out));
+        return std::max(fwd, adj_bytes(rows_out));
     }
 };
 
@@ -91,9 +106,9 @@ struct swdft2d_plan_s {
     // streams forked from and joined back to the caller's stream, one workspace slot each
     int conc = 1;
     size_t slot_bytes = 0;
-    cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t side[kConc] = {};
     cudaEvent_t fork_ev = nullptr;
-    cudaEvent_t join_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t join_ev[kConc] = {};
     // persistent batch (SWDFT_FLAG_PERSISTENT): per-array z offsets in the workspace, the
     // tile descriptors (pinned staging + device copy, allocated at the first execute)
     std::vector<size_t> z_off;
@@ -427,9 +442,10 @@ swdft_status for_each_array(swdft2d_plan_t plan, void *ws, cudaStream_t s, Body 
     for (int k = 0; k < plan->conc; ++k)
         if (cudaStreamWaitEvent(plan->side[k], plan->fork_ev, 0) != cudaSuccess) return SWDFT_ERR_CUDA;
     swdft_status st = SWDFT_OK;
+    const bool own_region = (plan->flags & SWDFT_FLAG_PERSISTENT) != 0;  // one region per array
     for (size_t i = 0; i < n && st == SWDFT_OK; ++i) {
         const int k = (int)(i % plan->conc);
-        void *slot = static_cast<char *>(ws) + (size_t)k * plan->slot_bytes;
+        void *slot = static_cast<char *>(ws) + (own_region ? plan->z_off[i] : (size_t)k * plan->slot_bytes);
         if (body(i, plan->side[k], slot) != cudaSuccess) st = SWDFT_ERR_CUDA;
     }
     // always join every side stream back (a capture must end with all streams joined)
@@ -553,13 +569,13 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
         // groups' kernels run on up to four side streams
         for (const auto &a : p->arrays) {
             p->z_off.push_back(ws);
-            ws += align_up(a.z_bytes(a.band_rows()));
+            ws += align_up(a.ws_bytes_for(a.band_rows(), SWDFT_ALGO_TREE_F32));
         }
         p->conc = 4;
     } else {
         // up to four arrays run at once (plan-owned streams), each with its own z slot
         for (const auto &a : p->arrays) ws = std::max(ws, align_up(a.ws_bytes_for(a.band_rows(), a.algo)));
-        p->conc = (int)std::min<size_t>(4, p->arrays.size());
+        p->conc = (int)std::min<size_t>(kConc, p->arrays.size());
         p->slot_bytes = ws;
         ws *= (size_t)p->conc;
     }
@@ -730,6 +746,9 @@ swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_g
         AdjColArgs c;
         c.G = static_cast<const float2 *>(d_grad_out[i]);
         c.gz = static_cast<float2 *>(slot);
+        c.side = a.adj_side_bytes(a.band_rows()) > 0
+                     ? reinterpret_cast<float2 *>(static_cast<char *>(slot) + align_up(a.z_bytes(a.band_rows())))
+                     : nullptr;
         c.P1 = a.P1;
         c.rows_out = a.band_rows();
         c.m0 = a.m0;
@@ -737,10 +756,14 @@ swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_g
         c.scale = norm_scale(plan->norm, a.n0, a.n1);
         c.om64 = plan->om64;
         c.B = 0;  // the launcher uses the one split built per window side
-        c.chunk = std::min(zrows, std::max<int64_t>((zrows + 7) / 8, 2 * a.n0));
+        c.chunk = a.adj_chunk(a.band_rows());
         if ((e = launch_adj_col(c, s)) != cudaSuccess) return e;
         AdjRowArgs r;
         r.gz = static_cast<const float2 *>(slot);
+        r.side = c.side;
+        r.col_chunk = c.chunk;
+        r.rows_out = c.rows_out;
+        r.m0 = a.m0;
         r.gx = gx + (size_t)a.q_begin * row_bytes;
         r.ld_out = a.N1;
         r.cplx = a.dtype == SWDFT_C64;
@@ -750,8 +773,9 @@ swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_g
         r.om64 = plan->om64;
         r.B = 0;  // the launcher uses the one split built per window side
         const int64_t target = (int64_t)plan->sm_count * 1024;
-        const int64_t nchunk = std::max<int64_t>(1, target / std::max<int64_t>(1, zrows << (a.m1 >= 6 ? 3 : std::min(a.m1, 2))));
-        r.chunk = std::min<int64_t>(a.N1, std::max<int64_t>((a.N1 + nchunk - 1) / nchunk, 2 * a.n1));
+        const int64_t nchunk = std::max<int64_t>(1, target / std::max<int64_t>(1, zrows << adj_row_split(a.m1)));
+        // chunks no shorter than n1: each re-walks n1-1 columns of warm-up
+        r.chunk = std::min<int64_t>(a.N1, std::max<int64_t>((a.N1 + nchunk - 1) / nchunk, a.n1));
         return launch_adj_row(r, s);
     });
 }
@@ -946,7 +970,7 @@ swdft_status swdft2d_destroy(swdft2d_plan_t plan) {
         cudaEventDestroy(plan->desc_uploaded);
     }
     if (plan->desc_host) cudaFreeHost(plan->desc_host);
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < kConc; ++k) {
         if (plan->side[k]) cudaStreamDestroy(plan->side[k]);
         if (plan->join_ev[k]) cudaEventDestroy(plan->join_ev[k]);
     }

@@ -178,21 +178,32 @@ cudaError_t launch_fused_tree(const FusedTreeArgs &a, cudaStream_t s);
 
 // Adjoint of the column levels: gz[r][q1][k1] = scale * sum_{j0,k0} G[r-j0][q1][k0][k1] w_{n0}^{+j0 k0}
 // for the rows_out + n0 - 1 z rows of a band (G holds rows_out window rows).
+// Work is split by window rows: chunks of `chunk` windows (>= n0-1; the last may be shorter),
+// each reading its rows of G once.  The n0-1 gz rows after a chunk (not the last) are written
+// to side[chunk index] instead of gz; adj_row adds them (AdjRowArgs.side).
 struct AdjColArgs {
     const float2 *G = nullptr;
     float2 *gz = nullptr;
+    float2 *side = nullptr;  // adj_side_elems(...) complex64, or null when there is one chunk
     int64_t P1 = 0, rows_out = 0;
     int m0 = 0, m1 = 0;
     float scale = 1.f;
     const float2 *om64 = nullptr;  // host table w_64^{-j}, 64 entries
     int B = 0;
-    int64_t chunk = 0;  // gz rows per thread (plus n0-1 warm-up steps)
+    int64_t chunk = 0;  // window rows per thread (plus n0-1 drain steps)
 };
+// Window rows per adj_col chunk the launcher actually uses, and its side buffer size.
+int64_t adj_col_chunk(int64_t rows_out, int m0, int64_t requested);
+int64_t adj_side_elems(int64_t rows_out, int m0, int64_t P1, int m1, int64_t requested);
 
 // Adjoint of the row levels: gx[r][p1] = sum_{j1,k1} gz[r][p1-j1][k1] w_{n1}^{+j1 k1}
 // (real part stored for float32 inputs), for zrows rows of N1 columns.
 struct AdjRowArgs {
     const float2 *gz = nullptr;
+    const float2 *side = nullptr;  // adj_col's side buffer (null: none)
+    int64_t col_chunk = 0;         // adj_col's chunk (adj_col_chunk), rows_out, m0
+    int64_t rows_out = 0;
+    int m0 = 0;
     void *gx = nullptr;
     int64_t ld_out = 0;
     int cplx = 0;
@@ -204,6 +215,8 @@ struct AdjRowArgs {
 };
 
 cudaError_t launch_adj_col(const AdjColArgs &a, cudaStream_t s);
+// log2 of the threads adj_row splits one row's transposed tree over, for n1 = 2^m1
+int adj_row_split(int m1);
 cudaError_t launch_adj_row(const AdjRowArgs &a, cudaStream_t s);
 
 }  // namespace swdft

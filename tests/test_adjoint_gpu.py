@@ -155,3 +155,22 @@ def test_autograd_gradient_matches_fp64_finite_differences(sw, n):
             fd[r, c] = (L(x64 + e) - L(x64 - e)) / (2 * h)
     scale = np.abs(fd).max()
     assert np.abs(g - fd).max() <= 1e-5 * scale + 1e-6, (np.abs(g - fd).max(), scale)
+
+
+def test_adjoint_of_persistent_batch_plan(sw):
+    """A persistent plan's adjoint runs its arrays on several streams; each array needs its
+    own gz region.  Results must equal the per-array plan's and the oracle's."""
+    shapes = [(70, 50, 8, 16, 0), (64, 64, 16, 4, 1), (90, 40, 32, 8, 0), (33, 60, 4, 32, 1),
+              (50, 50, 16, 16, 0), (41, 77, 2, 8, 1)]
+    Gs = [_G(70 + i, N0 - n0 + 1, N1 - n1 + 1, n0, n1) for i, (N0, N1, n0, n1, _) in enumerate(shapes)]
+    Gd = [torch.from_numpy(G).cuda() for G in Gs]
+    a = sw.Transform(shapes).adjoint(Gd)
+    b = sw.Transform(shapes, flags=sw.FLAG_PERSISTENT).adjoint(Gd)
+    torch.cuda.synchronize()
+    for u, v, G, (N0, N1, n0, n1, c) in zip(a, b, Gs, shapes):
+        assert torch.equal(u, v)
+        ref = oracle.swdft2d_adjoint(G, N0, N1)
+        if not c:
+            ref = ref.real
+        err = workloads.adjoint_error(v.cpu().numpy(), ref, workloads.adjoint_pixel_norms(G, N0, N1))
+        assert err <= TOL, f"{(N0, N1, n0, n1)}: {err:.3e}"
