@@ -185,6 +185,20 @@ def oracle_sample(x, seconds, seed=0):
                       f"(FP64 row-column sum, 1 thread), {dt:.1f} s"}, (q0, q1, ref)
 
 
+def cpu_tree_fig4():
+    """The paper-order FP32 tree on one host core at the Fig. 4 shapes (the paper's own
+    implementation is a single-threaded C program of this loop order)."""
+    import oracle
+    import workloads
+    x = workloads.random_array(8, 100, 100)
+    out = {}
+    for (_, _, a0, a1) in workloads.paper_fig4_shapes():
+        t0 = time.perf_counter()
+        oracle.tree2d(x, a0, a1, precision="f32", threads=1)
+        out[str(a0)] = round(1e3 * (time.perf_counter() - t0), 2)
+    return {"unit": "ms per transform", "cores": 1, "per_n_ms": out}
+
+
 def cpu_tree_sample(x, rows=96):
     """The paper's tree (Section 4.3 loop order) in FP32 with OpenMP on all host cores, on a
     band of output rows."""
@@ -432,6 +446,35 @@ def stream_measurement(torch, sw):
     return res
 
 
+def fig4_measurement(torch, sw):
+    """The paper's only timed workload (Fig. 4): one 100x100 array with square windows of
+    4..64.  GPU latency of one transform, launched directly and replayed from a CUDA graph
+    (too small to be bandwidth-bound: these are latency figures)."""
+    import workloads
+    x = torch.from_numpy(workloads.random_array(8, 100, 100)).cuda()
+    res = {"workload": "100x100 float32 N(0,1) (seed 8), n x n windows, n = 4..64", "per_n": {}}
+    s = torch.cuda.Stream()
+    for (M0, M1, a0, a1) in workloads.paper_fig4_shapes():
+        ent = {"coeffs": (M0 - a0 + 1) * (M1 - a1 + 1) * a0 * a1}
+        for name, flags in (("direct", 0), ("graph", sw.FLAG_GRAPH)):
+            t = sw.Transform([(M0, M1, a0, a1, sw.R32)], flags=flags)
+            out = t.empty_outputs()
+            with torch.cuda.stream(s):
+                for _ in range(5):
+                    t.forward([x], out)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                for _ in range(200):
+                    t.forward([x], out)
+                e1.record(s)
+            s.synchronize()
+            ent[f"{name}_us"] = round(1e3 * e0.elapsed_time(e1) / 200, 2)
+            del t, out
+        res["per_n"][str(a0)] = ent
+    return res
+
+
 # ----------------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -533,7 +576,8 @@ def run_ours(args):
         except Exception as e:  # noqa: BLE001
             extra["tensor_core"] = {"error": str(e)}
         for key, fn in (("batch", batch_measurement), ("adjoint", adjoint_measurement),
-                        ("volume", volume_measurement), ("stream", stream_measurement)):
+                        ("volume", volume_measurement), ("stream", stream_measurement),
+                        ("fig4_shapes", fig4_measurement)):
             try:
                 extra[key] = fn(torch, sw)
             except Exception as e:  # noqa: BLE001
@@ -603,6 +647,11 @@ def run_ours(args):
             line["cpu_tree"] = cpu_tree_sample(x)
         except Exception as e:  # noqa: BLE001
             line["cpu_tree"] = {"error": str(e)}
+        if isinstance(line.get("fig4_shapes"), dict) and "per_n" in line["fig4_shapes"]:
+            try:
+                line["fig4_shapes"]["cpu_tree"] = cpu_tree_fig4()
+            except Exception as e:  # noqa: BLE001
+                line["fig4_shapes"]["cpu_tree"] = {"error": str(e)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
