@@ -15,6 +15,8 @@ Contents (plain C in ``swdft2d_oracle.c`` / ``swdft2d_tree_ref.c``, loaded throu
 * :func:`swdftkd` / :func:`swdftkd_windows` -- the k-dimensional transform of Section 4.4
   (k <= 4) by its definition, direct or axis by axis (``swdftkd_oracle.c``).
 * :func:`treekd` -- the tree of Eq. kdfswft in FP64, with its node-operation count.
+* :func:`tree2d_radix` -- the 2D tree with radix-2 or radix-3 levels per axis (the ternary
+  trees Section 5 mentions; recurrence derived in ``swdft_radix_tree.c``), FP64.
 
 Arrays are numpy; outputs are complex128 with layout [q0][q1][k0][k1], where window q
 covers rows q0..q0+n0-1 and columns q1..q1+n1-1 (the paper's window end p = q + n - 1).
@@ -32,7 +34,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["swdft2d_oracle.c", "swdft2d_tree_ref.c", "swdftkd_oracle.c"]
+_SOURCES = ["swdft2d_oracle.c", "swdft2d_tree_ref.c", "swdftkd_oracle.c", "swdft_radix_tree.c"]
 _lib = None
 
 NORMS = ("unitary", "none", "inv_n")
@@ -75,9 +77,11 @@ def _load():
     lib.swo_swdftkd.argtypes = [P, i32, P, P, d, i32, i32, P]
     lib.swo_swdftkd_windows.argtypes = [P, i32, P, P, d, i32, i64, P, i32, P]
     lib.swt_treekd_f64.argtypes = [P, i32, P, P, d, P, P]
+    lib.swt_tree2d_radix_f64.argtypes = [P, i64, i64, i32, i32, d, P, P]
     for f in ("swo_swdft2d", "swo_swdft2d_windows", "swo_swdft2d_adjoint",
               "swo_swdft2d_adjoint_pixels", "swt_tree2d_f64", "swt_tree2d_f32",
-              "swo_openmp_available", "swo_swdftkd", "swo_swdftkd_windows", "swt_treekd_f64"):
+              "swo_openmp_available", "swo_swdftkd", "swo_swdftkd_windows", "swt_treekd_f64",
+              "swt_tree2d_radix_f64"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -260,4 +264,16 @@ def treekd(x, n: Sequence[int], norm: str = "unitary"):
     ops = ctypes.c_int64(0)
     _check(_load().swt_treekd_f64(_ptr(xs), K, _ptr(N), _ptr(nw), scale_for_kd(norm, nw),
                                   _ptr(out), ctypes.byref(ops)), "treekd")
+    return out, int(ops.value)
+
+
+def tree2d_radix(x, n0: int, n1: int, norm: str = "unitary"):
+    """The 2D tree with radix-2 or radix-3 levels per axis (n_i a power of 2 or of 3), FP64.
+    Returns (out (P0, P1, n0, n1) complex128, nodes evaluated)."""
+    xs = _as_c128(x)
+    N0, N1 = xs.shape
+    out = np.empty((N0 - n0 + 1, N1 - n1 + 1, n0, n1), dtype=np.complex128)
+    ops = ctypes.c_int64(0)
+    _check(_load().swt_tree2d_radix_f64(_ptr(xs), N0, N1, n0, n1, scale_for(norm, n0, n1),
+                                        _ptr(out), ctypes.byref(ops)), "tree2d_radix")
     return out, int(ops.value)
