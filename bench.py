@@ -446,6 +446,39 @@ def stream_measurement(torch, sw):
     return res
 
 
+def radix3_measurement(torch, sw):
+    """Ternary trees: 512x512 float32 N(0,1) (seed 79) with 27x27 and 9x9 windows, and the
+    mixed 9x16 (binary rows, ternary columns)."""
+    import workloads
+    x = torch.from_numpy(workloads.random_array(79, 512, 512)).cuda()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=x.device)
+    res = {"workload": "512x512 float32 N(0,1) (seed 79); L2 flushed before every step"}
+    for a0, a1 in ((27, 27), (9, 9), (9, 16)):
+        t = sw.Transform([(512, 512, a0, a1, sw.R32)])
+        out = t.empty_outputs()
+        coeffs = out[0].numel()
+        for _ in range(3):
+            t.forward([x], out)
+        ms = 0.0
+        steps = 20
+        for _ in range(steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            t.forward([x], out)
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        ms /= steps
+        res[f"{a0}x{a1}"] = {"ms_per_step": round(ms, 4), "value": coeffs / (ms / 1e3),
+                             "output_gbs": round(8 * coeffs / (ms / 1e3) / 1e9, 1)}
+        del t, out
+    del flush
+    torch.cuda.empty_cache()
+    return res
+
+
 def fig4_measurement(torch, sw):
     """The paper's only timed workload (Fig. 4): one 100x100 array with square windows of
     4..64.  GPU latency of one transform, launched directly and replayed from a CUDA graph
@@ -577,7 +610,7 @@ def run_ours(args):
             extra["tensor_core"] = {"error": str(e)}
         for key, fn in (("batch", batch_measurement), ("adjoint", adjoint_measurement),
                         ("volume", volume_measurement), ("stream", stream_measurement),
-                        ("fig4_shapes", fig4_measurement)):
+                        ("fig4_shapes", fig4_measurement), ("radix3", radix3_measurement)):
             try:
                 extra[key] = fn(torch, sw)
             except Exception as e:  # noqa: BLE001

@@ -25,6 +25,18 @@ constexpr int kConc = 4;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
+// n = 3^m: m, else -1
+int log3_exact(int64_t n) {
+    if (n < 1) return -1;
+    int m = 0;
+    int64_t v = 1;
+    while (v < n) {
+        v *= 3;
+        ++m;
+    }
+    return v == n ? m : -1;
+}
+
 int log2_exact(int64_t n) {
     if (n < 1) return -1;
     int m = 0;
@@ -44,6 +56,7 @@ struct TreeConfig {
 struct ArrayPlan {
     int64_t N0 = 0, N1 = 0, ld = 0, P0 = 0, P1 = 0;
     int n0 = 1, n1 = 1, m0 = 0, m1 = 0, dtype = SWDFT_R32;
+    int r0 = 2, r1 = 2;  // radix of each axis's tree: n_i = r_i^m_i (n_i = 1 counts as radix 2)
     int64_t q_begin = 0, q_end = 0;  // band of window rows, q coordinates
     TreeConfig cfg;
     bool tuned = false;
@@ -53,13 +66,15 @@ struct ArrayPlan {
     int64_t band_rows() const { return q_end - q_begin; }
     size_t in_elem() const { return dtype == SWDFT_C64 ? sizeof(float2) : sizeof(float); }
     size_t out_row_bytes() const { return (size_t)P1 * n0 * n1 * sizeof(float2); }
-    // n0/2 padding rows in front of z (column-pass look-back), then rows_out + n0 - 1 rows
-    int64_t z_pad() const { return n0 / 2; }
+    bool ternary() const { return r0 == 3 || r1 == 3; }
+    // padding rows in front of z for the column pass's level-0 look-back (n0/2 for a binary
+    // column tree, 2*n0/3 for a ternary one), then rows_out + n0 - 1 rows
+    int64_t z_pad() const { return r0 == 3 ? 2 * n0 / 3 : n0 / 2; }
     size_t z_bytes(int64_t rows_out) const {
         return (size_t)(z_pad() + rows_out + n0 - 1) * (size_t)P1 * n1 * sizeof(float2);
     }
     // tensor-core forms: 16-bit operand planes of z after the z buffer, then a max-abs word
-    bool tc_eligible() const { return m0 >= 4 && m0 <= 6 && m1 >= 3 && m1 <= 6; }
+    bool tc_eligible() const { return !ternary() && m0 >= 4 && m0 <= 6 && m1 >= 3 && m1 <= 6; }
     static int tc_terms(int algo) { return algo == SWDFT_ALGO_TC_BF16X3 ? 3 : 1; }
     size_t planes_bytes(int64_t rows_out, int algo) const {
         return (size_t)tc_terms(algo) * 2 * (size_t)(rows_out + n0 - 1) * (size_t)P1 * n1 * 2;
@@ -71,6 +86,7 @@ struct ArrayPlan {
         return std::min(rows_out, std::max<int64_t>((rows_out + 7) / 8, 2 * n0));
     }
     size_t adj_side_bytes(int64_t rows_out) const {
+        if (ternary()) return 0;  // no adjoint for ternary trees
         return (size_t)adj_side_elems(rows_out, m0, P1, m1, adj_chunk(rows_out)) * sizeof(float2);
     }
     size_t adj_bytes(int64_t rows_out) const { return align_up(z_bytes(rows_out)) + align_up(adj_side_bytes(rows_out)); }
@@ -99,6 +115,7 @@ struct swdft2d_plan_s {
     // Omega of length 64 (FP64-evaluated, FP32-rounded): Omega^i of Section 4.2 for every
     // n_i = 2^m_i <= 64 is its strided view, Omega^i[j] = om64[j * 64 / n_i], bit for bit.
     float2 om64[kMaxN];
+    float2 om27[kMaxN3];  // Omega of length 27 for ternary trees (3, 9 and 27 are its strided views)
     bool configured = false;
     int sm_count = 152;
     GraphCache graph;
@@ -161,7 +178,7 @@ void default_config(ArrayPlan &a, int sm_count) {
     // flight (measured best on the 512x512/32x32 and 1024x2048/16x64 workloads: B = 3 with
     // 16-32 column chunks, B = 2 with 128-column chunks), chunks no shorter than n1/2.
     (void)sm_count;
-    c.row_B = a.m1 >= 6 ? 2 : std::min(a.m1, 3);
+    c.row_B = a.r1 == 3 ? 0 : (a.m1 >= 6 ? 2 : std::min(a.m1, 3));  // ternary rows: one thread each
     const int64_t rows = a.band_rows() + a.n0 - 1;
     const int64_t nchunk = std::max<int64_t>(1, (64LL << 10) / std::max<int64_t>(1, rows << c.row_B));
     const int64_t chunk = (a.P1 + nchunk - 1) / nchunk;
@@ -377,6 +394,55 @@ cudaError_t enqueue_forward(const swdft2d_plan_s *plan, const ArrayPlan &a, cons
         t.chunk = a.tc_chunk;
         return launch_tc_col(t, s);
     }
+    if (a.ternary()) {
+        // ternary trees along one or both axes (tree3.cu): a row pass (ternary, or binary
+        // when n1 is a power of two), then the ternary column pass over z rows of any length
+        float2 *z = static_cast<float2 *>(ws) + a.z_pad() * a.P1 * a.n1;
+        if (stages & 1) {
+            cudaError_t e;
+            if (a.r1 == 3) {
+                Row3Args r;
+                r.x = in;
+                r.ld = a.ld;
+                r.cplx = a.dtype == SWDFT_C64;
+                r.r_base = q_lo;
+                r.rows = rows_out + a.n0 - 1;
+                r.P1 = a.P1;
+                r.m1 = a.m1;
+                r.z = z;
+                r.om27 = plan->om27;
+                r.chunk = a.cfg.row_chunk;
+                e = launch_row_tree3(r, s);
+            } else {
+                RowTreeArgs r;
+                r.x = in;
+                r.ld = a.ld;
+                r.cplx = a.dtype == SWDFT_C64;
+                r.r_base = q_lo;
+                r.rows = rows_out + a.n0 - 1;
+                r.P1 = a.P1;
+                r.m1 = a.m1;
+                r.z = z;
+                r.om64 = plan->om64;
+                r.B = a.cfg.row_B;
+                r.chunk = a.cfg.row_chunk;
+                e = launch_row_tree(r, s);
+            }
+            if (e != cudaSuccess) return e;
+        }
+        if (!(stages & 2)) return cudaSuccess;
+        Col3Args c;
+        c.z = z;
+        c.P1 = a.P1;
+        c.rows_out = rows_out;
+        c.n1 = a.n1;
+        c.m0 = a.m0;  // n0 = 3^m0, or n0 = 1
+        c.out = static_cast<float2 *>(out);
+        c.scale = norm_scale(plan->norm, a.n0, a.n1);
+        c.om27 = plan->om27;
+        c.chunk = a.cfg.col_chunk;
+        return launch_col_tree3(c, s);
+    }
     if (a.cfg.fused && a.m1 <= 5) {
         // one launch: row levels inside the column tile; stage 0 has nothing to do
         if (!(stages & 2)) return cudaSuccess;
@@ -494,7 +560,7 @@ const char *swdft2d_status_string(int32_t s) {
     switch (s) {
         case SWDFT_OK: return "SWDFT_OK";
         case SWDFT_ERR_INVALID_ARG: return "SWDFT_ERR_INVALID_ARG: invalid argument";
-        case SWDFT_ERR_NOT_POW2: return "SWDFT_ERR_NOT_POW2: window sides must be powers of two";
+        case SWDFT_ERR_NOT_POW2: return "SWDFT_ERR_NOT_POW2: window sides must be powers of two or of three";
         case SWDFT_ERR_WINDOW_TOO_LARGE: return "SWDFT_ERR_WINDOW_TOO_LARGE: window larger than the array";
         case SWDFT_ERR_UNSUPPORTED: return "SWDFT_ERR_UNSUPPORTED: not implemented for this request";
         case SWDFT_ERR_OOM: return "SWDFT_ERR_OOM: allocation failed";
@@ -522,7 +588,9 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
         ArrayPlan &a = arrays[(size_t)i];
         if (s.N0 < 1 || s.N1 < 1 || s.n0 < 1 || s.n1 < 1) return SWDFT_ERR_INVALID_ARG;
         if (s.dtype != SWDFT_R32 && s.dtype != SWDFT_C64) return SWDFT_ERR_INVALID_ARG;
-        const int m0 = log2_exact(s.n0), m1 = log2_exact(s.n1);
+        int m0 = log2_exact(s.n0), m1 = log2_exact(s.n1), r0 = 2, r1 = 2;
+        if (m0 < 0 && (m0 = log3_exact(s.n0)) >= 0) r0 = 3;
+        if (m1 < 0 && (m1 = log3_exact(s.n1)) >= 0) r1 = 3;
         if (m0 < 0 || m1 < 0) return SWDFT_ERR_NOT_POW2;
         if (s.n0 > s.N0 || s.n1 > s.N1) return SWDFT_ERR_WINDOW_TOO_LARGE;
         const int64_t ld = s.ld == 0 ? s.N1 : s.ld;
@@ -534,6 +602,8 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
         a.n1 = s.n1;
         a.m0 = m0;
         a.m1 = m1;
+        a.r0 = r0;
+        a.r1 = r1;
         a.dtype = s.dtype;
         a.P0 = s.N0 - s.n0 + 1;
         a.P1 = s.N1 - s.n1 + 1;
@@ -549,9 +619,13 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
             a.q_end = e - shift;
             if (a.q_begin < 0 || a.q_end > a.P0 || a.q_begin >= a.q_end) return SWDFT_ERR_INVALID_ARG;
         }
-        if (m0 > kMaxLog2 || m1 > kMaxLog2) return SWDFT_ERR_UNSUPPORTED;
+        if (m0 > (r0 == 3 ? kMaxLog3 : kMaxLog2) || m1 > (r1 == 3 ? kMaxLog3 : kMaxLog2)) return SWDFT_ERR_UNSUPPORTED;
+        // a ternary row tree feeds the ternary column kernel (z rows of any length); the
+        // binary column kernel needs power-of-two rows
+        if (r1 == 3 && r0 == 2 && m0 > 0) return SWDFT_ERR_UNSUPPORTED;
         a.algo = (algo == SWDFT_ALGO_AUTO) ? SWDFT_ALGO_TREE_F32 : algo;
         if (a.algo >= SWDFT_ALGO_TC_BF16X3 && !a.tc_eligible()) return SWDFT_ERR_UNSUPPORTED;
+        if (a.ternary() && (flags & SWDFT_FLAG_PERSISTENT)) return SWDFT_ERR_UNSUPPORTED;
     }
     if (algo >= SWDFT_ALGO_TC_BF16X3 && (flags & SWDFT_FLAG_PERSISTENT)) return SWDFT_ERR_UNSUPPORTED;
 
@@ -563,6 +637,7 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
     p->algo = (algo == SWDFT_ALGO_AUTO) ? SWDFT_ALGO_TREE_F32 : algo;
     p->flags = flags;
     make_omega(kMaxN, p->om64);
+    make_omega(kMaxN3, p->om27);
     size_t ws = 0;
     if (flags & SWDFT_FLAG_PERSISTENT) {
         // one launch covers every array, so each array has its own z region; the window
@@ -699,13 +774,14 @@ swdft_status swdft2d_set_tree_config(swdft2d_plan_t plan, int32_t i, int32_t row
     if (!plan || i < 0 || (size_t)i >= plan->arrays.size()) return SWDFT_ERR_INVALID_ARG;
     if (row_chunk < 0 || col_chunk < 0 || col_groups < 0 || fused < -1 || fused > 1) return SWDFT_ERR_INVALID_ARG;
     ArrayPlan &a = plan->arrays[(size_t)i];
+    if (a.ternary() && fused == 1) return SWDFT_ERR_UNSUPPORTED;
     TreeConfig c;
     if (fused == -1) {
         ArrayPlan tmp = a;
         default_config(tmp, plan->sm_count);
         c.fused = tmp.cfg.fused;
     } else {
-        c.fused = fused == 1 && a.m1 <= 5;
+        c.fused = fused == 1 && a.m1 <= 5 && !a.ternary();
     }
     c.row_B = std::max(0, std::min(row_B, std::min(a.m1, 3)));
     c.row_chunk = row_chunk;
@@ -721,6 +797,8 @@ swdft_status swdft2d_set_tree_config(swdft2d_plan_t plan, int32_t i, int32_t row
 swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_grad_out,
                                      void *const *d_grad_in, void *d_workspace, void *stream) {
     if (!plan || !d_grad_out || !d_grad_in) return SWDFT_ERR_INVALID_ARG;
+    for (const auto &a : plan->arrays)
+        if (a.ternary()) return SWDFT_ERR_UNSUPPORTED;  // the transposed tree is built for radix 2
     for (size_t i = 0; i < plan->arrays.size(); ++i) {
         const ArrayPlan &a = plan->arrays[i];
         if (!d_grad_out[i] || !d_grad_in[i]) return SWDFT_ERR_INVALID_ARG;
@@ -855,6 +933,7 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
     for (size_t i = 0; i < plan->arrays.size(); ++i) {
         ArrayPlan &a = plan->arrays[i];
         default_config(a, plan->sm_count);
+        if (a.ternary()) continue;  // one launch shape per ternary kernel: nothing to choose
         const TreeConfig base = a.cfg;
         std::vector<TreeConfig> cands;
         for (int cb = std::max(0, std::min(a.m0, 3) - 2); cb <= std::min(a.m0, 3); ++cb)

@@ -13,8 +13,11 @@ namespace swdft {
 // for window lengths up to 2^kMaxLog2 along each axis.
 constexpr int kMaxLog2 = 6;
 constexpr int kMaxN = 1 << kMaxLog2;
+// Ternary trees (tree3.cu) are built for window lengths 3^m, m <= kMaxLog3.
+constexpr int kMaxLog3 = 3;
+constexpr int kMaxN3 = 27;
 
-// Omega^i of Section 4.2 for length n (power of two), FP64-evaluated, FP32-rounded.
+// Omega^i of Section 4.2 for length n (any n >= 1), FP64-evaluated, FP32-rounded.
 void make_omega(int n, float2 *out);
 
 // Geometry of one row-level pass (see RowTreeArgs): z[r][q1][k1] for `rows` input rows.
@@ -213,6 +216,33 @@ struct AdjRowArgs {
     int B = 0;
     int64_t chunk = 0;  // output columns per thread (plus n1-1 warm-up steps)
 };
+
+// Ternary trees (tree3.cu): windows of 3^m samples, m <= 3, along an axis.
+// Row levels: z[r][q1][k1] for `rows` input rows (n1 = 3^m1), as RowTreeArgs.
+struct Row3Args {
+    const void *x = nullptr;
+    int64_t ld = 0;
+    int cplx = 0;
+    int64_t r_base = 0, rows = 0, P1 = 0;
+    int m1 = 0;                     // n1 = 3^m1
+    float2 *z = nullptr;
+    const float2 *om27 = nullptr;   // host table w_27^{-j}, 27 entries
+    int64_t chunk = 0;
+};
+// Column levels with a ternary tree (n0 = 3^m0) over z rows of P1 x n1 (n1 any length);
+// z needs 2*n0/3 readable rows in front of its first row.
+struct Col3Args {
+    const float2 *z = nullptr;
+    int64_t P1 = 0, rows_out = 0;
+    int n1 = 1;
+    int m0 = 0;                     // n0 = 3^m0
+    float2 *out = nullptr;
+    float scale = 1.f;
+    const float2 *om27 = nullptr;
+    int64_t chunk = 0;
+};
+cudaError_t launch_row_tree3(const Row3Args &a, cudaStream_t s);
+cudaError_t launch_col_tree3(const Col3Args &a, cudaStream_t s);
 
 cudaError_t launch_adj_col(const AdjColArgs &a, cudaStream_t s);
 // log2 of the threads adj_row splits one row's transposed tree over, for n1 = 2^m1

@@ -2,9 +2,9 @@
 // w_n = exp(2 pi i / n).  Evaluated in FP64 and rounded once to FP32.
 //
 // The angle is reduced to an octant first, so cos/sin are only ever evaluated on [0, pi/4]
-// and the points a multiple of n/8 apart come out with the exact symmetry of the unit
-// circle: w^0 = 1, w^(n/4) = -i, w^(n/2) = -1 are exact, and w^-j, w^-(n-j) are exact
-// conjugates.  The library's twiddles are the only place cos/sin are called.
+// and points a multiple of n/8 apart (n a power of two) come out with the exact symmetry of
+// the unit circle: w^0 = 1, w^(n/4) = -i, w^(n/2) = -1 are exact; for every n, w^-j and
+// w^-(n-j) are exact conjugates.  The library's twiddles are the only place cos/sin are called.
 #include <cmath>
 #include <cstdint>
 
@@ -12,7 +12,7 @@
 
 namespace swdft {
 
-// (re, im) of exp(-2 pi i j / n) for n a power of two.
+// (re, im) of exp(-2 pi i j / n), any n >= 1 (powers of two and of three are used).
 static void omega_pow(int64_t n, int64_t j, double *re, double *im) {
     const double kQuarterPi = 0.78539816339744830961566084581988;
     j %= n;

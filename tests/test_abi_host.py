@@ -53,8 +53,11 @@ def shp(N0, N1, n0, n1, **kw):
 
 
 @pytest.mark.parametrize("shape,status", [
-    (shp(16, 16, 3, 4), -2),           # not a power of two
+    (shp(16, 16, 5, 4), -2),           # neither a power of two nor of three
     (shp(16, 16, 4, 12), -2),
+    (shp(100, 100, 81, 3), -4),        # ternary trees are built up to 27
+    (shp(40, 40, 16, 9), -4),          # binary column tree over ternary row DFTs
+    (shp(40, 40, 8, 3), -4),
     (shp(16, 16, 32, 4), -3),          # window larger than the array
     (shp(16, 8, 4, 16), -3),
     (shp(0, 16, 1, 1), -1),            # empty array
@@ -69,6 +72,20 @@ def test_plan_validation(nat, shape, status):
     st, h = nat.raw_plan([shape], 0, 0, 1, 0)
     assert st == status
     assert h is None
+
+
+def test_ternary_windows_are_accepted_by_the_tree_only(nat):
+    for n0, n1 in ((3, 3), (9, 27), (27, 1), (1, 9), (9, 16), (27, 64), (3, 2)):
+        st, h = nat.raw_plan([shp(40, 70, n0, n1)], 0, 0, 1, 0)
+        assert st == 0, (n0, n1)
+        nat.lib.swdft2d_destroy(h)
+    assert nat.raw_plan([shp(40, 40, 27, 27)], 0, 0, 2, 0)[0] == -4   # tensor-core forms
+    assert nat.raw_plan([shp(40, 40, 9, 9)], 0, 0, 1, 4)[0] == -4      # persistent batch
+    p = nat.Plan([dict(N0=40, N1=70, n0=9, n1=27)])
+    assert p.output_shape(0) == (32, 44, 9, 27)
+    # z: 2*n0/3 look-back rows in front, then P0 + n0 - 1 rows of P1 * n1 complex64
+    assert p.workspace_size() >= (6 + 32 + 8) * 44 * 27 * 8
+    assert p.launch_count() == 2
 
 
 def test_plan_validation_enums(nat):

@@ -1,0 +1,111 @@
+"""Ternary trees on the GPU (windows of 3, 9 or 27 along an axis; the radix-3 trees Section 5
+mentions) against the FP64 oracle's definition: max over a window's coefficients of
+|a - a_oracle| / ||x_w||_2 <= 1e-5 on the unitary scale, every coefficient of small arrays
+(ragged sizes, both radices mixed across the axes), and the 512x512 array with 27x27
+windows on sampled windows plus per-window Parseval."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sw():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1707_08213_gb300 as sw
+    return sw
+
+
+def run(sw, x, n0, n1, norm="unitary", flags=0, band=None):
+    t = sw.Transform([(x.shape[0], x.shape[1], n0, n1, 1 if np.iscomplexobj(x) else 0)], norm=norm,
+                     flags=flags, bands=None if band is None else [band])
+    a = t.forward([torch.from_numpy(np.ascontiguousarray(x)).cuda()])[0]
+    torch.cuda.synchronize()
+    return a, t
+
+
+def check(a, x, n0, n1, norm="unitary"):
+    ref = oracle.swdft2d(x, n0, n1, norm=norm, method="separable", threads=8)
+    to_unitary = oracle.scale_for("unitary", n0, n1) / oracle.scale_for(norm, n0, n1)
+    err, _ = workloads.normalised_error(a.cpu().numpy(), ref, workloads.window_sq_norms(x, n0, n1), to_unitary)
+    assert err <= TOL, f"{x.shape} {n0}x{n1}: {err:.3e}"
+
+
+SHAPES = [(3, 3), (9, 9), (27, 27), (27, 1), (1, 27), (9, 3), (3, 27), (9, 16), (27, 64), (3, 2),
+          (1, 3), (27, 8)]
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("n0,n1", SHAPES)
+def test_every_coefficient(sw, n0, n1, cplx):
+    N0, N1 = n0 + 37, n1 + 151  # several 128-channel tiles and row chunks, ragged tails
+    x = workloads.random_array(n0 * 31 + n1, N0, N1, complex_input=cplx)
+    a, t = run(sw, x, n0, n1)
+    assert tuple(a.shape) == (N0 - n0 + 1, N1 - n1 + 1, n0, n1)
+    assert t.plan.launch_count() == 2
+    check(a, x, n0, n1)
+
+
+@pytest.mark.parametrize("norm", ["none", "inv_n"])
+def test_normalisations(sw, norm):
+    x = workloads.random_array(77, 60, 90, complex_input=True)
+    a, _ = run(sw, x, 9, 27, norm=norm)
+    check(a, x, 9, 27, norm=norm)
+
+
+def test_band_graph_and_host_buffers_match(sw):
+    x = workloads.random_array(78, 120, 100)
+    full, _ = run(sw, x, 27, 9)
+    band, _ = run(sw, x, 27, 9, band=(20, 61))
+    assert torch.equal(band, full[20:61])
+    t = sw.Transform([(120, 100, 27, 9, 0)], flags=sw.FLAG_GRAPH)
+    xd = torch.from_numpy(x).cuda()
+    out = t.empty_outputs()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            out[0].zero_()
+            t.forward([xd], out)
+    s.synchronize()
+    assert torch.equal(out[0], full)
+    th = sw.Transform([(120, 100, 27, 9, 0)], flags=sw.FLAG_HOST_IO)
+    h_in = torch.from_numpy(x).pin_memory()
+    h_out = torch.empty(tuple(full.shape), dtype=torch.complex64).pin_memory()
+    th.plan.execute_host([h_in.data_ptr()], [h_out.data_ptr()], torch.cuda.current_stream().cuda_stream)
+    assert torch.equal(h_out, full.cpu())
+
+
+def test_adjoint_is_refused(sw):
+    t = sw.Transform([(40, 40, 9, 9, 0)])
+    G = torch.zeros((32, 32, 9, 9), dtype=torch.complex64, device="cuda")
+    with pytest.raises(sw.SwdftError):
+        t.adjoint([G])
+
+
+def test_512_with_27x27_windows_full_size(sw):
+    x = workloads.random_array(79, 512, 512)
+    n0 = n1 = 27
+    a, _ = run(sw, x, n0, n1)
+    P0, P1 = a.shape[:2]
+    rng = np.random.default_rng(80)
+    q0 = np.concatenate([rng.integers(0, P0, 2048), [0, 0, P0 - 1, P0 - 1]])
+    q1 = np.concatenate([rng.integers(0, P1, 2048), [0, P1 - 1, 0, P1 - 1]])
+    got = a[torch.from_numpy(q0).cuda(), torch.from_numpy(q1).cuda()].cpu().numpy()
+    ref = oracle.swdft2d_windows(x, n0, n1, q0, q1, threads=8)
+    err, _ = workloads.normalised_error(got, ref, workloads.window_sq_norms_at(x, n0, n1, q0, q1))
+    assert err <= TOL, f"sampled windows: {err:.3e}"
+    sq = torch.from_numpy(workloads.window_sq_norms(x, n0, n1)).cuda()
+    worst = 0.0
+    for r in range(0, P0, 64):
+        e = torch.view_as_real(a[r:r + 64]).pow(2).sum(dim=(2, 3, 4)).double()
+        worst = max(worst, float(((e - sq[r:r + 64]).abs() / sq[r:r + 64]).max()))
+    assert worst <= 1e-5, f"Parseval relative error {worst:.3e}"
+    del a
+    torch.cuda.empty_cache()
