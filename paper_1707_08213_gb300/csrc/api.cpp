@@ -180,7 +180,8 @@ void default_config(ArrayPlan &a, int sm_count) {
     (void)sm_count;
     c.row_B = a.r1 == 3 ? 0 : (a.m1 >= 6 ? 2 : std::min(a.m1, 3));  // ternary rows: one thread each
     const int64_t rows = a.band_rows() + a.n0 - 1;
-    const int64_t nchunk = std::max<int64_t>(1, (64LL << 10) / std::max<int64_t>(1, rows << c.row_B));
+    const int64_t per_row = a.r1 == 3 ? (a.m1 >= 1 ? 3 : 1) : (int64_t(1) << c.row_B);  // threads per row
+    const int64_t nchunk = std::max<int64_t>(1, (64LL << 10) / std::max<int64_t>(1, rows * per_row));
     const int64_t chunk = (a.P1 + nchunk - 1) / nchunk;
     c.row_chunk = std::min<int64_t>(a.P1, std::max<int64_t>(chunk, std::max(1, a.n1 / 2)));
     // column levels: thread = (channel, residue, chunk of output rows); one 32-channel

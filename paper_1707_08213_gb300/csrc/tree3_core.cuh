@@ -105,4 +105,98 @@ struct SlidingTree3 {
     }
 };
 
+// The same tree split over three threads by node residue (M >= 1).  For t >= 2 a level-t
+// node i is computed from level-(t-1) node i mod 3^(t-1), which has the same residue mod 3,
+// so thread c (< 3) keeps only the nodes == c (mod 3) of every level: level 1's node c
+// (a three-term sum), then at level t the 3^(t-2) butterflies on i' == c (mod 3).  No data
+// passes between the three threads and no node is evaluated twice.  Thread c produces the
+// outputs k = c + 3 u, u < 3^(M-1), in that order.
+template <int M>
+struct SlidingTree3Split {
+    static_assert(M >= 1 && M <= kMaxLog3, "split ternary trees: windows 3, 9, 27");
+    static constexpr int kN = pow3(M);
+    static constexpr int kOut = pow3(M - 1);  // outputs per thread
+    static constexpr int kPeriod = M >= 2 ? 2 * pow3(M - 2) : 1;
+    static constexpr int kS1 = pow3(M - 1);
+    // FIFO of level t-1 (t >= 2): depth 2 s_t slots of 3^(t-2) values (nodes == c mod 3)
+    static constexpr int held(int t) { return t <= 1 ? 1 : pow3(t - 1); }  // level-t nodes held
+    static constexpr int fifo_off(int t) {
+        int o = 0;
+        for (int u = 2; u < t; ++u) o += 2 * pow3(M - u) * held(u - 1);
+        return o;
+    }
+    static constexpr int kFifo = M >= 2 ? fifo_off(M + 1) : 0;
+    // twiddles: level 1: w_3^{-c}, w_3^{-2c}; level t >= 2: w_{3^t}^{-i'}, w_{3^t}^{-2 i'} for
+    // each i' = c + 3 a, a < 3^(t-2)
+    static constexpr int tw_off(int t) {
+        int o = 2;
+        for (int u = 2; u < t; ++u) o += 2 * pow3(u - 2);
+        return o;
+    }
+    static constexpr int kTw = tw_off(M + 1);
+
+    float2 fifo[kFifo > 0 ? kFifo : 1];
+    float2 tw[kTw];
+
+    __device__ __forceinline__ void init(int c, const Omega27 &om) {
+        tw[0] = om.w[(9 * c) % kMaxN3];
+        tw[1] = om.w[(18 * c) % kMaxN3];
+        static_for<2, M + 1>([&](auto TT) {
+            constexpr int t = decltype(TT)::value;
+            constexpr int step = kMaxN3 / pow3(t);
+            static_for<0, pow3(t - 2)>([&](auto AA) {
+                constexpr int a = decltype(AA)::value;
+                const int ip = c + 3 * a;
+                tw[tw_off(t) + 2 * a] = om.w[(ip * step) % kMaxN3];
+                tw[tw_off(t) + 2 * a + 1] = om.w[(2 * ip * step) % kMaxN3];
+            });
+        });
+#pragma unroll
+        for (int i = 0; i < (kFifo > 0 ? kFifo : 1); ++i) fifo[i] = make_float2(0.f, 0.f);
+    }
+
+    // out[u] = level-M node c + 3 u at p.
+    template <int J>
+    __device__ __forceinline__ void step(float h, float2 x_p, float2 x_s1, float2 x_s2, float2 (&out)[kOut]) {
+        // level 1, node c: x(p - 2 s1) + w_3^{-c} x(p - s1) + w_3^{-2c} x(p)
+        float2 cur[kOut];
+        cur[0] = c_add(x_s2, c_add(c_mul(tw[0], x_s1), c_mul(tw[1], x_p)));
+        level<J, 2>(h, cur);
+#pragma unroll
+        for (int u = 0; u < kOut; ++u) out[u] = cur[u];
+    }
+
+  private:
+    // cur holds level T-1's nodes c + 3 a (a < held(T-1)) in slots a; on return level T's
+    // nodes c + 3 a' (a' < held(T)) in slots a'.
+    template <int J, int T>
+    __device__ __forceinline__ void level(float h, float2 (&cur)[kOut]) {
+        if constexpr (T <= M) {
+            constexpr int s = pow3(M - T);
+            constexpr int D = 2 * s;
+            constexpr int HP = held(T - 1);        // level T-1 nodes held = butterflies here
+            constexpr int off = fifo_off(T);
+            constexpr int now = (J % D) * HP;
+            constexpr int back1 = ((J + s) % D) * HP;
+            constexpr int tb = tw_off(T);
+            float2 nxt[kOut];
+#pragma unroll
+            for (int a = 0; a < HP; ++a) {
+                // node i' = c + 3 a of level T-1 (or node c of level 1 when T = 2)
+                const float2 a2 = cur[a];
+                const float2 a1 = fifo[off + back1 + a];
+                const float2 a0 = fifo[off + now + a];
+                fifo[off + now + a] = a2;
+                const float2 b1 = c_mul(tw[tb + 2 * a], a1);
+                const float2 b2 = c_mul(tw[tb + 2 * a + 1], a2);
+                // outputs i' + k 3^(T-1) = c + 3 (a + k 3^(T-2)): slots a + k * HP
+                bfly3(a0, b1, b2, h, nxt[a], nxt[a + HP], nxt[a + 2 * HP]);
+            }
+#pragma unroll
+            for (int a = 0; a < 3 * HP; ++a) cur[a] = nxt[a];
+            level<J, T + 1>(h, cur);
+        }
+    }
+};
+
 }  // namespace swdft
