@@ -446,6 +446,47 @@ def stream_measurement(torch, sw):
     return res
 
 
+def complex_measurement(torch, sw):
+    """complex_1024x2048: 1024x2048 complex64, 16x64 windows (16.4 GB of output per
+    transform, far above L2): the tree per pass, and the split-bf16 tensor-core form."""
+    import workloads
+    x = torch.from_numpy(workloads.complex_1024x2048().images[0]).cuda()
+    M0, M1, a0, a1 = 1024, 2048, 16, 64
+    res = {"workload": "complex_1024x2048: 1024x2048 complex64 re/im N(0,1) (seed 2), 16x64 windows"}
+    out = torch.empty((M0 - a0 + 1, M1 - a1 + 1, a0, a1), dtype=torch.complex64, device=x.device)
+    coeffs = out.numel()
+    res["coeffs_per_step"] = coeffs
+    sp = torch.cuda.current_stream().cuda_stream
+    for algo in ("tree", "tc_bf16x3"):
+        try:
+            t = sw.Transform([(M0, M1, a0, a1, sw.C64)], algo=algo)
+            ws = t._ws_ptr
+            for _ in range(2):
+                t.forward([x], [out])
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            steps, t_row, t_col = 5, 0.0, 0.0
+            for _ in range(steps):
+                ev[0].record()
+                t.plan.execute_stage(0, [x.data_ptr()], [out.data_ptr()], ws, sp)
+                ev[1].record()
+                t.plan.execute_stage(1, [x.data_ptr()], [out.data_ptr()], ws, sp)
+                ev[2].record()
+                torch.cuda.synchronize()
+                t_row += ev[0].elapsed_time(ev[1])
+                t_col += ev[1].elapsed_time(ev[2])
+            ms = (t_row + t_col) / steps
+            res[algo] = {"ms_per_step": round(ms, 4), "row_pass_ms": round(t_row / steps, 4),
+                         "column_pass_ms": round(t_col / steps, 4), "value": coeffs / (ms / 1e3),
+                         "output_gbs": round(8 * coeffs / (ms / 1e3) / 1e9, 1),
+                         "column_pass_output_gbs": round(8 * coeffs / (t_col / steps / 1e3) / 1e9, 1)}
+            del t
+        except Exception as e:  # noqa: BLE001
+            res[algo] = {"error": str(e)}
+    del out, x
+    torch.cuda.empty_cache()
+    return res
+
+
 def radix3_measurement(torch, sw):
     """Ternary trees: 512x512 float32 N(0,1) (seed 79) with 27x27 and 9x9 windows, and the
     mixed 9x16 (binary rows, ternary columns)."""
@@ -610,7 +651,8 @@ def run_ours(args):
             extra["tensor_core"] = {"error": str(e)}
         for key, fn in (("batch", batch_measurement), ("adjoint", adjoint_measurement),
                         ("volume", volume_measurement), ("stream", stream_measurement),
-                        ("fig4_shapes", fig4_measurement), ("radix3", radix3_measurement)):
+                        ("fig4_shapes", fig4_measurement), ("radix3", radix3_measurement),
+                        ("complex", complex_measurement)):
             try:
                 extra[key] = fn(torch, sw)
             except Exception as e:  # noqa: BLE001
