@@ -1,7 +1,8 @@
 """The multi-GPU split on the CPU: two gloo ranks each take a band of window rows (one
 process per GPU in production), and the concatenation of their bands equals the unsplit
-transform (Section 4.1, Eq. 2, by the FP64 oracle).  Also the band arithmetic and the
-max-over-ranks timing reduction."""
+transform (Section 4.1, Eq. 2, by the FP64 oracle); two ranks split a batch of images by
+longest processing time and together cover it.  Also the band arithmetic, the image
+assignment's balance bound and the max-over-ranks timing reduction."""
 import os
 import socket
 
@@ -76,3 +77,56 @@ def test_two_rank_band_split_equals_unsplit(tmp_path):
     assert np.array_equal(np.concatenate(parts, axis=0), full)
     for r in range(world):
         assert float(np.load(tmp_path / f"max{r}.npy")[0]) == 2.0
+
+
+
+def test_image_assignment_covers_and_balances():
+    sh = _load_sharding()
+    rng = np.random.default_rng(3)
+    sides = rng.choice([128, 256, 512, 1024], size=(256, 2))
+    wins = [(4, 4), (8, 8), (16, 16), (32, 32), (8, 32), (64, 16)]
+    costs = [sh.output_bytes(int(a), int(b), *wins[int(k)]) for (a, b), k in zip(sides, rng.integers(0, 6, 256))]
+    for world in (1, 2, 3, 4, 8, 300):
+        parts = sh.assign_images(costs, world)
+        assert len(parts) == world
+        assert sorted(i for p in parts for i in p) == list(range(len(costs)))
+        loads = [sum(costs[i] for i in p) for p in parts]
+        lower = max(max(costs), sum(costs) / world)  # no split can beat this
+        assert max(loads) <= (4 / 3 - 1 / (3 * world)) * lower * (1 + 1e-12) + 1e-9 or max(loads) == max(costs)
+    assert sh.assign_images([5, 5, 4, 3, 3], 2) == [[0, 3, 4], [1, 2]]
+    assert sh.assign_images([], 3) == [[], [], []]
+
+
+def _batch_worker(rank, world, port, outdir):
+    import sys
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import oracle
+    import workloads
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sh = _load_sharding()
+    shapes = [(20, 30, 4, 8), (40, 16, 8, 2), (12, 12, 4, 4), (33, 21, 16, 8), (25, 25, 2, 2)]
+    mine = sh.assign_images([sh.output_bytes(*s) for s in shapes], world)[rank]
+    for i in mine:
+        N0, N1, n0, n1 = shapes[i]
+        x = workloads.random_array(90 + i, N0, N1)
+        np.save(os.path.join(outdir, f"img{i}_rank{rank}.npy"), oracle.swdft2d(x, n0, n1))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_image_split_covers_the_batch(tmp_path):
+    import oracle
+    import workloads
+    world = 2
+    mp.spawn(_batch_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    shapes = [(20, 30, 4, 8), (40, 16, 8, 2), (12, 12, 4, 4), (33, 21, 16, 8), (25, 25, 2, 2)]
+    files = sorted(os.listdir(tmp_path))
+    assert len(files) == len(shapes)  # each image computed by exactly one rank
+    for i, (N0, N1, n0, n1) in enumerate(shapes):
+        got = [f for f in files if f.startswith(f"img{i}_")]
+        assert len(got) == 1
+        ref = oracle.swdft2d(workloads.random_array(90 + i, N0, N1), n0, n1)
+        assert np.array_equal(np.load(tmp_path / got[0]), ref)
