@@ -28,21 +28,27 @@ cudaError_t launch_adj_col(const AdjColArgs &a, cudaStream_t s) {
     if (a.rows_out <= 0 || nch <= 0) return cudaSuccess;
     if (a.m0 < 0 || a.m0 > kMaxLog2 || a.m1 < 0 || a.m1 > kMaxLog2 || zrows > INT32_MAX)
         return cudaErrorInvalidValue;
+    if (a.nz < 1 || a.nz > kAdjZ) return cudaErrorInvalidValue;
     AdjColParams p;
-    p.G = a.G;
-    p.gz = a.gz;
-    p.side = a.side;
+    for (int z = 0; z < kAdjZ; ++z) {
+        p.G[z] = a.G[z];
+        p.gz[z] = a.gz[z];
+        p.side[z] = a.side[z];
+    }
     p.nch = nch;
     p.rows_out = (int)a.rows_out;
     p.chunk = (int)adj_col_chunk(a.rows_out, a.m0, a.chunk);
-    if (p.chunk < a.rows_out && a.m0 > 0 && a.side == nullptr) return cudaErrorInvalidValue;
+    for (int z = 0; z < a.nz; ++z)
+        if (!a.G[z] || !a.gz[z] || (p.chunk < a.rows_out && a.m0 > 0 && a.side[z] == nullptr))
+            return cudaErrorInvalidValue;
     p.m1 = a.m1;
     p.scale = a.scale;
     for (int j = 0; j < kMaxN; ++j) p.om64[j] = a.om64[j];
     const int B = adj_col_B(a.m0);  // the one split built per window side
     const int threads = 128;
     const int64_t per_block = threads >> B;
-    dim3 grid((unsigned)((nch + per_block - 1) / per_block), (unsigned)((a.rows_out + p.chunk - 1) / p.chunk));
+    dim3 grid((unsigned)((nch + per_block - 1) / per_block), (unsigned)((a.rows_out + p.chunk - 1) / p.chunk),
+              (unsigned)a.nz);
     if (grid.y > 65535) return cudaErrorInvalidValue;
     switch (a.m0) {
 #define F(M_)                                                                \
@@ -60,14 +66,19 @@ cudaError_t launch_adj_col(const AdjColArgs &a, cudaStream_t s) {
 cudaError_t launch_adj_row(const AdjRowArgs &a, cudaStream_t s) {
     if (a.zrows <= 0 || a.N1 <= 0) return cudaSuccess;
     if (a.m1 < 0 || a.m1 > kMaxLog2 || a.zrows > INT32_MAX || a.N1 > INT32_MAX) return cudaErrorInvalidValue;
+    if (a.nz < 1 || a.nz > kAdjZ) return cudaErrorInvalidValue;
     AdjRowParams p;
-    p.gz = a.gz;
-    p.side = a.side;
+    for (int z = 0; z < kAdjZ; ++z) {
+        p.gz[z] = a.gz[z];
+        p.side[z] = a.side[z];
+        p.gx[z] = a.gx[z];
+    }
+    for (int z = 0; z < a.nz; ++z)
+        if (!a.gz[z] || !a.gx[z]) return cudaErrorInvalidValue;
     if (a.m0 < 0 || a.m0 > kMaxLog2 || a.rows_out > INT32_MAX) return cudaErrorInvalidValue;
     p.col_chunk = (int)adj_col_chunk(a.rows_out, a.m0, a.col_chunk);
     p.rows_out = (int)a.rows_out;
     p.n0m1 = (1 << a.m0) - 1;
-    p.gx = a.gx;
     p.ld_out = a.ld_out;
     p.zrows = (int)a.zrows;
     p.N1 = (int)a.N1;
@@ -77,7 +88,8 @@ cudaError_t launch_adj_row(const AdjRowArgs &a, cudaStream_t s) {
     const int B = adj_row_B(a.m1);  // the one split built per window side
     const int threads = 128;
     const int64_t per_block = threads >> B;
-    dim3 grid((unsigned)((a.zrows + per_block - 1) / per_block), (unsigned)((a.N1 + p.chunk - 1) / p.chunk));
+    dim3 grid((unsigned)((a.zrows + per_block - 1) / per_block), (unsigned)((a.N1 + p.chunk - 1) / p.chunk),
+              (unsigned)a.nz);
     if (grid.y > 65535) return cudaErrorInvalidValue;
     switch (a.m1) {
 #define F(M_)                                                                         \

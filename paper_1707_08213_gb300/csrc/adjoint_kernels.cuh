@@ -27,10 +27,11 @@
 
 namespace swdft {
 
+// Per array (grid z) pointers: arrays of one shape share a launch.
 struct AdjColParams {
-    const float2 *G;   // rows_out x P1 x n0 x n1
-    float2 *gz;        // (rows_out + n0 - 1) x P1 x n1
-    float2 *side;      // (chunks - 1) x (n0 - 1) x P1 x n1: rows shared with the next chunk
+    const float2 *G[kAdjZ];   // rows_out x P1 x n0 x n1
+    float2 *gz[kAdjZ];        // (rows_out + n0 - 1) x P1 x n1
+    float2 *side[kAdjZ];      // (chunks - 1) x (n0 - 1) x P1 x n1: rows shared with the next chunk
     int64_t nch;       // P1 * n1
     int rows_out;      // window rows of G
     int chunk;         // window rows per chunk (walked with n0 - 1 more drain steps)
@@ -40,9 +41,9 @@ struct AdjColParams {
 };
 
 struct AdjRowParams {
-    const float2 *gz;  // zrows x P1 x n1
-    const float2 *side;  // adj_col's side buffer (see AdjColParams), or null
-    void *gx;          // zrows rows of N1 elements (row stride ld_out)
+    const float2 *gz[kAdjZ];    // zrows x P1 x n1
+    const float2 *side[kAdjZ];  // adj_col's side buffers (see AdjColParams), or null
+    void *gx[kAdjZ];            // zrows rows of N1 elements (row stride ld_out)
     int64_t ld_out;
     int zrows;
     int N1, P1;
@@ -110,7 +111,9 @@ __global__ void __launch_bounds__(128) adj_col_kernel(const __grid_constant__ Ad
     const int n1 = 1 << p.m1;
     const int64_t grow = p.nch * n;  // elements per window row of G
     const float s = p.scale;
-    float2 *side = p.side + (int64_t)blockIdx.y * (n - 1) * p.nch + ch;
+    const float2 *G = p.G[blockIdx.z];
+    float2 *gz = p.gz[blockIdx.z];
+    float2 *side = p.side[blockIdx.z] + (int64_t)blockIdx.y * (n - 1) * p.nch + ch;
 
     // copy the G rows of steps [j0, j0 + GS) that exist (window row qb - 1 - j) into buffer b.
     // The block has 128 = R * CH threads, so copying thread i always takes channel i mod CH
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(128) adj_col_kernel(const __grid_constant__ Ad
     const int k0_f = threadIdx.x / CH;
     const int64_t cg_f = ch0 + cl_f;
     const bool ok_f = cg_f < p.nch;
-    const float2 *gsrc = p.G + (ok_f ? ((cg_f >> p.m1) * n + k0_f) * n1 + (cg_f & (n1 - 1)) : 0);
+    const float2 *gsrc = G + (ok_f ? ((cg_f >> p.m1) * n + k0_f) * n1 + (cg_f & (n1 - 1)) : 0);
     const int64_t kstep = (int64_t)R * n1;  // global distance between a thread's k0 values
     auto fetch = [&](int j0, int b) {
         const int cnt = min(GS, nwin - j0);
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(128) adj_col_kernel(const __grid_constant__ Ad
                     if (r >= qb && !last)
                         side[(int64_t)(r - qb) * p.nch] = y;
                     else
-                        p.gz[(int64_t)r * p.nch + ch] = y;
+                        gz[(int64_t)r * p.nch + ch] = y;
                 }
             }
             if constexpr (J % GS == GS - 1) __syncthreads();  // the buffer is refilled next group
@@ -195,14 +198,16 @@ __global__ void __launch_bounds__(128) adj_row_kernel(const __grid_constant__ Ad
     const int steps = p_hi - pa + 1;
 
     const int64_t rowlen = (int64_t)p.P1 * n;
-    const float2 *zrow = p.gz + (int64_t)(active ? row : 0) * rowlen + c;
+    const float2 *zrow = p.gz[blockIdx.z] + (int64_t)(active ? row : 0) * rowlen + c;
+    const float2 *sidez = p.side[blockIdx.z];
+    void *gx = p.gx[blockIdx.z];
     // the part of this z row adj_col's previous chunk left in its side buffer, if any
     const float2 *srow = nullptr;
-    if (p.side != nullptr && active && p.n0m1 > 0) {
+    if (sidez != nullptr && active && p.n0m1 > 0) {
         const int i = row / p.col_chunk;  // chunk whose windows start at row i * col_chunk
         const int off = row - i * p.col_chunk;
         if (i >= 1 && i * p.col_chunk < p.rows_out && off < p.n0m1)
-            srow = p.side + ((int64_t)(i - 1) * p.n0m1 + off) * rowlen + c;
+            srow = sidez + ((int64_t)(i - 1) * p.n0m1 + off) * rowlen + c;
     }
 
     auto load_z = [&](int j, float2 (&u)[Tree::kIn]) {
@@ -241,9 +246,9 @@ __global__ void __launch_bounds__(128) adj_row_kernel(const __grid_constant__ Ad
                 const float2 y = reduce_residues<R>(tree.template step<J>(u));
                 if (c == 0 && active && p1 < pb) {
                     if constexpr (CPLX)
-                        reinterpret_cast<float2 *>(p.gx)[(int64_t)row * p.ld_out + p1] = y;
+                        reinterpret_cast<float2 *>(gx)[(int64_t)row * p.ld_out + p1] = y;
                     else
-                        reinterpret_cast<float *>(p.gx)[(int64_t)row * p.ld_out + p1] = y.x;
+                        reinterpret_cast<float *>(gx)[(int64_t)row * p.ld_out + p1] = y.x;
                 }
             }
         });

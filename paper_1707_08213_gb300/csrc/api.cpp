@@ -123,6 +123,9 @@ struct swdft2d_plan_s {
     // streams forked from and joined back to the caller's stream, one workspace slot each
     int conc = 1;
     size_t slot_bytes = 0;
+    // all arrays of one shape and band (not persistent): the adjoint runs groups of up to
+    // kAdjZ arrays per launch, each array in its own workspace slot
+    bool uniform = false;
     cudaStream_t side[kConc] = {};
     cudaEvent_t fork_ev = nullptr;
     cudaEvent_t join_ev[kConc] = {};
@@ -653,7 +656,15 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
         for (const auto &a : p->arrays) ws = std::max(ws, align_up(a.ws_bytes_for(a.band_rows(), a.algo)));
         p->conc = (int)std::min<size_t>(kConc, p->arrays.size());
         p->slot_bytes = ws;
-        ws *= (size_t)p->conc;
+        const ArrayPlan &f = p->arrays.front();
+        p->uniform = p->arrays.size() > 1;
+        for (const auto &a : p->arrays)
+            p->uniform = p->uniform && a.N0 == f.N0 && a.N1 == f.N1 && a.ld == f.ld && a.n0 == f.n0 &&
+                         a.n1 == f.n1 && a.dtype == f.dtype && a.q_begin == f.q_begin && a.q_end == f.q_end &&
+                         !a.ternary();
+        const size_t slots = p->uniform ? std::max<size_t>((size_t)p->conc, std::min<size_t>(kAdjZ, p->arrays.size()))
+                                        : (size_t)p->conc;
+        ws *= slots;
     }
     p->ws_bytes = ws;
     *out = p;
@@ -696,6 +707,11 @@ swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t 
         int32_t k = 0;
         for (int m = 0; m <= kMaxLog2; ++m) k += (int)r[m] + (int)c[m];
         *launches = k;
+        return SWDFT_OK;
+    }
+    if (adjoint && plan->uniform) {
+        // one launch pair per group of up to kAdjZ arrays of the same shape
+        *launches = (int32_t)(2 * ((plan->arrays.size() + kAdjZ - 1) / kAdjZ));
         return SWDFT_OK;
     }
     int32_t n = 0;
@@ -810,24 +826,33 @@ swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_g
     swdft_status st = configure(plan);
     if (st != SWDFT_OK) return st;
     cudaStream_t s0 = static_cast<cudaStream_t>(stream);
-    return for_each_array(plan, d_workspace, s0, [&](size_t i, cudaStream_t s, void *slot) -> cudaError_t {
-        const ArrayPlan &a = plan->arrays[i];
+    // arrays first..first+nz-1 (one shape) in one launch pair; array k of the group uses slots[k]
+    auto enqueue_group = [&](size_t first, int nz, void *const *slots, cudaStream_t s) -> cudaError_t {
+        const ArrayPlan &a = plan->arrays[first];
         const int64_t zrows = a.band_rows() + a.n0 - 1;
         const size_t row_bytes = (size_t)a.N1 * a.in_elem();
-        char *gx = static_cast<char *>(d_grad_in[i]);
-        cudaError_t e;
-        // rows no window of the band touches get a zero gradient
-        if (a.q_begin > 0 && (e = cudaMemsetAsync(gx, 0, (size_t)a.q_begin * row_bytes, s)) != cudaSuccess) return e;
-        const int64_t tail = a.N0 - (a.q_begin + zrows);
-        if (tail > 0 && (e = cudaMemsetAsync(gx + (size_t)(a.q_begin + zrows) * row_bytes, 0,
-                                             (size_t)tail * row_bytes, s)) != cudaSuccess)
-            return e;
         AdjColArgs c;
-        c.G = static_cast<const float2 *>(d_grad_out[i]);
-        c.gz = static_cast<float2 *>(slot);
-        c.side = a.adj_side_bytes(a.band_rows()) > 0
-                     ? reinterpret_cast<float2 *>(static_cast<char *>(slot) + align_up(a.z_bytes(a.band_rows())))
-                     : nullptr;
+        AdjRowArgs r;
+        cudaError_t e;
+        for (int k = 0; k < nz; ++k) {
+            char *gx = static_cast<char *>(d_grad_in[first + k]);
+            // rows no window of the band touches get a zero gradient
+            if (a.q_begin > 0 && (e = cudaMemsetAsync(gx, 0, (size_t)a.q_begin * row_bytes, s)) != cudaSuccess)
+                return e;
+            const int64_t tail = a.N0 - (a.q_begin + zrows);
+            if (tail > 0 && (e = cudaMemsetAsync(gx + (size_t)(a.q_begin + zrows) * row_bytes, 0,
+                                                 (size_t)tail * row_bytes, s)) != cudaSuccess)
+                return e;
+            c.G[k] = static_cast<const float2 *>(d_grad_out[first + k]);
+            c.gz[k] = static_cast<float2 *>(slots[k]);
+            c.side[k] = a.adj_side_bytes(a.band_rows()) > 0
+                            ? reinterpret_cast<float2 *>(static_cast<char *>(slots[k]) + align_up(a.z_bytes(a.band_rows())))
+                            : nullptr;
+            r.gz[k] = c.gz[k];
+            r.side[k] = c.side[k];
+            r.gx[k] = gx + (size_t)a.q_begin * row_bytes;
+        }
+        c.nz = nz;
         c.P1 = a.P1;
         c.rows_out = a.band_rows();
         c.m0 = a.m0;
@@ -837,13 +862,10 @@ swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_g
         c.B = 0;  // the launcher uses the one split built per window side
         c.chunk = a.adj_chunk(a.band_rows());
         if ((e = launch_adj_col(c, s)) != cudaSuccess) return e;
-        AdjRowArgs r;
-        r.gz = static_cast<const float2 *>(slot);
-        r.side = c.side;
+        r.nz = nz;
         r.col_chunk = c.chunk;
         r.rows_out = c.rows_out;
         r.m0 = a.m0;
-        r.gx = gx + (size_t)a.q_begin * row_bytes;
         r.ld_out = a.N1;
         r.cplx = a.dtype == SWDFT_C64;
         r.zrows = zrows;
@@ -852,10 +874,26 @@ swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_g
         r.om64 = plan->om64;
         r.B = 0;  // the launcher uses the one split built per window side
         const int64_t target = (int64_t)plan->sm_count * 1024;
-        const int64_t nchunk = std::max<int64_t>(1, target / std::max<int64_t>(1, zrows << adj_row_split(a.m1)));
+        const int64_t nchunk =
+            std::max<int64_t>(1, target / std::max<int64_t>(1, (zrows << adj_row_split(a.m1)) * nz));
         // chunks no shorter than n1: each re-walks n1-1 columns of warm-up
         r.chunk = std::min<int64_t>(a.N1, std::max<int64_t>((a.N1 + nchunk - 1) / nchunk, a.n1));
         return launch_adj_row(r, s);
+    };
+    if (plan->uniform) {
+        // one launch pair per group of up to kAdjZ arrays, on the caller's stream
+        const size_t n = plan->arrays.size();
+        for (size_t first = 0; first < n; first += kAdjZ) {
+            const int nz = (int)std::min<size_t>(kAdjZ, n - first);
+            void *slots[kAdjZ];
+            for (int k = 0; k < nz; ++k) slots[k] = static_cast<char *>(d_workspace) + (size_t)k * plan->slot_bytes;
+            if (enqueue_group(first, nz, slots, s0) != cudaSuccess) return SWDFT_ERR_CUDA;
+        }
+        return SWDFT_OK;
+    }
+    return for_each_array(plan, d_workspace, s0, [&](size_t i, cudaStream_t s, void *slot) -> cudaError_t {
+        void *slots[1] = {slot};
+        return enqueue_group(i, 1, slots, s);
     });
 }
 

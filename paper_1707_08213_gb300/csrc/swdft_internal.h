@@ -184,10 +184,13 @@ cudaError_t launch_fused_tree(const FusedTreeArgs &a, cudaStream_t s);
 // Work is split by window rows: chunks of `chunk` windows (>= n0-1; the last may be shorter),
 // each reading its rows of G once.  The n0-1 gz rows after a chunk (not the last) are written
 // to side[chunk index] instead of gz; adj_row adds them (AdjRowArgs.side).
+// Arrays of one shape may share a launch: array z of nz (< kAdjZ) uses G[z], gz[z], side[z].
+constexpr int kAdjZ = 8;
 struct AdjColArgs {
-    const float2 *G = nullptr;
-    float2 *gz = nullptr;
-    float2 *side = nullptr;  // adj_side_elems(...) complex64, or null when there is one chunk
+    const float2 *G[kAdjZ] = {};
+    float2 *gz[kAdjZ] = {};
+    float2 *side[kAdjZ] = {};  // adj_side_elems(...) complex64 each, or null when there is one chunk
+    int nz = 1;
     int64_t P1 = 0, rows_out = 0;
     int m0 = 0, m1 = 0;
     float scale = 1.f;
@@ -202,12 +205,13 @@ int64_t adj_side_elems(int64_t rows_out, int m0, int64_t P1, int m1, int64_t req
 // Adjoint of the row levels: gx[r][p1] = sum_{j1,k1} gz[r][p1-j1][k1] w_{n1}^{+j1 k1}
 // (real part stored for float32 inputs), for zrows rows of N1 columns.
 struct AdjRowArgs {
-    const float2 *gz = nullptr;
-    const float2 *side = nullptr;  // adj_col's side buffer (null: none)
+    const float2 *gz[kAdjZ] = {};
+    const float2 *side[kAdjZ] = {};  // adj_col's side buffers (null: none)
+    void *gx[kAdjZ] = {};
+    int nz = 1;
     int64_t col_chunk = 0;         // adj_col's chunk (adj_col_chunk), rows_out, m0
     int64_t rows_out = 0;
     int m0 = 0;
-    void *gx = nullptr;
     int64_t ld_out = 0;
     int cplx = 0;
     int64_t zrows = 0, N1 = 0;

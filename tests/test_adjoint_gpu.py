@@ -174,3 +174,29 @@ def test_adjoint_of_persistent_batch_plan(sw):
             ref = ref.real
         err = workloads.adjoint_error(v.cpu().numpy(), ref, workloads.adjoint_pixel_norms(G, N0, N1))
         assert err <= TOL, f"{(N0, N1, n0, n1)}: {err:.3e}"
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_adjoint_of_same_shape_arrays_in_grouped_launches(sw, cplx):
+    """Eleven arrays of one shape: the adjoint runs them as a group of eight and a group of
+    three per launch; each result equals its one-array plan's bit for bit and the oracle's."""
+    N0, N1, n0, n1 = 70, 45, 16, 8
+    band = (5, 49)
+    P1 = N1 - n1 + 1
+    Gs = [_G(200 + i, band[1] - band[0], P1, n0, n1) for i in range(11)]
+    Gd = [torch.from_numpy(G).cuda() for G in Gs]
+    t = sw.Transform([(N0, N1, n0, n1, int(cplx))] * 11, bands=[band] * 11)
+    assert t.plan.launch_count(adjoint=True) == 4
+    got = t.adjoint(Gd)
+    torch.cuda.synchronize()
+    for i, (G, g) in enumerate(zip(Gs, got)):
+        one = sw.Transform([(N0, N1, n0, n1, int(cplx))], bands=[band]).adjoint([Gd[i]])[0]
+        torch.cuda.synchronize()
+        assert torch.equal(g, one)
+        full = np.zeros((N0 - n0 + 1, P1, n0, n1), np.complex64)
+        full[band[0]:band[1]] = G
+        ref = oracle.swdft2d_adjoint(full, N0, N1)
+        if not cplx:
+            ref = ref.real
+        err = workloads.adjoint_error(g.cpu().numpy(), ref, workloads.adjoint_pixel_norms(full, N0, N1))
+        assert err <= TOL, f"array {i}: {err:.3e}"
