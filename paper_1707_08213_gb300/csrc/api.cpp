@@ -175,7 +175,8 @@ int64_t col_chunk_for(const ArrayPlan &a, int nchunks) {
     return std::min(rows, std::max<int64_t>(chunk, 2 * a.n0));
 }
 
-void default_config(ArrayPlan &a, int sm_count) {
+// conc: arrays of the plan that run at once (their z buffers share L2).
+void default_config(ArrayPlan &a, int sm_count, int conc) {
     TreeConfig c;
     // row levels: thread = (row, residue, chunk of window columns).  About 64K threads in
     // flight (measured best on the 512x512/32x32 and 1024x2048/16x64 workloads: B = 3 with
@@ -191,8 +192,16 @@ void default_config(ArrayPlan &a, int sm_count) {
     // group per block (32 * 2^B threads)
     c.col_B = a.m0 >= 6 ? 3 : std::min(a.m0, 2);
     c.col_groups = 1;
-    c.col_chunk = col_chunk_for(a, 8);
-    c.fused = false;
+    // fused form (row levels inside the column tile, n1 <= 32): it recomputes each z value
+    // from the input (log2 n1 butterflies) instead of writing and re-reading z, which wins for
+    // small windows (z is 1/n0 of the output) and when the z of the arrays in flight would
+    // not stay in L2 (measured on 256..1024-square arrays with the 4x4 .. 64x16 windows:
+    // fused faster for n0 n1 <= 64 everywhere and for n0 >= 16 once z exceeds ~100 MB)
+    const bool can_fuse = !a.ternary() && a.m1 <= 5 && a.algo == SWDFT_ALGO_TREE_F32;
+    const bool small = a.n0 * a.n1 <= 64;
+    const double z_live = (double)a.z_bytes(a.band_rows()) * std::max(1, conc);
+    c.fused = can_fuse && (small || (a.n0 >= 16 && z_live > 96e6));
+    c.col_chunk = col_chunk_for(a, c.fused && small ? 16 : 8);
     a.cfg = c;
 }
 
@@ -204,7 +213,7 @@ swdft_status configure(swdft2d_plan_t plan) {
         return SWDFT_ERR_CUDA;
     plan->sm_count = sms > 0 ? sms : 152;
     for (auto &a : plan->arrays)
-        if (!a.tuned) default_config(a, plan->sm_count);
+        if (!a.tuned) default_config(a, plan->sm_count, plan->conc);
     if (plan->conc > 1) {
         if (cudaEventCreateWithFlags(&plan->fork_ev, cudaEventDisableTiming) != cudaSuccess) return SWDFT_ERR_CUDA;
         for (int k = 0; k < plan->conc; ++k) {
@@ -667,6 +676,8 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
         ws *= slots;
     }
     p->ws_bytes = ws;
+    // launch shapes known at plan time (so launch_count is right before the first execute)
+    for (auto &a : p->arrays) default_config(a, p->sm_count, p->conc);
     *out = p;
     return SWDFT_OK;
 }
@@ -795,7 +806,7 @@ swdft_status swdft2d_set_tree_config(swdft2d_plan_t plan, int32_t i, int32_t row
     TreeConfig c;
     if (fused == -1) {
         ArrayPlan tmp = a;
-        default_config(tmp, plan->sm_count);
+        default_config(tmp, plan->sm_count, plan->conc);
         c.fused = tmp.cfg.fused;
     } else {
         c.fused = fused == 1 && a.m1 <= 5 && !a.ternary();
@@ -971,7 +982,7 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SWDFT_ERR_CUDA;
     for (size_t i = 0; i < plan->arrays.size(); ++i) {
         ArrayPlan &a = plan->arrays[i];
-        default_config(a, plan->sm_count);
+        default_config(a, plan->sm_count, plan->conc);
         if (a.ternary()) continue;  // one launch shape per ternary kernel: nothing to choose
         const TreeConfig base = a.cfg;
         std::vector<TreeConfig> cands;

@@ -153,8 +153,11 @@ def test_execute_rejects_bad_buffers_before_cuda(nat):
 
 
 def test_launch_count(nat):
+    # small windows use the fused form (one launch), larger ones two passes
     p = nat.Plan([shp(16, 16, 4, 4), shp(32, 32, 8, 8)])
-    assert p.launch_count() == 4
+    assert p.launch_count() == 2
+    assert nat.Plan([shp(64, 64, 32, 32), shp(64, 64, 16, 64)]).launch_count() == 4
+    assert nat.Plan([shp(64, 64, 4, 4)]).launch_count(adjoint=True) == 2
 
 
 def test_twiddle_table_symmetry_via_plan(nat):
@@ -201,7 +204,8 @@ def test_kd_output_shape_workspace_and_launches(nat):
     # one and two dimensions run the 2D plan (two passes)
     assert nat.PlanKD((30,), (8,)).output_shape() == (23, 8)
     assert nat.PlanKD((30, 20), (8, 4)).output_shape() == (23, 17, 8, 4)
-    assert nat.PlanKD((30, 20), (8, 4)).launch_count() == 2
+    assert nat.PlanKD((30, 20), (8, 4)).launch_count() == 1      # fused form for small windows
+    assert nat.PlanKD((300, 200), (32, 16)).launch_count() == 2
 
 
 
