@@ -181,7 +181,6 @@ void default_config(ArrayPlan &a, int sm_count, int conc) {
     // row levels: thread = (row, residue, chunk of window columns).  About 64K threads in
     // flight (measured best on the 512x512/32x32 and 1024x2048/16x64 workloads: B = 3 with
     // 16-32 column chunks, B = 2 with 128-column chunks), chunks no shorter than n1/2.
-    (void)sm_count;
     c.row_B = a.r1 == 3 ? 0 : (a.m1 >= 6 ? 2 : std::min(a.m1, 3));  // ternary rows: one thread each
     const int64_t rows = a.band_rows() + a.n0 - 1;
     const int64_t per_row = a.r1 == 3 ? (a.m1 >= 1 ? 3 : 1) : (int64_t(1) << c.row_B);  // threads per row
@@ -201,7 +200,13 @@ void default_config(ArrayPlan &a, int sm_count, int conc) {
     const bool small = a.n0 * a.n1 <= 64;
     const double z_live = (double)a.z_bytes(a.band_rows()) * std::max(1, conc);
     c.fused = can_fuse && (small || (a.n0 >= 16 && z_live > 96e6));
-    c.col_chunk = col_chunk_for(a, c.fused && small ? 16 : 8);
+    // chunks of window rows: about eight per channel group (sixteen for fused small windows),
+    // more when there are few channel groups (narrow arrays), so that the pass has at least
+    // four blocks per SM; col_chunk_for keeps every chunk at 2 n0 rows or more
+    const int64_t ch_groups = (a.P1 * a.n1 + 31) / 32;
+    const int64_t want = (4LL * std::max(1, sm_count) + ch_groups - 1) / ch_groups;
+    const int nchunks = (int)std::min<int64_t>(65535, std::max<int64_t>(c.fused && small ? 16 : 8, want));
+    c.col_chunk = col_chunk_for(a, nchunks);
     a.cfg = c;
 }
 
