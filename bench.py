@@ -545,6 +545,24 @@ def fig4_measurement(torch, sw):
             s.synchronize()
             ent[f"{name}_us"] = round(1e3 * e0.elapsed_time(e1) / 200, 2)
             del t, out
+        # autotuned with algo="auto": tuned tree launch shapes, fused form, or the split-bf16
+        # tensor-core form, whichever the plan's own timing finds fastest
+        t = sw.Transform([(M0, M1, a0, a1, sw.R32)], algo="auto", flags=sw.FLAG_GRAPH)
+        out = t.empty_outputs()
+        with torch.cuda.stream(s):
+            t.autotune([x], out)
+            for _ in range(5):
+                t.forward([x], out)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(200):
+                t.forward([x], out)
+            e1.record(s)
+        s.synchronize()
+        ent["autotuned_graph_us"] = round(1e3 * e0.elapsed_time(e1) / 200, 2)
+        ent["autotuned_algo"] = t.plan.algo()
+        del t, out
         res["per_n"][str(a0)] = ent
     return res
 

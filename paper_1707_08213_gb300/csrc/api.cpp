@@ -61,6 +61,7 @@ struct ArrayPlan {
     TreeConfig cfg;
     bool tuned = false;
     int algo = SWDFT_ALGO_TREE_F32;  // per array: tree or one of the tensor-core forms
+    bool algo_auto = false;          // made with SWDFT_ALGO_AUTO: the autotuner may pick a form
     int64_t tc_chunk = 48;           // window rows per tensor-core CTA
 
     int64_t band_rows() const { return q_end - q_begin; }
@@ -96,6 +97,13 @@ struct ArrayPlan {
         const size_t fwd = algo >= SWDFT_ALGO_TC_BF16X3 ? align_up(planes_bytes(rows_out, algo)) + kAlign
                                                         : align_up(z_bytes(rows_out));
         return std::max(fwd, adj_bytes(rows_out));
+    }
+    // the workspace a plan reserves: room for the split-bf16 form too when the autotuner may
+    // choose it
+    size_t ws_bytes_plan(int64_t rows_out) const {
+        size_t w = ws_bytes_for(rows_out, algo);
+        if (algo_auto && tc_eligible()) w = std::max(w, ws_bytes_for(rows_out, SWDFT_ALGO_TC_BF16X3));
+        return w;
     }
 };
 
@@ -642,6 +650,7 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
         // binary column kernel needs power-of-two rows
         if (r1 == 3 && r0 == 2 && m0 > 0) return SWDFT_ERR_UNSUPPORTED;
         a.algo = (algo == SWDFT_ALGO_AUTO) ? SWDFT_ALGO_TREE_F32 : algo;
+        a.algo_auto = algo == SWDFT_ALGO_AUTO && !(flags & SWDFT_FLAG_PERSISTENT);
         if (a.algo >= SWDFT_ALGO_TC_BF16X3 && !a.tc_eligible()) return SWDFT_ERR_UNSUPPORTED;
         if (a.ternary() && (flags & SWDFT_FLAG_PERSISTENT)) return SWDFT_ERR_UNSUPPORTED;
     }
@@ -667,7 +676,7 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
         p->conc = 4;
     } else {
         // up to four arrays run at once (plan-owned streams), each with its own z slot
-        for (const auto &a : p->arrays) ws = std::max(ws, align_up(a.ws_bytes_for(a.band_rows(), a.algo)));
+        for (const auto &a : p->arrays) ws = std::max(ws, align_up(a.ws_bytes_plan(a.band_rows())));
         p->conc = (int)std::min<size_t>(kConc, p->arrays.size());
         p->slot_bytes = ws;
         const ArrayPlan &f = p->arrays.front();
@@ -705,7 +714,7 @@ swdft_status swdft2d_workspace_size(swdft2d_plan_t plan, size_t *bytes) {
 
 swdft_status swdft2d_get_algo(swdft2d_plan_t plan, int32_t *algo) {
     if (!plan || !algo) return SWDFT_ERR_INVALID_ARG;
-    *algo = plan->algo;
+    *algo = plan->arrays.front().algo;  // after autotuning, the form array 0 runs
     return SWDFT_OK;
 }
 
@@ -731,7 +740,8 @@ swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t 
         return SWDFT_OK;
     }
     int32_t n = 0;
-    for (const auto &a : plan->arrays) n += (!adjoint && a.cfg.fused && a.m1 <= 5) ? 1 : 2;
+    for (const auto &a : plan->arrays)
+        n += (!adjoint && a.algo == SWDFT_ALGO_TREE_F32 && a.cfg.fused && a.m1 <= 5) ? 1 : 2;
     *launches = n;
     return SWDFT_OK;
 }
@@ -934,7 +944,7 @@ swdft_status swdft2d_execute_host(swdft2d_plan_t plan, const void *const *h_in,
             const int64_t br = std::min(band, a.band_rows());
             in_max = std::max(in_max, align_up((size_t)a.N0 * a.ld * a.in_elem()));
             out_max = std::max(out_max, align_up((size_t)br * a.out_row_bytes()));
-            ws_max = std::max(ws_max, align_up(a.ws_bytes_for(br, a.algo)));
+            ws_max = std::max(ws_max, align_up(a.ws_bytes_plan(br)));
         }
         if (cudaMalloc(&plan->io_in, in_max) != cudaSuccess) return SWDFT_ERR_OOM;
         if (cudaMalloc(&plan->io_ws, ws_max) != cudaSuccess) return SWDFT_ERR_OOM;
@@ -987,6 +997,7 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SWDFT_ERR_CUDA;
     for (size_t i = 0; i < plan->arrays.size(); ++i) {
         ArrayPlan &a = plan->arrays[i];
+        if (a.algo_auto) a.algo = SWDFT_ALGO_TREE_F32;  // the tree is tuned first, then compared
         default_config(a, plan->sm_count, plan->conc);
         if (a.ternary()) continue;  // one launch shape per ternary kernel: nothing to choose
         const TreeConfig base = a.cfg;
@@ -1071,13 +1082,27 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
         }
         a.cfg = best_c;
         a.tuned = true;
+        // tree or dense contraction: with SWDFT_ALGO_AUTO, the split-bf16 tensor-core form (the
+        // one within the 1e-5 bar) competes with the tuned tree on the whole forward
+        if (a.algo_auto && a.tc_eligible()) {
+            a.algo = SWDFT_ALGO_TC_BF16X3;
+            float ms = 0.f;
+            ok = time_pass(best_c, 3, &ms);
+            if (!ok || ms >= best) a.algo = SWDFT_ALGO_TREE_F32;
+            else best = ms;
+            if (!ok) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return SWDFT_ERR_CUDA;
+            }
+        }
         if (const char *path = std::getenv("SWDFT_TUNE_CACHE")) {
             if (FILE *f = std::fopen(path, "a")) {
                 std::fprintf(f,
                              "{\"N0\": %lld, \"N1\": %lld, \"n0\": %d, \"n1\": %d, \"dtype\": %d, "
-                             "\"fused\": %d, \"row_B\": %d, \"row_chunk\": %lld, \"col_B\": %d, "
+                             "\"algo\": %d, \"fused\": %d, \"row_B\": %d, \"row_chunk\": %lld, \"col_B\": %d, "
                              "\"col_chunk\": %lld, \"col_groups\": %d, \"ms\": %.6f}\n",
-                             (long long)a.N0, (long long)a.N1, a.n0, a.n1, a.dtype, (int)best_c.fused,
+                             (long long)a.N0, (long long)a.N1, a.n0, a.n1, a.dtype, a.algo, (int)best_c.fused,
                              best_c.row_B, (long long)best_c.row_chunk, best_c.col_B,
                              (long long)best_c.col_chunk, best_c.col_groups, best);
                 std::fclose(f);

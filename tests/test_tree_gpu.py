@@ -228,3 +228,30 @@ def test_fused_tree_matches_oracle_and_two_pass(sw, N0, N1, n0, n1, cplx, chunk)
     assert t.plan.launch_count() == 1
     assert torch.equal(two, fused)
     assert_close_to_oracle(fused, x, n0, n1)
+
+
+@pytest.mark.parametrize("N0,N1,n0,n1", [(100, 100, 64, 64), (512, 512, 32, 32)])
+def test_autotune_chooses_tree_or_tensor_cores(sw, N0, N1, n0, n1, tmp_path, monkeypatch):
+    """With algo="auto" the autotuner times the tuned tree against the split-bf16 tensor-core
+    form and keeps the faster; either way the result stays within the 1e-5 bar."""
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("SWDFT_TUNE_CACHE", str(cache))
+    x = workloads.random_array(400 + n0, N0, N1)
+    t = sw.Transform([(N0, N1, n0, n1, 0)], algo="auto")
+    xd = torch.from_numpy(x).cuda()
+    t.autotune([xd])
+    assert t.plan.algo() in ("tree", "tc_bf16x3")
+    a = t.forward([xd])[0]
+    torch.cuda.synchronize()
+    assert sw._native.check_device() == 0
+    if N0 <= 100:
+        assert_close_to_oracle(a, x, n0, n1)
+    else:
+        q0, q1 = _sample_windows(N0 - n0 + 1, N1 - n1 + 1, 512, 9)
+        got = a[torch.from_numpy(q0).cuda(), torch.from_numpy(q1).cuda()].cpu().numpy()
+        ref = oracle.swdft2d_windows(x, n0, n1, q0, q1, threads=ORACLE_THREADS)
+        err, _ = workloads.normalised_error(got, ref, workloads.window_sq_norms_at(x, n0, n1, q0, q1))
+        assert err <= TOL
+    import json
+    line = json.loads(cache.read_text().strip().splitlines()[-1])
+    assert line["algo"] in (1, 2) and (line["algo"] == 2) == (t.plan.algo() == "tc_bf16x3")
