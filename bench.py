@@ -62,7 +62,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the tensor-core, batch and adjoint side measurements")
+                    help="skip the side measurements (tensor-core forms, batch, adjoint, volume, stream, Fig. 4 shapes, radix 3, complex workload)")
     return ap.parse_args()
 
 
