@@ -4,7 +4,8 @@ include/swdftkd.h) with the FP64 k-dimensional oracle.
 Bar as for 2D: max over coefficients of |a_gpu - a_oracle| / ||x_w||_2 <= 1e-5 per window on
 the unitary scale.  Small arrays are compared on every coefficient (shapes that span
 several 32-channel tiles and row chunks, with ragged tails and windows of 1 and 64 along
-some axes); the 128^3 volume on sampled windows plus per-window Parseval over all windows.
+some axes); the 128^3 volume and a 32^4 complex array on sampled windows plus per-window
+Parseval over all windows.
 """
 import numpy as np
 import pytest
@@ -120,5 +121,31 @@ def test_volume_128_full_size(sw):
         e = torch.view_as_real(a[r:r + 16]).pow(2).sum(dim=(3, 4, 5, 6)).double()
         worst = max(worst, float(((e - sq[r:r + 16]).abs() / sq[r:r + 16]).max()))
     assert worst <= 1e-5, f"Parseval relative error {worst:.3e}"
+    del a
+    torch.cuda.empty_cache()
+
+
+def test_four_dimensions_full_size(sw):
+    """32^4 complex, 4x4x4x4 windows (29^4 x 256 coefficients, 1.45 GB): sampled windows
+    against the oracle plus Parseval on every window."""
+    x = workloads.random_array_kd(46, (32, 32, 32, 32), complex_input=True)
+    n = (4, 4, 4, 4)
+    a, t = run_kd(sw, x, n)
+    assert t.plan.launch_count() == 4
+    P = a.shape[:4]
+    rng = np.random.default_rng(47)
+    q = np.stack([rng.integers(0, p, 2048) for p in P], axis=1)
+    q = np.concatenate([q, np.zeros((1, 4), np.int64), np.array([[p - 1 for p in P]])])
+    qd = torch.from_numpy(q).cuda()
+    got = a[qd[:, 0], qd[:, 1], qd[:, 2], qd[:, 3]].cpu().numpy()
+    ref = oracle.swdftkd_windows(x, n, q, threads=THREADS)
+    err, _ = workloads.normalised_error(got, ref, workloads.window_sq_norms_kd_at(x, n, q))
+    assert err <= TOL, f"sampled windows: {err:.3e}"
+    sq = torch.from_numpy(workloads.window_sq_norms_kd(x, n)).cuda()
+    worst = 0.0
+    for r in range(0, P[0], 8):
+        e = torch.view_as_real(a[r:r + 8]).pow(2).sum(dim=(4, 5, 6, 7, 8)).double()
+        worst = max(worst, float(((e - sq[r:r + 8]).abs() / sq[r:r + 8]).max()))
+    assert worst <= 1e-5, f"Parseval {worst:.3e}"
     del a
     torch.cuda.empty_cache()
