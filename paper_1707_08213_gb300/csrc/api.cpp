@@ -62,6 +62,7 @@ struct ArrayPlan {
     bool tuned = false;
     int algo = SWDFT_ALGO_TREE_F32;  // per array: tree or one of the tensor-core forms
     bool algo_auto = false;          // made with SWDFT_ALGO_AUTO: the autotuner may pick a form
+    bool batch_fused = false;        // persistent batch: run in a fused group (no row tiles, no z)
     int64_t tc_chunk = 48;           // window rows per tensor-core CTA
 
     int64_t band_rows() const { return q_end - q_begin; }
@@ -152,6 +153,13 @@ struct swdft2d_plan_s {
     int col_off[kMaxLog2 + 1] = {}, col_n[kMaxLog2 + 1] = {};
     int64_t row_items[kMaxLog2 + 1] = {}, col_items[kMaxLog2 + 1] = {};
     int64_t row_slots[kMaxLog2 + 1] = {}, col_slots[kMaxLog2 + 1] = {};
+    // fused groups, index m0 * kBatchFusedM1 + m1, on their own side streams
+    static constexpr int kFz = (kMaxLog2 + 1) * kBatchFusedM1;
+    int fz_off[kFz] = {}, fz_n[kFz] = {};
+    int64_t fz_items[kFz] = {}, fz_slots[kFz] = {};
+    bool any_fused = false;
+    cudaStream_t fside[kConc] = {};
+    cudaEvent_t fjoin_ev[kConc] = {};
     // host-buffer pipeline (SWDFT_FLAG_HOST_IO), allocated at the first execute_host
     bool io_ready = false;
     int64_t io_band = 0;
@@ -236,7 +244,7 @@ swdft_status configure(swdft2d_plan_t plan) {
     }
     if (plan->flags & SWDFT_FLAG_PERSISTENT) {
         const size_t n = plan->arrays.size();
-        plan->desc_bytes = sizeof(BatchImage) * n + 2 * sizeof(BatchClassEntry) * n;
+        plan->desc_bytes = sizeof(BatchImage) * n + 3 * sizeof(BatchClassEntry) * n;
         if (cudaHostAlloc((void **)&plan->desc_host, plan->desc_bytes, cudaHostAllocDefault) != cudaSuccess)
             return SWDFT_ERR_OOM;
         if (cudaMalloc((void **)&plan->desc_dev, plan->desc_bytes) != cudaSuccess) return SWDFT_ERR_OOM;
@@ -247,6 +255,20 @@ swdft_status configure(swdft2d_plan_t plan) {
             if (batch_blocks_per_sm(m, &row_bps, &col_bps) != cudaSuccess) return SWDFT_ERR_CUDA;
             plan->row_slots[m] = (int64_t)plan->sm_count * std::max(1, row_bps);
             plan->col_slots[m] = (int64_t)plan->sm_count * std::max(1, col_bps);
+        }
+        if (plan->any_fused) {
+            for (const auto &a : plan->arrays) {
+                if (!a.batch_fused) continue;
+                const int f = a.m0 * kBatchFusedM1 + a.m1;
+                if (plan->fz_slots[f] > 0) continue;
+                int bps = 0;
+                if (batch_fused_blocks_per_sm(a.m0, a.m1, &bps) != cudaSuccess) return SWDFT_ERR_CUDA;
+                plan->fz_slots[f] = (int64_t)plan->sm_count * std::max(1, bps);
+            }
+            for (int k = 0; k < plan->conc; ++k) {
+                if (cudaStreamCreateWithFlags(&plan->fside[k], cudaStreamNonBlocking) != cudaSuccess) return SWDFT_ERR_CUDA;
+                if (cudaEventCreateWithFlags(&plan->fjoin_ev[k], cudaEventDisableTiming) != cudaSuccess) return SWDFT_ERR_CUDA;
+            }
         }
     }
     plan->configured = true;
@@ -260,6 +282,7 @@ void fill_batch(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out
     BatchImage *imgs = reinterpret_cast<BatchImage *>(plan->desc_host);
     BatchClassEntry *row_ent = reinterpret_cast<BatchClassEntry *>(imgs + n);
     BatchClassEntry *col_ent = row_ent + n;
+    BatchClassEntry *fz_ent = col_ent + n;
     for (size_t i = 0; i < n; ++i) {
         const ArrayPlan &a = plan->arrays[i];
         BatchImage d;
@@ -286,6 +309,7 @@ void fill_batch(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out
         d.m0 = a.m0;
         d.m1 = a.m1;
         d.cplx = a.dtype == SWDFT_C64;
+        d.fused = a.batch_fused ? 1 : 0;
         const int rows_per_block = 128 >> batch_row_B(a.m1);
         d.row_blocks = (int)((zrows + rows_per_block - 1) / rows_per_block);
         d.row_chunks = (int)((a.P1 + d.row.chunk - 1) / d.row.chunk);
@@ -300,7 +324,7 @@ void fill_batch(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out
         plan->row_off[m] = pos;
         int64_t items = 0;
         for (size_t i = 0; i < n; ++i)
-            if (imgs[i].m1 == m) {
+            if (imgs[i].m1 == m && !imgs[i].fused) {
                 row_ent[pos].item0 = items;
                 row_ent[pos].img = (int)i;
                 row_ent[pos].pad = 0;
@@ -315,7 +339,7 @@ void fill_batch(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out
         plan->col_off[m] = pos;
         int64_t items = 0;
         for (size_t i = 0; i < n; ++i)
-            if (imgs[i].m0 == m) {
+            if (imgs[i].m0 == m && !imgs[i].fused) {
                 col_ent[pos].item0 = items;
                 col_ent[pos].img = (int)i;
                 col_ent[pos].pad = 0;
@@ -324,6 +348,22 @@ void fill_batch(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out
             }
         plan->col_n[m] = pos - plan->col_off[m];
         plan->col_items[m] = items;
+    }
+    // fused groups: column tiles of the fused arrays, grouped by (m0, m1)
+    pos = 0;
+    for (int f = 0; f < swdft2d_plan_s::kFz; ++f) {
+        plan->fz_off[f] = pos;
+        int64_t items = 0;
+        for (size_t i = 0; i < n; ++i)
+            if (imgs[i].fused && imgs[i].m0 * kBatchFusedM1 + imgs[i].m1 == f) {
+                fz_ent[pos].item0 = items;
+                fz_ent[pos].img = (int)i;
+                fz_ent[pos].pad = 0;
+                items += (int64_t)imgs[i].col_blocks * imgs[i].col_chunks;
+                ++pos;
+            }
+        plan->fz_n[f] = pos - plan->fz_off[f];
+        plan->fz_items[f] = items;
     }
 }
 
@@ -334,12 +374,29 @@ swdft_status launch_batch(swdft2d_plan_t plan, const unsigned char *desc, cudaSt
     const BatchImage *imgs = reinterpret_cast<const BatchImage *>(desc);
     const BatchClassEntry *row_ent = reinterpret_cast<const BatchClassEntry *>(imgs + n);
     const BatchClassEntry *col_ent = row_ent + n;
-    for (int phase = 0; phase < 2; ++phase) {
+    const BatchClassEntry *fz_ent = col_ent + n;
+    swdft_status st = SWDFT_OK;
+    // fused groups need no z: they start with the row groups on their own streams and are
+    // joined at the end
+    if (plan->any_fused) {
+        if (cudaEventRecord(plan->fork_ev, s) != cudaSuccess) return SWDFT_ERR_CUDA;
+        int k = 0;
+        for (int j = 0; j < plan->conc; ++j)
+            if (cudaStreamWaitEvent(plan->fside[j], plan->fork_ev, 0) != cudaSuccess) return SWDFT_ERR_CUDA;
+        for (int f = 0; f < swdft2d_plan_s::kFz && st == SWDFT_OK; ++f) {
+            if (plan->fz_n[f] == 0) continue;
+            if (launch_batch_fused_class(f / kBatchFusedM1, f % kBatchFusedM1, imgs, fz_ent + plan->fz_off[f],
+                                         plan->fz_n[f], plan->fz_items[f], plan->om64, plan->fz_slots[f],
+                                         plan->fside[k % plan->conc]) != cudaSuccess)
+                st = SWDFT_ERR_CUDA;
+            ++k;
+        }
+    }
+    for (int phase = 0; phase < 2 && st == SWDFT_OK; ++phase) {
         const bool col = phase == 1;
         if (cudaEventRecord(plan->fork_ev, s) != cudaSuccess) return SWDFT_ERR_CUDA;
         for (int k = 0; k < plan->conc; ++k)
             if (cudaStreamWaitEvent(plan->side[k], plan->fork_ev, 0) != cudaSuccess) return SWDFT_ERR_CUDA;
-        swdft_status st = SWDFT_OK;
         int k = 0;
         for (int m = 0; m <= kMaxLog2 && st == SWDFT_OK; ++m) {
             const int cnt = col ? plan->col_n[m] : plan->row_n[m];
@@ -355,9 +412,14 @@ swdft_status launch_batch(swdft2d_plan_t plan, const unsigned char *desc, cudaSt
             if (cudaEventRecord(plan->join_ev[j], plan->side[j]) != cudaSuccess) st = SWDFT_ERR_CUDA;
             if (cudaStreamWaitEvent(s, plan->join_ev[j], 0) != cudaSuccess) st = SWDFT_ERR_CUDA;
         }
-        if (st != SWDFT_OK) return st;
     }
-    return SWDFT_OK;
+    // always join the fused streams back (a capture must end with every stream joined)
+    if (plan->any_fused)
+        for (int j = 0; j < plan->conc; ++j) {
+            if (cudaEventRecord(plan->fjoin_ev[j], plan->fside[j]) != cudaSuccess) st = SWDFT_ERR_CUDA;
+            if (cudaStreamWaitEvent(s, plan->fjoin_ev[j], 0) != cudaSuccess) st = SWDFT_ERR_CUDA;
+        }
+    return st;
 }
 
 // Direct (non-graph) persistent execute: refill the staging once its previous upload ran,
@@ -674,6 +736,13 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
             ws += align_up(a.ws_bytes_for(a.band_rows(), SWDFT_ALGO_TREE_F32));
         }
         p->conc = 4;
+        // small windows (n0 n1 <= 64, where z is 1/n0 >= 1/8 of the output) run in fused
+        // groups; measured on the 256-image batch, fusing larger windows as well was slower
+        // (28.1 ms with every n0 >= 16 fused, 26.9 with none, 26.2 with small windows only)
+        for (auto &a : p->arrays) {
+            a.batch_fused = !a.ternary() && a.m1 < kBatchFusedM1 && a.n0 * a.n1 <= 64;
+            p->any_fused = p->any_fused || a.batch_fused;
+        }
     } else {
         // up to four arrays run at once (plan-owned streams), each with its own z slot
         for (const auto &a : p->arrays) ws = std::max(ws, align_up(a.ws_bytes_plan(a.band_rows())));
@@ -724,13 +793,18 @@ swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t 
     // adjoint: column + row adjoint pass per array
     if (!adjoint && (plan->flags & SWDFT_FLAG_PERSISTENT)) {
         // one persistent kernel per row-window group and per column-window group
-        bool r[kMaxLog2 + 1] = {}, c[kMaxLog2 + 1] = {};
+        bool r[kMaxLog2 + 1] = {}, c[kMaxLog2 + 1] = {}, f[swdft2d_plan_s::kFz] = {};
         for (const auto &a : plan->arrays) {
-            r[a.m1] = true;
-            c[a.m0] = true;
+            if (a.batch_fused) {
+                f[a.m0 * kBatchFusedM1 + a.m1] = true;
+            } else {
+                r[a.m1] = true;
+                c[a.m0] = true;
+            }
         }
         int32_t k = 0;
         for (int m = 0; m <= kMaxLog2; ++m) k += (int)r[m] + (int)c[m];
+        for (int j = 0; j < swdft2d_plan_s::kFz; ++j) k += (int)f[j];
         *launches = k;
         return SWDFT_OK;
     }
@@ -1130,6 +1204,8 @@ swdft_status swdft2d_destroy(swdft2d_plan_t plan) {
     }
     if (plan->desc_host) cudaFreeHost(plan->desc_host);
     for (int k = 0; k < kConc; ++k) {
+        if (plan->fside[k]) cudaStreamDestroy(plan->fside[k]);
+        if (plan->fjoin_ev[k]) cudaEventDestroy(plan->fjoin_ev[k]);
         if (plan->side[k]) cudaStreamDestroy(plan->side[k]);
         if (plan->join_ev[k]) cudaEventDestroy(plan->join_ev[k]);
     }

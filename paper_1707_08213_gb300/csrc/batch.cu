@@ -10,9 +10,12 @@
 // kernels concurrently on forked streams: first every row group, then (after a join) every
 // column group.  A block finds its tile's array by binary search over the group's tile
 // offsets and calls the same tile functions the per-array kernels use.  Every array has its
-// own z region of the workspace.  No inter-block waits.
+// own z region of the workspace.  No inter-block waits.  Arrays the plan marks fused skip
+// both groups: a fused group per (m0, m1) (batch_fused.cuh) runs their column tiles with
+// the row levels evaluated in the tile, concurrently with the row groups.
 #include <algorithm>
 
+#include "batch_fused.cuh"
 #include "tree_kernels.cuh"
 
 namespace swdft {
@@ -113,6 +116,38 @@ cudaError_t launch_batch_class(bool col, int m, const BatchImage *d_images, cons
             return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+cudaError_t batch_fused_blocks_per_sm(int m0, int m1, int *bps) {
+    if (m1 < 0 || m1 >= kBatchFusedM1) return cudaErrorInvalidValue;
+    switch (m0) {
+        case 0: return bfu_bps<0>(m1, bps);
+        case 1: return bfu_bps<1>(m1, bps);
+        case 2: return bfu_bps<2>(m1, bps);
+        case 3: return bfu_bps<3>(m1, bps);
+        case 4: return bfu_bps<4>(m1, bps);
+        case 5: return bfu_bps<5>(m1, bps);
+        case 6: return bfu_bps<6>(m1, bps);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_batch_fused_class(int m0, int m1, const BatchImage *d_images, const BatchClassEntry *ent,
+                                     int nent, int64_t nitems, const float2 *om64, int64_t slots, cudaStream_t s) {
+    if (nent <= 0 || nitems <= 0) return cudaSuccess;
+    Omega64 om;
+    for (int j = 0; j < kMaxN; ++j) om.w[j] = om64[j];
+    const unsigned grid = (unsigned)std::min<int64_t>(nitems, std::max<int64_t>(1, slots));
+    switch (m0) {
+        case 0: return bfu_launch<0>(m1, d_images, ent, nent, nitems, om, grid, s);
+        case 1: return bfu_launch<1>(m1, d_images, ent, nent, nitems, om, grid, s);
+        case 2: return bfu_launch<2>(m1, d_images, ent, nent, nitems, om, grid, s);
+        case 3: return bfu_launch<3>(m1, d_images, ent, nent, nitems, om, grid, s);
+        case 4: return bfu_launch<4>(m1, d_images, ent, nent, nitems, om, grid, s);
+        case 5: return bfu_launch<5>(m1, d_images, ent, nent, nitems, om, grid, s);
+        case 6: return bfu_launch<6>(m1, d_images, ent, nent, nitems, om, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace swdft

@@ -1,0 +1,8 @@
+// Persistent fused batch kernels: instantiations (split so they compile in parallel).
+#include "batch_fused.cuh"
+
+namespace swdft {
+
+SWDFT_BFU_INSTANTIATE(4)
+
+}  // namespace swdft

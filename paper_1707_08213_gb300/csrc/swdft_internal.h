@@ -53,6 +53,7 @@ struct BatchImage {
     RowGeom row;
     ColGeom col;
     int m0, m1, cplx;
+    int fused;  // row levels inside the column tile (no row tiles, no z)
     int row_blocks, row_chunks;  // row pass: blocks of (128 >> B) rows x chunks of columns
     int col_blocks, col_chunks;  // column pass: blocks of 32 * groups channels x row chunks
 };
@@ -109,6 +110,12 @@ struct BatchClassEntry {
 cudaError_t launch_batch_class(bool col, int m, const BatchImage *d_images, const BatchClassEntry *ent, int nent,
                                int64_t nitems, const float2 *om64, int64_t slots, cudaStream_t s);
 cudaError_t batch_blocks_per_sm(int m, int *row_bps, int *col_bps);
+// Fused groups (arrays with n0 = 2^m0, n1 = 2^m1, m1 <= 5): column tiles that evaluate their
+// own row levels from the input, as fused_tree_kernel does for one array.
+constexpr int kBatchFusedM1 = 6;  // m1 = 0..5
+cudaError_t launch_batch_fused_class(int m0, int m1, const BatchImage *d_images, const BatchClassEntry *ent,
+                                     int nent, int64_t nitems, const float2 *om64, int64_t slots, cudaStream_t s);
+cudaError_t batch_fused_blocks_per_sm(int m0, int m1, int *bps);
 // Launch choices the batch kernels use for a window side of 2^m.
 int batch_row_B(int m1);
 int batch_col_B(int m0);

@@ -1,6 +1,7 @@
 """The persistent batched launch (SWDFT_FLAG_PERSISTENT): many arrays of uneven sizes and
-window shapes in two persistent kernels, optionally replayed from a CUDA graph, against the
-FP64 oracle (Section 4.1, Eq. 2; per-window error / window norm <= 1e-5)."""
+window shapes in persistent kernels per window group (row, column and fused groups),
+optionally replayed from a CUDA graph, against the FP64 oracle (Section 4.1, Eq. 2;
+per-window error / window norm <= 1e-5)."""
 import numpy as np
 import pytest
 import torch
@@ -42,8 +43,12 @@ def test_persistent_batch_of_mixed_shapes(sw, flags):
     xs = _inputs()
     f = sw.FLAG_PERSISTENT | (sw.FLAG_GRAPH if "graph" in flags else 0)
     t = sw.Transform([(N0, N1, n0, n1, int(c)) for (N0, N1, n0, n1, c) in MIXED], flags=f)
-    # one persistent kernel per row-window group and per column-window group
-    assert t.plan.launch_count() == len({n1 for _, _, _, n1, _ in MIXED}) + len({n0 for _, _, n0, _, _ in MIXED})
+    # one persistent kernel per row-window group and per column-window group of the two-pass
+    # arrays, and one per (n0, n1) group of the fused arrays (small windows, n0 n1 <= 64)
+    fused = [(n0, n1) for _, _, n0, n1, _ in MIXED if n0 * n1 <= 64]
+    two = [(n0, n1) for _, _, n0, n1, _ in MIXED if (n0, n1) not in fused]
+    assert t.plan.launch_count() == len({b for _, b in two}) + len({a for a, _ in two}) + len(set(fused))
+    assert t.plan.launch_count() == 12
     xd = [torch.from_numpy(x).cuda() for x in xs]
     outs = t.empty_outputs()
     s = torch.cuda.Stream()
