@@ -62,7 +62,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the side measurements (tensor-core forms, batch, adjoint, volume, stream, Fig. 4 shapes, radix 3, complex workload)")
+                    help="skip the side measurements (tensor-core forms, batch, adjoint, volume, stream, Fig. 4 shapes, radix 3, complex and small workloads)")
     return ap.parse_args()
 
 
@@ -183,6 +183,17 @@ def oracle_sample(x, seconds, seed=0):
     return {"value": count * n0 * n1 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{count} random windows of the 512x512/32x32 workload "
                       f"(FP64 row-column sum, 1 thread), {dt:.1f} s"}, (q0, q1, ref)
+
+
+def oracle_small():
+    """The FP64 oracle (direct double sum, one thread) on the whole small workload."""
+    import oracle
+    import workloads
+    x = workloads.small_uniform_64().images[0]
+    t0 = time.perf_counter()
+    oracle.swdft2d(x, 8, 8, method="direct", threads=1)
+    return {"oracle_s": round(time.perf_counter() - t0, 3), "cores": 1,
+            "kind": "oracle, direct double sum of Eq. 2, every window"}
 
 
 def cpu_tree_fig4():
@@ -487,6 +498,32 @@ def complex_measurement(torch, sw):
     return res
 
 
+def small_measurement(torch, sw):
+    """small_uniform_64: 64x64 float32 U[-1,1) (seed 0), 8x8 windows (1.66 MB of output):
+    latency-bound, so microseconds per transform, launched directly and from a graph."""
+    import workloads
+    x = torch.from_numpy(workloads.small_uniform_64().images[0]).cuda()
+    res = {"workload": "small_uniform_64: 64x64 f32 U[-1,1) (seed 0), 8x8 windows"}
+    s = torch.cuda.Stream()
+    for name, flags in (("direct", 0), ("graph", sw.FLAG_GRAPH)):
+        t = sw.Transform([(64, 64, 8, 8, sw.R32)], flags=flags)
+        out = t.empty_outputs()
+        with torch.cuda.stream(s):
+            for _ in range(5):
+                t.forward([x], out)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(500):
+                t.forward([x], out)
+            e1.record(s)
+        s.synchronize()
+        res[f"{name}_us"] = round(1e3 * e0.elapsed_time(e1) / 500, 2)
+        res["launches"] = t.plan.launch_count()
+        del t, out
+    return res
+
+
 def radix3_measurement(torch, sw):
     """Ternary trees: 512x512 float32 N(0,1) (seed 79) with 27x27 and 9x9 windows, and the
     mixed 9x16 (binary rows, ternary columns)."""
@@ -670,7 +707,7 @@ def run_ours(args):
         for key, fn in (("batch", batch_measurement), ("adjoint", adjoint_measurement),
                         ("volume", volume_measurement), ("stream", stream_measurement),
                         ("fig4_shapes", fig4_measurement), ("radix3", radix3_measurement),
-                        ("complex", complex_measurement)):
+                        ("complex", complex_measurement), ("small", small_measurement)):
             try:
                 extra[key] = fn(torch, sw)
             except Exception as e:  # noqa: BLE001
@@ -740,6 +777,11 @@ def run_ours(args):
             line["cpu_tree"] = cpu_tree_sample(x)
         except Exception as e:  # noqa: BLE001
             line["cpu_tree"] = {"error": str(e)}
+        if isinstance(line.get("small"), dict) and "graph_us" in line["small"]:
+            try:
+                line["small"]["cpu"] = oracle_small()
+            except Exception as e:  # noqa: BLE001
+                line["small"]["cpu"] = {"error": str(e)}
         if isinstance(line.get("fig4_shapes"), dict) and "per_n" in line["fig4_shapes"]:
             try:
                 line["fig4_shapes"]["cpu_tree"] = cpu_tree_fig4()
