@@ -599,9 +599,56 @@ def fig4_measurement(torch, sw):
         s.synchronize()
         ent["autotuned_graph_us"] = round(1e3 * e0.elapsed_time(e1) / 200, 2)
         ent["autotuned_algo"] = t.plan.algo()
-        del t, out
+        ref = out[0]
+        del t
+        # the paper's two other curves, as library calls on the same GPU (comparison only):
+        # per-window direct DFT (Eq. 2 as one product of the window matrix with the n0n1-point
+        # DFT matrix, cuBLAS) and per-window FFT (cuFFT over the unfolded windows)
+        for name, fn in (("library_direct_us", _fig4_direct(torch, a0, a1)),
+                         ("library_fft_us", _fig4_fft(torch, a0, a1))):
+            with torch.cuda.stream(s):
+                got = fn(x)
+                for _ in range(3):
+                    fn(x)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                for _ in range(20):
+                    fn(x)
+                e1.record(s)
+            s.synchronize()
+            ent[name] = round(1e3 * e0.elapsed_time(e1) / 20, 2)
+            ent[name.replace("_us", "_max_abs_diff_vs_tree")] = float((got - ref).abs().max())
+            del got
+        del out, ref
         res["per_n"][str(a0)] = ent
+    res["library_curves"] = ("per-window direct DFT (torch.matmul with the n0n1-point DFT "
+                             "matrix, cuBLAS) and per-window FFT (torch.fft.fft2, cuFFT) over "
+                             "unfolded windows: comparison only, not the library's path")
     return res
+
+
+def _fig4_direct(torch, n0, n1):
+    """Every window's DFT straight from Eq. 2: the window matrix (P0 P1 x n0 n1) times the
+    n0 n1-point 2D DFT matrix kron(F_n0, F_n1) (symmetric), unitary scale."""
+    import numpy as np
+    k0, k1 = np.arange(n0), np.arange(n1)
+    F0 = np.exp(-2j * np.pi * (np.outer(k0, k0) % n0) / n0)
+    F1 = np.exp(-2j * np.pi * (np.outer(k1, k1) % n1) / n1)
+    F = torch.from_numpy(np.kron(F0, F1) / np.sqrt(n0 * n1)).to(torch.complex64).cuda()
+
+    def run(x):
+        w = x.unfold(0, n0, 1).unfold(1, n1, 1)
+        P0, P1 = w.shape[0], w.shape[1]
+        return (w.reshape(P0 * P1, n0 * n1).to(torch.complex64) @ F).reshape(P0, P1, n0, n1)
+    return run
+
+
+def _fig4_fft(torch, n0, n1):
+    """Every window's DFT by its own 2D FFT (cuFFT, batched over windows), unitary scale."""
+    def run(x):
+        return torch.fft.fft2(x.unfold(0, n0, 1).unfold(1, n1, 1), norm="ortho")
+    return run
 
 
 # ----------------------------------------------------------------------- our arm

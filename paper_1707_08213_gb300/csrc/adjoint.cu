@@ -1,10 +1,24 @@
 // Adjoint passes (transposed tree): launchers.  Instantiations live in adj_m*.cu.
 #include <algorithm>
+#include <atomic>
 
 #include "adjoint_kernels.cuh"
 #include "tree_kernels.cuh"
 
 namespace swdft {
+
+// gz[qb + o][ch] += side[b - 1][o][ch] for every chunk boundary qb = b * chunk (b >= 1) and
+// o < n0 - 1: the rows two adj_col chunks share.  Grid z = array.
+__global__ void __launch_bounds__(256) adj_fold_kernel(const __grid_constant__ AdjFoldParams p) {
+    float2 *gz = p.gz[blockIdx.z];
+    const float2 *side = p.side[blockIdx.z];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / p.per_row + 1;  // boundary
+        float2 *dst = gz + b * p.chunk * p.nch + (i - (b - 1) * p.per_row);
+        *dst = c_add(*dst, side[i]);
+    }
+}
 
 int64_t adj_col_chunk(int64_t rows_out, int m0, int64_t requested) {
     const int64_t n = int64_t(1) << m0;
@@ -18,6 +32,10 @@ int64_t adj_side_elems(int64_t rows_out, int m0, int64_t P1, int m1, int64_t req
     const int64_t chunk = adj_col_chunk(rows_out, m0, requested);
     const int64_t nchunks = (rows_out + chunk - 1) / chunk;
     return (nchunks - 1) * ((int64_t(1) << m0) - 1) * (P1 << m1);
+}
+
+int adj_col_launches(int64_t rows_out, int m0, int64_t requested) {
+    return rows_out > 0 && adj_side_elems(rows_out, m0, 1, 0, requested) > 0 ? 2 : 1;
 }
 
 int adj_row_split(int m1) { return adj_row_B(m1); }
@@ -38,9 +56,9 @@ cudaError_t launch_adj_col(const AdjColArgs &a, cudaStream_t s) {
     p.nch = nch;
     p.rows_out = (int)a.rows_out;
     p.chunk = (int)adj_col_chunk(a.rows_out, a.m0, a.chunk);
+    const int64_t side_elems = adj_side_elems(a.rows_out, a.m0, a.P1, a.m1, a.chunk);
     for (int z = 0; z < a.nz; ++z)
-        if (!a.G[z] || !a.gz[z] || (p.chunk < a.rows_out && a.m0 > 0 && a.side[z] == nullptr))
-            return cudaErrorInvalidValue;
+        if (!a.G[z] || !a.gz[z] || (side_elems > 0 && a.side[z] == nullptr)) return cudaErrorInvalidValue;
     p.m1 = a.m1;
     p.scale = a.scale;
     for (int j = 0; j < kMaxN; ++j) p.om64[j] = a.om64[j];
@@ -60,6 +78,20 @@ cudaError_t launch_adj_col(const AdjColArgs &a, cudaStream_t s) {
         default:
             return cudaErrorInvalidValue;
     }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || side_elems == 0) return e;
+    // the rows two chunks share: gz += side, one launch for every array
+    AdjFoldParams f;
+    for (int z = 0; z < kAdjZ; ++z) {
+        f.gz[z] = a.gz[z];
+        f.side[z] = a.side[z];
+    }
+    f.nch = nch;
+    f.per_row = ((int64_t(1) << a.m0) - 1) * nch;
+    f.total = side_elems;
+    f.chunk = p.chunk;
+    const int64_t fb = std::min<int64_t>((side_elems + 255) / 256, 4096);
+    adj_fold_kernel<<<dim3((unsigned)fb, 1, (unsigned)a.nz), 256, 0, s>>>(f);
     return cudaGetLastError();
 }
 
@@ -70,26 +102,48 @@ cudaError_t launch_adj_row(const AdjRowArgs &a, cudaStream_t s) {
     AdjRowParams p;
     for (int z = 0; z < kAdjZ; ++z) {
         p.gz[z] = a.gz[z];
-        p.side[z] = a.side[z];
         p.gx[z] = a.gx[z];
     }
     for (int z = 0; z < a.nz; ++z)
         if (!a.gz[z] || !a.gx[z]) return cudaErrorInvalidValue;
-    if (a.m0 < 0 || a.m0 > kMaxLog2 || a.rows_out > INT32_MAX) return cudaErrorInvalidValue;
-    p.col_chunk = (int)adj_col_chunk(a.rows_out, a.m0, a.col_chunk);
-    p.rows_out = (int)a.rows_out;
-    p.n0m1 = (1 << a.m0) - 1;
+    // 16-byte staging copies of gz rows (n1 >= 2)
+    for (int z = 0; z < a.nz; ++z)
+        if (a.m1 >= 1 && (uintptr_t)a.gz[z] % 16 != 0) return cudaErrorInvalidValue;
     p.ld_out = a.ld_out;
     p.zrows = (int)a.zrows;
     p.N1 = (int)a.N1;
     p.P1 = (int)(a.N1 - (int64_t(1) << a.m1) + 1);
-    p.chunk = (int)std::min<int64_t>(a.chunk > 0 ? a.chunk : a.N1, a.N1);
     for (int j = 0; j < kMaxN; ++j) p.om64[j] = a.om64[j];
     const int B = adj_row_B(a.m1);  // the one split built per window side
     const int threads = 128;
     const int64_t per_block = threads >> B;
-    dim3 grid((unsigned)((a.zrows + per_block - 1) / per_block), (unsigned)((a.N1 + p.chunk - 1) / p.chunk),
-              (unsigned)a.nz);
+    const int64_t row_blocks = (a.zrows + per_block - 1) / per_block;
+    int64_t chunk = a.chunk;
+    if (chunk <= 0) {
+        // as many column chunks as keep one wave of resident blocks busy (the pass is
+        // latency-bound: a second, partial wave would nearly double its time), none shorter
+        // than n1 (each re-walks n1 - 1 columns of warm-up)
+        static std::atomic<int> bps_cache[kMaxLog2 + 1][2];  // 0: not queried yet
+        int bps = bps_cache[a.m1][a.cplx ? 1 : 0].load(std::memory_order_relaxed);
+        if (bps <= 0) {
+            switch (a.m1) {
+#define F(M_)                                                  \
+    case M_:                                                   \
+        bps = adj_row_bps_mb<M_, adj_row_B(M_)>(a.cplx);       \
+        break;
+                F(0) F(1) F(2) F(3) F(4) F(5) F(6)
+#undef F
+                default:
+                    return cudaErrorInvalidValue;
+            }
+            bps_cache[a.m1][a.cplx ? 1 : 0].store(bps, std::memory_order_relaxed);
+        }
+        const int64_t slots = (int64_t)std::max(1, a.sm_count) * std::max(1, bps);
+        const int64_t nchunk = std::max<int64_t>(1, slots / std::max<int64_t>(1, row_blocks * a.nz));
+        chunk = std::max<int64_t>((a.N1 + nchunk - 1) / nchunk, int64_t(1) << a.m1);
+    }
+    p.chunk = (int)std::min<int64_t>(chunk, a.N1);
+    dim3 grid((unsigned)row_blocks, (unsigned)((a.N1 + p.chunk - 1) / p.chunk), (unsigned)a.nz);
     if (grid.y > 65535) return cudaErrorInvalidValue;
     switch (a.m1) {
 #define F(M_)                                                                         \

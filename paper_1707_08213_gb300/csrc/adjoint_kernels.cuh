@@ -12,8 +12,9 @@
 // adj_col splits the work by WINDOW rows: chunk i takes windows q0 in [qa, qb) and reads
 // those rows of G exactly once (G is the large operand: n0 times gz).  Its outputs cover z
 // rows [qa, qb + n0 - 2]; rows >= qb are shared with chunk i+1, so chunk i writes them to a
-// side buffer, side[i][r - qb][ch] (n0-1 rows per chunk boundary), and adj_row adds them to
-// gz rows [qb, qb + n0 - 2] as it reads them.  Every gz row is written exactly once.
+// side buffer, side[i][r - qb][ch] (n0-1 rows per chunk boundary), and adj_fold then adds
+// them to gz rows [qb, qb + n0 - 2].  No atomics: the result is deterministic.  adj_row
+// stages gz rows through shared memory, GS steps at a time.
 //
 // Lanes hold (residue c in the low B bits, channel or row above): the 2^B partials of one
 // output are reduced with shuffles and lane c = 0 stores.  G is read once, coalesced: for a
@@ -42,16 +43,21 @@ struct AdjColParams {
 
 struct AdjRowParams {
     const float2 *gz[kAdjZ];    // zrows x P1 x n1
-    const float2 *side[kAdjZ];  // adj_col's side buffers (see AdjColParams), or null
     void *gx[kAdjZ];            // zrows rows of N1 elements (row stride ld_out)
     int64_t ld_out;
     int zrows;
     int N1, P1;
     int chunk;         // output columns per thread (plus n1 - 1 warm-up steps)
-    int col_chunk;     // adj_col's window rows per chunk
-    int rows_out;      // window rows of G
-    int n0m1;          // n0 - 1: side rows per chunk boundary
     float2 om64[kMaxN];  // w_64^{-j}: every power-of-two length's twiddles
+};
+
+struct AdjFoldParams {
+    float2 *gz[kAdjZ];
+    const float2 *side[kAdjZ];
+    int64_t nch;       // P1 * n1
+    int64_t per_row;   // (n0 - 1) * nch: side values per chunk boundary
+    int64_t total;     // (chunks - 1) * per_row
+    int chunk;         // window rows per adj_col chunk
 };
 
 template <int R>
@@ -74,9 +80,17 @@ __host__ __device__ constexpr size_t adj_col_smem(int M, int B) {
     return sizeof(float2) * 2 * kAdjGroup * (size_t(1) << M) * adj_col_channels(B);
 }
 
-__device__ __forceinline__ void adj_cp_async_8(void *smem, const void *gmem, bool valid) {
+// G is read once: its lines are marked evict-first in L2, so that the gz rows this pass
+// writes (n0 times smaller) are still in L2 when adj_row reads them.
+__device__ __forceinline__ uint64_t adj_policy_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void adj_cp_async_8(void *smem, const void *gmem, bool valid, uint64_t pol) {
     const unsigned dst = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(gmem), "r"(valid ? 8 : 0)
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2, %3;\n" ::"r"(dst), "l"(gmem),
+                 "r"(valid ? 8 : 0), "l"(pol)
                  : "memory");
 }
 __device__ __forceinline__ void adj_cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
@@ -124,13 +138,14 @@ __global__ void __launch_bounds__(128) adj_col_kernel(const __grid_constant__ Ad
     const bool ok_f = cg_f < p.nch;
     const float2 *gsrc = G + (ok_f ? ((cg_f >> p.m1) * n + k0_f) * n1 + (cg_f & (n1 - 1)) : 0);
     const int64_t kstep = (int64_t)R * n1;  // global distance between a thread's k0 values
+    const uint64_t pol = adj_policy_evict_first();
     auto fetch = [&](int j0, int b) {
         const int cnt = min(GS, nwin - j0);
         float2 *dst = sg + b * GS * STEP + k0_f * CH + cl_f;
         const float2 *src = gsrc + (int64_t)(qb - 1 - j0) * grow;
         for (int st = 0; st < cnt; ++st) {
 #pragma unroll
-            for (int t = 0; t < n / R; ++t) adj_cp_async_8(dst + t * R * CH, src + t * kstep, ok_f);
+            for (int t = 0; t < n / R; ++t) adj_cp_async_8(dst + t * R * CH, src + t * kstep, ok_f, pol);
             dst += STEP;
             src -= grow;
         }
@@ -180,69 +195,113 @@ __global__ void __launch_bounds__(128) adj_col_kernel(const __grid_constant__ Ad
     }
 }
 
+// gz staging for adj_row: a block's rows (128 >> B of them) need n1 values per row per step,
+// consecutive steps reading consecutive (descending) q1, so GS steps of one row are one
+// contiguous run of GS * n1 values.  Groups of GS steps (16 KB per block) are copied by
+// cp.async into a double-buffered ring, one group ahead of use, 16 bytes per copy (8 for
+// n1 = 1); rows are padded by R values so that the 2^B lanes of 32 / 2^B rows hit distinct banks.
+template <int M, int B>
+struct AdjRowStage {
+    static constexpr int R = 1 << B;
+    static constexpr int kRows = 128 >> B;  // rows per block
+    static constexpr int kN = 1 << M;
+    static constexpr int kGS0 = 2048 / (kRows * kN);
+    static constexpr int kGS = kGS0 < 1 ? 1 : (kGS0 > 16 ? 16 : kGS0);  // steps per group
+    static constexpr int kRow = kGS * kN + R;    // staged values per row (padded)
+    static constexpr int kPiece = kN >= 2 ? 2 : 1;  // values per copy
+    static constexpr int kPerRow = kGS * kN / kPiece;  // copies per row per group
+    static constexpr size_t kBytes = sizeof(float2) * 2 * kRows * kRow;
+    static_assert(kPerRow <= 128 && 128 % kPerRow == 0, "copies of a group must tile the block");
+    static_assert(kPiece == 1 || kRow % 2 == 0, "16-byte copies need 16-byte aligned rows");
+};
+
+template <int M, int B>
+__host__ __device__ constexpr size_t adj_row_smem() { return AdjRowStage<M, B>::kBytes; }
+
+__device__ __forceinline__ void adj_cp_async_16(void *smem, const void *gmem, bool valid) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(gmem), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void adj_cp_async_8_plain(void *smem, const void *gmem, bool valid) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(gmem), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+
 template <int M, int B, bool CPLX>
 __global__ void __launch_bounds__(128) adj_row_kernel(const __grid_constant__ AdjRowParams p) {
     using Tree = SlidingTreeAdjoint<M, B>;
-    constexpr int R = 1 << B;
-    constexpr int n = 1 << M;
-    // gz loads issued PF steps ahead (a divisor of the unroll period; two for the larger
-    // trees, whose registers are already mostly taken by their FIFOs)
-    constexpr int PF = M >= 5 ? 2 : (Tree::kPeriod >= 4 ? 4 : Tree::kPeriod);
+    using St = AdjRowStage<M, B>;
+    constexpr int R = St::R;
+    constexpr int n = St::kN;
+    constexpr int GS = St::kGS;
+    constexpr int UNR = Tree::kPeriod > GS ? Tree::kPeriod : GS;
+    extern __shared__ float2 sz[];  // [2][kRows][kRow]
+
     const int c = threadIdx.x & (R - 1);
-    const int row = blockIdx.x * (blockDim.x >> B) + (threadIdx.x >> B);
+    const int rl = threadIdx.x >> B;  // this thread's row within the block
+    const int row0 = blockIdx.x * St::kRows;
+    const int row = row0 + rl;
     const bool active = row < p.zrows;
     const int pa = blockIdx.y * p.chunk;
     if (pa >= p.N1) return;  // uniform per block
     const int pb = min(pa + p.chunk, p.N1);
     const int p_hi = min(pb + n - 2, p.N1 - 1);
     const int steps = p_hi - pa + 1;
+    const int q1_top = p_hi - (n - 1);  // q1 of step 0; step j reads q1_top - j
 
     const int64_t rowlen = (int64_t)p.P1 * n;
-    const float2 *zrow = p.gz[blockIdx.z] + (int64_t)(active ? row : 0) * rowlen + c;
-    const float2 *sidez = p.side[blockIdx.z];
+    const float2 *gz = p.gz[blockIdx.z];
     void *gx = p.gx[blockIdx.z];
-    // the part of this z row adj_col's previous chunk left in its side buffer, if any
-    const float2 *srow = nullptr;
-    if (sidez != nullptr && active && p.n0m1 > 0) {
-        const int i = row / p.col_chunk;  // chunk whose windows start at row i * col_chunk
-        const int off = row - i * p.col_chunk;
-        if (i >= 1 && i * p.col_chunk < p.rows_out && off < p.n0m1)
-            srow = sidez + ((int64_t)(i - 1) * p.n0m1 + off) * rowlen + c;
-    }
 
-    auto load_z = [&](int j, float2 (&u)[Tree::kIn]) {
-        const int q1 = p_hi - j - (n - 1);
-        if (active && j < steps && q1 >= 0 && q1 < p.P1) {
-            const float2 *g = zrow + (int64_t)q1 * n;
+    // copying thread i always takes piece i mod kPerRow of rows i / kPerRow + t * (128 / kPerRow)
+    constexpr int kRowStep = 128 / St::kPerRow;
+    constexpr int kCopies = St::kRows / kRowStep;
+    const int off_f = (threadIdx.x % St::kPerRow) * St::kPiece;  // value offset in the group's run
+    const int rl_f = threadIdx.x / St::kPerRow;
+    const int dq_f = off_f / n;  // q1 of this piece relative to the group's lowest q1
+    auto fetch = [&](int j0, int b) {
+        const int q1lo = q1_top - j0 - (GS - 1);
+        const int q = q1lo + dq_f;
+        const bool qok = q >= 0 && q < p.P1;
+        const int64_t goff = (int64_t)q1lo * n + off_f;
+        float2 *dst = sz + (b * St::kRows + rl_f) * St::kRow + off_f;
 #pragma unroll
-            for (int t = 0; t < Tree::kIn; ++t) u[t] = __ldg(g + (t << B));
-            if (srow != nullptr) {
-                const float2 *h = srow + (int64_t)q1 * n;
-#pragma unroll
-                for (int t = 0; t < Tree::kIn; ++t) u[t] = c_add(u[t], __ldg(h + (t << B)));
-            }
-        } else {
-#pragma unroll
-            for (int t = 0; t < Tree::kIn; ++t) u[t] = make_float2(0.f, 0.f);
+        for (int t = 0; t < kCopies; ++t) {
+            const int r = row0 + rl_f + t * kRowStep;
+            const bool ok = qok && r < p.zrows;
+            const float2 *src = ok ? gz + (int64_t)r * rowlen + goff : gz;
+            if constexpr (St::kPiece == 2)
+                adj_cp_async_16(dst + t * kRowStep * St::kRow, src, ok);
+            else
+                adj_cp_async_8_plain(dst + t * kRowStep * St::kRow, src, ok);
         }
+        adj_cp_async_commit();
     };
 
     Tree tree;
     tree.init(c, p.om64);
-    float2 buf[PF][Tree::kIn];
-#pragma unroll
-    for (int d = 0; d < PF; ++d) load_z(d, buf[d]);
-    for (int jb = 0; jb < steps; jb += Tree::kPeriod) {
-        static_for<0, Tree::kPeriod>([&](auto JJ) {
+    fetch(0, 0);
+    for (int jb = 0; jb < steps; jb += UNR) {
+        static_for<0, UNR>([&](auto JJ) {
             constexpr int J = decltype(JJ)::value;
-            constexpr int SL = J % PF;
             const int j = jb + J;
+            if constexpr (J % GS == 0) {
+                if (j + GS < steps) {
+                    fetch(j + GS, ((j / GS) + 1) & 1);
+                    adj_cp_async_wait_1();
+                } else {
+                    adj_cp_async_wait_0();
+                }
+                __syncthreads();
+            }
             if (j < steps) {
                 const int p1 = p_hi - j;
+                const float2 *src = sz + (((j / GS) & 1) * St::kRows + rl) * St::kRow + (GS - 1 - (J % GS)) * n + c;
                 float2 u[Tree::kIn];
 #pragma unroll
-                for (int t = 0; t < Tree::kIn; ++t) u[t] = buf[SL][t];
-                load_z(j + PF, buf[SL]);
+                for (int t = 0; t < Tree::kIn; ++t) u[t] = src[t * R];
                 const float2 y = reduce_residues<R>(tree.template step<J>(u));
                 if (c == 0 && active && p1 < pb) {
                     if constexpr (CPLX)
@@ -251,6 +310,7 @@ __global__ void __launch_bounds__(128) adj_row_kernel(const __grid_constant__ Ad
                         reinterpret_cast<float *>(gx)[(int64_t)row * p.ld_out + p1] = y.x;
                 }
             }
+            if constexpr (J % GS == GS - 1) __syncthreads();  // the buffer is refilled next group
         });
     }
 }
@@ -259,6 +319,8 @@ template <int M, int B>
 void adj_col_launch_mb(const AdjColParams &p, dim3 g, dim3 b, cudaStream_t s);
 template <int M, int B>
 void adj_row_launch_mb(const AdjRowParams &p, int cplx, dim3 g, dim3 b, cudaStream_t s);
+template <int M, int B>
+int adj_row_bps_mb(int cplx);  // resident 128-thread blocks per SM (occupancy API; 0 on error)
 
 // The residue split each adjoint pass uses for a window side 2^M (registers without spills).
 __host__ __device__ constexpr int adj_col_B(int M) { return M <= 4 ? (M < 1 ? M : 1) : M - 3; }
@@ -279,10 +341,30 @@ __host__ __device__ constexpr int adj_row_B(int M) { return M >= 4 ? 3 : (M < 2 
     template <>                                                                                  \
     void adj_row_launch_mb<M_, adj_row_B(M_)>(const AdjRowParams &p, int cplx, dim3 g, dim3 b,   \
                                               cudaStream_t s) {                                  \
+        constexpr size_t smem = adj_row_smem<M_, adj_row_B(M_)>();                               \
+        static const bool attr_set =                                                             \
+            smem <= 48 * 1024 ||                                                                 \
+            (cudaFuncSetAttribute(adj_row_kernel<M_, adj_row_B(M_), true>,                       \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==     \
+                 cudaSuccess &&                                                                  \
+             cudaFuncSetAttribute(adj_row_kernel<M_, adj_row_B(M_), false>,                      \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==     \
+                 cudaSuccess);                                                                   \
+        (void)attr_set;                                                                          \
         if (cplx)                                                                                \
-            adj_row_kernel<M_, adj_row_B(M_), true><<<g, b, 0, s>>>(p);                          \
+            adj_row_kernel<M_, adj_row_B(M_), true><<<g, b, smem, s>>>(p);                       \
         else                                                                                     \
-            adj_row_kernel<M_, adj_row_B(M_), false><<<g, b, 0, s>>>(p);                         \
+            adj_row_kernel<M_, adj_row_B(M_), false><<<g, b, smem, s>>>(p);                      \
+    }                                                                                            \
+    template <>                                                                                  \
+    int adj_row_bps_mb<M_, adj_row_B(M_)>(int cplx) {                                            \
+        constexpr size_t smem = adj_row_smem<M_, adj_row_B(M_)>();                               \
+        int nb = 0;                                                                              \
+        cudaError_t e = cplx ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(                    \
+                                   &nb, adj_row_kernel<M_, adj_row_B(M_), true>, 128, smem)      \
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(                    \
+                                   &nb, adj_row_kernel<M_, adj_row_B(M_), false>, 128, smem);    \
+        return e == cudaSuccess ? nb : 0;                                                        \
     }
 
 }  // namespace swdft

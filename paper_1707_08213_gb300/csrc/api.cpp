@@ -81,11 +81,13 @@ struct ArrayPlan {
     size_t planes_bytes(int64_t rows_out, int algo) const {
         return (size_t)tc_terms(algo) * 2 * (size_t)(rows_out + n0 - 1) * (size_t)P1 * n1 * 2;
     }
-    // adjoint: window rows per adj_col chunk (about eight chunks, none shorter than 2*n0:
-    // chunks read disjoint rows of G, and each costs n0-1 drain steps and n0-1 side rows),
-    // gz where the forward pass keeps z, then the chunks' side rows
+    // adjoint: window rows per adj_col chunk (at most eight chunks, none shorter than 4*n0:
+    // chunks read disjoint rows of G, and each costs n0-1 drain steps and n0-1 side rows,
+    // which a second launch folds into gz), gz where the forward pass keeps z, then the
+    // chunks' side rows.  It depends on the array's shape only, so an array's adjoint has
+    // the same bits in every plan.
     int64_t adj_chunk(int64_t rows_out) const {
-        return std::min(rows_out, std::max<int64_t>((rows_out + 7) / 8, 2 * n0));
+        return std::min(rows_out, std::max<int64_t>((rows_out + 7) / 8, 4 * n0));
     }
     size_t adj_side_bytes(int64_t rows_out) const {
         if (ternary()) return 0;  // no adjoint for ternary trees
@@ -744,16 +746,17 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
             p->any_fused = p->any_fused || a.batch_fused;
         }
     } else {
-        // up to four arrays run at once (plan-owned streams), each with its own z slot
-        for (const auto &a : p->arrays) ws = std::max(ws, align_up(a.ws_bytes_plan(a.band_rows())));
-        p->conc = (int)std::min<size_t>(kConc, p->arrays.size());
-        p->slot_bytes = ws;
+        // up to four arrays run at once (plan-owned streams), each with its own z slot;
+        // arrays of one shape run their adjoint passes in groups of up to kAdjZ launches
         const ArrayPlan &f = p->arrays.front();
         p->uniform = p->arrays.size() > 1;
         for (const auto &a : p->arrays)
             p->uniform = p->uniform && a.N0 == f.N0 && a.N1 == f.N1 && a.ld == f.ld && a.n0 == f.n0 &&
                          a.n1 == f.n1 && a.dtype == f.dtype && a.q_begin == f.q_begin && a.q_end == f.q_end &&
                          !a.ternary();
+        for (const auto &a : p->arrays) ws = std::max(ws, align_up(a.ws_bytes_plan(a.band_rows())));
+        p->conc = (int)std::min<size_t>(kConc, p->arrays.size());
+        p->slot_bytes = ws;
         const size_t slots = p->uniform ? std::max<size_t>((size_t)p->conc, std::min<size_t>(kAdjZ, p->arrays.size()))
                                         : (size_t)p->conc;
         ws *= slots;
@@ -808,14 +811,18 @@ swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t 
         *launches = k;
         return SWDFT_OK;
     }
+    // (the column adjoint adds a second launch when its chunks share rows)
     if (adjoint && plan->uniform) {
-        // one launch pair per group of up to kAdjZ arrays of the same shape
-        *launches = (int32_t)(2 * ((plan->arrays.size() + kAdjZ - 1) / kAdjZ));
+        // one launch pair (or three) per group of up to kAdjZ arrays of the same shape
+        const ArrayPlan &a = plan->arrays.front();
+        const int per = 1 + adj_col_launches(a.band_rows(), a.m0, a.adj_chunk(a.band_rows()));
+        *launches = (int32_t)(per * ((plan->arrays.size() + kAdjZ - 1) / kAdjZ));
         return SWDFT_OK;
     }
     int32_t n = 0;
     for (const auto &a : plan->arrays)
-        n += (!adjoint && a.algo == SWDFT_ALGO_TREE_F32 && a.cfg.fused && a.m1 <= 5) ? 1 : 2;
+        n += adjoint ? 1 + adj_col_launches(a.band_rows(), a.m0, a.adj_chunk(a.band_rows()))
+                     : ((a.algo == SWDFT_ALGO_TREE_F32 && a.cfg.fused && a.m1 <= 5) ? 1 : 2);
     *launches = n;
     return SWDFT_OK;
 }
@@ -949,7 +956,6 @@ swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_g
                             ? reinterpret_cast<float2 *>(static_cast<char *>(slots[k]) + align_up(a.z_bytes(a.band_rows())))
                             : nullptr;
             r.gz[k] = c.gz[k];
-            r.side[k] = c.side[k];
             r.gx[k] = gx + (size_t)a.q_begin * row_bytes;
         }
         c.nz = nz;
@@ -963,9 +969,6 @@ swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_g
         c.chunk = a.adj_chunk(a.band_rows());
         if ((e = launch_adj_col(c, s)) != cudaSuccess) return e;
         r.nz = nz;
-        r.col_chunk = c.chunk;
-        r.rows_out = c.rows_out;
-        r.m0 = a.m0;
         r.ld_out = a.N1;
         r.cplx = a.dtype == SWDFT_C64;
         r.zrows = zrows;
@@ -973,11 +976,8 @@ swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_g
         r.m1 = a.m1;
         r.om64 = plan->om64;
         r.B = 0;  // the launcher uses the one split built per window side
-        const int64_t target = (int64_t)plan->sm_count * 1024;
-        const int64_t nchunk =
-            std::max<int64_t>(1, target / std::max<int64_t>(1, (zrows << adj_row_split(a.m1)) * nz));
-        // chunks no shorter than n1: each re-walks n1-1 columns of warm-up
-        r.chunk = std::min<int64_t>(a.N1, std::max<int64_t>((a.N1 + nchunk - 1) / nchunk, a.n1));
+        r.chunk = 0;  // the launcher fills one wave of resident blocks
+        r.sm_count = plan->sm_count;
         return launch_adj_row(r, s);
     };
     if (plan->uniform) {

@@ -190,7 +190,7 @@ cudaError_t launch_fused_tree(const FusedTreeArgs &a, cudaStream_t s);
 // for the rows_out + n0 - 1 z rows of a band (G holds rows_out window rows).
 // Work is split by window rows: chunks of `chunk` windows (>= n0-1; the last may be shorter),
 // each reading its rows of G once.  The n0-1 gz rows after a chunk (not the last) are written
-// to side[chunk index] instead of gz; adj_row adds them (AdjRowArgs.side).
+// to side[chunk index]; a second launch adds them into gz, so gz is complete on return.
 // Arrays of one shape may share a launch: array z of nz (< kAdjZ) uses G[z], gz[z], side[z].
 constexpr int kAdjZ = 8;
 struct AdjColArgs {
@@ -208,24 +208,23 @@ struct AdjColArgs {
 // Window rows per adj_col chunk the launcher actually uses, and its side buffer size.
 int64_t adj_col_chunk(int64_t rows_out, int m0, int64_t requested);
 int64_t adj_side_elems(int64_t rows_out, int m0, int64_t P1, int m1, int64_t requested);
+// Kernel launches launch_adj_col makes (2 when chunk boundaries share rows, else 1).
+int adj_col_launches(int64_t rows_out, int m0, int64_t requested);
 
 // Adjoint of the row levels: gx[r][p1] = sum_{j1,k1} gz[r][p1-j1][k1] w_{n1}^{+j1 k1}
 // (real part stored for float32 inputs), for zrows rows of N1 columns.
 struct AdjRowArgs {
     const float2 *gz[kAdjZ] = {};
-    const float2 *side[kAdjZ] = {};  // adj_col's side buffers (null: none)
     void *gx[kAdjZ] = {};
     int nz = 1;
-    int64_t col_chunk = 0;         // adj_col's chunk (adj_col_chunk), rows_out, m0
-    int64_t rows_out = 0;
-    int m0 = 0;
     int64_t ld_out = 0;
     int cplx = 0;
     int64_t zrows = 0, N1 = 0;
     int m1 = 0;
     const float2 *om64 = nullptr;  // host table w_64^{-j}, 64 entries
     int B = 0;
-    int64_t chunk = 0;  // output columns per thread (plus n1-1 warm-up steps)
+    int64_t chunk = 0;  // output columns per thread (plus n1-1 warm-up steps); 0: one wave
+    int sm_count = 152;  // for chunk = 0
 };
 
 // Ternary trees (tree3.cu): windows of 3^m samples, m <= 3, along an axis.

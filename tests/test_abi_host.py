@@ -157,7 +157,9 @@ def test_launch_count(nat):
     p = nat.Plan([shp(16, 16, 4, 4), shp(32, 32, 8, 8)])
     assert p.launch_count() == 2
     assert nat.Plan([shp(64, 64, 32, 32), shp(64, 64, 16, 64)]).launch_count() == 4
-    assert nat.Plan([shp(64, 64, 4, 4)]).launch_count(adjoint=True) == 2
+    # adjoint: column pass, the fold of the rows its chunks share, row pass
+    assert nat.Plan([shp(64, 64, 4, 4)]).launch_count(adjoint=True) == 3
+    assert nat.Plan([shp(18, 64, 4, 4)]).launch_count(adjoint=True) == 2  # one chunk: no fold
 
 
 def test_twiddle_table_symmetry_via_plan(nat):

@@ -180,13 +180,13 @@ def test_adjoint_of_persistent_batch_plan(sw):
 def test_adjoint_of_same_shape_arrays_in_grouped_launches(sw, cplx):
     """Eleven arrays of one shape: the adjoint runs them as a group of eight and a group of
     three per launch; each result equals its one-array plan's bit for bit and the oracle's."""
-    N0, N1, n0, n1 = 70, 45, 16, 8
+    N0, N1, n0, n1 = 70, 45, 8, 8  # two column chunks: the fold launch runs too
     band = (5, 49)
     P1 = N1 - n1 + 1
     Gs = [_G(200 + i, band[1] - band[0], P1, n0, n1) for i in range(11)]
     Gd = [torch.from_numpy(G).cuda() for G in Gs]
     t = sw.Transform([(N0, N1, n0, n1, int(cplx))] * 11, bands=[band] * 11)
-    assert t.plan.launch_count(adjoint=True) == 4
+    assert t.plan.launch_count(adjoint=True) == 6  # per group: column pass, fold, row pass
     got = t.adjoint(Gd)
     torch.cuda.synchronize()
     for i, (G, g) in enumerate(zip(Gs, got)):
