@@ -23,6 +23,11 @@ namespace swdft {
 // and y(p) is the sum of the 2^B partials (reduced by the caller).
 // ------------------------------------------------------------------------------------
 
+// w * d + a: two fused multiply-adds per component
+__device__ __forceinline__ float2 c_fma(float2 w, float2 d, float2 a) {
+    return make_float2(fmaf(w.x, d.x, fmaf(-w.y, d.y, a.x)), fmaf(w.x, d.y, fmaf(w.y, d.x, a.y)));
+}
+
 __host__ __device__ constexpr int ta_slots(int B, int v) { return v > B ? tg_held(B, v - 1) : 1; }
 __host__ __device__ constexpr int ta_off(int M, int B, int v) {
     // rings are laid out from level M down to level 1
@@ -88,12 +93,12 @@ struct SlidingTreeAdjoint {
                     const float2 s = c_add(cur[t], cur[t + Hp]);
                     const float2 old = ring[base + t];
                     ring[base + t] = s;
-                    cur[t] = c_add(c_mul(tw[tb + t], d), old);
+                    cur[t] = c_fma(tw[tb + t], d, old);
                 }
             } else {
                 const float2 old = ring[base];
                 ring[base] = cur[0];
-                cur[0] = c_add(c_mul(tw[tb], cur[0]), old);
+                cur[0] = c_fma(tw[tb], cur[0], old);
             }
             level<J, V - 1>(cur);
         }
