@@ -490,6 +490,19 @@ def complex_measurement(torch, sw):
                          "column_pass_ms": round(t_col / steps, 4), "value": coeffs / (ms / 1e3),
                          "output_gbs": round(8 * coeffs / (ms / 1e3) / 1e9, 1),
                          "column_pass_output_gbs": round(8 * coeffs / (t_col / steps / 1e3) / 1e9, 1)}
+            # the whole transform as a caller runs it (the tree goes in sub-bands whose z
+            # stays in L2 when the whole z would not)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                t.forward([x], [out])
+            e1.record()
+            torch.cuda.synchronize()
+            fms = e0.elapsed_time(e1) / steps
+            res[algo]["forward_ms"] = round(fms, 4)
+            res[algo]["forward_value"] = coeffs / (fms / 1e3)
+            res[algo]["forward_launches"] = t.plan.launch_count()
             del t
         except Exception as e:  # noqa: BLE001
             res[algo] = {"error": str(e)}

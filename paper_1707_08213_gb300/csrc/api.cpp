@@ -193,6 +193,15 @@ int64_t col_chunk_for(const ArrayPlan &a, int nchunks) {
     return std::min(rows, std::max<int64_t>(chunk, 2 * a.n0));
 }
 
+// Column-pass row chunks: about eight per channel group (sixteen for fused small windows),
+// more when there are few channel groups (narrow arrays), so that the pass has at least four
+// blocks per SM.
+int col_nchunks(const ArrayPlan &a, int sm_count, bool fused_small) {
+    const int64_t ch_groups = (a.P1 * a.n1 + 31) / 32;
+    const int64_t want = (4LL * std::max(1, sm_count) + ch_groups - 1) / ch_groups;
+    return (int)std::min<int64_t>(65535, std::max<int64_t>(fused_small ? 16 : 8, want));
+}
+
 // conc: arrays of the plan that run at once (their z buffers share L2).
 void default_config(ArrayPlan &a, int sm_count, int conc) {
     TreeConfig c;
@@ -218,13 +227,8 @@ void default_config(ArrayPlan &a, int sm_count, int conc) {
     const bool small = a.n0 * a.n1 <= 64;
     const double z_live = (double)a.z_bytes(a.band_rows()) * std::max(1, conc);
     c.fused = can_fuse && (small || (a.n0 >= 16 && z_live > 96e6));
-    // chunks of window rows: about eight per channel group (sixteen for fused small windows),
-    // more when there are few channel groups (narrow arrays), so that the pass has at least
-    // four blocks per SM; col_chunk_for keeps every chunk at 2 n0 rows or more
-    const int64_t ch_groups = (a.P1 * a.n1 + 31) / 32;
-    const int64_t want = (4LL * std::max(1, sm_count) + ch_groups - 1) / ch_groups;
-    const int nchunks = (int)std::min<int64_t>(65535, std::max<int64_t>(c.fused && small ? 16 : 8, want));
-    c.col_chunk = col_chunk_for(a, nchunks);
+    // chunks of window rows (col_nchunks); col_chunk_for keeps every chunk at 2 n0 rows or more
+    c.col_chunk = col_chunk_for(a, col_nchunks(a, sm_count, c.fused && small));
     a.cfg = c;
 }
 
