@@ -324,12 +324,21 @@ def batch_measurement(torch, sw):
            "coeffs_per_step": coeffs, "output_bytes_per_step": 8 * coeffs}
     outs = None
     s = torch.cuda.Stream()
-    for name, flags in (("persistent_graph", sw.FLAG_PERSISTENT | sw.FLAG_GRAPH),
-                        ("per_array_graph", sw.FLAG_GRAPH)):
-        t = sw.Transform(shapes, flags=flags)
+    # the third form: per-array graph after the plan's autotuner chose, per shape, the tree's
+    # launch shapes, two-pass or fused levels, and tree or split-bf16 tensor-core form
+    for name, flags, algo in (("persistent_graph", sw.FLAG_PERSISTENT | sw.FLAG_GRAPH, "tree"),
+                              ("per_array_graph", sw.FLAG_GRAPH, "tree"),
+                              ("per_array_graph_autotuned", sw.FLAG_GRAPH, "auto")):
+        t = sw.Transform(shapes, flags=flags, algo=algo)
         if outs is None:
             outs = t.empty_outputs()
+        tune_s = None
         with torch.cuda.stream(s):
+            if algo == "auto":
+                t0 = time.perf_counter()
+                t.autotune(xd, outs)
+                s.synchronize()
+                tune_s = time.perf_counter() - t0
             for _ in range(3):
                 t.forward(xd, outs)
             ts = []
@@ -345,6 +354,9 @@ def batch_measurement(torch, sw):
         res[name] = {"ms_per_step": round(ms, 4), "value": coeffs / (ms / 1e3),
                      "output_gbs": round(8 * coeffs / (ms / 1e3) / 1e9, 1),
                      "launches": t.plan.launch_count()}
+        if tune_s is not None:
+            res[name]["autotune_s"] = round(tune_s, 2)
+            res[name]["algo_array0"] = t.plan.algo()
         del t
     del outs, xd
     torch.cuda.empty_cache()

@@ -1075,6 +1075,20 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SWDFT_ERR_CUDA;
     for (size_t i = 0; i < plan->arrays.size(); ++i) {
         ArrayPlan &a = plan->arrays[i];
+        // an array of the same shape, band and form tuned earlier in this call: same choice
+        bool copied = false;
+        for (size_t j = 0; j < i && !copied; ++j) {
+            const ArrayPlan &b = plan->arrays[j];
+            if (b.tuned && b.N0 == a.N0 && b.N1 == a.N1 && b.ld == a.ld && b.n0 == a.n0 && b.n1 == a.n1 &&
+                b.dtype == a.dtype && b.q_begin == a.q_begin && b.q_end == a.q_end && b.algo_auto == a.algo_auto &&
+                (a.algo_auto || b.algo == a.algo)) {
+                a.cfg = b.cfg;
+                a.algo = b.algo;
+                a.tuned = true;
+                copied = true;
+            }
+        }
+        if (copied) continue;
         if (a.algo_auto) a.algo = SWDFT_ALGO_TREE_F32;  // the tree is tuned first, then compared
         default_config(a, plan->sm_count, plan->conc);
         if (a.ternary()) continue;  // one launch shape per ternary kernel: nothing to choose

@@ -230,6 +230,23 @@ def test_fused_tree_matches_oracle_and_two_pass(sw, N0, N1, n0, n1, cplx, chunk)
     assert_close_to_oracle(fused, x, n0, n1)
 
 
+def test_autotune_times_each_shape_once(sw, tmp_path, monkeypatch):
+    """A batch with repeated shapes: the autotuner times each distinct shape once and gives
+    the repeats the same choice; every array still matches the oracle."""
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("SWDFT_TUNE_CACHE", str(cache))
+    shapes = [(90, 70, 16, 8), (64, 80, 8, 32), (90, 70, 16, 8), (90, 70, 16, 8), (64, 80, 8, 32)]
+    xs = [workloads.random_array(600 + i, s[0], s[1]) for i, s in enumerate(shapes)]
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    t = sw.Transform([(s[0], s[1], s[2], s[3], 0) for s in shapes], algo="auto", flags=sw.FLAG_GRAPH)
+    t.autotune(xd)
+    outs = t.forward(xd)
+    torch.cuda.synchronize()
+    assert len(cache.read_text().strip().splitlines()) == 2
+    for s, x, a in zip(shapes, xs, outs):
+        assert_close_to_oracle(a, x, s[2], s[3])
+
+
 @pytest.mark.parametrize("N0,N1,n0,n1", [(100, 100, 64, 64), (512, 512, 32, 32)])
 def test_autotune_chooses_tree_or_tensor_cores(sw, N0, N1, n0, n1, tmp_path, monkeypatch):
     """With algo="auto" the autotuner times the tuned tree against the split-bf16 tensor-core
