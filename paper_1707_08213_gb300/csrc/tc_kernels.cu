@@ -266,7 +266,8 @@ __global__ void __launch_bounds__(TC_THREADS) tc_col_kernel(const __grid_constan
 // can express -- so each row's A is written to shared memory (K-major) from the staged input
 // rows.  The epilogue writes z directly as the column pass's operand planes.
 
-constexpr int TCR_ROWS = 8;  // input rows per CTA
+constexpr int TCR_ROWS = 8;      // input rows per CTA
+constexpr int TCR_THREADS = 256;  // two threads per position (TMEM lane): A groups and epilogue halves
 
 struct TcRowParams {
     const void *x;       // first input row of the band
@@ -285,31 +286,39 @@ __host__ __device__ constexpr int tcr_K(int M1, bool cplx) {
 size_t tc_row_smem_bytes(int m1, bool cplx, int terms) {
     const int n1 = 1 << m1, K = tcr_K(m1, cplx), N = 2 * n1, nb = terms == 3 ? 2 : 1;
     const int W = TC_CH + n1;  // staged columns per row (n1 - 1 look-ahead, rounded)
-    return (size_t)TCR_ROWS * W * (cplx ? 2 : 1) * 4 + (size_t)nb * N * K * 2 + (size_t)nb * TC_CH * K * 2 + 64 +
-           1024 + 8192;
+    // staged rows, B (nb sets), A (two buffers of nb sets), barriers and TMEM slot, alignment
+    return (size_t)TCR_ROWS * W * (cplx ? 2 : 1) * 4 + (size_t)nb * N * K * 2 + (size_t)2 * nb * TC_CH * K * 2 +
+           64 + 1024 + 8192;
 }
 
+// Pipelined over the CTA's rows: while the tensor core multiplies row r (A buffer and TMEM
+// accumulator r mod 2), the threads write row r-1's epilogue and build row r+1's A.  Thread
+// (m, h): position m = TMEM lane, h = which half of the A chunks it builds and which part of
+// D (Re or Im k1; both when n1 < 16) it stores.
 template <int M1, bool CPLX, int TERMS, bool F16>
-__global__ void __launch_bounds__(TC_THREADS) tc_row_kernel(const __grid_constant__ TcRowParams p) {
+__global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_constant__ TcRowParams p) {
     constexpr int n1 = 1 << M1;
     constexpr int K = tcr_K(M1, CPLX);
     constexpr int N = 2 * n1;
     constexpr int KS = K / 16;
     constexpr int NB = TERMS == 3 ? 2 : 1;
     constexpr int W = TC_CH + n1;
-    constexpr uint32_t TMEM_COLS = N < 32 ? 32 : N;
+    constexpr uint32_t TMEM_COLS = 2 * N < 32 ? 32 : 2 * N;  // two accumulators
     constexpr uint32_t B_BYTES = N * K * 2, A_BYTES = TC_CH * K * 2;
     constexpr uint32_t IDESC = umma_idesc_f16(TC_CH, N, !F16, /*a_mn=*/false, /*b_mn=*/false);
+    constexpr bool SPLIT = n1 >= 16;  // epilogue halves: Re by h = 0, Im by h = 1
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char *sB = smem;                                   // NB x B_BYTES
-    unsigned char *sA = sB + NB * B_BYTES;                      // NB x A_BYTES
-    float *sx = reinterpret_cast<float *>(sA + NB * A_BYTES);   // TCR_ROWS x W (x2 complex)
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sx + TCR_ROWS * W * (CPLX ? 2 : 1));
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+    unsigned char *sA = sB + NB * B_BYTES;                      // 2 buffers x NB x A_BYTES
+    float *sx = reinterpret_cast<float *>(sA + 2 * NB * A_BYTES);  // TCR_ROWS x W (x2 complex)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sx + TCR_ROWS * W * (CPLX ? 2 : 1));  // 2 barriers
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int m = tid & (TC_CH - 1);  // this thread's position in the tile = its TMEM lane
+    const int h = tid >> 7;           // 0 or 1
     const int q1_0 = blockIdx.x * TC_CH;
     const int r0 = blockIdx.y * TCR_ROWS;
     if (r0 >= p.zrows) return;  // uniform per block
@@ -321,11 +330,12 @@ __global__ void __launch_bounds__(TC_THREADS) tc_row_kernel(const __grid_constan
         tmem_relinquish();
     }
     if (tid == 0) {
-        mbar_init(bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         fence_barrier_init();
     }
     // B = realified F1 (K-major): rows n (Re k1 | Im k1), columns k (Re j1 | Im j1 | zero pad)
-    for (int e = tid; e < N * K; e += TC_THREADS) {
+    for (int e = tid; e < N * K; e += TCR_THREADS) {
         const int n = e / K, k = e - (e / K) * K;
         const int k1 = n & (n1 - 1);
         const bool in_im = CPLX && k >= n1 && k < 2 * n1;
@@ -340,7 +350,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_row_kernel(const __grid_constan
         if (NB == 2) *reinterpret_cast<uint16_t *>(sB + B_BYTES + off) = to_bits<F16>(v - from_bits<F16>(hi));
     }
     // stage the CTA's input rows (columns q1_0 .. q1_0 + W - 1; zero beyond the array)
-    for (int e = tid; e < nrows * W; e += TC_THREADS) {
+    for (int e = tid; e < nrows * W; e += TCR_THREADS) {
         const int rr = e / W, c = e - (e / W) * W;
         const int col = q1_0 + c;
         if (CPLX) {
@@ -361,98 +371,122 @@ __global__ void __launch_bounds__(TC_THREADS) tc_row_kernel(const __grid_constan
     const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
     const uint32_t lbo = 128u, sbo = (uint32_t)(K / 8) * 128u;  // K-major, both operands
 
-    const int m = tid;                  // this thread's position in the tile = its TMEM lane
     const int pos = q1_0 + m;
     const int64_t nch = (int64_t)p.P1 * n1;
-    bool ok = true;
-    for (int rr = 0; rr < nrows && ok; ++rr) {
-        // A row m: x[pos + k] (Re, then Im), 8 elements (one 16-byte chunk) at a time
+    bool ok = true, done = true;
+    int issued = 0;  // rows whose UMMAs were committed
+    for (int rr = 0; rr <= nrows; ++rr) {
+        if (rr < nrows) {
+            // A row m of buffer rr & 1: x[pos + k] (Re, then Im), this thread's half of the
+            // 16-byte chunks.  The buffer's last reader, row rr - 2's UMMAs, completed: every
+            // thread waited for them in row rr - 2's epilogue.
+            unsigned char *a_buf = sA + (rr & 1) * NB * A_BYTES;
 #pragma unroll
-        for (int g = 0; g < K / 8; ++g) {
-            uint16_t hv[8], lv[8];
+            for (int g = h; g < K / 8; g += 2) {
+                uint16_t hv[8], lv[8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int k = 8 * g + e;
-                float v = 0.f;
-                if (CPLX) {
-                    if (k < n1) v = sx[(rr * W + m + k) * 2];
-                    else if (k < 2 * n1) v = sx[(rr * W + m + k - n1) * 2 + 1];
-                } else if (k < n1) {
-                    v = sx[rr * W + m + k];
+                for (int e = 0; e < 8; ++e) {
+                    const int k = 8 * g + e;
+                    float v = 0.f;
+                    if (CPLX) {
+                        if (k < n1) v = sx[(rr * W + m + k) * 2];
+                        else if (k < 2 * n1) v = sx[(rr * W + m + k - n1) * 2 + 1];
+                    } else if (k < n1) {
+                        v = sx[rr * W + m + k];
+                    }
+                    hv[e] = to_bits<F16>(v);
+                    lv[e] = to_bits<F16>(v - from_bits<F16>(hv[e]));
                 }
-                hv[e] = to_bits<F16>(v);
-                lv[e] = to_bits<F16>(v - from_bits<F16>(hv[e]));
-            }
-            const uint32_t off = (uint32_t)((m >> 3) * (K / 8) + g) * 128u + (uint32_t)(m & 7) * 16u;
-            uint4 h4, l4;
-            h4.x = hv[0] | ((uint32_t)hv[1] << 16); h4.y = hv[2] | ((uint32_t)hv[3] << 16);
-            h4.z = hv[4] | ((uint32_t)hv[5] << 16); h4.w = hv[6] | ((uint32_t)hv[7] << 16);
-            *reinterpret_cast<uint4 *>(sA + off) = h4;
-            if (NB == 2) {
-                l4.x = lv[0] | ((uint32_t)lv[1] << 16); l4.y = lv[2] | ((uint32_t)lv[3] << 16);
-                l4.z = lv[4] | ((uint32_t)lv[5] << 16); l4.w = lv[6] | ((uint32_t)lv[7] << 16);
-                *reinterpret_cast<uint4 *>(sA + A_BYTES + off) = l4;
+                const uint32_t off = (uint32_t)((m >> 3) * (K / 8) + g) * 128u + (uint32_t)(m & 7) * 16u;
+                uint4 h4, l4;
+                h4.x = hv[0] | ((uint32_t)hv[1] << 16); h4.y = hv[2] | ((uint32_t)hv[3] << 16);
+                h4.z = hv[4] | ((uint32_t)hv[5] << 16); h4.w = hv[6] | ((uint32_t)hv[7] << 16);
+                *reinterpret_cast<uint4 *>(a_buf + off) = h4;
+                if (NB == 2) {
+                    l4.x = lv[0] | ((uint32_t)lv[1] << 16); l4.y = lv[2] | ((uint32_t)lv[3] << 16);
+                    l4.z = lv[4] | ((uint32_t)lv[5] << 16); l4.w = lv[6] | ((uint32_t)lv[7] << 16);
+                    *reinterpret_cast<uint4 *>(a_buf + A_BYTES + off) = l4;
+                }
             }
         }
         fence_proxy_async_smem();
         tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
+        // A of row rr is complete; row rr - 2's TMEM reads are done; every wait so far succeeded
+        ok = __syncthreads_and(done);
+        if (!ok) break;  // block-uniform
+        if (rr < nrows) {
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t a_base = sA0 + (uint32_t)((rr & 1) * NB) * A_BYTES;
+                const uint32_t d_tmem = tmem + (uint32_t)((rr & 1) * N);
 #pragma unroll
-            for (int t = 0; t < TERMS; ++t) {
-                const int a_set = (t == 2) ? 1 : 0, b_set = (t == 1) ? 1 : 0;
+                for (int t = 0; t < TERMS; ++t) {
+                    const int a_set = (t == 2) ? 1 : 0, b_set = (t == 1) ? 1 : 0;
 #pragma unroll
-                for (int ks = 0; ks < KS; ++ks)
-                    umma_f16(tmem, smem_desc(sA0 + a_set * A_BYTES + ks * 256, lbo, sbo),
-                             smem_desc(sB0 + b_set * B_BYTES + ks * 256, lbo, sbo), IDESC, (t | ks) != 0);
+                    for (int ks = 0; ks < KS; ++ks)
+                        umma_f16(d_tmem, smem_desc(a_base + a_set * A_BYTES + ks * 256, lbo, sbo),
+                                 smem_desc(sB0 + b_set * B_BYTES + ks * 256, lbo, sbo), IDESC, (t | ks) != 0);
+                }
+                umma_commit(&bar[rr & 1]);
             }
-            umma_commit(bar);
+            issued = rr + 1;
         }
-        const bool done = mbar_wait(bar, (uint32_t)(rr & 1), TC_MAX_POLLS);
-        tc_fence_after();
-        float acc[N];
+        if (rr >= 1) {
+            // epilogue of row e = rr - 1: its D is accumulator e mod 2, barrier e mod 2 in its
+            // (e / 2)-th phase
+            const int er = rr - 1;
+            // warp-uniform, so that the warp's tcgen05.ld below is never divergent
+            done = __all_sync(0xffffffffu, mbar_wait(&bar[er & 1], (uint32_t)((er >> 1) & 1), TC_MAX_POLLS));
+            tc_fence_after();
+            if (done && (SPLIT || h == 0)) {
+                constexpr int NC = SPLIT ? n1 : N;  // columns this thread reads
+                const int c0 = SPLIT ? h * n1 : 0;
+                float acc[NC];
 #pragma unroll
-        for (int c = 0; c < N; c += 16) {
-            float v[16];
-            tmem_ld_16(tmem + ((uint32_t)(warp * 32) << 16) + c, v);
-            tmem_ld_wait();
+                for (int c = 0; c < NC; c += 16) {
+                    float v[16];
+                    tmem_ld_16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((er & 1) * N + c0 + c), v);
+                    tmem_ld_wait();
 #pragma unroll
-            for (int u = 0; u < 16; ++u) acc[c + u] = v[u];
-        }
-        tc_fence_before();
-        ok = __syncthreads_and(done);  // A and TMEM are free for the next row
-        if (ok && pos < p.P1) {
-            // z for this position: acc[k1] = Re, acc[n1 + k1] = Im -> operand planes
-            const int64_t base = (int64_t)(r0 + rr) * nch + (int64_t)pos * n1;
+                    for (int u = 0; u < 16; ++u)
+                        if (c + u < NC) acc[c + u] = v[u];
+                }
+                if (pos < p.P1) {
+                    // z for this position: Re k1 (part 0) and Im k1 (part 1) -> operand planes
+                    const int64_t base = (int64_t)(r0 + er) * nch + (int64_t)pos * n1;
 #pragma unroll
-            for (int part = 0; part < 2; ++part) {
+                    for (int pp = 0; pp < (SPLIT ? 1 : 2); ++pp) {
+                        const int part = SPLIT ? h : pp;
 #pragma unroll
-                for (int g = 0; g < n1 / 8; ++g) {
-                    uint16_t hv[8], lv[8];
+                        for (int g = 0; g < n1 / 8; ++g) {
+                            uint16_t hv[8], lv[8];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const float v = acc[part * n1 + 8 * g + e];
-                        hv[e] = to_bits<F16>(v);
-                        lv[e] = to_bits<F16>(v - from_bits<F16>(hv[e]));
-                    }
-                    uint4 h4, l4;
-                    h4.x = hv[0] | ((uint32_t)hv[1] << 16); h4.y = hv[2] | ((uint32_t)hv[3] << 16);
-                    h4.z = hv[4] | ((uint32_t)hv[5] << 16); h4.w = hv[6] | ((uint32_t)hv[7] << 16);
-                    *reinterpret_cast<uint4 *>(p.planes + part * p.plane_elems + base + 8 * g) = h4;
-                    if (TERMS == 3) {
-                        l4.x = lv[0] | ((uint32_t)lv[1] << 16); l4.y = lv[2] | ((uint32_t)lv[3] << 16);
-                        l4.z = lv[4] | ((uint32_t)lv[5] << 16); l4.w = lv[6] | ((uint32_t)lv[7] << 16);
-                        *reinterpret_cast<uint4 *>(p.planes + (2 + part) * p.plane_elems + base + 8 * g) = l4;
+                            for (int e = 0; e < 8; ++e) {
+                                const float v = acc[(SPLIT ? 0 : part * n1) + 8 * g + e];
+                                hv[e] = to_bits<F16>(v);
+                                lv[e] = to_bits<F16>(v - from_bits<F16>(hv[e]));
+                            }
+                            uint4 h4, l4;
+                            h4.x = hv[0] | ((uint32_t)hv[1] << 16); h4.y = hv[2] | ((uint32_t)hv[3] << 16);
+                            h4.z = hv[4] | ((uint32_t)hv[5] << 16); h4.w = hv[6] | ((uint32_t)hv[7] << 16);
+                            *reinterpret_cast<uint4 *>(p.planes + part * p.plane_elems + base + 8 * g) = h4;
+                            if (TERMS == 3) {
+                                l4.x = lv[0] | ((uint32_t)lv[1] << 16); l4.y = lv[2] | ((uint32_t)lv[3] << 16);
+                                l4.z = lv[4] | ((uint32_t)lv[5] << 16); l4.w = lv[6] | ((uint32_t)lv[7] << 16);
+                                *reinterpret_cast<uint4 *>(p.planes + (2 + part) * p.plane_elems + base + 8 * g) = l4;
+                            }
+                        }
                     }
                 }
             }
         }
     }
+    if (ok) ok = __syncthreads_and(done);  // the last row's wait (block-uniform: no break)
     if (!ok) {
+        // a wait gave up: flag it, give the UMMAs in flight a last bounded wait, then release
         if (tid == 0) atomicExch(&g_tc_status, 1);
-        mbar_wait(bar, 0, 64);
-        mbar_wait(bar, 1, 64);
+        if (issued >= 1) mbar_wait(&bar[(issued - 1) & 1], (uint32_t)(((issued - 1) >> 1) & 1), 64);
+        if (issued >= 2) mbar_wait(&bar[(issued - 2) & 1], (uint32_t)(((issued - 2) >> 1) & 1), 64);
     }
     tc_fence_before();
     __syncthreads();
@@ -562,7 +596,7 @@ static cudaError_t launch_tc_row_t(const TcRowParams &p, dim3 grid, size_t smem,
     auto k = tc_row_kernel<M1, CPLX, TERMS, F16>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, TC_THREADS, smem, s>>>(p);
+    k<<<grid, TCR_THREADS, smem, s>>>(p);
     return cudaGetLastError();
 }
 
