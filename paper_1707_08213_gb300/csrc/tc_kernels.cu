@@ -267,7 +267,8 @@ __global__ void __launch_bounds__(TC_THREADS) tc_col_kernel(const __grid_constan
 // rows.  The epilogue writes z directly as the column pass's operand planes.
 
 constexpr int TCR_ROWS = 8;      // input rows per CTA
-constexpr int TCR_THREADS = 256;  // two threads per position (TMEM lane): A groups and epilogue halves
+constexpr int TCR_THREADS = 512;  // four threads per position (TMEM lane): A chunks and epilogue slices
+constexpr int TCR_TQ = TCR_THREADS / TC_CH;
 
 struct TcRowParams {
     const void *x;       // first input row of the band
@@ -293,8 +294,8 @@ size_t tc_row_smem_bytes(int m1, bool cplx, int terms) {
 
 // Pipelined over the CTA's rows: while the tensor core multiplies row r (A buffer and TMEM
 // accumulator r mod 2), the threads write row r-1's epilogue and build row r+1's A.  Thread
-// (m, h): position m = TMEM lane, h = which half of the A chunks it builds and which part of
-// D (Re or Im k1; both when n1 < 16) it stores.
+// (m, h), h < 4: position m = TMEM lane; it builds A chunks g = h mod 4 and stores slice h of
+// D's 2 n1 columns (slices of max(16, n1/2) columns: Re k1 then Im k1).
 template <int M1, bool CPLX, int TERMS, bool F16>
 __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_constant__ TcRowParams p) {
     constexpr int n1 = 1 << M1;
@@ -306,7 +307,8 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
     constexpr uint32_t TMEM_COLS = 2 * N < 32 ? 32 : 2 * N;  // two accumulators
     constexpr uint32_t B_BYTES = N * K * 2, A_BYTES = TC_CH * K * 2;
     constexpr uint32_t IDESC = umma_idesc_f16(TC_CH, N, !F16, /*a_mn=*/false, /*b_mn=*/false);
-    constexpr bool SPLIT = n1 >= 16;  // epilogue halves: Re by h = 0, Im by h = 1
+    constexpr int SW = N / 4 < 16 ? 16 : N / 4;  // D columns per epilogue slice (tcgen05.ld x16)
+    constexpr int NSL = N / SW;                   // slices: 1 (n1 = 8), 2 (n1 = 16) or 4
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -318,7 +320,7 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int m = tid & (TC_CH - 1);  // this thread's position in the tile = its TMEM lane
-    const int h = tid >> 7;           // 0 or 1
+    const int h = tid >> 7;           // 0 .. TCR_TQ - 1
     const int q1_0 = blockIdx.x * TC_CH;
     const int r0 = blockIdx.y * TCR_ROWS;
     if (r0 >= p.zrows) return;  // uniform per block
@@ -382,7 +384,7 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
             // thread waited for them in row rr - 2's epilogue.
             unsigned char *a_buf = sA + (rr & 1) * NB * A_BYTES;
 #pragma unroll
-            for (int g = h; g < K / 8; g += 2) {
+            for (int g = h; g < K / 8; g += TCR_TQ) {
                 uint16_t hv[8], lv[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
@@ -438,43 +440,41 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
             // warp-uniform, so that the warp's tcgen05.ld below is never divergent
             done = __all_sync(0xffffffffu, mbar_wait(&bar[er & 1], (uint32_t)((er >> 1) & 1), TC_MAX_POLLS));
             tc_fence_after();
-            if (done && (SPLIT || h == 0)) {
-                constexpr int NC = SPLIT ? n1 : N;  // columns this thread reads
-                const int c0 = SPLIT ? h * n1 : 0;
-                float acc[NC];
+            if (done && h < NSL) {
+                const int c0 = h * SW;  // first D column of this slice
+                float acc[SW];
 #pragma unroll
-                for (int c = 0; c < NC; c += 16) {
+                for (int c = 0; c < SW; c += 16) {
                     float v[16];
                     tmem_ld_16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((er & 1) * N + c0 + c), v);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int u = 0; u < 16; ++u)
-                        if (c + u < NC) acc[c + u] = v[u];
+                    for (int u = 0; u < 16; ++u) acc[c + u] = v[u];
                 }
                 if (pos < p.P1) {
-                    // z for this position: Re k1 (part 0) and Im k1 (part 1) -> operand planes
+                    // z for this position: each group of 8 D columns is 8 consecutive k1 of one
+                    // part (column c: part c / n1, 0 = Re and 1 = Im; k1 = c mod n1) -> planes
                     const int64_t base = (int64_t)(r0 + er) * nch + (int64_t)pos * n1;
 #pragma unroll
-                    for (int pp = 0; pp < (SPLIT ? 1 : 2); ++pp) {
-                        const int part = SPLIT ? h : pp;
+                    for (int g = 0; g < SW / 8; ++g) {
+                        const int cc = c0 + 8 * g;
+                        const int part = cc / n1;
+                        const int64_t off = base + (cc - part * n1);
+                        uint16_t hv[8], lv[8];
 #pragma unroll
-                        for (int g = 0; g < n1 / 8; ++g) {
-                            uint16_t hv[8], lv[8];
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                const float v = acc[(SPLIT ? 0 : part * n1) + 8 * g + e];
-                                hv[e] = to_bits<F16>(v);
-                                lv[e] = to_bits<F16>(v - from_bits<F16>(hv[e]));
-                            }
-                            uint4 h4, l4;
-                            h4.x = hv[0] | ((uint32_t)hv[1] << 16); h4.y = hv[2] | ((uint32_t)hv[3] << 16);
-                            h4.z = hv[4] | ((uint32_t)hv[5] << 16); h4.w = hv[6] | ((uint32_t)hv[7] << 16);
-                            *reinterpret_cast<uint4 *>(p.planes + part * p.plane_elems + base + 8 * g) = h4;
-                            if (TERMS == 3) {
-                                l4.x = lv[0] | ((uint32_t)lv[1] << 16); l4.y = lv[2] | ((uint32_t)lv[3] << 16);
-                                l4.z = lv[4] | ((uint32_t)lv[5] << 16); l4.w = lv[6] | ((uint32_t)lv[7] << 16);
-                                *reinterpret_cast<uint4 *>(p.planes + (2 + part) * p.plane_elems + base + 8 * g) = l4;
-                            }
+                        for (int e = 0; e < 8; ++e) {
+                            const float v = acc[8 * g + e];
+                            hv[e] = to_bits<F16>(v);
+                            lv[e] = to_bits<F16>(v - from_bits<F16>(hv[e]));
+                        }
+                        uint4 h4, l4;
+                        h4.x = hv[0] | ((uint32_t)hv[1] << 16); h4.y = hv[2] | ((uint32_t)hv[3] << 16);
+                        h4.z = hv[4] | ((uint32_t)hv[5] << 16); h4.w = hv[6] | ((uint32_t)hv[7] << 16);
+                        *reinterpret_cast<uint4 *>(p.planes + part * p.plane_elems + off) = h4;
+                        if (TERMS == 3) {
+                            l4.x = lv[0] | ((uint32_t)lv[1] << 16); l4.y = lv[2] | ((uint32_t)lv[3] << 16);
+                            l4.z = lv[4] | ((uint32_t)lv[5] << 16); l4.w = lv[6] | ((uint32_t)lv[7] << 16);
+                            *reinterpret_cast<uint4 *>(p.planes + (2 + part) * p.plane_elems + off) = l4;
                         }
                     }
                 }
