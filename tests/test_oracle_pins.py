@@ -3,6 +3,8 @@
 Pins used (arXiv 1707.08213):
 * library routine: every window equals numpy.fft.fft2 of its patch times the scale
   (Section 4.1, Eq. 2: a 2D DFT per window);
+* brute force: Eq. 2 as nested loops with their own exponentials on arrays up to 12 x 12,
+  every pair of window sides in {1, 2, 4, 8};
 * closed forms: a pure 2D complex exponential gives one bin of known magnitude and phase;
   a real cosine gives two; the DC bin is the scaled window sum;
 * invariants: per-window Parseval (unitary scale), linearity, the sliding shift identity
@@ -59,6 +61,28 @@ def test_every_window_is_numpy_fft2(oracle_lib, method, N0, N1, n0, n1, cplx):
     a = oracle_lib.swdft2d(x, n0, n1, norm="unitary", method=method)
     assert a.shape == (N0 - n0 + 1, N1 - n1 + 1, n0, n1)
     np.testing.assert_allclose(a, ref, rtol=0, atol=1e-13 * max(1.0, np.abs(x).max() * n0 * n1))
+
+
+@pytest.mark.parametrize("n0", [1, 2, 4, 8])
+@pytest.mark.parametrize("n1", [1, 2, 4, 8])
+def test_brute_force_loops(oracle_lib, n0, n1):
+    """Eq. 2 as plain nested loops with their own exponentials (no numpy FFT, no matrices),
+    on arrays of at most 12 x 12, every pair of window sides in {1, 2, 4, 8}."""
+    N0, N1 = min(12, n0 + 3), min(12, n1 + 4)
+    x = _rand(7 * n0 + n1, N0, N1)
+    a = oracle_lib.swdft2d(x, n0, n1, norm="none", method="direct")
+    worst = 0.0
+    for q0 in range(N0 - n0 + 1):
+        for q1 in range(N1 - n1 + 1):
+            for k0 in range(n0):
+                for k1 in range(n1):
+                    acc = 0j
+                    for j0 in range(n0):
+                        for j1 in range(n1):
+                            ang = -2.0 * math.pi * (j0 * k0 / n0 + j1 * k1 / n1)
+                            acc += x[q0 + j0, q1 + j1] * complex(math.cos(ang), math.sin(ang))
+                    worst = max(worst, abs(a[q0, q1, k0, k1] - acc))
+    assert worst <= 1e-12 * n0 * n1
 
 
 @pytest.mark.parametrize("norm,scale", [("none", lambda n0, n1: 1.0),
