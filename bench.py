@@ -464,6 +464,28 @@ def stream_measurement(torch, sw):
         res[f"rows_per_push_{R}"] = {"pushes": pushes, "us_per_push": round(1e3 * ms / pushes, 2),
                                      "coeffs_per_s": coeffs / (ms / 1e3),
                                      "output_gbs": round(8 * coeffs / (ms / 1e3) / 1e9, 1)}
+        # the same pushes captured once into a CUDA graph and replayed: the device's time per
+        # push without the Python caller's per-call overhead
+        try:
+            g = torch.cuda.CUDAGraph()
+            cs = torch.cuda.Stream()
+            cs.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(cs):
+                with torch.cuda.graph(g, stream=cs):
+                    run()
+            torch.cuda.current_stream().wait_stream(cs)
+            g.replay()
+            torch.cuda.synchronize()
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            gms = e0.elapsed_time(e1)
+            res[f"rows_per_push_{R}"]["graph_us_per_push"] = round(1e3 * gms / pushes, 2)
+            res[f"rows_per_push_{R}"]["graph_output_gbs"] = round(8 * coeffs / (gms / 1e3) / 1e9, 1)
+            del g
+        except Exception as e:  # noqa: BLE001
+            res[f"rows_per_push_{R}"]["graph_error"] = str(e)[:200]
         del st, out
     torch.cuda.empty_cache()
     return res
