@@ -17,11 +17,12 @@
 // keeps v = hi + lo (hi = bf16(v), lo = bf16(v - hi)) for both z and F0 and accumulates
 // hi*hi + hi*lo + lo*hi, dropping only lo*lo (~2^-16 relative per product).
 //
-// One CTA = 128 threads = the 128 TMEM lanes = 128 channels.  Thread 0 issues the TMA loads
-// and the UMMAs; every wait on an mbarrier is bounded and a time-out sets an error word and
-// skips ahead to the TMEM release.  The epilogue reads D with tcgen05.ld and each thread
-// stores its channel's n0 coefficients: for fixed k0 a warp writes 32 consecutive channels
-// (256 contiguous bytes), the same pattern as the tree kernel.
+// One CTA = 128 channels = the 128 TMEM lanes, with two threads per channel (256 threads).
+// Thread 0 issues the TMA loads and the UMMAs; every wait on an mbarrier is bounded and a
+// time-out sets an error word and skips ahead to the TMEM release.  The epilogue reads D with
+// tcgen05.ld and each thread stores half of its channel's n0 coefficients: for fixed k0 a
+// warp writes 32 consecutive channels (256 contiguous bytes), the same pattern as the tree
+// kernel.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -37,7 +38,7 @@ namespace swdft {
 __device__ int g_tc_status;  // 0 = ok; 1 = an mbarrier wait timed out
 
 constexpr int TC_CH = 128;      // channels per CTA = UMMA M = TMEM lanes
-constexpr int TC_THREADS = 128;
+constexpr int TCC_THREADS = 256;  // column GEMM: two threads per channel (TMEM lane), k0 halves
 constexpr uint32_t TC_MAX_POLLS = 4000;  // x up to ~1 ms per poll
 
 struct TcColParams {
@@ -111,7 +112,7 @@ __device__ __forceinline__ uint32_t kmajor_off(int n, int k, int K) {
 }
 
 template <int M0, int TERMS, bool F16>
-__global__ void __launch_bounds__(TC_THREADS) tc_col_kernel(const __grid_constant__ TcColParams p) {
+__global__ void __launch_bounds__(TCC_THREADS) tc_col_kernel(const __grid_constant__ TcColParams p) {
     constexpr int n0 = 1 << M0;
     constexpr int K = 2 * n0;   // realified contraction length
     constexpr int N = 2 * n0;   // realified output columns (Re k0 | Im k0)
@@ -133,7 +134,9 @@ __global__ void __launch_bounds__(TC_THREADS) tc_col_kernel(const __grid_constan
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2);
 
     const int tid = threadIdx.x;
-    const int warp = tid >> 5, lane = tid & 31;
+    const int warp = tid >> 5;
+    const int m = tid & (TC_CH - 1);  // this thread's channel in the tile = its TMEM lane
+    const int h = tid / TC_CH;        // which half of the k0 outputs it stores
     const int64_t ch0 = (int64_t)blockIdx.x * TC_CH;
     const int qa = blockIdx.y * p.chunk;
     if (qa >= p.rows_out) return;  // uniform per block
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_col_kernel(const __grid_constan
         fence_barrier_init();
     }
     // B = realified F0 (K-major): rows n (Re k0 | Im k0), columns k (Re j0 | Im j0)
-    for (int e = tid; e < N * K; e += TC_THREADS) {
+    for (int e = tid; e < N * K; e += TCC_THREADS) {
         const int n = e / K, k = e - (e / K) * K;
         const int k0 = n & (n0 - 1), j0 = k & (n0 - 1);
         const float2 w = p.om64[((j0 * k0) & (n0 - 1)) << (6 - M0)];  // (C, -S)
@@ -176,10 +179,11 @@ __global__ void __launch_bounds__(TC_THREADS) tc_col_kernel(const __grid_constan
     ok = __syncthreads_and(mbar_wait(&bars[0], 0, TC_MAX_POLLS));  // block-uniform
 
     const int n1 = 1 << p.m1;
-    const int64_t ch = ch0 + warp * 32 + lane;
+    constexpr int HK = n0 / 2;  // k0 values per thread: [h HK, (h + 1) HK)
+    const int64_t ch = ch0 + m;
     const bool active = ch < p.nch;
     const int64_t q1 = ch >> p.m1, k1 = ch & (n1 - 1);
-    float2 *dst = p.out + (int64_t)qa * p.orow + q1 * ((int64_t)n0 * n1) + k1;
+    float2 *dst = p.out + (int64_t)qa * p.orow + q1 * ((int64_t)n0 * n1) + (int64_t)(h * HK) * n1 + k1;
     const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
     static_assert(n0 >= 16, "each 16-row k-step must lie in one plane");
     const uint32_t a_lbo = 128u;  // K-group stride of A: consecutive 16-byte rows
@@ -222,21 +226,35 @@ __global__ void __launch_bounds__(TC_THREADS) tc_col_kernel(const __grid_constan
         if (!ok) break;
         tc_fence_after();
         if (tid == 0 && i + 1 < L) issue(i + 1);
-        // epilogue: this thread's TMEM lane = its channel; columns [0, n0) Re, [n0, 2n0) Im
-        const uint32_t lane_addr = tmem + (uint32_t)((i & 1) * N) + ((uint32_t)(warp * 32) << 16);
-        float acc[N];
+        // epilogue: this thread's TMEM lane = its channel (warp w reads lanes 32 (w mod 4));
+        // columns k0 (Re) and n0 + k0 (Im) for its half of the k0
+        const uint32_t lane_addr = tmem + (uint32_t)((i & 1) * N) + ((uint32_t)((warp & 3) * 32) << 16);
+        float re[HK], im[HK];
 #pragma unroll
-        for (int c = 0; c < N; c += 16) {
-            float v[16];
-            tmem_ld_16(lane_addr + c, v);
-            tmem_ld_wait();  // the loaded registers are valid only after the wait
+        for (int part = 0; part < 2; ++part) {
+            float *acc = part ? im : re;
+            const uint32_t col = lane_addr + (uint32_t)(part * n0 + h * HK);
+            if constexpr (HK >= 16) {
 #pragma unroll
-            for (int u = 0; u < 16; ++u) acc[c + u] = v[u];
+                for (int c = 0; c < HK; c += 16) {
+                    float v[16];
+                    tmem_ld_16(col + c, v);
+                    tmem_ld_wait();  // the loaded registers are valid only after the wait
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) acc[c + u] = v[u];
+                }
+            } else {
+                float v[8];
+                tmem_ld_8(col, v);
+                tmem_ld_wait();
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u] = v[u];
+            }
         }
         if (active) {
 #pragma unroll
-            for (int k0 = 0; k0 < n0; ++k0)
-                __stcs(dst + (int64_t)k0 * n1, make_float2(out_scale * acc[k0], out_scale * acc[n0 + k0]));
+            for (int k = 0; k < HK; ++k)
+                __stcs(dst + (int64_t)k * n1, make_float2(out_scale * re[k], out_scale * im[k]));
         }
         dst += p.orow;
     }
@@ -530,7 +548,7 @@ static cudaError_t launch_tc_col_t(const TcColParams &p, dim3 grid, size_t smem,
     auto k = tc_col_kernel<M0, TERMS, F16>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, TC_THREADS, smem, s>>>(p);
+    k<<<grid, TCC_THREADS, smem, s>>>(p);
     return cudaGetLastError();
 }
 
