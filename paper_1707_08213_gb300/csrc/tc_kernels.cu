@@ -105,6 +105,26 @@ __device__ __forceinline__ float from_bits(uint16_t b) {
     }
 }
 
+// Two values as packed 16-bit pairs (first value in the low half): hi = round(v) and
+// lo = round(v - hi), with one paired conversion for each (the same bits as converting
+// each value on its own).
+template <bool F16>
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t &hi, uint32_t &lo) {
+    if constexpr (F16) {
+        const __half2 h = __floats2half2_rn(a, b);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    }
+}
+
 // Byte offset of element (n, k) in a K-major, no-swizzle operand of K columns: 8x8 core
 // matrices of 128 bytes, K-adjacent core matrices 128 B apart, 8-row groups K*16 B apart.
 __device__ __forceinline__ uint32_t kmajor_off(int n, int k, int K) {
@@ -354,6 +374,10 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
         mbar_init(&bar[1], 1);
         fence_barrier_init();
     }
+    // the twiddle table in shared memory: the B build below indexes it per lane
+    __shared__ float2 s_om[kMaxN];
+    if (tid < kMaxN) s_om[tid] = p.om64[tid];
+    __syncthreads();
     // B = realified F1 (K-major): rows n (Re k1 | Im k1), columns k (Re j1 | Im j1 | zero pad)
     for (int e = tid; e < N * K; e += TCR_THREADS) {
         const int n = e / K, k = e - (e / K) * K;
@@ -361,7 +385,7 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
         const bool in_im = CPLX && k >= n1 && k < 2 * n1;
         const bool pad = CPLX ? (k >= 2 * n1) : (k >= n1);
         const int j1 = k & (n1 - 1);
-        const float2 w = p.om64[((j1 * k1) & (n1 - 1)) << (6 - M1)];  // (C, -S)
+        const float2 w = s_om[((j1 * k1) & (n1 - 1)) << (6 - M1)];  // (C, -S)
         const bool out_im = n >= n1;
         const float v = pad ? 0.f : ((out_im == in_im) ? w.x : (in_im ? -w.y : w.y));
         const uint16_t hi = to_bits<F16>(v);
@@ -403,30 +427,26 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
             unsigned char *a_buf = sA + (rr & 1) * NB * A_BYTES;
 #pragma unroll
             for (int g = h; g < K / 8; g += TCR_TQ) {
-                uint16_t hv[8], lv[8];
+                float v[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const int k = 8 * g + e;
-                    float v = 0.f;
+                    v[e] = 0.f;
                     if (CPLX) {
-                        if (k < n1) v = sx[(rr * W + m + k) * 2];
-                        else if (k < 2 * n1) v = sx[(rr * W + m + k - n1) * 2 + 1];
+                        if (k < n1) v[e] = sx[(rr * W + m + k) * 2];
+                        else if (k < 2 * n1) v[e] = sx[(rr * W + m + k - n1) * 2 + 1];
                     } else if (k < n1) {
-                        v = sx[rr * W + m + k];
+                        v[e] = sx[rr * W + m + k];
                     }
-                    hv[e] = to_bits<F16>(v);
-                    lv[e] = to_bits<F16>(v - from_bits<F16>(hv[e]));
                 }
                 const uint32_t off = (uint32_t)((m >> 3) * (K / 8) + g) * 128u + (uint32_t)(m & 7) * 16u;
                 uint4 h4, l4;
-                h4.x = hv[0] | ((uint32_t)hv[1] << 16); h4.y = hv[2] | ((uint32_t)hv[3] << 16);
-                h4.z = hv[4] | ((uint32_t)hv[5] << 16); h4.w = hv[6] | ((uint32_t)hv[7] << 16);
+                split_pair<F16>(v[0], v[1], h4.x, l4.x);
+                split_pair<F16>(v[2], v[3], h4.y, l4.y);
+                split_pair<F16>(v[4], v[5], h4.z, l4.z);
+                split_pair<F16>(v[6], v[7], h4.w, l4.w);
                 *reinterpret_cast<uint4 *>(a_buf + off) = h4;
-                if (NB == 2) {
-                    l4.x = lv[0] | ((uint32_t)lv[1] << 16); l4.y = lv[2] | ((uint32_t)lv[3] << 16);
-                    l4.z = lv[4] | ((uint32_t)lv[5] << 16); l4.w = lv[6] | ((uint32_t)lv[7] << 16);
-                    *reinterpret_cast<uint4 *>(a_buf + A_BYTES + off) = l4;
-                }
+                if (NB == 2) *reinterpret_cast<uint4 *>(a_buf + A_BYTES + off) = l4;
             }
         }
         fence_proxy_async_smem();
@@ -478,22 +498,14 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
                         const int cc = c0 + 8 * g;
                         const int part = cc / n1;
                         const int64_t off = base + (cc - part * n1);
-                        uint16_t hv[8], lv[8];
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const float v = acc[8 * g + e];
-                            hv[e] = to_bits<F16>(v);
-                            lv[e] = to_bits<F16>(v - from_bits<F16>(hv[e]));
-                        }
+                        const float *v = acc + 8 * g;
                         uint4 h4, l4;
-                        h4.x = hv[0] | ((uint32_t)hv[1] << 16); h4.y = hv[2] | ((uint32_t)hv[3] << 16);
-                        h4.z = hv[4] | ((uint32_t)hv[5] << 16); h4.w = hv[6] | ((uint32_t)hv[7] << 16);
+                        split_pair<F16>(v[0], v[1], h4.x, l4.x);
+                        split_pair<F16>(v[2], v[3], h4.y, l4.y);
+                        split_pair<F16>(v[4], v[5], h4.z, l4.z);
+                        split_pair<F16>(v[6], v[7], h4.w, l4.w);
                         *reinterpret_cast<uint4 *>(p.planes + part * p.plane_elems + off) = h4;
-                        if (TERMS == 3) {
-                            l4.x = lv[0] | ((uint32_t)lv[1] << 16); l4.y = lv[2] | ((uint32_t)lv[3] << 16);
-                            l4.z = lv[4] | ((uint32_t)lv[5] << 16); l4.w = lv[6] | ((uint32_t)lv[7] << 16);
-                            *reinterpret_cast<uint4 *>(p.planes + (2 + part) * p.plane_elems + off) = l4;
-                        }
+                        if (TERMS == 3) *reinterpret_cast<uint4 *>(p.planes + (2 + part) * p.plane_elems + off) = l4;
                     }
                 }
             }
