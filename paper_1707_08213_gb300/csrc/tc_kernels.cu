@@ -414,6 +414,7 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
     const uint32_t tmem = *tmem_slot;
     const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
     const uint32_t lbo = 128u, sbo = (uint32_t)(K / 8) * 128u;  // K-major, both operands
+    const uint64_t a_desc0 = smem_desc(sA0, lbo, sbo), b_desc0 = smem_desc(sB0, lbo, sbo);
 
     const int pos = q1_0 + m;
     const int64_t nch = (int64_t)p.P1 * n1;
@@ -457,15 +458,18 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
         if (rr < nrows) {
             if (tid == 0) {
                 tc_fence_after();
-                const uint32_t a_base = sA0 + (uint32_t)((rr & 1) * NB) * A_BYTES;
+                // descriptors of the other operand tiles: the base descriptors plus the byte
+                // offset / 16 (every shared address here is below 2^18, so the 14-bit start
+                // field never carries)
+                const uint64_t a_base = a_desc0 + (uint64_t)(((rr & 1) * NB * A_BYTES) >> 4);
                 const uint32_t d_tmem = tmem + (uint32_t)((rr & 1) * N);
 #pragma unroll
                 for (int t = 0; t < TERMS; ++t) {
                     const int a_set = (t == 2) ? 1 : 0, b_set = (t == 1) ? 1 : 0;
 #pragma unroll
                     for (int ks = 0; ks < KS; ++ks)
-                        umma_f16(d_tmem, smem_desc(a_base + a_set * A_BYTES + ks * 256, lbo, sbo),
-                                 smem_desc(sB0 + b_set * B_BYTES + ks * 256, lbo, sbo), IDESC, (t | ks) != 0);
+                        umma_f16(d_tmem, a_base + (uint64_t)((a_set * A_BYTES + ks * 256) >> 4),
+                                 b_desc0 + (uint64_t)((b_set * B_BYTES + ks * 256) >> 4), IDESC, (t | ks) != 0);
                 }
                 umma_commit(&bar[rr & 1]);
             }
