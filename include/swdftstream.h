@@ -4,18 +4,21 @@
  * each push emits the windows its rows complete.
  *
  * Section 4.3 observes that with the trees innermost the 2D Tree SWDFT suits data that
- * arrive in order: with the tree T kept, a new window costs O(n0 n1).  Here the part of T
- * that is kept between pushes is level m1 of the last n0-1 rows (their row DFTs, Eq.
- * rowfswft2d's final level, "z"): a push runs the row levels on its new rows only, then the
- * column levels (Eq. colfswft2d) over the kept rows and the new ones.  Output of a push:
- * the window rows whose last row arrived in it, [q0][q1][k0][k1] complex64 as in
- * swdft2d.h (q0 counted from the first row ever pushed), scaled like swdft2d_execute.
- * Results are bit-identical to one swdft2d_execute over all rows pushed so far.
+ * arrive in order: with the tree T kept, a new window costs O(n0 n1).  Here what is kept
+ * between pushes is the last n0-1 rows: for n1 <= 32 and pushes of at most 4 n0 rows the
+ * input rows themselves (a push
+ * copies its rows after them and one launch evaluates the row levels, Eq. rowfswft2d,
+ * inside the column tiles of the column levels, Eq. colfswft2d); otherwise level m1 of
+ * those rows (their row DFTs, "z": a push runs the row levels on its new rows only, then
+ * the column levels over the kept rows and the new ones).  Output of a push: the window
+ * rows whose last row arrived in it, [q0][q1][k0][k1] complex64 as in swdft2d.h (q0
+ * counted from the first row ever pushed), scaled like swdft2d_execute.  Results are
+ * bit-identical to one swdft2d_execute over all rows pushed so far.
  *
- * Cost per push of R rows: the row levels of R rows plus the column levels of R + n0 - 1
- * z rows (O(n0 n1) per window once R >= n0; the column levels' warm-up re-evaluates n0-1
- * rows' worth of nodes per push, which is cheaper on this GPU than reading and writing the
- * column levels' own state, several times larger than the kept z rows).
+ * Cost per push of R rows: the column levels of R + n0 - 1 rows (O(n0 n1) per window once
+ * R >= n0; the column levels' warm-up re-evaluates n0-1 rows' worth of nodes per push,
+ * which is cheaper on this GPU than reading and writing the column levels' own state,
+ * several times larger than the kept rows).
  *
  * Memory: the caller owns a device state buffer of swdft2d_stream_state_size bytes
  * (256-byte aligned, no initialisation) and passes the same buffer to every push of one

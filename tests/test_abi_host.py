@@ -230,8 +230,11 @@ def test_stream_validation(nat, args, status):
 
 def test_stream_state_and_push_bookkeeping(nat):
     s = nat.StreamPlan(40, 8, 4, max_rows=5)
-    # n0/2 look-back rows + 2(n0-1) + max_rows kept rows of P1*n1 complex64
-    assert s.state_size() == (4 + 14 + 5) * 37 * 4 * 8
+    # n1 <= 32, max_rows <= 4 n0: 2(n0-1) + max_rows kept input rows of N1 float32
+    assert s.state_size() == (14 + 5) * 40 * 4
+    # otherwise: n0/2 look-back rows + 2(n0-1) + max_rows kept z rows of P1*n1 complex64
+    assert nat.StreamPlan(70, 8, 64, max_rows=5).state_size() == (4 + 14 + 5) * 7 * 64 * 8
+    assert nat.StreamPlan(40, 8, 4, max_rows=33).state_size() == (4 + 14 + 33) * 37 * 4 * 8
     # pushes of zero rows enqueue nothing and need no pointers
     assert s.push(0, 0, 0, 0, 0) == (0, 0)
     assert s.rows_seen() == 0

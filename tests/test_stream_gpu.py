@@ -1,7 +1,8 @@
 """The streaming form (include/swdftstream.h): rows pushed over time in pieces of any size;
 the window rows each push emits must be the same rows of one transform of the whole array
-(bit for bit: the same kernels evaluate the same nodes), and within 1e-5 of the FP64 oracle
-(Section 4.1 Eq. 2, per-window error / window norm)."""
+(bit for bit: the same node arithmetic, whether the kept rows are input rows (n1 <= 32 and
+pushes of at most 4 n0 rows) or z rows), and within 1e-5 of the FP64 oracle (Section 4.1 Eq. 2, per-window error /
+window norm)."""
 import numpy as np
 import pytest
 import torch
@@ -61,9 +62,11 @@ def check(sw, x, n0, n1, got, norm="unitary"):
 @pytest.mark.parametrize("N0,N1,n0,n1,cplx,pieces,max_rows", [
     (150, 77, 16, 8, False, [1, 3, 16, 5, 1, 1, 40, 7, 2, 40, 40], 40),
     (90, 64, 8, 32, True, [1] * 90, 1),                 # one row per push: many history moves
-    (70, 50, 1, 16, False, [2, 5, 9, 30, 30], 30),      # n0 = 1: no history
+    (70, 50, 1, 16, False, [2, 5, 9, 30, 30], 30),      # n0 = 1: no history (z rows kept)
     (200, 40, 64, 4, True, [10, 63, 1, 64, 64], 64),    # the longest column tree
     (41, 33, 32, 1, False, [31, 1, 9], 31),             # n1 = 1, first window after 32 rows
+    (60, 100, 8, 64, False, [1, 5, 20, 20, 14], 20),    # n1 = 64: kept rows are z rows
+    (50, 90, 16, 64, True, [1] * 50, 1),                # the same, one row per push
 ])
 def test_pieces_match_one_transform(sw, N0, N1, n0, n1, cplx, pieces, max_rows):
     x = workloads.random_array(N0 + N1 + n0, N0, N1, complex_input=cplx)
