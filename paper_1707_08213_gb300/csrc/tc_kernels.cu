@@ -304,9 +304,10 @@ __global__ void __launch_bounds__(TCC_THREADS) tc_col_kernel(const __grid_consta
 // can express -- so each row's A is written to shared memory (K-major) from the staged input
 // rows.  The epilogue writes z directly as the column pass's operand planes.
 
-constexpr int TCR_ROWS = 8;      // input rows per CTA
-constexpr int TCR_THREADS = 512;  // four threads per position (TMEM lane): A chunks and epilogue slices
-constexpr int TCR_TQ = TCR_THREADS / TC_CH;
+constexpr int TCR_ROWS = 8;  // input rows per CTA
+constexpr int TCR_TQ = 2;    // threads per position (TMEM lane): A chunks and epilogue slices
+constexpr int TCR_ISSUER = TCR_TQ * TC_CH;  // one more warp whose lane 0 issues the UMMAs
+constexpr int TCR_THREADS = TCR_ISSUER + 32;
 
 struct TcRowParams {
     const void *x;       // first input row of the band
@@ -332,8 +333,9 @@ size_t tc_row_smem_bytes(int m1, bool cplx, int terms) {
 
 // Pipelined over the CTA's rows: while the tensor core multiplies row r (A buffer and TMEM
 // accumulator r mod 2), the threads write row r-1's epilogue and build row r+1's A.  Thread
-// (m, h), h < 4: position m = TMEM lane; it builds A chunks g = h mod 4 and stores slice h of
-// D's 2 n1 columns (slices of max(16, n1/2) columns: Re k1 then Im k1).
+// (m, h), h < TCR_TQ: position m = TMEM lane; it builds A chunks g = h mod TCR_TQ and stores
+// slice h of D's 2 n1 columns (slices of max(16, 2 n1 / TCR_TQ) columns: Re k1 then Im k1).
+// A last warp issues the UMMAs, so that issuing them is off the other threads' path.
 template <int M1, bool CPLX, int TERMS, bool F16>
 __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_constant__ TcRowParams p) {
     constexpr int n1 = 1 << M1;
@@ -345,8 +347,8 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
     constexpr uint32_t TMEM_COLS = 2 * N < 32 ? 32 : 2 * N;  // two accumulators
     constexpr uint32_t B_BYTES = N * K * 2, A_BYTES = TC_CH * K * 2;
     constexpr uint32_t IDESC = umma_idesc_f16(TC_CH, N, !F16, /*a_mn=*/false, /*b_mn=*/false);
-    constexpr int SW = N / 4 < 16 ? 16 : N / 4;  // D columns per epilogue slice (tcgen05.ld x16)
-    constexpr int NSL = N / SW;                   // slices: 1 (n1 = 8), 2 (n1 = 16) or 4
+    constexpr int SW = N / TCR_TQ < 16 ? 16 : N / TCR_TQ;  // D columns per epilogue slice
+    constexpr int NSL = N / SW;                             // slices: 1 (n1 = 8) or TCR_TQ
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -358,7 +360,8 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int m = tid & (TC_CH - 1);  // this thread's position in the tile = its TMEM lane
-    const int h = tid >> 7;           // 0 .. TCR_TQ - 1
+    const int h = tid >> 7;           // 0 .. TCR_TQ - 1; TCR_TQ for the issuing warp
+    const bool worker = h < TCR_TQ;
     const int q1_0 = blockIdx.x * TC_CH;
     const int r0 = blockIdx.y * TCR_ROWS;
     if (r0 >= p.zrows) return;  // uniform per block
@@ -421,7 +424,7 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
     bool ok = true, done = true;
     int issued = 0;  // rows whose UMMAs were committed
     for (int rr = 0; rr <= nrows; ++rr) {
-        if (rr < nrows) {
+        if (rr < nrows && worker) {
             // A row m of buffer rr & 1: x[pos + k] (Re, then Im), this thread's half of the
             // 16-byte chunks.  The buffer's last reader, row rr - 2's UMMAs, completed: every
             // thread waited for them in row rr - 2's epilogue.
@@ -456,7 +459,7 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
         ok = __syncthreads_and(done);
         if (!ok) break;  // block-uniform
         if (rr < nrows) {
-            if (tid == 0) {
+            if (tid == TCR_ISSUER) {
                 tc_fence_after();
                 // descriptors of the other operand tiles: the base descriptors plus the byte
                 // offset / 16 (every shared address here is below 2^18, so the 14-bit start
@@ -475,7 +478,7 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
             }
             issued = rr + 1;
         }
-        if (rr >= 1) {
+        if (rr >= 1 && worker) {
             // epilogue of row e = rr - 1: its D is accumulator e mod 2, barrier e mod 2 in its
             // (e / 2)-th phase
             const int er = rr - 1;
