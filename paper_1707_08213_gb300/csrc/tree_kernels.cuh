@@ -278,9 +278,13 @@ __device__ __forceinline__ void col_tile(const ColGeom &p, int64_t ch_block, int
     col_tile_impl<M, B>(p, ch_block, chunk_idx, om64, ring, stage, slice);
 }
 
-// grid: x = 32-channel groups, y = chunks of window rows, z = slices (kD passes; 1 in 2D)
+// grid: x = 32-channel groups, y = chunks of window rows, z = slices (kD passes; 1 in 2D).
+// Two resident 256-thread blocks per SM cap a thread at 128 registers; the 64-point tree
+// (M = 6) needs about 150 and spilled under that cap, so it asks for one block (the pass
+// alone measured 5-6% faster on 512x512 and 1024x1024 with 64x16 windows).  The fused
+// kernel keeps two blocks: with one, 1024x1024 with 64x16 windows went from 1.37 to 1.56 ms.
 template <int M, int B>
-__global__ void __launch_bounds__(256, 2) col_tree_kernel(const __grid_constant__ ColParams p) {
+__global__ void __launch_bounds__(256, (M >= 6 ? 1 : 2)) col_tree_kernel(const __grid_constant__ ColParams p) {
     extern __shared__ float2 ring[];  // col_ring_rows(M) x (32 * groups)
     col_tile<M, B>(p.g, blockIdx.x, blockIdx.y, p.om.w, ring, blockIdx.z);
 }
