@@ -149,7 +149,9 @@ swdft_status swdft2d_execute_host(swdft2d_plan_t plan, const void *const *h_in,
 
 /* Time every candidate kernel configuration of this plan on the given buffers (CUDA
  * events on `stream`) and keep the fastest; the choice is reused by later executes and
- * recorded in the cache file named by the SWDFT_TUNE_CACHE environment variable, if set. */
+ * recorded in the cache file named by the SWDFT_TUNE_CACHE environment variable, if set.
+ * Arrays of the same shape, band and algorithm setting are timed once (the first of them)
+ * and share its choice. */
 swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out,
                               void *d_workspace, void *stream);
 
