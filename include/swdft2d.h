@@ -90,7 +90,9 @@ typedef enum {
 enum {
     SWDFT_FLAG_GRAPH = 1u,    /* capture each execute's launch sequence in a CUDA graph, replay after */
     SWDFT_FLAG_HOST_IO = 2u,  /* plan owns device staging so swdft2d_execute_host can run */
-    SWDFT_FLAG_PERSISTENT = 4u /* batch: one persistent launch over all (image, tile) items */
+    SWDFT_FLAG_PERSISTENT = 4u, /* batch: one persistent launch over all (image, tile) items */
+    SWDFT_FLAG_AUTOTUNE = 8u    /* the first swdft2d_execute runs swdft2d_autotune on its own
+                                 * buffers first (blocking; skipped if its stream is capturing) */
 };
 
 /* One array of a batch.  row_begin/row_end select a band of output window rows in the

@@ -20,11 +20,11 @@ from typing import Dict, Sequence, Tuple
 import torch
 
 from . import _native
-from ._native import (ALGOS, C64, FLAG_GRAPH, FLAG_HOST_IO, FLAG_PERSISTENT, NORMS, R32, Plan,
+from ._native import (ALGOS, C64, FLAG_AUTOTUNE, FLAG_GRAPH, FLAG_HOST_IO, FLAG_PERSISTENT, NORMS, R32, Plan,
                       PlanKD, StreamPlan, SwdftError, status_string, version)
 
 __all__ = ["swdft2d", "swdft2d_adjoint", "Transform", "Plan", "SwdftError", "SWDFT2dFunction",
-           "status_string", "version", "FLAG_GRAPH", "FLAG_HOST_IO", "FLAG_PERSISTENT",
+           "status_string", "version", "FLAG_AUTOTUNE", "FLAG_GRAPH", "FLAG_HOST_IO", "FLAG_PERSISTENT",
            "TransformKD", "PlanKD", "swdftkd", "SlidingStream", "StreamPlan"]
 
 

@@ -30,7 +30,7 @@ NORMS = {"unitary": 0, "none": 1, "inv_n": 2}
 POS = {"start": 0, "end": 1}
 ALGOS = {"auto": 0, "tree": 1, "tc_bf16x3": 2, "tc_bf16": 3, "tc_f16_scaled": 4, "tc_f16": 5}
 ALGO_NAMES = {v: k for k, v in ALGOS.items()}
-FLAG_GRAPH, FLAG_HOST_IO, FLAG_PERSISTENT = 1, 2, 4
+FLAG_GRAPH, FLAG_HOST_IO, FLAG_PERSISTENT, FLAG_AUTOTUNE = 1, 2, 4, 8
 
 # every symbol include/*.h declare
 EXPORTS = (

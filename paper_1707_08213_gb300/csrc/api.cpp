@@ -128,6 +128,7 @@ struct swdft2d_plan_s {
     float2 om64[kMaxN];
     float2 om27[kMaxN3];  // Omega of length 27 for ternary trees (3, 9 and 27 are its strided views)
     bool configured = false;
+    bool autotuned = false;  // SWDFT_FLAG_AUTOTUNE: the first execute has tuned the plan
     int sm_count = 152;
     GraphCache graph;
     // several arrays (not persistent): up to kConc of them run concurrently on plan-owned
@@ -673,7 +674,7 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
     if (norm < SWDFT_NORM_UNITARY || norm > SWDFT_NORM_INV_N) return SWDFT_ERR_INVALID_ARG;
     if (pos != SWDFT_POS_START && pos != SWDFT_POS_END) return SWDFT_ERR_INVALID_ARG;
     if (algo < SWDFT_ALGO_AUTO || algo > SWDFT_ALGO_TC_F16) return SWDFT_ERR_INVALID_ARG;
-    if (flags & ~(uint32_t)(SWDFT_FLAG_GRAPH | SWDFT_FLAG_HOST_IO | SWDFT_FLAG_PERSISTENT))
+    if (flags & ~(uint32_t)(SWDFT_FLAG_GRAPH | SWDFT_FLAG_HOST_IO | SWDFT_FLAG_PERSISTENT | SWDFT_FLAG_AUTOTUNE))
         return SWDFT_ERR_INVALID_ARG;
 
     std::vector<ArrayPlan> arrays((size_t)batch);
@@ -838,6 +839,16 @@ swdft_status swdft2d_execute(swdft2d_plan_t plan, const void *const *d_in, void 
     if (st != SWDFT_OK) return st;
     if ((st = configure(plan)) != SWDFT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((plan->flags & SWDFT_FLAG_AUTOTUNE) && !plan->autotuned) {
+        // tune on this execute's buffers first (the timing runs synchronise, so not while the
+        // stream is being captured into a graph)
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return SWDFT_ERR_CUDA;
+        if (cs == cudaStreamCaptureStatusNone) {
+            if ((st = swdft2d_autotune(plan, d_in, d_out, d_workspace, stream)) != SWDFT_OK) return st;
+            plan->autotuned = true;
+        }
+    }
     const bool persistent = (plan->flags & SWDFT_FLAG_PERSISTENT) != 0;
     if (!(plan->flags & SWDFT_FLAG_GRAPH) || s == nullptr)
         return persistent ? enqueue_batch(plan, d_in, d_out, d_workspace, s)

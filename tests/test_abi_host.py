@@ -94,6 +94,9 @@ def test_plan_validation_enums(nat):
     assert nat.raw_plan(good, 0, 2, 1, 0)[0] == -1      # position convention
     assert nat.raw_plan(good, 0, 0, 9, 0)[0] == -1      # algorithm
     assert nat.raw_plan(good, 0, 0, 1, 1 << 9)[0] == -1  # unknown flag
+    st, h = nat.raw_plan(good, 0, 0, 1, nat.FLAG_AUTOTUNE | nat.FLAG_GRAPH)  # tune on first execute
+    assert st == 0
+    nat.lib.swdft2d_destroy(h)
     assert nat.raw_plan([], 0, 0, 1, 0)[0] == -1          # empty batch
     st = nat.lib.swdft2d_plan(None, 1, None, 0, 0, 1, 0)
     assert st == -1

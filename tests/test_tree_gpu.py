@@ -230,6 +230,23 @@ def test_fused_tree_matches_oracle_and_two_pass(sw, N0, N1, n0, n1, cplx, chunk)
     assert_close_to_oracle(fused, x, n0, n1)
 
 
+def test_autotune_flag_tunes_on_the_first_execute(sw, tmp_path, monkeypatch):
+    """SWDFT_FLAG_AUTOTUNE: the first forward tunes the plan (one tuning record), later
+    forwards reuse the choice; results match the oracle throughout."""
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("SWDFT_TUNE_CACHE", str(cache))
+    x = workloads.random_array(650, 90, 120)
+    xd = torch.from_numpy(x).cuda()
+    t = sw.Transform([(90, 120, 16, 32, 0)], algo="auto", flags=sw.FLAG_AUTOTUNE | sw.FLAG_GRAPH)
+    assert not cache.exists()
+    a = t.forward([xd])[0]
+    b = t.forward([xd])[0]
+    torch.cuda.synchronize()
+    assert len(cache.read_text().strip().splitlines()) == 1
+    assert torch.equal(a, b)
+    assert_close_to_oracle(b, x, 16, 32)
+
+
 def test_autotune_times_each_shape_once(sw, tmp_path, monkeypatch):
     """A batch with repeated shapes: the autotuner times each distinct shape once and gives
     the repeats the same choice; every array still matches the oracle."""
