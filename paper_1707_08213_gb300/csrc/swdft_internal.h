@@ -255,8 +255,6 @@ cudaError_t launch_row_tree3(const Row3Args &a, cudaStream_t s);
 cudaError_t launch_col_tree3(const Col3Args &a, cudaStream_t s);
 
 cudaError_t launch_adj_col(const AdjColArgs &a, cudaStream_t s);
-// log2 of the threads adj_row splits one row's transposed tree over, for n1 = 2^m1
-int adj_row_split(int m1);
 cudaError_t launch_adj_row(const AdjRowArgs &a, cudaStream_t s);
 
 }  // namespace swdft
