@@ -1,7 +1,9 @@
 """Shapes at the edges of what the kernels take, against the FP64 oracle (Section 4.1, Eq. 2;
 per-window error / window norm <= 1e-5): a 2^20-sample row and a 2^20-row column with
 64-point windows (grid limits, 64-bit offsets), the largest windows (64 x 64), arrays that
-hold exactly one window, windows of one sample, and a persistent batch of many tiny arrays."""
+hold exactly one window, windows of one sample, a persistent batch of many tiny arrays, and
+the adjoint (per-pixel error / pixel norm <= 1e-5) on a 2^20-sample row and a 2^17-row
+column."""
 import numpy as np
 import pytest
 import torch
@@ -102,3 +104,32 @@ def test_persistent_batch_of_many_tiny_arrays(sw):
         ref = oracle.swdft2d(x, n0, n1, method="direct")
         err, _ = workloads.normalised_error(o.cpu().numpy(), ref, workloads.window_sq_norms(x, n0, n1))
         assert err <= TOL
+
+
+def _adjoint_sampled(sw, N0, N1, n0, n1, cplx, count, seed):
+    P0, P1 = N0 - n0 + 1, N1 - n1 + 1
+    rng = np.random.default_rng(seed)
+    G = (rng.standard_normal((P0, P1, n0, n1), dtype=np.float32)
+         + 1j * rng.standard_normal((P0, P1, n0, n1), dtype=np.float32)).astype(np.complex64)
+    t = sw.Transform([(N0, N1, n0, n1, int(cplx))])
+    g = t.adjoint([torch.from_numpy(G).cuda()])[0]
+    torch.cuda.synchronize()
+    rs = np.concatenate([rng.integers(0, N0, count), [0, N0 - 1, 0, N0 - 1]])
+    cs = np.concatenate([rng.integers(0, N1, count), [0, 0, N1 - 1, N1 - 1]])
+    got = g[torch.from_numpy(rs).cuda(), torch.from_numpy(cs).cuda()].cpu().numpy()
+    ref = oracle.swdft2d_adjoint_pixels(G, N0, N1, rs, cs, threads=8)
+    if not cplx:
+        ref = ref.real
+    norms = workloads.adjoint_pixel_norms(G, N0, N1)[rs, cs]
+    err = workloads.adjoint_error(got, ref, norms)
+    assert err <= TOL, f"adjoint {N0}x{N1} {n0}x{n1}: {err:.3e}"
+    del g
+    torch.cuda.empty_cache()
+
+
+def test_adjoint_long_row(sw):
+    _adjoint_sampled(sw, 1, 1 << 20, 1, 64, False, 4096, 11)
+
+
+def test_adjoint_tall_column(sw):
+    _adjoint_sampled(sw, 1 << 17, 8, 64, 8, True, 4096, 12)
