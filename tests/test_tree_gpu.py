@@ -212,6 +212,33 @@ def test_complex_1024x2048_full_size(sw):
     _full_size_check(sw, wl.images[0], 16, 64, count=2048, seed=12)
 
 
+def test_sinusoids_512_every_coefficient_tree_and_split_bf16(sw):
+    """The 512x512 / 32x32 workload in full: all 236,913,664 coefficients of the FP32 tree
+    and of the split-bf16 tensor-core form against the FP64 oracle (row-column form, in
+    bands of window rows), per-window error / window norm <= 1e-5 for both."""
+    wl = workloads.sinusoids_512()
+    x = wl.images[0]
+    n0 = n1 = 32
+    P0 = x.shape[0] - n0 + 1
+    xd = torch.from_numpy(x).cuda()
+    outs = {algo: sw.Transform([(512, 512, n0, n1, 0)], algo=algo).forward([xd])[0]
+            for algo in ("tree", "tc_bf16x3")}
+    torch.cuda.synchronize()
+    assert sw._native.check_device() == 0
+    sq = workloads.window_sq_norms(x, n0, n1)
+    worst = {algo: 0.0 for algo in outs}
+    band = 32
+    for r in range(0, P0, band):
+        rows = min(band, P0 - r)
+        ref = oracle.swdft2d(x[r:r + rows + n0 - 1], n0, n1, method="separable", threads=ORACLE_THREADS)
+        for algo, a in outs.items():
+            err, _ = workloads.normalised_error(a[r:r + rows].cpu().numpy(), ref, sq[r:r + rows])
+            worst[algo] = max(worst[algo], err)
+    assert worst["tree"] <= TOL and worst["tc_bf16x3"] <= TOL, worst
+    del outs
+    torch.cuda.empty_cache()
+
+
 FUSED_SHAPES = [(41, 67, 8, 16, False), (61, 35, 32, 4, True), (90, 75, 64, 8, False),
                 (70, 100, 16, 32, True), (100, 100, 32, 32, False), (23, 50, 1, 32, False),
                 (50, 23, 32, 1, True), (9, 9, 8, 8, False)]
