@@ -242,21 +242,30 @@ swdft_status configure(swdft2d_plan_t plan) {
     plan->sm_count = sms > 0 ? sms : 152;
     for (auto &a : plan->arrays)
         if (!a.tuned) default_config(a, plan->sm_count, plan->conc);
+    // every object below is created once: a configure that failed part way (out of memory)
+    // keeps what it made, the plan's destroy frees it, and the next call resumes
     if (plan->conc > 1) {
-        if (cudaEventCreateWithFlags(&plan->fork_ev, cudaEventDisableTiming) != cudaSuccess) return SWDFT_ERR_CUDA;
+        if (!plan->fork_ev && cudaEventCreateWithFlags(&plan->fork_ev, cudaEventDisableTiming) != cudaSuccess)
+            return SWDFT_ERR_CUDA;
         for (int k = 0; k < plan->conc; ++k) {
-            if (cudaStreamCreateWithFlags(&plan->side[k], cudaStreamNonBlocking) != cudaSuccess) return SWDFT_ERR_CUDA;
-            if (cudaEventCreateWithFlags(&plan->join_ev[k], cudaEventDisableTiming) != cudaSuccess) return SWDFT_ERR_CUDA;
+            if (!plan->side[k] && cudaStreamCreateWithFlags(&plan->side[k], cudaStreamNonBlocking) != cudaSuccess)
+                return SWDFT_ERR_CUDA;
+            if (!plan->join_ev[k] && cudaEventCreateWithFlags(&plan->join_ev[k], cudaEventDisableTiming) != cudaSuccess)
+                return SWDFT_ERR_CUDA;
         }
     }
     if (plan->flags & SWDFT_FLAG_PERSISTENT) {
         const size_t n = plan->arrays.size();
         plan->desc_bytes = sizeof(BatchImage) * n + 3 * sizeof(BatchClassEntry) * n;
-        if (cudaHostAlloc((void **)&plan->desc_host, plan->desc_bytes, cudaHostAllocDefault) != cudaSuccess)
+        if (!plan->desc_host &&
+            cudaHostAlloc((void **)&plan->desc_host, plan->desc_bytes, cudaHostAllocDefault) != cudaSuccess)
             return SWDFT_ERR_OOM;
-        if (cudaMalloc((void **)&plan->desc_dev, plan->desc_bytes) != cudaSuccess) return SWDFT_ERR_OOM;
-        if (cudaMalloc((void **)&plan->desc_graph, plan->desc_bytes) != cudaSuccess) return SWDFT_ERR_OOM;
-        if (cudaEventCreateWithFlags(&plan->desc_uploaded, cudaEventDisableTiming) != cudaSuccess) return SWDFT_ERR_CUDA;
+        if (!plan->desc_dev && cudaMalloc((void **)&plan->desc_dev, plan->desc_bytes) != cudaSuccess)
+            return SWDFT_ERR_OOM;
+        if (!plan->desc_graph && cudaMalloc((void **)&plan->desc_graph, plan->desc_bytes) != cudaSuccess)
+            return SWDFT_ERR_OOM;
+        if (!plan->desc_uploaded && cudaEventCreateWithFlags(&plan->desc_uploaded, cudaEventDisableTiming) != cudaSuccess)
+            return SWDFT_ERR_CUDA;
         for (int m = 0; m <= kMaxLog2; ++m) {
             int row_bps = 0, col_bps = 0;
             if (batch_blocks_per_sm(m, &row_bps, &col_bps) != cudaSuccess) return SWDFT_ERR_CUDA;
@@ -273,8 +282,10 @@ swdft_status configure(swdft2d_plan_t plan) {
                 plan->fz_slots[f] = (int64_t)plan->sm_count * std::max(1, bps);
             }
             for (int k = 0; k < plan->conc; ++k) {
-                if (cudaStreamCreateWithFlags(&plan->fside[k], cudaStreamNonBlocking) != cudaSuccess) return SWDFT_ERR_CUDA;
-                if (cudaEventCreateWithFlags(&plan->fjoin_ev[k], cudaEventDisableTiming) != cudaSuccess) return SWDFT_ERR_CUDA;
+                if (!plan->fside[k] && cudaStreamCreateWithFlags(&plan->fside[k], cudaStreamNonBlocking) != cudaSuccess)
+                    return SWDFT_ERR_CUDA;
+                if (!plan->fjoin_ev[k] && cudaEventCreateWithFlags(&plan->fjoin_ev[k], cudaEventDisableTiming) != cudaSuccess)
+                    return SWDFT_ERR_CUDA;
             }
         }
     }
@@ -1035,14 +1046,18 @@ swdft_status swdft2d_execute_host(swdft2d_plan_t plan, const void *const *h_in,
             out_max = std::max(out_max, align_up((size_t)br * a.out_row_bytes()));
             ws_max = std::max(ws_max, align_up(a.ws_bytes_plan(br)));
         }
-        if (cudaMalloc(&plan->io_in, in_max) != cudaSuccess) return SWDFT_ERR_OOM;
-        if (cudaMalloc(&plan->io_ws, ws_max) != cudaSuccess) return SWDFT_ERR_OOM;
+        // created once, as in configure: a failed attempt keeps what it made for the next
+        if (!plan->io_in && cudaMalloc(&plan->io_in, in_max) != cudaSuccess) return SWDFT_ERR_OOM;
+        if (!plan->io_ws && cudaMalloc(&plan->io_ws, ws_max) != cudaSuccess) return SWDFT_ERR_OOM;
         for (int k = 0; k < 2; ++k)
-            if (cudaMalloc(&plan->io_out[k], out_max) != cudaSuccess) return SWDFT_ERR_OOM;
-        if (cudaStreamCreateWithFlags(&plan->io_copy, cudaStreamNonBlocking) != cudaSuccess) return SWDFT_ERR_CUDA;
+            if (!plan->io_out[k] && cudaMalloc(&plan->io_out[k], out_max) != cudaSuccess) return SWDFT_ERR_OOM;
+        if (!plan->io_copy && cudaStreamCreateWithFlags(&plan->io_copy, cudaStreamNonBlocking) != cudaSuccess)
+            return SWDFT_ERR_CUDA;
         for (int k = 0; k < 2; ++k) {
-            if (cudaEventCreateWithFlags(&plan->io_done[k], cudaEventDisableTiming) != cudaSuccess) return SWDFT_ERR_CUDA;
-            if (cudaEventCreateWithFlags(&plan->io_copied[k], cudaEventDisableTiming) != cudaSuccess) return SWDFT_ERR_CUDA;
+            if (!plan->io_done[k] && cudaEventCreateWithFlags(&plan->io_done[k], cudaEventDisableTiming) != cudaSuccess)
+                return SWDFT_ERR_CUDA;
+            if (!plan->io_copied[k] && cudaEventCreateWithFlags(&plan->io_copied[k], cudaEventDisableTiming) != cudaSuccess)
+                return SWDFT_ERR_CUDA;
         }
         plan->io_band = band;
         plan->io_ready = true;
@@ -1241,16 +1256,15 @@ swdft_status swdft2d_destroy(swdft2d_plan_t plan) {
     if (plan->fork_ev) cudaEventDestroy(plan->fork_ev);
     if (plan->desc_dev) cudaFree(plan->desc_dev);
     if (plan->desc_graph) cudaFree(plan->desc_graph);
-    if (plan->io_ready) {
-        cudaFree(plan->io_in);
-        cudaFree(plan->io_ws);
-        for (int k = 0; k < 2; ++k) {
-            cudaFree(plan->io_out[k]);
-            if (plan->io_done[k]) cudaEventDestroy(plan->io_done[k]);
-            if (plan->io_copied[k]) cudaEventDestroy(plan->io_copied[k]);
-        }
-        if (plan->io_copy) cudaStreamDestroy(plan->io_copy);
+    // host-buffer staging, including what a set-up that ran out of memory left behind
+    if (plan->io_in) cudaFree(plan->io_in);
+    if (plan->io_ws) cudaFree(plan->io_ws);
+    for (int k = 0; k < 2; ++k) {
+        if (plan->io_out[k]) cudaFree(plan->io_out[k]);
+        if (plan->io_done[k]) cudaEventDestroy(plan->io_done[k]);
+        if (plan->io_copied[k]) cudaEventDestroy(plan->io_copied[k]);
     }
+    if (plan->io_copy) cudaStreamDestroy(plan->io_copy);
     delete plan;
     return SWDFT_OK;
 }
