@@ -4,8 +4,8 @@
  * The operation (Richardson & Eddy, "The 2D Tree Sliding Window Discrete Fourier
  * Transform", arXiv 1707.08213):
  *
- *   Section 4.1, Eq. (2): for an N0 x N1 array x and n0 x n1 windows (n_i = 2^m_i,
- *   n_i <= N_i), every window position gets its 2D DFT
+ *   Section 4.1, Eq. (2): for an N0 x N1 array x and n0 x n1 windows (n_i = 2^m_i <= 64,
+ *   or 3^m_i <= 27 with ternary trees; n_i <= N_i), every window position gets its 2D DFT
  *
  *     a[q0,q1,k0,k1] = c * sum_{j0<n0} sum_{j1<n1} x[q0+j0, q1+j1] w_{n0}^{-j0 k0} w_{n1}^{-j1 k1}
  *
@@ -56,7 +56,8 @@ typedef struct swdft2d_plan_s *swdft2d_plan_t; /* opaque, library-owned */
 typedef enum {
     SWDFT_OK = 0,
     SWDFT_ERR_INVALID_ARG = -1,       /* null pointer, bad enum, negative size, bad band */
-    SWDFT_ERR_NOT_POW2 = -2,          /* n0 or n1 is not a power of two (radix-2 only, Sec. 4.2) */
+    SWDFT_ERR_NOT_POW2 = -2,          /* n0 or n1 is neither a power of two (Sec. 4.2's radix-2
+                                       * tree) nor a power of three (ternary trees) */
     SWDFT_ERR_WINDOW_TOO_LARGE = -3,  /* n_i > N_i: no window position exists */
     SWDFT_ERR_UNSUPPORTED = -4,       /* valid request this build does not implement */
     SWDFT_ERR_OOM = -5,               /* host or device allocation of plan-owned memory failed */
