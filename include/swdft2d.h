@@ -102,7 +102,8 @@ enum {
 typedef struct {
     int64_t N0, N1;  /* array rows and columns, >= 1 */
     int64_t ld;      /* input row stride in elements, >= N1; 0 means N1 */
-    int32_t n0, n1;  /* window rows and columns: powers of two, 1 <= n_i <= N_i */
+    int32_t n0, n1;  /* window rows and columns: powers of two (<= 64) or of three (<= 27),
+                      * 1 <= n_i <= N_i; a ternary n1 needs a ternary (or 1) n0 */
     int32_t dtype;   /* swdft_dtype of the input */
     int32_t reserved;
     int64_t row_begin, row_end;
@@ -112,8 +113,9 @@ typedef struct {
  * validates every shape (SWDFT_ERR_NOT_POW2 / WINDOW_TOO_LARGE / INVALID_ARG), builds the
  * twiddle vectors Omega^0, Omega^1 of Section 4.2 in FP64 and rounds them to FP32, and
  * picks kernels.  SWDFT_ERR_UNSUPPORTED for an algorithm or window size this build lacks
- * (tree: n_i <= 64; tensor-core forms: 16 <= n0 <= 64, 8 <= n1 <= 64, no persistent batch).
- * *plan is NULL on any error. */
+ * (tree: n_i <= 64, or 3, 9, 27; tensor-core forms: powers of two with 16 <= n0 <= 64 and
+ * 8 <= n1 <= 64, no persistent batch; ternary windows: tree only, no persistent batch, no
+ * adjoint).  *plan is NULL on any error. */
 swdft_status swdft2d_plan(swdft2d_plan_t *plan, int32_t batch, const swdft2d_shape *shapes,
                           int32_t norm, int32_t pos, int32_t algo, uint32_t flags);
 
