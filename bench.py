@@ -60,6 +60,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="seconds of oracle work the reference arm spends (warm-up + timed steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the side measurements (tensor-core forms, batch, adjoint, volume, stream, Fig. 4 shapes, radix 3, complex and small workloads)")
@@ -238,7 +240,7 @@ def run_reference(args):
     t0 = time.perf_counter()
     oracle.swdft2d_windows(x, n0, n1, [0] * 32, [0] * 32)
     per = (time.perf_counter() - t0) / 32
-    budget = 150.0  # seconds of oracle work for warm-up + timed steps together
+    budget = args.ref_seconds  # seconds of oracle work for warm-up + timed steps together
     per_step = max(1, int(budget / max(1, args.steps + args.warmup) / max(per, 1e-9)))
     rng = np.random.default_rng(0)
     for _ in range(args.warmup):
