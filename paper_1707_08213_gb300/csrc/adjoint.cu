@@ -38,7 +38,6 @@ int adj_col_launches(int64_t rows_out, int m0, int64_t requested) {
     return rows_out > 0 && adj_side_elems(rows_out, m0, 1, 0, requested) > 0 ? 2 : 1;
 }
 
-
 cudaError_t launch_adj_col(const AdjColArgs &a, cudaStream_t s) {
     const int64_t nch = a.P1 << a.m1;
     const int64_t zrows = a.rows_out + (int64_t(1) << a.m0) - 1;
