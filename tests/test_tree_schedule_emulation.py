@@ -3,10 +3,11 @@
 The sliding tree of Section 4.2 along one axis runs on the GPU as a walk over window-end
 positions p in which every level keeps a FIFO of the values it needs again s_v steps later,
 optionally split over 2^B threads by node residue (tree_core.cuh, SlidingTree), and its
-transpose walks p downwards (adjoint_core.cuh, SlidingTreeAdjoint).  These tests replay
+transpose walks p downwards (adjoint_core.cuh, SlidingTreeAdjoint); the ternary tree of
+windows 3^M splits by residue mod 3 (tree3_core.cuh, SlidingTree3Split).  These tests replay
 exactly those schedules -- the same FIFO depths, slot indices (step index modulo the FIFO
 depth), node residues and twiddle indices -- in plain Python for every window length
-2^M <= 64 and split B <= min(M, 3), and compare with numpy's FFT of every window (forward)
+2^M <= 64 and split B <= min(M, 3) (and 3^M <= 27), and compare with numpy's FFT of every window (forward)
 and with the explicit overlap-add of every window's inverse DFT (adjoint).  They pin the
 index arithmetic of the kernels' register schedules without a GPU.
 """
@@ -135,3 +136,57 @@ def test_adjoint_schedule_gives_the_overlap_add_of_inverse_dfts(M, B):
         ref[q:q + n] += np.fft.ifft(G[q]) * n  # sum_k G[q][k] w^{+jk}
     y = sum(adjoint_walk(M, B, c, G, N) for c in range(1 << B))
     np.testing.assert_allclose(y, ref, atol=1e-9)
+
+
+def ternary_walk(M, c, x):
+    """Thread c (< 3) of the ternary tree split by residue mod 3 (tree3_core.cuh): its
+    level-M nodes c + 3u, u < 3^(M-1), at every position p."""
+    n = 3 ** M
+    w27 = np.exp(-2j * np.pi * np.arange(27) / 27)
+    s1 = 3 ** (M - 1)
+
+    def held_t(t):  # level-t nodes one thread holds
+        return 1 if t <= 1 else 3 ** (t - 1)
+
+    tw = {t: [(w27[(ip * (27 // 3 ** t)) % 27], w27[(2 * ip * (27 // 3 ** t)) % 27])
+              for ip in (c + 3 * a for a in range(3 ** (t - 2)))] for t in range(2, M + 1)}
+    # level t-1 is read s_t and 2 s_t steps back: a FIFO of 2 s_t slots
+    fifos = {t: [[0j] * held_t(t - 1) for _ in range(2 * 3 ** (M - t))] for t in range(2, M + 1)}
+    period = 2 * 3 ** (M - 2) if M >= 2 else 1
+    w3 = np.exp(-2j * np.pi / 3)
+    outs = []
+    for j, p in enumerate(range(len(x))):
+        J = j % period
+        xs1 = x[p - s1] if p - s1 >= 0 else 0j
+        xs2 = x[p - 2 * s1] if p - 2 * s1 >= 0 else 0j
+        cur = [xs2 + w3 ** c * xs1 + w3 ** (2 * c) * x[p]]  # level 1, node c
+        for t in range(2, M + 1):
+            s = 3 ** (M - t)
+            D = 2 * s
+            hp = held_t(t - 1)
+            nxt = [0j] * (3 * hp)
+            for a in range(hp):
+                a2 = cur[a]
+                a1 = fifos[t][(J + s) % D][a]
+                a0 = fifos[t][J % D][a]
+                fifos[t][J % D][a] = a2
+                b1 = tw[t][a][0] * a1
+                b2 = tw[t][a][1] * a2
+                for k in range(3):
+                    nxt[a + k * hp] = a0 + w3 ** k * b1 + w3 ** (2 * k) * b2
+            cur = nxt
+        outs.append(cur)
+    return outs
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_ternary_schedule_gives_every_windows_dft(M):
+    n = 3 ** M
+    rng = np.random.default_rng(500 + M)
+    x = rng.standard_normal(n + 17) + 1j * rng.standard_normal(n + 17)
+    for c in range(3):
+        outs = ternary_walk(M, c, x)
+        ks = [c + 3 * u for u in range(3 ** (M - 1))]
+        for p in range(n - 1, len(x)):
+            ref = np.fft.fft(x[p - n + 1:p + 1])
+            np.testing.assert_allclose(outs[p], ref[ks], atol=1e-9)
