@@ -168,6 +168,32 @@ def gpu_id_for(torch, dev):
 
 # ----------------------------------------------------------------------- CPU baselines
 
+def host_info():
+    """The host the CPU figures ran on: logical cores, CPU model and machine."""
+    import platform
+    info = {"nproc": os.cpu_count(), "machine": platform.machine()}
+    try:
+        fields = {}
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k, _, v = ln.partition(":")
+                k, v = k.strip(), v.strip()
+                if k and v and k not in fields:
+                    fields[k] = v
+        model = fields.get("model name") or fields.get("Model name")
+        if not model and "CPU implementer" in fields:  # Arm: implementer / part numbers
+            model = f"implementer {fields['CPU implementer']} part {fields.get('CPU part', '?')}"
+        if model:
+            info["cpu_model"] = model
+    except OSError:
+        pass
+    try:
+        info["affinity"] = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        pass
+    return info
+
+
 def oracle_sample(x, seconds, seed=0):
     """Time the FP64 oracle (row-column form, 1 thread) on random windows for ~seconds."""
     import numpy as np
@@ -184,7 +210,8 @@ def oracle_sample(x, seconds, seed=0):
     dt = time.perf_counter() - t0
     return {"value": count * n0 * n1 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{count} random windows of the 512x512/32x32 workload "
-                      f"(FP64 row-column sum, 1 thread), {dt:.1f} s"}, (q0, q1, ref)
+                      f"(FP64 row-column sum, 1 thread), {dt:.1f} s",
+            "host": host_info()}, (q0, q1, ref)
 
 
 def oracle_small():
@@ -222,8 +249,9 @@ def cpu_tree_sample(x, rows=96):
     oracle.tree2d(band, n0, n1, precision="f32", threads=cores)
     dt = time.perf_counter() - t0
     return {"value": rows * P1 * n0 * n1 / dt, "unit": UNIT, "cores": cores,
-            "kind": "paper tree, FP32, OpenMP",
-            "sample": f"output rows 0..{rows - 1} ({rows}x{P1} windows), {dt:.2f} s"}
+            "kind": "paper tree, FP32, OpenMP", "threads": cores,
+            "sample": f"output rows 0..{rows - 1} ({rows}x{P1} windows), {dt:.2f} s",
+            "host": host_info()}
 
 
 # ----------------------------------------------------------------------- reference arm
@@ -259,7 +287,7 @@ def run_reference(args):
             "config": config_dict({"reference": "FP64 CPU oracle (direct definition, Eq. 2, "
                                                 "row-column order)"}),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "host": host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
