@@ -185,7 +185,7 @@ def host_info():
             model = f"implementer {fields['CPU implementer']} part {fields.get('CPU part', '?')}"
         if model:
             info["cpu_model"] = model
-    except OSError:
+    except (OSError, ValueError):
         pass
     try:
         info["affinity"] = len(os.sched_getaffinity(0))
