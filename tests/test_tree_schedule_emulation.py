@@ -9,7 +9,10 @@ exactly those schedules -- the same FIFO depths, slot indices (step index modulo
 depth), node residues and twiddle indices -- in plain Python for every window length
 2^M <= 64 and split B <= min(M, 3) (and 3^M <= 27), and compare with numpy's FFT of every window (forward)
 and with the explicit overlap-add of every window's inverse DFT (adjoint).  They pin the
-index arithmetic of the kernels' register schedules without a GPU.
+index arithmetic of the kernels' register schedules without a GPU.  The last tests replay
+the two adjoint passes whole -- cp.async staging into shared memory, chunking of window rows
+and columns, the side rows two column chunks share and the fold that adds them -- block by
+block, for every window side the adjoint passes build.
 """
 import numpy as np
 import pytest
@@ -70,8 +73,10 @@ def forward_walk(M, B, c, x):
     return outs
 
 
-def adjoint_walk(M, B, c, G, N):
-    """Thread c's partial of y[p] = sum_j sum_k G[p-j][k] w_n^{+jk}, p = N-1 .. 0."""
+def adjoint_tree(M, B, c, feeds):
+    """Thread c of the transposed tree (adjoint_core.cuh, SlidingTreeAdjoint) over the steps
+    j = 0, 1, ..: feeds[j] = its held level-M inputs (k = c + 2^B t) at step j, each a value
+    or an array over independent lanes; returns the thread's partial output at every step."""
     n = 1 << M
     om = np.exp(-2j * np.pi * np.arange(n) / n)
     cb = c & ((1 << B) - 1)
@@ -84,12 +89,10 @@ def adjoint_walk(M, B, c, G, N):
     rings = {v: [[0j] * (held(B, v - 1) if v > B else 1) for _ in range(1 << (M - v))]
              for v in range(1, M + 1)}
     period = 1 << (M - 1) if M >= 1 else 1
-    y = np.zeros(N, complex)
-    for j, p in enumerate(range(N - 1, -1, -1)):
+    outs = []
+    for j, feed in enumerate(feeds):
         J = j % period
-        q = p - (n - 1)
-        ks = [cb + (t << B) for t in range(held(B, M))]
-        cur = [G[q][k] if 0 <= q < len(G) else 0j for k in ks]
+        cur = list(feed)
         for v in range(M, 0, -1):
             slot = J % (1 << (M - v))
             if v > B:
@@ -104,8 +107,20 @@ def adjoint_walk(M, B, c, G, N):
                 old = rings[v][slot][0]
                 rings[v][slot][0] = cur[0]
                 cur[0] = tw[v][0] * cur[0] + old
-        y[p] = cur[0]
-    return y
+        outs.append(cur[0])
+    return outs
+
+
+def adjoint_walk(M, B, c, G, N):
+    """Thread c's partial of y[p] = sum_j sum_k G[p-j][k] w_n^{+jk}, p = N-1 .. 0."""
+    n = 1 << M
+    cb = c & ((1 << B) - 1)
+    ks = [cb + (t << B) for t in range(held(B, M))]
+    feeds = []
+    for p in range(N - 1, -1, -1):
+        q = p - (n - 1)
+        feeds.append([G[q][k] if 0 <= q < len(G) else 0j for k in ks])
+    return np.array(adjoint_tree(M, B, c, feeds))[::-1]
 
 
 SPLITS = [(M, B) for M in range(0, 7) for B in range(0, min(M, 3) + 1)]
@@ -190,3 +205,218 @@ def test_ternary_schedule_gives_every_windows_dft(M):
         for p in range(n - 1, len(x)):
             ref = np.fft.fft(x[p - n + 1:p + 1])
             np.testing.assert_allclose(outs[p], ref[ks], atol=1e-9)
+
+
+# ---------------------------------------------------------------------------------------------
+# The two adjoint passes (adjoint_kernels.cuh, adjoint.cu) with their shared-memory staging,
+# chunking and side-row fold, replayed block by block: every staged value a thread reads is
+# checked against the operand it stands for, every output is written exactly once, and the
+# result equals the explicit overlap-add of every window's inverse DFT (A^H G, scale 1).
+
+def adj_col_B(M):
+    return M if M < 1 else (1 if M <= 4 else M - 3)
+
+
+def adj_row_B(M):
+    return 3 if M >= 4 else (M if M < 2 else 2)
+
+
+def adj_col_chunk(rows_out, n, requested):
+    chunk = requested if requested > 0 else rows_out
+    chunk = max(chunk, n - 1)
+    return max(1, min(chunk, rows_out))
+
+
+def emulate_adj_col(G, n0, n1, chunk_req):
+    """adj_col_kernel over its grid (channel blocks x window-row chunks), then adj_fold_kernel.
+    G: (rows_out, P1, n0, n1).  Returns gz as (rows_out + n0 - 1, P1 * n1)."""
+    rows_out, P1 = G.shape[0], G.shape[1]
+    M, m1 = n0.bit_length() - 1, n1.bit_length() - 1
+    B = adj_col_B(M)
+    R, n, CH, GS = 1 << B, n0, 128 >> B, 2
+    STEP = n * CH
+    nch = P1 * n1
+    Gf = G.reshape(-1)
+    grow = nch * n
+    chunk = adj_col_chunk(rows_out, n, chunk_req)
+    nchunks = -(-rows_out // chunk)
+    gz = np.full((rows_out + n - 1) * nch, np.nan, complex)
+    side = np.full(max(nchunks - 1, 0) * (n - 1) * nch, np.nan, complex)
+    for bx in range(-(-nch // CH)):
+        ch0 = bx * CH
+        for by in range(nchunks):
+            qa = by * chunk
+            qb = min(qa + chunk, rows_out)
+            last = qb == rows_out
+            p_hi, nwin = qb + n - 2, qb - qa
+            steps = nwin + n - 1
+            sg = np.full(2 * GS * STEP, np.nan, complex)
+
+            def fetch(j0, b):
+                for tid in range(128):
+                    cl_f, k0_f = tid & (CH - 1), tid // CH
+                    cg_f = ch0 + cl_f
+                    ok = cg_f < nch
+                    gsrc = ((cg_f >> m1) * n + k0_f) * n1 + (cg_f & (n1 - 1)) if ok else 0
+                    dst = b * GS * STEP + k0_f * CH + cl_f
+                    src = gsrc + (qb - 1 - j0) * grow
+                    for _ in range(min(GS, nwin - j0)):
+                        for t in range(n // R):
+                            sg[dst + t * R * CH] = Gf[src + t * R * n1] if ok else 0
+                        dst += STEP
+                        src -= grow
+
+            if nwin > 0:
+                fetch(0, 0)
+            feeds = [[] for _ in range(R)]
+            lanes = np.arange(CH)
+            for j in range(steps):
+                if j % GS == 0 and j + GS < nwin:
+                    fetch(j + GS, (j // GS + 1) & 1)
+                for c in range(R):
+                    ks = [c + R * t for t in range(held(B, M))]
+                    if j < nwin:
+                        base = (((j // GS) & 1) * GS + j % GS) * STEP
+                        u = [sg[base + k * CH + lanes] for k in ks]
+                        # the staged values are G[qb - 1 - j][q1][k0][k1] of each lane's channel
+                        ch = ch0 + lanes
+                        ok = ch < nch
+                        for k, uk in zip(ks, u):
+                            want = np.where(ok, G[qb - 1 - j, np.minimum(ch, nch - 1) >> m1, k,
+                                                  np.minimum(ch, nch - 1) & (n1 - 1)], 0)
+                            np.testing.assert_array_equal(uk, want)
+                    else:
+                        u = [np.zeros(CH, complex) for _ in ks]
+                    feeds[c].append(u)
+            y = sum(np.array(adjoint_tree(M, B, c, feeds[c])) for c in range(R))  # (steps, CH)
+            for j in range(steps):
+                r = p_hi - j
+                for chl in range(CH):
+                    ch = ch0 + chl
+                    if ch >= nch:
+                        continue
+                    if r >= qb and not last:
+                        i = by * (n - 1) * nch + (r - qb) * nch + ch
+                        assert np.isnan(side[i]), "side value written twice"
+                        side[i] = y[j, chl]
+                    else:
+                        assert np.isnan(gz[r * nch + ch]), "gz value written twice"
+                        gz[r * nch + ch] = y[j, chl]
+    # adj_fold_kernel: gz rows [qb, qb + n0 - 2] += the side rows of boundary qb
+    per_row = (n - 1) * nch
+    assert side.size == (nchunks - 1) * per_row
+    for i in range(side.size):
+        b = i // per_row + 1
+        gz[b * chunk * nch + (i - (b - 1) * per_row)] += side[i]
+    assert not np.isnan(gz).any(), "a gz value was never written"
+    return gz.reshape(rows_out + n - 1, nch)
+
+
+def emulate_adj_row(gz, N1, n1, chunk):
+    """adj_row_kernel over its grid (row blocks x column chunks) with its cp.async staging.
+    gz: (zrows, P1 * n1).  Returns gx (zrows, N1), complex (the real path stores .real)."""
+    zrows = gz.shape[0]
+    M = n1.bit_length() - 1
+    B = adj_row_B(M)
+    R, n = 1 << B, n1
+    kRows = 128 >> B
+    GS = min(16, max(1, 2048 // (kRows * n)))
+    kRow = GS * n + R
+    kPiece = 2 if n >= 2 else 1
+    kPerRow = GS * n // kPiece
+    assert kPerRow <= 128 and 128 % kPerRow == 0 and (kPiece == 1 or kRow % 2 == 0)
+    kRowStep = 128 // kPerRow
+    kCopies = kRows // kRowStep
+    P1 = N1 - n + 1
+    rowlen = P1 * n
+    gzf = gz.reshape(-1)
+    chunk = min(chunk, N1)
+    gx = np.full((zrows, N1), np.nan, complex)
+    for bx in range(-(-zrows // kRows)):
+        row0 = bx * kRows
+        for by in range(-(-N1 // chunk)):
+            pa = by * chunk
+            pb = min(pa + chunk, N1)
+            p_hi = min(pb + n - 2, N1 - 1)
+            steps = p_hi - pa + 1
+            q1_top = p_hi - (n - 1)
+            sz = np.full(2 * kRows * kRow, np.nan, complex)
+
+            def fetch(j0, b):
+                q1lo = q1_top - j0 - (GS - 1)
+                for tid in range(128):
+                    off_f = (tid % kPerRow) * kPiece
+                    rl_f = tid // kPerRow
+                    q = q1lo + off_f // n
+                    qok = 0 <= q < P1
+                    goff = q1lo * n + off_f
+                    dst = (b * kRows + rl_f) * kRow + off_f
+                    for t in range(kCopies):
+                        r = row0 + rl_f + t * kRowStep
+                        ok = qok and r < zrows
+                        d = dst + t * kRowStep * kRow
+                        if kPiece == 2:  # 16-byte copies: both ends 16-byte aligned
+                            assert d % 2 == 0 and (not ok or (r * rowlen + goff) % 2 == 0)
+                        for e in range(kPiece):
+                            sz[d + e] = gzf[r * rowlen + goff + e] if ok else 0
+
+            fetch(0, 0)
+            lanes = np.arange(kRows)
+            rows = row0 + lanes
+            feeds = [[] for _ in range(R)]
+            for j in range(steps):
+                if j % GS == 0 and j + GS < steps:
+                    fetch(j + GS, (j // GS + 1) & 1)
+                q1 = q1_top - j
+                for c in range(R):
+                    base = (((j // GS) & 1) * kRows + lanes) * kRow + (GS - 1 - j % GS) * n + c
+                    u = [sz[base + t * R] for t in range(held(B, M))]
+                    for t, ut in enumerate(u):  # gz[row][q1][k1 = c + R t], 0 outside
+                        valid = (rows < zrows) & (0 <= q1 < P1)
+                        want = np.where(valid, gz[np.minimum(rows, zrows - 1),
+                                                  min(max(q1, 0), P1 - 1) * n + c + R * t], 0)
+                        np.testing.assert_array_equal(ut, want)
+                    feeds[c].append(u)
+            y = sum(np.array(adjoint_tree(M, B, c, feeds[c])) for c in range(R))  # (steps, kRows)
+            for j in range(steps):
+                p1 = p_hi - j
+                if p1 >= pb:
+                    continue
+                for rl in range(kRows):
+                    if row0 + rl < zrows:
+                        assert np.isnan(gx[row0 + rl, p1]), "gx value written twice"
+                        gx[row0 + rl, p1] = y[j, rl]
+    assert not np.isnan(gx).any(), "a gx value was never written"
+    return gx
+
+
+def overlap_add_of_inverse_dfts(G, N0, N1):
+    """A^H G at scale 1: every window's sum_k G[q][k] w^{+j.k} added at its position."""
+    P0, P1, n0, n1 = G.shape
+    out = np.zeros((N0, N1), complex)
+    for q0 in range(P0):
+        for q1 in range(P1):
+            out[q0:q0 + n0, q1:q1 + n1] += np.fft.ifft2(G[q0, q1]) * (n0 * n1)
+    return out
+
+
+ADJ_CASES = [(1, 64), (2, 32), (4, 16), (8, 8), (16, 4), (32, 2), (64, 1)]
+
+
+@pytest.mark.parametrize("n0,n1", ADJ_CASES)
+def test_adjoint_passes_with_staging_chunks_and_fold(n0, n1):
+    rows_out, P1 = 21, 5
+    N0, N1 = rows_out + n0 - 1, P1 + n1 - 1
+    rng = np.random.default_rng(7 * n0 + n1)
+    G = rng.standard_normal((rows_out, P1, n0, n1)) + 1j * rng.standard_normal((rows_out, P1, n0, n1))
+    ref = overlap_add_of_inverse_dfts(G, N0, N1)
+    ref_z = None
+    for col_chunk in (0, 1, 5, 8):  # one chunk; the n0 - 1 minimum; ragged chunks
+        gz = emulate_adj_col(G, n0, n1, col_chunk)
+        if ref_z is None:
+            ref_z = gz
+        else:
+            np.testing.assert_allclose(gz, ref_z, atol=1e-9)
+    for row_chunk in (N1, n1, 3):  # one chunk; the n1 minimum; chunks shorter than a window
+        gx = emulate_adj_row(ref_z, N1, n1, row_chunk)
+        np.testing.assert_allclose(gx, ref, atol=1e-8)
