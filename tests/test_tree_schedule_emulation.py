@@ -33,8 +33,10 @@ def tw_offset(B, v):
     return sum(1 if w <= B else held(B, w - 1) for w in range(1, v))
 
 
-def forward_walk(M, B, c, x):
-    """Thread c's outputs (nodes k = c + 2^B t of level M) at every position p."""
+def forward_tree(M, B, c, feeds):
+    """Thread c of the sliding tree (tree_core.cuh, SlidingTree) over the steps j = 0, 1, ..:
+    feeds[j] = (x at the window's end position, x n/2 positions earlier), values or arrays over
+    independent lanes; returns the thread's level-M nodes k = c + 2^B t at every step."""
     n = 1 << M
     om = np.exp(-2j * np.pi * np.arange(n) / n)
     tw = [0j] * max(1, tw_offset(B, M + 1))
@@ -49,14 +51,13 @@ def forward_walk(M, B, c, x):
     fifos = {u: [[0j] * held(B, u) for _ in range(fifo_depth(M, u))] for u in range(1, M)}
     period = 1 << (M - 2) if M >= 2 else 1  # the kernels' unroll period
     outs = []
-    for j, p in enumerate(range(len(x))):
+    for j, (xp, xs) in enumerate(feeds):
         J = j % period
-        cur = [x[p]] + [0j] * (held(B, M) - 1)
-        look_back = x[max(p - n // 2, 0)] if M >= 1 else 0j  # level 0 is re-read, no FIFO
+        cur = [xp] + [0j] * (held(B, M) - 1)
         for v in range(1, M + 1):
             hp = held(B, v - 1)
             if v == 1:
-                old = [look_back]
+                old = [xs]  # level 0 is re-read, no FIFO
             else:
                 slot = J % fifo_depth(M, v - 1)
                 old = list(fifos[v - 1][slot])
@@ -71,6 +72,13 @@ def forward_walk(M, B, c, x):
                     cur[t] = old[t] + prod
         outs.append(cur[:held(B, M)])
     return outs
+
+
+def forward_walk(M, B, c, x):
+    """Thread c's outputs (nodes k = c + 2^B t of level M) at every position p of x."""
+    n = 1 << M
+    feeds = [(x[p], x[max(p - n // 2, 0)] if M >= 1 else 0j) for p in range(len(x))]
+    return forward_tree(M, B, c, feeds)
 
 
 def adjoint_tree(M, B, c, feeds):
@@ -420,3 +428,210 @@ def test_adjoint_passes_with_staging_chunks_and_fold(n0, n1):
     for row_chunk in (N1, n1, 3):  # one chunk; the n1 minimum; chunks shorter than a window
         gx = emulate_adj_row(ref_z, N1, n1, row_chunk)
         np.testing.assert_allclose(gx, ref, atol=1e-8)
+
+
+# ---------------------------------------------------------------------------------------------
+# The forward passes (tree_kernels.cuh) replayed block by block: row_tile (two-pass form, row
+# levels into z), col_tile_impl with its shared-memory ring of z rows filled one step group
+# ahead by either stage -- ZStageLoad (cp.async copies of z, with the n0/2 padding rows in
+# front of z that only incomplete border trees read) or ZStageRowDft (the fused form's row
+# levels by warp shuffles) -- and the scaled stores of every window's coefficients.
+
+def tg_period(M):
+    return 1 << (M - 2) if M >= 2 else 1
+
+
+def col_group(M):
+    return max(tg_period(M), 8)
+
+
+def col_ring_rows(M):
+    need = ((1 << (M - 1)) if M >= 1 else 0) + 2 * col_group(M)
+    r = 1
+    while r < need:
+        r <<= 1
+    return r
+
+
+def emulate_row_pass(x, n1, B, chunk, pad):
+    """row_tree_kernel over (row blocks of 128 >> B rows) x (chunks of window columns): returns
+    z with `pad` padding rows (NaN: never written by the row pass) in front."""
+    rows, N1 = x.shape
+    M = n1.bit_length() - 1
+    R, P1 = 1 << B, N1 - n1 + 1
+    z = np.full((pad + rows, P1 * n1), np.nan, complex)
+    for qa in range(0, P1, chunk):
+        qb = min(qa + chunk, P1)
+        steps = (qb - qa) + (n1 - 1)
+        assert qb + n1 - 2 <= N1 - 1  # last column read
+        feeds = [(x[:, qa + j], x[:, max(qa + j - n1 // 2, 0)] if M >= 1 else 0j) for j in range(steps)]
+        for c in range(R):
+            outs = forward_tree(M, B, c, feeds)
+            for j in range(n1 - 1, steps):
+                q1 = qa + j - (n1 - 1)
+                for t, o in enumerate(outs[j]):
+                    col = q1 * n1 + c + (t << B)
+                    assert np.isnan(z[pad:, col]).all(), "z value written twice"
+                    z[pad:, col] = o
+    return z
+
+
+class LoadStage:
+    """ZStageLoad: ring rows from z (band row rr is z row pad + rr), zero for channels past nch."""
+
+    def __init__(self, z, pad, nch):
+        self.z, self.pad, self.nch = z, pad, nch
+
+    def fetch(self, ring, r_lo, r_hi, CH, ch0, RD):
+        for rr in range(r_lo, r_hi):
+            assert 0 <= self.pad + rr < self.z.shape[0]  # every copy source inside z
+            cc = np.arange(CH)
+            ok = ch0 + cc < self.nch
+            ring[(rr & (RD - 1)) * CH + cc] = np.where(ok, self.z[self.pad + rr, np.minimum(ch0 + cc, self.nch - 1)], 0)
+
+    def check(self, got, zr, ch):  # a copy: bit for bit (NaN for padding rows)
+        ok = ch < self.nch
+        np.testing.assert_array_equal(got, np.where(ok, self.z[self.pad + zr, np.minimum(ch, self.nch - 1)], 0))
+
+
+class RowDftStage:
+    """ZStageRowDft: each warp computes the n1-point DFTs of 32 channels of one input row by
+    shuffles; lane (i, d) holds node i at position p - d."""
+
+    def __init__(self, x, n1):
+        self.x, self.n1 = x, n1
+        self.M1 = n1.bit_length() - 1
+        self.zrows, N1 = x.shape
+        self.P1 = N1 - n1 + 1
+        self.om64 = np.exp(-2j * np.pi * np.arange(64) / 64)
+
+    def row_dft(self, r, ch0):
+        M1, n1 = self.M1, self.n1
+        lane = np.arange(32)
+        l = lane & (n1 - 1)
+        base = lane - l
+        q1 = (ch0 >> M1) + (lane >> M1)
+        v = np.zeros(32, complex)
+        valid = (0 <= r < self.zrows) & (q1 < self.P1)
+        col = q1 + n1 - 1 - l
+        if valid.any():
+            assert col[valid].max() < self.x.shape[1]
+            v[valid] = self.x[r, col[valid]]
+        for t in range(1, M1 + 1):
+            i, d = l >> (M1 - t), l & ((1 << (M1 - t)) - 1)
+            src = base + ((i & ((1 << (t - 1)) - 1)) << (M1 - t + 1)) + d
+            assert ((src >= base) & (src + (1 << (M1 - t)) < base + n1)).all()  # own window's lanes
+            v = v[src + (1 << (M1 - t))] + self.om64[i << (6 - t)] * v[src]
+        return v
+
+    def fetch(self, ring, r_lo, r_hi, CH, ch0, RD):
+        for rr in range(r_lo, r_hi):
+            for g in range(CH >> 5):
+                ring[(rr & (RD - 1)) * CH + g * 32 + np.arange(32)] = self.row_dft(rr, ch0 + g * 32)
+
+    def check(self, got, zr, ch):  # the n1-point DFT of the window's row (0 outside x)
+        q1, k1 = ch >> self.M1, ch & (self.n1 - 1)
+        want = np.zeros(len(ch), complex)
+        if 0 <= zr < self.zrows:
+            for i in np.nonzero(q1 < self.P1)[0]:
+                want[i] = np.fft.fft(self.x[zr, q1[i]:q1[i] + self.n1])[k1[i]]
+        np.testing.assert_allclose(got, want, atol=1e-12)
+
+
+def emulate_col_pass(stage, n0, B, groups, m1, P1, rows_out, chunk, scale):
+    """col_tile_impl over (blocks of 32 * groups channels) x (chunks of window rows); returns
+    the output (rows_out, P1, n0, n1), every value written exactly once."""
+    M = n0.bit_length() - 1
+    R, n, n1 = 1 << B, n0, 1 << m1
+    kP, kH, RD = col_group(M), n0 // 2, col_ring_rows(M)
+    assert kP % tg_period(M) == 0 and RD >= kH + 2 * kP
+    CH, nch = 32 * groups, P1 << m1
+    out = np.full((rows_out, P1, n0, n1), np.nan, complex)
+    my = np.arange(CH)
+    for ch0 in range(0, nch, CH):
+        ch = ch0 + my
+        active = ch < nch
+        for qa in range(0, rows_out, chunk):
+            qb = min(qa + chunk, rows_out)
+            steps, zr_end = (qb - qa) + (n - 1), qb + n - 1
+            ring = np.full(RD * CH, np.nan, complex)
+            stage.fetch(ring, qa - kH, min(qa + kP, zr_end), CH, ch0, RD)
+            feeds = []
+            for jb in range(0, steps, kP):
+                if jb + kP < steps:
+                    stage.fetch(ring, qa + jb + kP, min(qa + jb + 2 * kP, zr_end), CH, ch0, RD)
+                for j in range(jb, min(jb + kP, steps)):
+                    zr = qa + j
+                    xp = ring[(zr & (RD - 1)) * CH + my]
+                    xs = ring[((zr - kH) & (RD - 1)) * CH + my] if M >= 1 else 0j
+                    stage.check(xp, zr, ch)
+                    if M >= 1:
+                        stage.check(xs, zr - kH, ch)
+                    feeds.append((xp, xs))
+            for c in range(R):
+                outs = forward_tree(M, B, c, feeds)
+                for j in range(n - 1, steps):
+                    q0 = qa + j - (n - 1)
+                    for t, o in enumerate(outs[j]):
+                        k0 = c + R * t
+                        for i in np.nonzero(active)[0]:
+                            q1, k1 = ch[i] >> m1, ch[i] & (n1 - 1)
+                            assert np.isnan(out[q0, q1, k0, k1]), "output written twice"
+                            out[q0, q1, k0, k1] = scale * o[i]
+    assert not np.isnan(out).any(), "an output was never written"
+    return out
+
+
+def every_window_dft(x, n0, n1, scale):
+    N0, N1 = x.shape
+    P0, P1 = N0 - n0 + 1, N1 - n1 + 1
+    ref = np.empty((P0, P1, n0, n1), complex)
+    for q0 in range(P0):
+        for q1 in range(P1):
+            ref[q0, q1] = np.fft.fft2(x[q0:q0 + n0, q1:q1 + n1]) * scale
+    return ref
+
+
+def col_split(m0):
+    return 3 if m0 >= 6 else min(m0, 2)
+
+
+FWD_CASES = [  # (n0, n1, rows_out, P1, groups, column chunks)
+    (1, 8, 5, 7, 1, (5, 2)),
+    (2, 4, 6, 9, 2, (6, 4)),
+    (4, 16, 7, 3, 1, (7, 3)),
+    (8, 2, 9, 19, 2, (9, 4)),
+    (16, 1, 11, 37, 1, (11, 5)),
+    (32, 4, 6, 10, 1, (6, 4)),
+    (64, 1, 5, 33, 1, (5, 2)),
+]
+
+
+@pytest.mark.parametrize("n0,n1,rows_out,P1,groups,chunks", FWD_CASES)
+def test_two_pass_forward_with_ring_staging(n0, n1, rows_out, P1, groups, chunks):
+    rng = np.random.default_rng(1000 + n0 * 64 + n1)
+    N0, N1 = rows_out + n0 - 1, P1 + n1 - 1
+    x = rng.standard_normal((N0, N1)) + 1j * rng.standard_normal((N0, N1))
+    scale = 1 / np.sqrt(n0 * n1)
+    ref = every_window_dft(x, n0, n1, scale)
+    m1 = n1.bit_length() - 1
+    pad = n0 // 2
+    for row_chunk in (P1, max(1, n1 // 2)):
+        z = emulate_row_pass(x, n1, min(m1, 3), row_chunk, pad)
+        for chunk in chunks:
+            out = emulate_col_pass(LoadStage(z, pad, P1 * n1), n0, col_split(n0.bit_length() - 1),
+                                   groups, m1, P1, rows_out, chunk, scale)
+            np.testing.assert_allclose(out, ref, atol=1e-9)
+
+
+@pytest.mark.parametrize("n0,n1,rows_out,P1,groups,chunks", [c for c in FWD_CASES if c[1] <= 32])
+def test_fused_forward_with_row_dfts_by_shuffles(n0, n1, rows_out, P1, groups, chunks):
+    rng = np.random.default_rng(2000 + n0 * 64 + n1)
+    N0, N1 = rows_out + n0 - 1, P1 + n1 - 1
+    x = rng.standard_normal((N0, N1))
+    ref = every_window_dft(x, n0, n1, 1.0)
+    m1 = n1.bit_length() - 1
+    for chunk in chunks:
+        out = emulate_col_pass(RowDftStage(x, n1), n0, col_split(n0.bit_length() - 1), groups, m1,
+                               P1, rows_out, chunk, 1.0)
+        np.testing.assert_allclose(out, ref, atol=1e-9)
