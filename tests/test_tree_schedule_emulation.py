@@ -9,10 +9,13 @@ exactly those schedules -- the same FIFO depths, slot indices (step index modulo
 depth), node residues and twiddle indices -- in plain Python for every window length
 2^M <= 64 and split B <= min(M, 3) (and 3^M <= 27), and compare with numpy's FFT of every window (forward)
 and with the explicit overlap-add of every window's inverse DFT (adjoint).  They pin the
-index arithmetic of the kernels' register schedules without a GPU.  The last tests replay
-the two adjoint passes whole -- cp.async staging into shared memory, chunking of window rows
-and columns, the side rows two column chunks share and the fold that adds them -- block by
-block, for every window side the adjoint passes build.
+index arithmetic of the kernels' register schedules without a GPU.
+
+The later tests replay whole passes block by block, with each block's shared-memory staging:
+the two adjoint passes (cp.async staging, chunking of window rows and columns, the side rows
+two column chunks share and the fold that adds them) for every window side they build, and
+the forward passes (row_tile into z; col_tile_impl with its ring of z rows fed by copies of z
+or by the fused form's shuffled row DFTs).
 """
 import numpy as np
 import pytest
