@@ -15,7 +15,8 @@ The later tests replay whole passes block by block, with each block's shared-mem
 the two adjoint passes (cp.async staging, chunking of window rows and columns, the side rows
 two column chunks share and the fold that adds them) for every window side they build, and
 the forward passes (row_tile into z; col_tile_impl with its ring of z rows fed by copies of z
-or by the fused form's shuffled row DFTs).
+or by the fused form's shuffled row DFTs), and the ternary passes (row_tree3_kernel's staged
+run write-back; col_tree3_kernel's ring and its staged copy-out).
 """
 import numpy as np
 import pytest
@@ -164,12 +165,11 @@ def test_adjoint_schedule_gives_the_overlap_add_of_inverse_dfts(M, B):
     np.testing.assert_allclose(y, ref, atol=1e-9)
 
 
-def ternary_walk(M, c, x):
-    """Thread c (< 3) of the ternary tree split by residue mod 3 (tree3_core.cuh): its
-    level-M nodes c + 3u, u < 3^(M-1), at every position p."""
-    n = 3 ** M
+def ternary_tree(M, c, feeds):
+    """Thread c (< 3) of the ternary tree split by residue mod 3 (tree3_core.cuh) over the
+    steps j = 0, 1, ..: feeds[j] = (x at the window end p, x at p - s_1, x at p - 2 s_1),
+    s_1 = 3^(M-1), values or lane arrays; returns its level-M nodes c + 3u, u < 3^(M-1)."""
     w27 = np.exp(-2j * np.pi * np.arange(27) / 27)
-    s1 = 3 ** (M - 1)
 
     def held_t(t):  # level-t nodes one thread holds
         return 1 if t <= 1 else 3 ** (t - 1)
@@ -181,11 +181,9 @@ def ternary_walk(M, c, x):
     period = 2 * 3 ** (M - 2) if M >= 2 else 1
     w3 = np.exp(-2j * np.pi / 3)
     outs = []
-    for j, p in enumerate(range(len(x))):
+    for j, (xp, xs1, xs2) in enumerate(feeds):
         J = j % period
-        xs1 = x[p - s1] if p - s1 >= 0 else 0j
-        xs2 = x[p - 2 * s1] if p - 2 * s1 >= 0 else 0j
-        cur = [xs2 + w3 ** c * xs1 + w3 ** (2 * c) * x[p]]  # level 1, node c
+        cur = [xs2 + w3 ** c * xs1 + w3 ** (2 * c) * xp]  # level 1, node c
         for t in range(2, M + 1):
             s = 3 ** (M - t)
             D = 2 * s
@@ -203,6 +201,14 @@ def ternary_walk(M, c, x):
             cur = nxt
         outs.append(cur)
     return outs
+
+
+def ternary_walk(M, c, x):
+    """Thread c's level-M nodes at every position p of x (zero before the array)."""
+    s1 = 3 ** (M - 1)
+    feeds = [(x[p], x[p - s1] if p - s1 >= 0 else 0j, x[p - 2 * s1] if p - 2 * s1 >= 0 else 0j)
+             for p in range(len(x))]
+    return ternary_tree(M, c, feeds)
 
 
 @pytest.mark.parametrize("M", [1, 2, 3])
@@ -638,3 +644,156 @@ def test_fused_forward_with_row_dfts_by_shuffles(n0, n1, rows_out, P1, groups, c
         out = emulate_col_pass(RowDftStage(x, n1), n0, col_split(n0.bit_length() - 1), groups, m1,
                                P1, rows_out, chunk, 1.0)
         np.testing.assert_allclose(out, ref, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------------------------
+# The ternary passes (tree3.cu) replayed block by block: row_tree3_kernel with its output
+# stage [row][step][k1] written back in runs, and col_tree3_kernel with its ring of z rows
+# (look-backs s_1 and 2 s_1 rows up, 2 n0 / 3 padding rows in front of z) and, when n1 is not
+# a multiple of 4, its double-buffered output stage copied out by consecutive threads.
+
+def emulate_row_pass3(x, n1, chunk, pad):
+    rows, N1 = x.shape
+    M = {1: 0, 3: 1, 9: 2, 27: 3}[n1]
+    n, R, OUT = n1, (3 if M >= 1 else 1), (3 ** (M - 1) if M >= 1 else 1)
+    S1 = 3 ** (M - 1) if M >= 1 else 0
+    UNR = 6
+    assert M < 2 or UNR % (2 * 3 ** (M - 2)) == 0
+    P1 = N1 - n + 1
+    zrow = P1 * n
+    z = np.full((pad + rows) * zrow, np.nan, complex)
+    written = np.zeros(z.shape, int)
+    for row0 in range(0, rows, 32):
+        nrows = min(32, rows - row0)
+        lanes = np.arange(32)
+        xr = x[np.minimum(row0 + lanes, rows - 1)]  # lanes past the last row re-read row0's
+        xr[row0 + lanes >= rows] = x[row0]
+        for qa in range(0, P1, chunk):
+            qb = min(qa + chunk, P1)
+            steps = (qb - qa) + (n - 1)
+            stage = np.full(32 * UNR * n, np.nan, complex)
+            feeds = [(xr[:, qa + j], xr[:, max(qa + j - S1, 0)], xr[:, max(qa + j - 2 * S1, 0)])
+                     for j in range(steps)]
+            outs = {c: (ternary_tree(M, c, feeds) if M >= 1 else [[f[0]] for f in feeds]) for c in range(R)}
+            for jb in range(0, steps, UNR):
+                for j in range(jb, min(jb + UNR, steps)):
+                    if j >= n - 1:
+                        for c in range(R):
+                            for u in range(OUT):
+                                stage[(lanes * UNR + (j - jb)) * n + c + 3 * u] = outs[c][j][u]
+                j0, j1 = max(jb, n - 1), min(jb + UNR, steps)
+                if j1 > j0:
+                    run, q, sofs = (j1 - j0) * n, qa + j0 - (n - 1), (j0 - jb) * n
+                    for r in range(nrows):
+                        zq = (pad + row0 + r) * zrow + q * n
+                        sq = sofs + r * UNR * n
+                        assert q * n + run <= zrow  # inside the row
+                        z[zq:zq + run] = stage[sq:sq + run]
+                        written[zq:zq + run] += 1
+    assert (written[pad * zrow:] == 1).all(), "z value not written exactly once"
+    return z.reshape(pad + rows, zrow)
+
+
+def emulate_col_pass3(z, pad, n0, n1, P1, rows_out, chunk, scale):
+    M = {1: 0, 3: 1, 9: 2, 27: 3}[n0]
+    n, R, OUT = n0, (3 if M >= 1 else 1), (3 ** (M - 1) if M >= 1 else 1)
+    S1 = 3 ** (M - 1) if M >= 1 else 0
+    W = 64
+    G = 6 if M >= 3 else 8
+    assert M < 2 or G % (2 * 3 ** (M - 2)) == 0
+    need = (2 * S1 if M >= 1 else 0) + 2 * G
+    RD = 1 << (need - 1).bit_length()
+    T = max(1, W // n1)
+    CH = T * n1
+    nch = P1 * n1
+    orow_len = nch * n
+    staged = n1 % 4 != 0
+    out = np.full(rows_out * orow_len, np.nan, complex)
+    written = np.zeros(out.shape, int)
+    my = np.arange(W)
+    for bx in range(-(-P1 // T)):
+        q1_0 = bx * T
+        ch0 = q1_0 * n1
+        ch = ch0 + my
+        active = (my < CH) & (ch < nch)
+        tile_elems = min(T, nch // n1 - q1_0) * n * n1
+        q1l, k1 = my // n1, my % n1
+        for qa in range(0, rows_out, chunk):
+            qb = min(qa + chunk, rows_out)
+            steps, zr_end = (qb - qa) + (n - 1), qb + n - 1
+            ring = np.full(RD * W, np.nan, complex)
+
+            def fetch(r_lo, r_hi):
+                for rr in range(r_lo, r_hi):
+                    assert 0 <= pad + rr < z.shape[0]
+                    cc = np.arange(CH)
+                    ok = ch0 + cc < nch
+                    ring[(rr & (RD - 1)) * W + cc] = np.where(ok, z[pad + rr, np.minimum(ch0 + cc, nch - 1)], 0)
+
+            fetch(qa - 2 * S1, min(qa + G, zr_end))
+            feeds = []
+            for jb in range(0, steps, G):
+                if jb + G < steps:
+                    fetch(qa + jb + G, min(qa + jb + 2 * G, zr_end))
+                for j in range(jb, min(jb + G, steps)):
+                    zr = qa + j
+                    f = tuple(ring[((zr - d) & (RD - 1)) * W + my] for d in (0, S1, 2 * S1))
+                    for d, v in zip((0, S1, 2 * S1), f):  # the live lanes read z rows zr - d
+                        if M >= 1 or d == 0:
+                            np.testing.assert_array_equal(v[active], z[pad + zr - d, ch[active]])
+                    feeds.append(f)
+            outs = {c: (ternary_tree(M, c, feeds) if M >= 1 else [[f[0]] for f in feeds]) for c in range(R)}
+            orow = qa * orow_len + q1_0 * n * n1
+            stage = [np.full(W * n, np.nan, complex) for _ in range(2)]
+            buf = 0
+            for j in range(n - 1, steps):
+                if staged:
+                    st = stage[buf]
+                    for c in range(R):
+                        for u in range(OUT):
+                            idx = q1l * n * n1 + c * n1 + k1 + 3 * u * n1
+                            st[idx[my < CH]] = scale * outs[c][j][u][my < CH]
+                    e = np.arange(tile_elems)
+                    out[orow + e] = st[e]
+                    written[orow + e] += 1
+                    buf ^= 1
+                else:
+                    for c in range(R):
+                        for u in range(OUT):
+                            idx = orow + q1l * n * n1 + c * n1 + k1 + 3 * u * n1
+                            out[idx[active]] = scale * outs[c][j][u][active]
+                            written[idx[active]] += 1
+                orow += orow_len
+    assert (written == 1).all(), "output not written exactly once"
+    return out.reshape(rows_out, P1, n0, n1)
+
+
+TERNARY_CASES = [  # (n0, n1, rows_out, P1, column chunks); n1 of 2^k comes from the binary row pass
+    (1, 9, 5, 9, (5, 2)),
+    (3, 3, 7, 30, (7, 3)),
+    (9, 1, 8, 70, (8, 5)),
+    (9, 4, 6, 21, (6, 4)),
+    (27, 2, 5, 40, (5, 3)),
+    (3, 27, 6, 5, (6, 4)),
+    (27, 27, 3, 4, (3, 2)),
+    (3, 64, 4, 3, (4, 3)),
+]
+
+
+@pytest.mark.parametrize("n0,n1,rows_out,P1,chunks", TERNARY_CASES)
+def test_ternary_passes_with_staging(n0, n1, rows_out, P1, chunks):
+    rng = np.random.default_rng(3000 + n0 * 64 + n1)
+    N0, N1 = rows_out + n0 - 1, P1 + n1 - 1
+    x = rng.standard_normal((N0, N1)) + 1j * rng.standard_normal((N0, N1))
+    scale = 1 / np.sqrt(n0 * n1)
+    ref = every_window_dft(x, n0, n1, scale)
+    pad = 2 * n0 // 3
+    for row_chunk in (P1, 4):
+        if n1 in (1, 3, 9, 27):
+            z = emulate_row_pass3(x, n1, min(row_chunk, P1), pad)
+        else:
+            m1 = n1.bit_length() - 1
+            z = emulate_row_pass(x, n1, min(m1, 3), min(row_chunk, P1), pad)
+        for chunk in chunks:
+            out = emulate_col_pass3(z, pad, n0, n1, P1, rows_out, chunk, scale)
+            np.testing.assert_allclose(out, ref, atol=1e-9)
