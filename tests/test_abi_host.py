@@ -257,3 +257,25 @@ def test_stream_state_and_push_bookkeeping(nat):
         s.push(0, 6, 0, 0, 0)      # more rows than max_rows
     with pytest.raises(nat.SwdftError):
         s.push(0, 2, 20, 0, 0)     # row stride shorter than a row
+
+
+def test_persistent_batch_launches_one_kernel_per_window_class(nat):
+    """A persistent plan runs one kernel per row-window exponent, per column-window exponent
+    and per fused (m0, m1) pair, whatever the number of arrays: repeating arrays adds no
+    launch, and the 256-image uneven batch needs at most two per distinct window shape."""
+    import workloads
+    one = [shp(256, 256, 4, 4), shp(512, 128, 32, 32), shp(128, 1024, 64, 16)]
+    base = nat.Plan(one, flags=nat.FLAG_PERSISTENT).launch_count()
+    assert 1 <= base <= 5
+    for k in (2, 7, 40):
+        assert nat.Plan(one * k, flags=nat.FLAG_PERSISTENT).launch_count() == base
+    # per-array plans launch once or twice per array instead
+    assert nat.Plan(one * 7).launch_count() >= 7 * 3
+    _, sides, widx = workloads.uneven_batch_shapes()
+    shapes = [shp(int(sides[i, 0]), int(sides[i, 1]), *workloads.UNEVEN_WINDOWS[int(widx[i])])
+              for i in range(len(widx))]
+    windows = {workloads.UNEVEN_WINDOWS[int(w)] for w in widx}
+    n_pers = nat.Plan(shapes, flags=nat.FLAG_PERSISTENT).launch_count()
+    # at most a row and a column kernel, or one fused kernel, per distinct window shape
+    assert 1 <= n_pers <= 2 * len(windows)
+    assert nat.Plan(shapes).launch_count() >= len(shapes)
