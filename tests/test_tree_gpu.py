@@ -175,10 +175,13 @@ def test_batch_of_mixed_shapes(sw):
 # ------------------------------------------------------------- full-size workloads
 
 def _sample_windows(P0, P1, count, seed):
+    """count seeded random windows, then every window of the four edges and the centre."""
     rng = np.random.default_rng(seed)
-    q0 = list(rng.integers(0, P0, count)) + [0, 0, P0 - 1, P0 - 1, P0 // 2]
-    q1 = list(rng.integers(0, P1, count)) + [0, P1 - 1, 0, P1 - 1, P1 // 2]
-    return np.array(q0), np.array(q1)
+    q0 = [rng.integers(0, P0, count), np.zeros(P1, np.int64), np.full(P1, P0 - 1),
+          np.arange(P0), np.arange(P0), [P0 // 2]]
+    q1 = [rng.integers(0, P1, count), np.arange(P1), np.arange(P1),
+          np.zeros(P0, np.int64), np.full(P0, P1 - 1), [P1 // 2]]
+    return np.concatenate(q0).astype(np.int64), np.concatenate(q1).astype(np.int64)
 
 
 def _full_size_check(sw, x, n0, n1, count, seed):
@@ -209,7 +212,7 @@ def test_sinusoids_512_full_size(sw):
 
 def test_complex_1024x2048_full_size(sw):
     wl = workloads.complex_1024x2048()
-    _full_size_check(sw, wl.images[0], 16, 64, count=2048, seed=12)
+    _full_size_check(sw, wl.images[0], 16, 64, count=65536, seed=12)
 
 
 def test_sinusoids_512_every_coefficient_tree_and_split_bf16(sw):
