@@ -3,8 +3,8 @@
 Bar (Section 4.1, Eq. 2): max over coefficients of |a_gpu - a_oracle| / ||x_w||_2 <= 1e-5
 per window, on the unitary scale.  Small arrays are compared on every coefficient, with
 launch configurations forced so that trees are split over several threads and position
-chunks end in ragged tails; the full-size workloads are compared on sampled windows plus
-per-window Parseval over every window.
+chunks end in ragged tails; the full-size workloads are compared on seeded sampled windows
+plus every window of the four edges, and per-window Parseval over every window.
 """
 import math
 
