@@ -22,14 +22,16 @@ namespace swdft {
 
 // Launch choices the batch kernels use for a window side of 2^m (as the per-array defaults):
 // column tiles of 128 threads (256 for 64-point trees), row tiles of 128 threads.
-int batch_row_B(int m1) { return m1 >= 6 ? 2 : std::min(m1, 3); }
-int batch_col_B(int m0) { return m0 >= 6 ? 3 : std::min(m0, 2); }
-int batch_col_groups(int m0) { return m0 >= 6 ? 1 : (4 >> batch_col_B(m0)); }
-static constexpr int kRowThreads = 128;
-
 __host__ __device__ constexpr int bcol_B(int m0) { return m0 >= 6 ? 3 : (m0 < 2 ? m0 : 2); }
 __host__ __device__ constexpr int bcol_threads(int m0) { return m0 >= 6 ? 256 : 128; }
 __host__ __device__ constexpr int brow_B(int m1) { return m1 >= 6 ? 2 : (m1 < 3 ? m1 : 3); }
+static constexpr int kRowThreads = 128;
+static_assert(32 * (1 << bcol_B(6)) == bcol_threads(6) && 32 * (1 << bcol_B(5)) * (4 >> bcol_B(5)) == 128,
+              "column tiles: 2^B residue warps x 32-channel groups fill the block");
+
+int batch_row_B(int m1) { return brow_B(m1); }
+int batch_col_B(int m0) { return bcol_B(m0); }
+int batch_col_groups(int m0) { return m0 >= 6 ? 1 : (4 >> bcol_B(m0)); }
 
 // The class's arrays in item order: item0 = first tile of the array within the class.
 __device__ __forceinline__ int find_entry(const BatchClassEntry *__restrict__ ent, int n, int64_t item) {
