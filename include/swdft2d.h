@@ -35,8 +35,9 @@
  * Errors: every call returns a swdft_status; nothing aborts, exits or throws across the
  * ABI.  Argument checks happen before any CUDA call.  A CUDA launch or copy failure
  * returns SWDFT_ERR_CUDA; asynchronous faults surface at the next synchronising call.
- * The only device-side waits are the tensor-core kernels' mbarrier waits; each gives up
- * after a bounded number of polls and records it (see swdft2d_check_device).
+ * The only device-side waits are the tensor-core kernels' mbarrier waits (and the one of
+ * swdft2d_selftest_wait_timeout); each gives up after a bounded number of polls and records
+ * it (see swdft2d_check_device).
  *
  * Threads and streams: a plan is immutable after swdft2d_plan except for its tuning
  * state, graph and staging buffers; do not execute one plan on two streams at once.
@@ -59,10 +60,10 @@ typedef enum {
     SWDFT_ERR_NOT_POW2 = -2,          /* n0 or n1 is neither a power of two (Sec. 4.2's radix-2
                                        * tree) nor a power of three (ternary trees) */
     SWDFT_ERR_WINDOW_TOO_LARGE = -3,  /* n_i > N_i: no window position exists */
-    SWDFT_ERR_UNSUPPORTED = -4,       /* valid request this build does not implement */
+    SWDFT_ERR_UNSUPPORTED = -4,       /* valid request the library does not implement */
     SWDFT_ERR_OOM = -5,               /* host or device allocation of plan-owned memory failed */
     SWDFT_ERR_CUDA = -6,              /* a CUDA runtime call failed (launch, copy, graph) */
-    SWDFT_ERR_DEVICE_TIMEOUT = -7,    /* reserved: a bounded device wait ran out */
+    SWDFT_ERR_DEVICE_TIMEOUT = -7,    /* a bounded device wait ran out (swdft2d_check_device) */
     SWDFT_ERR_WORKSPACE = -8          /* workspace pointer null or misaligned while size > 0 */
 } swdft_status;
 
@@ -112,7 +113,7 @@ typedef struct {
 /* Create a plan for `batch` arrays (Section 4.1's problem for each).  Host work only:
  * validates every shape (SWDFT_ERR_NOT_POW2 / WINDOW_TOO_LARGE / INVALID_ARG), builds the
  * twiddle vectors Omega^0, Omega^1 of Section 4.2 in FP64 and rounds them to FP32, and
- * picks kernels.  SWDFT_ERR_UNSUPPORTED for an algorithm or window size this build lacks
+ * picks kernels.  SWDFT_ERR_UNSUPPORTED for an algorithm or window size the library lacks
  * (tree: n_i <= 64, or 3, 9, 27; tensor-core forms: powers of two with 16 <= n0 <= 64 and
  * 8 <= n1 <= 64, no persistent batch; ternary windows: tree only, no persistent batch, no
  * adjoint).  *plan is NULL on any error. */
@@ -204,6 +205,23 @@ swdft_status swdft2d_execute_static_scratch(const void *d_in, int64_t N0, int64_
  * incomplete); SWDFT_OK otherwise.  Reads and resets the library's device status word
  * (synchronous copy).  SWDFT_ERR_CUDA if the read fails. */
 swdft_status swdft2d_check_device(void);
+
+/* Self-test of that time-out path: enqueues on `stream` one block whose thread waits on a
+ * shared-memory mbarrier that nothing arrives on, for at most `polls` polls (1..4096; each
+ * suspends the thread for at most about 1 ms), then records the time-out in the device
+ * status word exactly as the tensor-core kernels do, so that the next swdft2d_check_device
+ * returns SWDFT_ERR_DEVICE_TIMEOUT.  Nothing faults and the context stays usable.
+ * SWDFT_ERR_INVALID_ARG for polls out of range (checked before any CUDA call). */
+swdft_status swdft2d_selftest_wait_timeout(int32_t polls, void *stream);
+
+/* Fault injection for tests: the library's next `after` allocations succeed and every later
+ * one fails with SWDFT_ERR_OOM, until a call with after < 0 turns injection off (the
+ * default).  Counted allocations: plan and stream objects (host), a persistent plan's
+ * descriptor tables (pinned host and device) and the device buffers of
+ * swdft2d_execute_host.  Process-wide (one atomic counter).  A call that fails this way
+ * keeps what it did allocate, so repeating it once injection is off completes it.  Always
+ * returns SWDFT_OK. */
+swdft_status swdft2d_inject_alloc_failure(int64_t after);
 
 /* Free the plan and everything it owns.  NULL is accepted. */
 swdft_status swdft2d_destroy(swdft2d_plan_t plan);

@@ -38,7 +38,7 @@ EXPORTS = (
     "swdft2d_execute", "swdft2d_execute_adjoint", "swdft2d_execute_host", "swdft2d_autotune",
     "swdft2d_launch_count", "swdft2d_destroy", "swdft2d_status_string", "swdft2d_version",
     "swdft2d_execute_stage", "swdft2d_set_tree_config", "swdft2d_execute_static_scratch",
-    "swdft2d_check_device",
+    "swdft2d_check_device", "swdft2d_inject_alloc_failure", "swdft2d_selftest_wait_timeout",
     "swdftkd_plan", "swdftkd_output_shape", "swdftkd_workspace_size", "swdftkd_launch_count",
     "swdftkd_execute", "swdftkd_destroy",
     "swdft2d_stream_create", "swdft2d_stream_state_size", "swdft2d_stream_push",
@@ -86,6 +86,8 @@ def _load() -> ctypes.CDLL:
         "swdft2d_set_tree_config": ([P, i32, i32, i64, i32, i64, i32, i32], i32),
         "swdft2d_execute_static_scratch": ([P, i64, i64, i64, i32, i32, i32, i32, P, P], i32),
         "swdft2d_check_device": ([], i32),
+        "swdft2d_inject_alloc_failure": ([i64], i32),
+        "swdft2d_selftest_wait_timeout": ([i32, P], i32),
         "swdft2d_destroy": ([P], i32),
         "swdft2d_status_string": ([i32], ctypes.c_char_p),
         "swdft2d_version": ([], i32),
@@ -220,6 +222,19 @@ class Plan:
 def check_device() -> int:
     """SWDFT_OK, or ERR_DEVICE_TIMEOUT if a bounded device wait gave up since the last call."""
     return int(lib.swdft2d_check_device())
+
+
+def selftest_wait_timeout(polls: int, stream: int = 0) -> None:
+    """Enqueue one block whose bounded device wait runs out on purpose (at most `polls` polls
+    of about 1 ms); the next check_device() then reports ERR_DEVICE_TIMEOUT."""
+    _check(lib.swdft2d_selftest_wait_timeout(int(polls), ctypes.c_void_p(stream or None)),
+           "swdft2d_selftest_wait_timeout")
+
+
+def inject_alloc_failure(after: int) -> None:
+    """Let the library's next `after` allocations succeed and fail every later one with
+    SWDFT_ERR_OOM; after < 0 turns injection off."""
+    _check(lib.swdft2d_inject_alloc_failure(int(after)), "swdft2d_inject_alloc_failure")
 
 
 def version() -> int:

@@ -4,6 +4,7 @@
 #include "swdft2d.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -13,6 +14,18 @@
 #include <vector>
 
 #include "swdft_internal.h"
+
+namespace swdft {
+// allocations that may still succeed before injected failures; -1: no injection
+static std::atomic<int64_t> g_alloc_budget{-1};
+
+bool alloc_fails() {
+    int64_t v = g_alloc_budget.load(std::memory_order_relaxed);
+    while (v > 0)
+        if (g_alloc_budget.compare_exchange_weak(v, v - 1, std::memory_order_relaxed)) return false;
+    return v == 0;
+}
+}  // namespace swdft
 
 using namespace swdft;
 
@@ -257,12 +270,13 @@ swdft_status configure(swdft2d_plan_t plan) {
     if (plan->flags & SWDFT_FLAG_PERSISTENT) {
         const size_t n = plan->arrays.size();
         plan->desc_bytes = sizeof(BatchImage) * n + 3 * sizeof(BatchClassEntry) * n;
-        if (!plan->desc_host &&
-            cudaHostAlloc((void **)&plan->desc_host, plan->desc_bytes, cudaHostAllocDefault) != cudaSuccess)
+        if (!plan->desc_host && (alloc_fails() || cudaHostAlloc((void **)&plan->desc_host, plan->desc_bytes,
+                                                                cudaHostAllocDefault) != cudaSuccess))
             return SWDFT_ERR_OOM;
-        if (!plan->desc_dev && cudaMalloc((void **)&plan->desc_dev, plan->desc_bytes) != cudaSuccess)
+        if (!plan->desc_dev && (alloc_fails() || cudaMalloc((void **)&plan->desc_dev, plan->desc_bytes) != cudaSuccess))
             return SWDFT_ERR_OOM;
-        if (!plan->desc_graph && cudaMalloc((void **)&plan->desc_graph, plan->desc_bytes) != cudaSuccess)
+        if (!plan->desc_graph &&
+            (alloc_fails() || cudaMalloc((void **)&plan->desc_graph, plan->desc_bytes) != cudaSuccess))
             return SWDFT_ERR_OOM;
         if (!plan->desc_uploaded && cudaEventCreateWithFlags(&plan->desc_uploaded, cudaEventDisableTiming) != cudaSuccess)
             return SWDFT_ERR_CUDA;
@@ -736,7 +750,7 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
     }
     if (algo >= SWDFT_ALGO_TC_BF16X3 && (flags & SWDFT_FLAG_PERSISTENT)) return SWDFT_ERR_UNSUPPORTED;
 
-    swdft2d_plan_s *p = new (std::nothrow) swdft2d_plan_s();
+    swdft2d_plan_s *p = alloc_fails() ? nullptr : new (std::nothrow) swdft2d_plan_s();
     if (!p) return SWDFT_ERR_OOM;
     p->arrays = std::move(arrays);
     p->norm = norm;
@@ -1047,10 +1061,11 @@ swdft_status swdft2d_execute_host(swdft2d_plan_t plan, const void *const *h_in,
             ws_max = std::max(ws_max, align_up(a.ws_bytes_plan(br)));
         }
         // created once, as in configure: a failed attempt keeps what it made for the next
-        if (!plan->io_in && cudaMalloc(&plan->io_in, in_max) != cudaSuccess) return SWDFT_ERR_OOM;
-        if (!plan->io_ws && cudaMalloc(&plan->io_ws, ws_max) != cudaSuccess) return SWDFT_ERR_OOM;
+        if (!plan->io_in && (alloc_fails() || cudaMalloc(&plan->io_in, in_max) != cudaSuccess)) return SWDFT_ERR_OOM;
+        if (!plan->io_ws && (alloc_fails() || cudaMalloc(&plan->io_ws, ws_max) != cudaSuccess)) return SWDFT_ERR_OOM;
         for (int k = 0; k < 2; ++k)
-            if (!plan->io_out[k] && cudaMalloc(&plan->io_out[k], out_max) != cudaSuccess) return SWDFT_ERR_OOM;
+            if (!plan->io_out[k] && (alloc_fails() || cudaMalloc(&plan->io_out[k], out_max) != cudaSuccess))
+                return SWDFT_ERR_OOM;
         if (!plan->io_copy && cudaStreamCreateWithFlags(&plan->io_copy, cudaStreamNonBlocking) != cudaSuccess)
             return SWDFT_ERR_CUDA;
         for (int k = 0; k < 2; ++k) {
@@ -1231,6 +1246,18 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
     cudaEventDestroy(e1);
     destroy_graph(plan->graph);
     return SWDFT_OK;
+}
+
+swdft_status swdft2d_inject_alloc_failure(int64_t after) {
+    swdft::g_alloc_budget.store(after < 0 ? -1 : after, std::memory_order_relaxed);
+    return SWDFT_OK;
+}
+
+swdft_status swdft2d_selftest_wait_timeout(int32_t polls, void *stream) {
+    if (polls < 1 || polls > 4096) return SWDFT_ERR_INVALID_ARG;
+    return launch_wait_timeout_probe((uint32_t)polls, static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? SWDFT_OK
+               : SWDFT_ERR_CUDA;
 }
 
 swdft_status swdft2d_check_device(void) {

@@ -182,7 +182,7 @@ swdft_status swdftkd_plan(swdftkd_plan_t *out, const swdftkd_shape *shape, int32
         if (shape->n[d] > kMaxN) return SWDFT_ERR_UNSUPPORTED;
     if (flags != 0) return SWDFT_ERR_UNSUPPORTED;
 
-    swdftkd_plan_t p = new (std::nothrow) swdftkd_plan_s;
+    swdftkd_plan_t p = alloc_fails() ? nullptr : new (std::nothrow) swdftkd_plan_s;
     if (!p) return SWDFT_ERR_OOM;
     p->k = K;
     p->dtype = shape->dtype;

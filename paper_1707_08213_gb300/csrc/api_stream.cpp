@@ -67,7 +67,7 @@ swdft_status swdft2d_stream_create(swdft2d_stream_t *out, int64_t N1, int32_t n0
     if (n1 > N1) return SWDFT_ERR_WINDOW_TOO_LARGE;
     if (n0 > kMaxN || n1 > kMaxN) return SWDFT_ERR_UNSUPPORTED;
     if (N1 - n1 + 1 > INT32_MAX || max_rows > INT32_MAX / 2) return SWDFT_ERR_UNSUPPORTED;
-    swdft2d_stream_t s = new (std::nothrow) swdft2d_stream_s;
+    swdft2d_stream_t s = alloc_fails() ? nullptr : new (std::nothrow) swdft2d_stream_s;
     if (!s) return SWDFT_ERR_OOM;
     s->N1 = N1;
     s->P1 = N1 - n1 + 1;

@@ -9,6 +9,11 @@
 
 namespace swdft {
 
+// Fault injection (swdft2d_inject_alloc_failure): true when the allocation about to be made
+// must fail.  Every allocation the library makes asks first, host and device alike.
+bool alloc_fails();
+
+
 // Tree kernels keep every butterfly level of one window axis in registers; they are built
 // for window lengths up to 2^kMaxLog2 along each axis.
 constexpr int kMaxLog2 = 6;
@@ -96,6 +101,8 @@ struct TcRowArgs {
 cudaError_t launch_tc_row(const TcRowArgs &a, cudaStream_t s);
 // Device error word of the tensor-core kernels (1 = a bounded wait timed out).
 cudaError_t tc_status(int *status, bool reset);
+// One block whose bounded mbarrier wait runs out on purpose (sets that word; no fault).
+cudaError_t launch_wait_timeout_probe(uint32_t polls, cudaStream_t s);
 
 // One array of a window-exponent group in a persistent batch launch: item0 = the group's
 // first tile of this array (tiles are numbered array by array within the group).

@@ -279,3 +279,38 @@ def test_persistent_batch_launches_one_kernel_per_window_class(nat):
     # at most a row and a column kernel, or one fused kernel, per distinct window shape
     assert 1 <= n_pers <= 2 * len(windows)
     assert nat.Plan(shapes).launch_count() >= len(shapes)
+
+
+def test_injected_allocation_failures(nat):
+    """swdft2d_inject_alloc_failure: with no allocation left every plan, kD plan and stream
+    creation fails with SWDFT_ERR_OOM and leaves no handle; with one left the first creation
+    succeeds and the next fails; after < 0 restores normal behaviour."""
+    try:
+        nat.inject_alloc_failure(0)
+        st, h = nat.raw_plan([shp(16, 16, 4, 4)], 0, 0, 1, 0)
+        assert st == -5 and h is None
+        with pytest.raises(nat.SwdftError) as e:
+            nat.PlanKD((8, 8, 8), (2, 2, 2))
+        assert e.value.status == -5
+        st, h = nat.raw_stream(16, 4, 4, 0, 0, 1)
+        assert st == -5 and h is None
+        nat.inject_alloc_failure(1)
+        p = nat.Plan([shp(16, 16, 4, 4)])
+        with pytest.raises(nat.SwdftError) as e:
+            nat.Plan([shp(16, 16, 4, 4)])
+        assert e.value.status == -5
+        assert p.output_shape(0) == (13, 13, 4, 4)
+        # invalid arguments are still reported as such, before any allocation
+        st, _ = nat.raw_plan([shp(16, 16, 5, 4)], 0, 0, 1, 0)
+        assert st == -2
+    finally:
+        nat.inject_alloc_failure(-1)
+    assert nat.Plan([shp(16, 16, 4, 4)]).output_shape(0) == (13, 13, 4, 4)
+    assert nat.StreamPlan(16, 4, 4).state_size() > 0
+
+
+def test_selftest_wait_timeout_checks_its_argument_first(nat):
+    for polls in (0, -3, 4097):
+        with pytest.raises(nat.SwdftError) as e:
+            nat.selftest_wait_timeout(polls)
+        assert e.value.status == -1
