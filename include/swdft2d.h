@@ -202,15 +202,15 @@ swdft_status swdft2d_execute_static_scratch(const void *d_in, int64_t N0, int64_
 
 /* Device-side health of the current device: SWDFT_ERR_DEVICE_TIMEOUT if, since the last
  * call, a tensor-core kernel gave up on one of its bounded waits (its outputs are then
- * incomplete); SWDFT_OK otherwise.  Reads and resets the library's device status word
- * (synchronous copy).  SWDFT_ERR_CUDA if the read fails. */
+ * incomplete) or swdft2d_selftest_wait_timeout ran; SWDFT_OK otherwise.  Reads and resets
+ * the library's device status words (synchronous copies).  SWDFT_ERR_CUDA if a read fails. */
 swdft_status swdft2d_check_device(void);
 
 /* Self-test of that time-out path: enqueues on `stream` one block whose thread waits on a
  * shared-memory mbarrier that nothing arrives on, for at most `polls` polls (1..4096; each
- * suspends the thread for at most about 1 ms), then records the time-out in the device
- * status word exactly as the tensor-core kernels do, so that the next swdft2d_check_device
- * returns SWDFT_ERR_DEVICE_TIMEOUT.  Nothing faults and the context stays usable.
+ * suspends the thread for at most about 1 ms), then records the time-out in a device
+ * status word of its own, read and reset with the tensor-core kernels' word by
+ * swdft2d_check_device, which then returns SWDFT_ERR_DEVICE_TIMEOUT.  Nothing faults and the context stays usable.
  * SWDFT_ERR_INVALID_ARG for polls out of range (checked before any CUDA call). */
 swdft_status swdft2d_selftest_wait_timeout(int32_t polls, void *stream);
 

@@ -1261,9 +1261,10 @@ swdft_status swdft2d_selftest_wait_timeout(int32_t polls, void *stream) {
 }
 
 swdft_status swdft2d_check_device(void) {
-    int status = 0;
-    if (tc_status(&status, true) != cudaSuccess) return SWDFT_ERR_CUDA;
-    return status ? SWDFT_ERR_DEVICE_TIMEOUT : SWDFT_OK;
+    int status = 0, probe = 0;
+    if (tc_status(&status, true) != cudaSuccess || probe_status(&probe, true) != cudaSuccess)
+        return SWDFT_ERR_CUDA;
+    return (status || probe) ? SWDFT_ERR_DEVICE_TIMEOUT : SWDFT_OK;
 }
 
 swdft_status swdft2d_destroy(swdft2d_plan_t plan) {

@@ -101,8 +101,10 @@ struct TcRowArgs {
 cudaError_t launch_tc_row(const TcRowArgs &a, cudaStream_t s);
 // Device error word of the tensor-core kernels (1 = a bounded wait timed out).
 cudaError_t tc_status(int *status, bool reset);
-// One block whose bounded mbarrier wait runs out on purpose (sets that word; no fault).
+// One block whose bounded mbarrier wait runs out on purpose (selftest.cu; no fault), and its
+// own device word (1 = that wait timed out).
 cudaError_t launch_wait_timeout_probe(uint32_t polls, cudaStream_t s);
+cudaError_t probe_status(int *status, bool reset);
 
 // One array of a window-exponent group in a persistent batch launch: item0 = the group's
 // first tile of this array (tiles are numbered array by array within the group).

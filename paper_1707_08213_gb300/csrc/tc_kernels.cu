@@ -684,23 +684,6 @@ cudaError_t launch_tc_row(const TcRowArgs &a, cudaStream_t s) {
     }
 }
 
-// Self-test of the time-out path: one thread waits on a shared-memory mbarrier that nothing
-// arrives on, at most `polls` polls, and records the time-out as the tensor-core kernels do.
-__global__ void __launch_bounds__(32) wait_timeout_probe(uint32_t polls) {
-    __shared__ __align__(8) uint64_t bar;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        fence_barrier_init();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && !mbar_wait(&bar, 0, polls)) atomicExch(&g_tc_status, 1);
-}
-
-cudaError_t launch_wait_timeout_probe(uint32_t polls, cudaStream_t s) {
-    wait_timeout_probe<<<1, 32, 0, s>>>(polls);
-    return cudaGetLastError();
-}
-
 cudaError_t tc_status(int *status, bool reset) {
     cudaError_t e = cudaMemcpyFromSymbol(status, g_tc_status, sizeof(int));
     if (e == cudaSuccess && reset) {
