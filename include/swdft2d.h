@@ -155,11 +155,27 @@ swdft_status swdft2d_execute_host(swdft2d_plan_t plan, const void *const *h_in,
 
 /* Time every candidate kernel configuration of this plan on the given buffers (CUDA
  * events on `stream`) and keep the fastest; the choice is reused by later executes and
- * recorded in the cache file named by the SWDFT_TUNE_CACHE environment variable, if set.
+ * recorded in the cache file named by the SWDFT_TUNE_CACHE environment variable, if set
+ * (see the tuning cache below).
  * Arrays of the same shape, band and algorithm setting are timed once (the first of them)
  * and share its choice. */
 swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out,
                               void *d_workspace, void *stream);
+
+/* Tuning cache.  With SWDFT_TUNE_CACHE set, swdft2d_autotune first applies the records that
+ * file already holds for this GPU (below) and times only the arrays without one; each array
+ * it times appends one line, a JSON object with the GPU name, the array (N0, N1, ld, n0, n1,
+ * dtype, q_begin, q_end, whether the plan's algorithm is SWDFT_ALGO_AUTO), the choice
+ * (algorithm, fused, row_B, row_chunk, col_B, col_chunk, col_groups) and its time in ms.
+ *
+ * swdft2d_load_tuning applies such records to a plan without timing anything: each array
+ * takes the last record of `path` made on the GPU named `gpu_name` (NULL: the current
+ * device's name) for the same array whose choice the plan can run.  *applied (may be NULL)
+ * receives the number of arrays set.  A missing file or lines in another layout apply
+ * nothing.  Host only when gpu_name is given; SWDFT_ERR_CUDA if the device name is needed
+ * and cannot be read. */
+swdft_status swdft2d_load_tuning(swdft2d_plan_t plan, const char *path, const char *gpu_name,
+                                 int32_t *applied);
 
 /* One pass of the forward tree only, for profiling: stage 0 runs the row levels
  * (Eq. rowfswft2d) of every array into the workspace, stage 1 the column levels

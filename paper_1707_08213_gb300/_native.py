@@ -37,6 +37,7 @@ EXPORTS = (
     "swdft2d_plan", "swdft2d_output_shape", "swdft2d_workspace_size", "swdft2d_get_algo",
     "swdft2d_execute", "swdft2d_execute_adjoint", "swdft2d_execute_host", "swdft2d_autotune",
     "swdft2d_launch_count", "swdft2d_destroy", "swdft2d_status_string", "swdft2d_version",
+    "swdft2d_load_tuning",
     "swdft2d_execute_stage", "swdft2d_set_tree_config", "swdft2d_execute_static_scratch",
     "swdft2d_check_device", "swdft2d_inject_alloc_failure", "swdft2d_selftest_wait_timeout",
     "swdftkd_plan", "swdftkd_output_shape", "swdftkd_workspace_size", "swdftkd_launch_count",
@@ -82,6 +83,7 @@ def _load() -> ctypes.CDLL:
         "swdft2d_execute_host": ([P, PP, PP, P], i32),
         "swdft2d_autotune": ([P, PP, PP, P, P], i32),
         "swdft2d_launch_count": ([P, i32, ctypes.POINTER(i32)], i32),
+        "swdft2d_load_tuning": ([P, ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(i32)], i32),
         "swdft2d_execute_stage": ([P, i32, PP, PP, P, P], i32),
         "swdft2d_set_tree_config": ([P, i32, i32, i64, i32, i64, i32, i32], i32),
         "swdft2d_execute_static_scratch": ([P, i64, i64, i64, i32, i32, i32, i32, P, P], i32),
@@ -174,6 +176,15 @@ class Plan:
         _check(lib.swdft2d_launch_count(self.handle, int(adjoint), ctypes.byref(v)),
                "swdft2d_launch_count")
         return int(v.value)
+
+    def load_tuning(self, path: str, gpu_name: str = None) -> int:
+        """Apply the tuning-cache records of `path` made on `gpu_name` (None: this device);
+        returns the number of arrays set."""
+        n = ctypes.c_int32()
+        _check(lib.swdft2d_load_tuning(self.handle, str(path).encode(),
+                                       None if gpu_name is None else gpu_name.encode(), ctypes.byref(n)),
+               "swdft2d_load_tuning")
+        return int(n.value)
 
     def execute(self, in_ptrs, out_ptrs, ws_ptr: int, stream: int = 0):
         _check(lib.swdft2d_execute(self.handle, _ptr_array(in_ptrs), _ptr_array(out_ptrs),

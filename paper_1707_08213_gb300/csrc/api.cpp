@@ -670,6 +670,96 @@ void destroy_graph(GraphCache &g) {
     g.stream = nullptr;
 }
 
+// The autotuner's record of one array: one JSON object per line of the tuning cache, read
+// back by swdft2d_load_tuning with the same layout (GPU name, array, choice, time).
+#define SWDFT_TUNE_FIELDS(GPU, MS)                                                                \
+    "{\"gpu\": \"" GPU "\", \"N0\": %lld, \"N1\": %lld, \"ld\": %lld, \"n0\": %d, \"n1\": %d, "        \
+    "\"dtype\": %d, \"q_begin\": %lld, \"q_end\": %lld, \"auto\": %d, \"algo\": %d, \"fused\": %d, "   \
+    "\"row_B\": %d, \"row_chunk\": %lld, \"col_B\": %d, \"col_chunk\": %lld, \"col_groups\": %d, "     \
+    "\"ms\": " MS "}"
+
+struct TuneRecord {
+    char gpu[128];
+    long long N0, N1, ld, q_begin, q_end, row_chunk, col_chunk;
+    int n0, n1, dtype, autoflag, algo, fused, row_B, col_B, col_groups;
+    double ms;
+};
+
+bool parse_tune_record(const char *line, TuneRecord *r) {
+    const int got = std::sscanf(line, SWDFT_TUNE_FIELDS("%127[^\"]", "%lf"), r->gpu, &r->N0, &r->N1, &r->ld,
+                                &r->n0, &r->n1, &r->dtype, &r->q_begin, &r->q_end, &r->autoflag, &r->algo,
+                                &r->fused, &r->row_B, &r->row_chunk, &r->col_B, &r->col_chunk, &r->col_groups,
+                                &r->ms);
+    return got == 18;
+}
+
+void write_tune_record(FILE *f, const char *gpu, const ArrayPlan &a, const TreeConfig &c, double ms) {
+    std::fprintf(f, SWDFT_TUNE_FIELDS("%s", "%.6f") "\n", gpu, (long long)a.N0, (long long)a.N1, (long long)a.ld,
+                 a.n0, a.n1, a.dtype, (long long)a.q_begin, (long long)a.q_end, a.algo_auto ? 1 : 0, a.algo,
+                 c.fused ? 1 : 0, c.row_B, (long long)c.row_chunk, c.col_B, (long long)c.col_chunk, c.col_groups,
+                 ms);
+}
+
+// A record for this array (same GPU, shape, row stride, band, dtype and algorithm setting)
+// whose choice is one the plan can run: its configuration and algorithm.
+bool tune_record_applies(const TuneRecord &r, const char *gpu, const ArrayPlan &a, TreeConfig *c, int *algo) {
+    if (std::strcmp(r.gpu, gpu) != 0 || r.N0 != a.N0 || r.N1 != a.N1 || r.ld != a.ld || r.n0 != a.n0 ||
+        r.n1 != a.n1 || r.dtype != a.dtype || r.q_begin != a.q_begin || r.q_end != a.q_end ||
+        (r.autoflag != 0) != a.algo_auto || a.ternary())
+        return false;
+    if (a.algo_auto ? !(r.algo == SWDFT_ALGO_TREE_F32 || (r.algo == SWDFT_ALGO_TC_BF16X3 && a.tc_eligible()))
+                    : r.algo != a.algo)
+        return false;
+    if (r.row_B < 0 || r.row_B > std::min(a.m1, 3) || r.col_B < 0 || r.col_B > std::min(a.m0, 3) ||
+        r.row_chunk < 0 || r.col_chunk < 0 || r.col_groups < 1 || r.col_groups > 8 || r.fused < 0 || r.fused > 1 ||
+        (r.fused == 1 && a.m1 > 5))
+        return false;
+    c->fused = r.fused == 1;
+    c->row_B = r.row_B;
+    c->row_chunk = r.row_chunk;
+    c->col_B = r.col_B;
+    c->col_chunk = r.col_chunk;
+    c->col_groups = r.col_groups;
+    *algo = r.algo;
+    return true;
+}
+
+// Apply the last applicable record of `path` to every array; loaded[i] = 1 for those set.
+int load_tuning(swdft2d_plan_t plan, const char *path, const char *gpu, std::vector<char> &loaded) {
+    loaded.assign(plan->arrays.size(), 0);
+    FILE *f = std::fopen(path, "r");
+    if (!f) return 0;
+    std::vector<TreeConfig> cfg(plan->arrays.size());
+    std::vector<int> algo(plan->arrays.size(), 0);
+    char line[1024];
+    TuneRecord r;
+    while (std::fgets(line, sizeof line, f)) {
+        if (!parse_tune_record(line, &r)) continue;
+        for (size_t i = 0; i < plan->arrays.size(); ++i)
+            if (tune_record_applies(r, gpu, plan->arrays[i], &cfg[i], &algo[i])) loaded[i] = 1;
+    }
+    std::fclose(f);
+    int n = 0;
+    for (size_t i = 0; i < plan->arrays.size(); ++i) {
+        if (!loaded[i]) continue;
+        ArrayPlan &a = plan->arrays[i];
+        a.cfg = cfg[i];
+        a.algo = algo[i];
+        a.tuned = true;
+        ++n;
+    }
+    if (n > 0) destroy_graph(plan->graph);
+    return n;
+}
+
+bool device_name(char *buf, size_t len) {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return false;
+    std::snprintf(buf, len, "%s", prop.name);
+    return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1112,10 +1202,19 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
     if (st != SWDFT_OK) return st;
     if ((st = configure(plan)) != SWDFT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // arrays with a record in the tuning cache for this GPU take it without timing
+    const char *cache = std::getenv("SWDFT_TUNE_CACHE");
+    char gpu[256] = "unknown";
+    std::vector<char> loaded(plan->arrays.size(), 0);
+    if (cache) {
+        if (!device_name(gpu, sizeof gpu)) return SWDFT_ERR_CUDA;
+        load_tuning(plan, cache, gpu, loaded);
+    }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SWDFT_ERR_CUDA;
     for (size_t i = 0; i < plan->arrays.size(); ++i) {
         ArrayPlan &a = plan->arrays[i];
+        if (loaded[i]) continue;
         // an array of the same shape, band and form tuned earlier in this call: same choice
         bool copied = false;
         for (size_t j = 0; j < i && !copied; ++j) {
@@ -1229,15 +1328,9 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
                 return SWDFT_ERR_CUDA;
             }
         }
-        if (const char *path = std::getenv("SWDFT_TUNE_CACHE")) {
-            if (FILE *f = std::fopen(path, "a")) {
-                std::fprintf(f,
-                             "{\"N0\": %lld, \"N1\": %lld, \"n0\": %d, \"n1\": %d, \"dtype\": %d, "
-                             "\"algo\": %d, \"fused\": %d, \"row_B\": %d, \"row_chunk\": %lld, \"col_B\": %d, "
-                             "\"col_chunk\": %lld, \"col_groups\": %d, \"ms\": %.6f}\n",
-                             (long long)a.N0, (long long)a.N1, a.n0, a.n1, a.dtype, a.algo, (int)best_c.fused,
-                             best_c.row_B, (long long)best_c.row_chunk, best_c.col_B,
-                             (long long)best_c.col_chunk, best_c.col_groups, best);
+        if (cache) {
+            if (FILE *f = std::fopen(cache, "a")) {
+                write_tune_record(f, gpu, a, best_c, best);
                 std::fclose(f);
             }
         }
@@ -1258,6 +1351,22 @@ swdft_status swdft2d_selftest_wait_timeout(int32_t polls, void *stream) {
     return launch_wait_timeout_probe((uint32_t)polls, static_cast<cudaStream_t>(stream)) == cudaSuccess
                ? SWDFT_OK
                : SWDFT_ERR_CUDA;
+}
+
+swdft_status swdft2d_load_tuning(swdft2d_plan_t plan, const char *path, const char *gpu_name,
+                                 int32_t *applied) {
+    if (applied) *applied = 0;
+    if (!plan || !path) return SWDFT_ERR_INVALID_ARG;
+    char gpu[256];
+    if (gpu_name) {
+        std::snprintf(gpu, sizeof gpu, "%s", gpu_name);
+    } else if (!device_name(gpu, sizeof gpu)) {
+        return SWDFT_ERR_CUDA;
+    }
+    std::vector<char> loaded;
+    const int n = load_tuning(plan, path, gpu, loaded);
+    if (applied) *applied = n;
+    return SWDFT_OK;
 }
 
 swdft_status swdft2d_check_device(void) {

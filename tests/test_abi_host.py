@@ -314,3 +314,48 @@ def test_selftest_wait_timeout_checks_its_argument_first(nat):
         with pytest.raises(nat.SwdftError) as e:
             nat.selftest_wait_timeout(polls)
         assert e.value.status == -1
+
+
+def _tune_line(gpu, N0, N1, n0, n1, algo=1, auto=0, fused=0, row_B=2, row_chunk=0, col_B=2, col_chunk=0,
+               col_groups=1, dtype=0, ld=None, q_begin=0, q_end=None):
+    """One tuning-cache record in the layout swdft2d_autotune writes."""
+    rec = {"gpu": gpu, "N0": N0, "N1": N1, "ld": N1 if ld is None else ld, "n0": n0, "n1": n1,
+           "dtype": dtype, "q_begin": q_begin, "q_end": N0 - n0 + 1 if q_end is None else q_end,
+           "auto": auto, "algo": algo, "fused": fused, "row_B": row_B, "row_chunk": row_chunk,
+           "col_B": col_B, "col_chunk": col_chunk, "col_groups": col_groups, "ms": 0.125}
+    return json.dumps(rec) + "\n"
+
+
+def test_load_tuning_applies_records_of_the_named_gpu(nat, tmp_path):
+    """swdft2d_load_tuning on the host: the last applicable record for the named GPU sets the
+    array's choice (here the fused form: one launch instead of two, and the tensor-core form
+    for an AUTO plan); other GPUs, other arrays, choices the plan cannot run and lines in
+    another layout are ignored."""
+    cache = tmp_path / "tune.jsonl"
+    assert nat.Plan([shp(300, 300, 16, 16)]).load_tuning(str(tmp_path / "missing.jsonl"), "G") == 0
+    cache.write_text(
+        "not a record\n" +
+        _tune_line("Other GPU", 300, 300, 16, 16, fused=1) +
+        _tune_line("Test GPU", 300, 300, 16, 16, fused=0) +
+        _tune_line("Test GPU", 300, 300, 16, 16, fused=1, row_chunk=64, col_chunk=32) +   # last wins
+        _tune_line("Test GPU", 300, 300, 16, 16, fused=1, row_B=7) +                      # invalid split
+        _tune_line("Test GPU", 300, 301, 16, 16, fused=1) +                               # another array
+        _tune_line("Test GPU", 300, 300, 16, 16, algo=2, auto=1))                         # AUTO plans only
+    p = nat.Plan([shp(300, 300, 16, 16)])
+    assert p.launch_count() == 2
+    assert p.load_tuning(str(cache), "Other GPU") == 1 and p.launch_count() == 1
+    p = nat.Plan([shp(300, 300, 16, 16)])
+    assert p.load_tuning(str(cache), "Another GPU") == 0 and p.launch_count() == 2
+    two = nat.Plan([shp(300, 300, 16, 16), shp(64, 64, 8, 8)])
+    assert two.load_tuning(str(cache), "Test GPU") == 1
+    assert two.launch_count() == 1 + 1  # the first fused now; the second (8x8) was fused already
+    auto = nat.Plan([shp(300, 300, 16, 16)], algo="auto")
+    assert auto.algo() == "tree"
+    assert auto.load_tuning(str(cache), "Test GPU") == 1 and auto.algo() == "tc_bf16x3"
+    band = nat.Plan([shp(300, 300, 16, 16, row_begin=10, row_end=50)])
+    assert band.load_tuning(str(cache), "Test GPU") == 0
+    import torch
+    if not torch.cuda.is_available():  # no device to take the GPU name from
+        with pytest.raises(nat.SwdftError) as e:
+            nat.Plan([shp(300, 300, 16, 16)]).load_tuning(str(cache))
+        assert e.value.status == -6

@@ -294,6 +294,35 @@ def test_autotune_times_each_shape_once(sw, tmp_path, monkeypatch):
         assert_close_to_oracle(a, x, s[2], s[3])
 
 
+def test_autotune_takes_this_gpus_cached_records(sw, tmp_path, monkeypatch):
+    """With SWDFT_TUNE_CACHE holding a record for this GPU and array, autotune applies it
+    without timing (nothing appended) and the plan makes the same choice; another GPU's
+    record is not applied."""
+    import json
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("SWDFT_TUNE_CACHE", str(cache))
+    x = workloads.random_array(660, 120, 100)
+    xd = torch.from_numpy(x).cuda()
+    t = sw.Transform([(120, 100, 16, 16, 0)], algo="auto")
+    t.autotune([xd])
+    first = cache.read_text()
+    assert len(first.strip().splitlines()) == 1
+    rec = json.loads(first)
+    assert rec["gpu"] == torch.cuda.get_device_name()
+    t2 = sw.Transform([(120, 100, 16, 16, 0)], algo="auto")
+    t2.autotune([xd])
+    assert cache.read_text() == first
+    assert t2.plan.algo() == t.plan.algo() and t2.plan.launch_count() == t.plan.launch_count()
+    a = t2.forward([xd])[0]
+    torch.cuda.synchronize()
+    assert_close_to_oracle(a, x, 16, 16)
+    rec["gpu"] = "another GPU"
+    other = tmp_path / "other.jsonl"
+    other.write_text(json.dumps(rec) + "\n")
+    assert sw.Transform([(120, 100, 16, 16, 0)], algo="auto").plan.load_tuning(str(other)) == 0
+    assert sw.Transform([(120, 100, 16, 16, 0)], algo="auto").plan.load_tuning(str(cache)) == 1
+
+
 @pytest.mark.parametrize("N0,N1,n0,n1", [(100, 100, 64, 64), (512, 512, 32, 32)])
 def test_autotune_chooses_tree_or_tensor_cores(sw, N0, N1, n0, n1, tmp_path, monkeypatch):
     """With algo="auto" the autotuner times the tuned tree against the split-bf16 tensor-core
