@@ -348,3 +348,30 @@ def test_autotune_chooses_tree_or_tensor_cores(sw, N0, N1, n0, n1, tmp_path, mon
     import json
     line = json.loads(cache.read_text().strip().splitlines()[-1])
     assert line["algo"] in (1, 2) and (line["algo"] == 2) == (t.plan.algo() == "tc_bf16x3")
+
+
+@pytest.mark.parametrize("N0,N1,n0,n1,cplx", [(40, 70, 8, 16, False), (36, 90, 4, 64, True),
+                                              (50, 45, 32, 2, False)])
+def test_row_pass_leaves_level_m1_of_every_tree(sw, N0, N1, n0, n1, cplx):
+    """The row levels alone (stage 0, Eq. rowfswft2d) leave in z level m1 of the tree at every
+    position whose row tree is complete: the oracle tree's level-m1 dump T[p0][p1][0][k1] at
+    p1 = q1 + n1 - 1 (the level invariant: the n1-point DFT of x[p0][p1-n1+1 .. p1]), per row
+    window within 1e-5 of its norm."""
+    x = workloads.random_array(700 + n1, N0, N1, complex_input=cplx)
+    t = sw.Transform([(N0, N1, n0, n1, _dt(x))])
+    t.plan.set_tree_config(0, 2, 0, 2, 0, 1, 0)  # two passes: z goes through the workspace
+    xd = torch.from_numpy(x).cuda()
+    out = t.empty_outputs()
+    t.plan.execute_stage(0, [xd.data_ptr()], [out[0].data_ptr()], t._ws_ptr,
+                         torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    P1, pad = N1 - n1 + 1, n0 // 2
+    z = t.workspace.view(torch.complex64)[pad * P1 * n1:(pad + N0) * P1 * n1].reshape(N0, P1, n1)
+    z = z.cpu().numpy()
+    _, _, dump = oracle.tree2d(x, n0, n1, norm="none", dump_level=int(math.log2(n1)))
+    ref = dump[:, n1 - 1:, :n1]
+    sq = np.abs(x) ** 2
+    c = np.concatenate([np.zeros((N0, 1)), np.cumsum(sq, axis=1)], axis=1)
+    norms = np.sqrt(c[:, n1:] - c[:, :P1])  # ||x[r][q1 .. q1+n1-1]||
+    err = (np.abs(z - ref).max(axis=2) / np.maximum(norms, 1e-30)).max()
+    assert err <= TOL, f"level m1 vs the oracle's dump: {err:.3e}"
