@@ -6,8 +6,6 @@ launch configurations forced so that trees are split over several threads and po
 chunks end in ragged tails; the full-size workloads are compared on seeded sampled windows
 plus every window of the four edges, and per-window Parseval over every window.
 """
-import math
-
 import numpy as np
 import pytest
 import torch
@@ -294,35 +292,6 @@ def test_autotune_times_each_shape_once(sw, tmp_path, monkeypatch):
         assert_close_to_oracle(a, x, s[2], s[3])
 
 
-def test_autotune_takes_this_gpus_cached_records(sw, tmp_path, monkeypatch):
-    """With SWDFT_TUNE_CACHE holding a record for this GPU and array, autotune applies it
-    without timing (nothing appended) and the plan makes the same choice; another GPU's
-    record is not applied."""
-    import json
-    cache = tmp_path / "tune.jsonl"
-    monkeypatch.setenv("SWDFT_TUNE_CACHE", str(cache))
-    x = workloads.random_array(660, 120, 100)
-    xd = torch.from_numpy(x).cuda()
-    t = sw.Transform([(120, 100, 16, 16, 0)], algo="auto")
-    t.autotune([xd])
-    first = cache.read_text()
-    assert len(first.strip().splitlines()) == 1
-    rec = json.loads(first)
-    assert rec["gpu"] == torch.cuda.get_device_name()
-    t2 = sw.Transform([(120, 100, 16, 16, 0)], algo="auto")
-    t2.autotune([xd])
-    assert cache.read_text() == first
-    assert t2.plan.algo() == t.plan.algo() and t2.plan.launch_count() == t.plan.launch_count()
-    a = t2.forward([xd])[0]
-    torch.cuda.synchronize()
-    assert_close_to_oracle(a, x, 16, 16)
-    rec["gpu"] = "another GPU"
-    other = tmp_path / "other.jsonl"
-    other.write_text(json.dumps(rec) + "\n")
-    assert sw.Transform([(120, 100, 16, 16, 0)], algo="auto").plan.load_tuning(str(other)) == 0
-    assert sw.Transform([(120, 100, 16, 16, 0)], algo="auto").plan.load_tuning(str(cache)) == 1
-
-
 @pytest.mark.parametrize("N0,N1,n0,n1", [(100, 100, 64, 64), (512, 512, 32, 32)])
 def test_autotune_chooses_tree_or_tensor_cores(sw, N0, N1, n0, n1, tmp_path, monkeypatch):
     """With algo="auto" the autotuner times the tuned tree against the split-bf16 tensor-core
@@ -348,30 +317,3 @@ def test_autotune_chooses_tree_or_tensor_cores(sw, N0, N1, n0, n1, tmp_path, mon
     import json
     line = json.loads(cache.read_text().strip().splitlines()[-1])
     assert line["algo"] in (1, 2) and (line["algo"] == 2) == (t.plan.algo() == "tc_bf16x3")
-
-
-@pytest.mark.parametrize("N0,N1,n0,n1,cplx", [(40, 70, 8, 16, False), (36, 90, 4, 64, True),
-                                              (50, 45, 32, 2, False)])
-def test_row_pass_leaves_level_m1_of_every_tree(sw, N0, N1, n0, n1, cplx):
-    """The row levels alone (stage 0, Eq. rowfswft2d) leave in z level m1 of the tree at every
-    position whose row tree is complete: the oracle tree's level-m1 dump T[p0][p1][0][k1] at
-    p1 = q1 + n1 - 1 (the level invariant: the n1-point DFT of x[p0][p1-n1+1 .. p1]), per row
-    window within 1e-5 of its norm."""
-    x = workloads.random_array(700 + n1, N0, N1, complex_input=cplx)
-    t = sw.Transform([(N0, N1, n0, n1, _dt(x))])
-    t.plan.set_tree_config(0, 2, 0, 2, 0, 1, 0)  # two passes: z goes through the workspace
-    xd = torch.from_numpy(x).cuda()
-    out = t.empty_outputs()
-    t.plan.execute_stage(0, [xd.data_ptr()], [out[0].data_ptr()], t._ws_ptr,
-                         torch.cuda.current_stream().cuda_stream)
-    torch.cuda.synchronize()
-    P1, pad = N1 - n1 + 1, n0 // 2
-    z = t.workspace.view(torch.complex64)[pad * P1 * n1:(pad + N0) * P1 * n1].reshape(N0, P1, n1)
-    z = z.cpu().numpy()
-    _, _, dump = oracle.tree2d(x, n0, n1, norm="none", dump_level=int(math.log2(n1)))
-    ref = dump[:, n1 - 1:, :n1]
-    sq = np.abs(x) ** 2
-    c = np.concatenate([np.zeros((N0, 1)), np.cumsum(sq, axis=1)], axis=1)
-    norms = np.sqrt(c[:, n1:] - c[:, :P1])  # ||x[r][q1 .. q1+n1-1]||
-    err = (np.abs(z - ref).max(axis=2) / np.maximum(norms, 1e-30)).max()
-    assert err <= TOL, f"level m1 vs the oracle's dump: {err:.3e}"
