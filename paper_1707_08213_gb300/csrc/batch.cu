@@ -21,37 +21,24 @@
 namespace swdft {
 
 // Launch choices the batch kernels use for a window side of 2^m (as the per-array defaults):
-// column tiles of 128 threads (256 for 64-point trees), row tiles of 128 threads.
-__host__ __device__ constexpr int bcol_B(int m0) { return m0 >= 6 ? 3 : (m0 < 2 ? m0 : 2); }
-__host__ __device__ constexpr int bcol_threads(int m0) { return m0 >= 6 ? 256 : 128; }
+// column tiles of 128 threads (256 for 64-point trees; bfu_B / bfu_threads / bfu_groups of
+// batch_fused.cuh, shared with the fused groups), row tiles of 128 threads.
 __host__ __device__ constexpr int brow_B(int m1) { return m1 >= 6 ? 2 : (m1 < 3 ? m1 : 3); }
 static constexpr int kRowThreads = 128;
-static_assert(32 * (1 << bcol_B(6)) == bcol_threads(6) && 32 * (1 << bcol_B(5)) * (4 >> bcol_B(5)) == 128,
+static_assert(32 * (1 << bfu_B(6)) * bfu_groups(6) == bfu_threads(6) &&
+                  32 * (1 << bfu_B(5)) * bfu_groups(5) == bfu_threads(5),
               "column tiles: 2^B residue warps x 32-channel groups fill the block");
 
 int batch_row_B(int m1) { return brow_B(m1); }
-int batch_col_B(int m0) { return bcol_B(m0); }
-int batch_col_groups(int m0) { return m0 >= 6 ? 1 : (4 >> bcol_B(m0)); }
-
-// The class's arrays in item order: item0 = first tile of the array within the class.
-__device__ __forceinline__ int find_entry(const BatchClassEntry *__restrict__ ent, int n, int64_t item) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(&ent[mid].item0) <= item)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
+int batch_col_B(int m0) { return bfu_B(m0); }
+int batch_col_groups(int m0) { return bfu_groups(m0); }
 
 template <int M1>
 __global__ void __launch_bounds__(kRowThreads)
     batch_row_kernel(const BatchImage *__restrict__ imgs, const BatchClassEntry *__restrict__ ent, int nent,
                      int64_t nitems, const __grid_constant__ Omega64 om) {
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const int e = find_entry(ent, nent, it);
+        const int e = bfu_find_entry(ent, nent, it);
         const BatchImage &d = imgs[__ldg(&ent[e].img)];
         const int64_t local = it - __ldg(&ent[e].item0);
         const int rb = (int)(local % d.row_blocks);
@@ -65,22 +52,20 @@ __global__ void __launch_bounds__(kRowThreads)
 }
 
 template <int M0>
-__global__ void __launch_bounds__(bcol_threads(M0), M0 >= 6 ? 2 : 4)
+__global__ void __launch_bounds__(bfu_threads(M0), M0 >= 6 ? 2 : 4)
     batch_col_kernel(const BatchImage *__restrict__ imgs, const BatchClassEntry *__restrict__ ent, int nent,
                      int64_t nitems, const __grid_constant__ Omega64 om) {
     extern __shared__ float2 ring[];
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const int e = find_entry(ent, nent, it);
+        const int e = bfu_find_entry(ent, nent, it);
         const BatchImage &d = imgs[__ldg(&ent[e].img)];
         const int64_t local = it - __ldg(&ent[e].item0);
         const int64_t cb = local % d.col_blocks;
         const int ck = (int)(local / d.col_blocks);
         const ColGeom g = d.col;
-        col_tile<M0, bcol_B(M0)>(g, cb, ck, om.w, ring);
+        col_tile<M0, bfu_B(M0)>(g, cb, ck, om.w, ring);
     }
 }
-
-static size_t bcol_smem(int m0) { return sizeof(float2) * col_ring_rows(m0) * 32 * batch_col_groups(m0); }
 
 cudaError_t batch_blocks_per_sm(int m, int *row_bps, int *col_bps) {
     cudaError_t e = cudaErrorInvalidValue;
@@ -90,7 +75,7 @@ cudaError_t batch_blocks_per_sm(int m, int *row_bps, int *col_bps) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(row_bps, batch_row_kernel<M_>, kRowThreads, 0);  \
         if (e != cudaSuccess) return e;                                                                    \
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(col_bps, batch_col_kernel<M_>,                \
-                                                             bcol_threads(M_), bcol_smem(M_));
+                                                             bfu_threads(M_), bfu_smem(M_));
         F(0) F(1) F(2) F(3) F(4) F(5) F(6)
 #undef F
         default:
@@ -108,7 +93,7 @@ cudaError_t launch_batch_class(bool col, int m, const BatchImage *d_images, cons
 #define F(M_)                                                                                                 \
     case M_:                                                                                                  \
         if (col)                                                                                              \
-            batch_col_kernel<M_><<<grid, bcol_threads(M_), bcol_smem(M_), s>>>(d_images, ent, nent, nitems, om); \
+            batch_col_kernel<M_><<<grid, bfu_threads(M_), bfu_smem(M_), s>>>(d_images, ent, nent, nitems, om); \
         else                                                                                                  \
             batch_row_kernel<M_><<<grid, kRowThreads, 0, s>>>(d_images, ent, nent, nitems, om);               \
         break;
