@@ -226,8 +226,9 @@ swdft_status swdft2d_check_device(void);
  * shared-memory mbarrier that nothing arrives on, for at most `polls` polls (1..4096; each
  * suspends the thread for at most about 1 ms), then records the time-out in a device
  * status word of its own, read and reset with the tensor-core kernels' word by
- * swdft2d_check_device, which then returns SWDFT_ERR_DEVICE_TIMEOUT.  Nothing faults and the context stays usable.
- * SWDFT_ERR_INVALID_ARG for polls out of range (checked before any CUDA call). */
+ * swdft2d_check_device, which then returns SWDFT_ERR_DEVICE_TIMEOUT.  Nothing faults and
+ * the context stays usable.  SWDFT_ERR_INVALID_ARG for polls out of range (checked before
+ * any CUDA call). */
 swdft_status swdft2d_selftest_wait_timeout(int32_t polls, void *stream);
 
 /* Fault injection for tests: the library's next `after` allocations succeed and every later

@@ -764,7 +764,7 @@ bool device_name(char *buf, size_t len) {
 
 extern "C" {
 
-int32_t swdft2d_version(void) { return 100; }
+int32_t swdft2d_version(void) { return 200; }  // 0.2.0: tuning cache read-back, failure test hooks
 
 const char *swdft2d_status_string(int32_t s) {
     switch (s) {
