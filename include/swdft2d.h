@@ -207,11 +207,16 @@ swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t 
  * (held on every GPU that loads it, until exit), and the output is produced in bands of
  * window rows whose z fits there.  Arguments as in swdft2d_shape / swdft2d_execute
  * (ld = 0 means N1); output layout as for swdft2d_execute with all P0 window rows.
- * Errors: as swdft2d_plan for the shape; SWDFT_ERR_WORKSPACE when even a one-row band
+ * Radix-2 trees only: windows of 2^m <= 64 per side.  Errors: SWDFT_ERR_UNSUPPORTED for
+ * windows of 3, 9 or 27 samples on a side (ternary trees, which plans accept) and for sides
+ * above 64; SWDFT_ERR_NOT_POW2 for sides that are neither powers of two nor of three;
+ * otherwise as swdft2d_plan for the shape; SWDFT_ERR_WORKSPACE when even a one-row band
  * needs more than 32 MiB, i.e. (3*n0/2) * (N1-n1+1) * n1 * 8 bytes > 32 MiB.
- * The first call on a device looks up the array's address there (do it before any stream
- * capture).  All calls share the array and it keeps the last call's contents: calls that
- * overlap on the GPU race and must be serialised by the caller. */
+ * The first call on a device looks up the array's address there and the device's SM count
+ * (do it before any stream capture); both are kept until exit, so the entry point must not
+ * be used on a device after cudaDeviceReset.  All calls share the array and it keeps the
+ * last call's contents: calls that overlap on the GPU race and must be serialised by the
+ * caller. */
 swdft_status swdft2d_execute_static_scratch(const void *d_in, int64_t N0, int64_t N1, int64_t ld,
                                             int32_t n0, int32_t n1, int32_t dtype, int32_t norm,
                                             void *d_out, void *stream);

@@ -38,8 +38,9 @@ def sources():
 
 
 def _headers():
+    # every header a translation unit may include: the kernel headers and all public headers
     hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    hs.append(os.path.join(INCLUDE, "swdft2d.h"))
+    hs += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     return sorted(hs)
 
 

@@ -198,22 +198,11 @@ float norm_scale(int norm, int n0, int n1) {
     }
 }
 
-// Column pass: about eight chunks of window rows per channel group (measured best on the
-// 512x512/32x32 and 1024x2048/16x64 workloads: many small blocks balance the SMs better than
-// a few long ones), but never fewer than 2*n0 rows so warm-up stays under a third.
-int64_t col_chunk_for(const ArrayPlan &a, int nchunks) {
-    const int64_t rows = a.band_rows();
-    int64_t chunk = (rows + nchunks - 1) / nchunks;
-    return std::min(rows, std::max<int64_t>(chunk, 2 * a.n0));
-}
+// Column-pass row chunks (default_col_nchunks / default_col_chunk in swdft_internal.h).
+int64_t col_chunk_for(const ArrayPlan &a, int nchunks) { return default_col_chunk(a.band_rows(), a.n0, nchunks); }
 
-// Column-pass row chunks: about eight per channel group (sixteen for fused small windows),
-// more when there are few channel groups (narrow arrays), so that the pass has at least four
-// blocks per SM.
 int col_nchunks(const ArrayPlan &a, int sm_count, bool fused_small) {
-    const int64_t ch_groups = (a.P1 * a.n1 + 31) / 32;
-    const int64_t want = (4LL * std::max(1, sm_count) + ch_groups - 1) / ch_groups;
-    return (int)std::min<int64_t>(65535, std::max<int64_t>(fused_small ? 16 : 8, want));
+    return default_col_nchunks(a.P1 * a.n1, sm_count, fused_small);
 }
 
 // conc: arrays of the plan that run at once (their z buffers share L2).
@@ -222,15 +211,13 @@ void default_config(ArrayPlan &a, int sm_count, int conc) {
     // row levels: thread = (row, residue, chunk of window columns).  About 64K threads in
     // flight (measured best on the 512x512/32x32 and 1024x2048/16x64 workloads: B = 3 with
     // 16-32 column chunks, B = 2 with 128-column chunks), chunks no shorter than n1/2.
-    c.row_B = a.r1 == 3 ? 0 : (a.m1 >= 6 ? 2 : std::min(a.m1, 3));  // ternary rows: one thread each
+    c.row_B = a.r1 == 3 ? 0 : default_row_B(a.m1);  // ternary rows: one thread each
     const int64_t rows = a.band_rows() + a.n0 - 1;
     const int64_t per_row = a.r1 == 3 ? (a.m1 >= 1 ? 3 : 1) : (int64_t(1) << c.row_B);  // threads per row
-    const int64_t nchunk = std::max<int64_t>(1, (64LL << 10) / std::max<int64_t>(1, rows * per_row));
-    const int64_t chunk = (a.P1 + nchunk - 1) / nchunk;
-    c.row_chunk = std::min<int64_t>(a.P1, std::max<int64_t>(chunk, std::max(1, a.n1 / 2)));
+    c.row_chunk = default_row_chunk(a.P1, rows, per_row, a.n1);
     // column levels: thread = (channel, residue, chunk of output rows); one 32-channel
     // group per block (32 * 2^B threads)
-    c.col_B = a.m0 >= 6 ? 3 : std::min(a.m0, 2);
+    c.col_B = default_col_B(a.m0);
     c.col_groups = 1;
     // fused form (row levels inside the column tile, n1 <= 32): it recomputes each z value
     // from the input (log2 n1 butterflies) instead of writing and re-reading z, which wins for
@@ -714,6 +701,12 @@ bool tune_record_applies(const TuneRecord &r, const char *gpu, const ArrayPlan &
         r.row_chunk < 0 || r.col_chunk < 0 || r.col_groups < 1 || r.col_groups > 8 || r.fused < 0 || r.fused > 1 ||
         (r.fused == 1 && a.m1 > 5))
         return false;
+    // chunks so short that a pass would need more than 65535 of them (the grid's y limit) on
+    // this array's band: a stale or hand-edited record, not one the autotuner writes
+    const auto too_many = [](int64_t extent, long long chunk) {
+        return chunk > 0 && (extent + chunk - 1) / chunk > 65535;
+    };
+    if (too_many(a.P1, r.row_chunk) || too_many(a.band_rows(), r.col_chunk)) return false;
     c->fused = r.fused == 1;
     c->row_B = r.row_B;
     c->row_chunk = r.row_chunk;

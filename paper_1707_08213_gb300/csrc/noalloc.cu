@@ -11,7 +11,10 @@
 // in bands of window rows whose z fits in that array.
 //
 // The first call on a device looks up the array's device address on that device
-// (cudaGetSymbolAddress), so make that first call before any stream capture.  Every call
+// (cudaGetSymbolAddress) and its SM count, so make that first call before any stream
+// capture.  Both are kept for the life of the process: a cudaDeviceReset (or anything else
+// that destroys the device's primary context) unloads the array and leaves the kept address
+// dangling, so this entry point must not be called on a device after it was reset.  Every call
 // shares the one array: calls that overlap on the GPU (different streams, or different host
 // threads) race on it and must be serialised by the caller.  The array keeps the last call's
 // contents; nothing in it needs to start at zero (the row pass writes every z row the column
@@ -32,22 +35,36 @@ __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 constexpr int kMaxDevices = 128;
 void *g_scratch_addr[kMaxDevices] = {};
+int g_sm_count[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
-// Device address of g_static_scratch on the current device, looked up once per device.
-// (In host code the symbol itself is only a host-side stand-in, never a device address.)
-swdft_status scratch_address(void **out) {
+// Device address of g_static_scratch on the current device and its SM count, looked up once
+// per device.  (In host code the symbol itself is only a host-side stand-in, never a device
+// address.)
+swdft_status scratch_address(void **out, int *sm_count) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return SWDFT_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return SWDFT_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (!g_scratch_addr[dev]) {
         void *p = nullptr;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            return SWDFT_ERR_CUDA;
         if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return SWDFT_ERR_CUDA;
+        g_sm_count[dev] = sms;
         g_scratch_addr[dev] = p;
     }
     *out = g_scratch_addr[dev];
+    *sm_count = g_sm_count[dev];
     return SWDFT_OK;
+}
+
+// n = 3^m (m >= 1)
+bool power_of_three(int64_t n) {
+    if (n < 3) return false;
+    while (n % 3 == 0) n /= 3;
+    return n == 1;
 }
 
 int log2_pow2(int64_t n) {
@@ -69,6 +86,8 @@ extern "C" swdft_status swdft2d_execute_static_scratch(const void *d_in, int64_t
     if (dtype != SWDFT_R32 && dtype != SWDFT_C64) return SWDFT_ERR_INVALID_ARG;
     if (norm < SWDFT_NORM_UNITARY || norm > SWDFT_NORM_INV_N) return SWDFT_ERR_INVALID_ARG;
     const int m0 = log2_pow2(n0), m1 = log2_pow2(n1);
+    // radix-2 trees only: windows of 3, 9 or 27 (which plans accept) are not offered here
+    if ((m0 < 0 && power_of_three(n0)) || (m1 < 0 && power_of_three(n1))) return SWDFT_ERR_UNSUPPORTED;
     if (m0 < 0 || m1 < 0) return SWDFT_ERR_NOT_POW2;
     if (n0 > N0 || n1 > N1) return SWDFT_ERR_WINDOW_TOO_LARGE;
     if (m0 > kMaxLog2 || m1 > kMaxLog2) return SWDFT_ERR_UNSUPPORTED;
@@ -85,7 +104,8 @@ extern "C" swdft_status swdft2d_execute_static_scratch(const void *d_in, int64_t
     if (band < 1) return SWDFT_ERR_WORKSPACE;           // one band does not fit the array
 
     void *scratch = nullptr;
-    swdft_status st = scratch_address(&scratch);
+    int sm_count = 0;
+    swdft_status st = scratch_address(&scratch, &sm_count);
     if (st != SWDFT_OK) return st;
 
     float2 om64[kMaxN];
@@ -109,8 +129,9 @@ extern "C" swdft_status swdft2d_execute_static_scratch(const void *d_in, int64_t
         r.m1 = m1;
         r.z = z;
         r.om64 = om64;
-        r.B = std::min(m1, 2);
-        r.chunk = P1;
+        // the launch shapes the planned entry points use for a band of this size
+        r.B = default_row_B(m1);
+        r.chunk = default_row_chunk(P1, r.rows, int64_t(1) << r.B, n1);
         if (launch_row_tree(r, s) != cudaSuccess) return SWDFT_ERR_CUDA;
         ColTreeArgs c;
         c.z = z;
@@ -121,9 +142,9 @@ extern "C" swdft_status swdft2d_execute_static_scratch(const void *d_in, int64_t
         c.out = static_cast<float2 *>(d_out) + (size_t)q * out_row;
         c.scale = scale;
         c.om64 = om64;
-        c.B = std::min(m0, 2);
-        c.chunk = rows_out;
-        c.groups = 2;
+        c.B = default_col_B(m0);
+        c.chunk = default_col_chunk(rows_out, n0, default_col_nchunks(P1 * n1, sm_count, false));
+        c.groups = 1;
         if (launch_col_tree(c, s) != cudaSuccess) return SWDFT_ERR_CUDA;
     }
     return SWDFT_OK;

@@ -25,6 +25,40 @@ constexpr int kMaxN3 = 27;
 // Omega^i of Section 4.2 for length n (any n >= 1), FP64-evaluated, FP32-rounded.
 void make_omega(int n, float2 *out);
 
+// Default launch shapes of the binary tree's two passes over a band of window rows (used by
+// the plans and by the allocation-free entry point alike; measured on the 512x512/32x32 and
+// 1024x2048/16x64 workloads).
+//  * row levels: thread = (row, residue, chunk of window columns); B = 3 (2 for 64-point
+//    trees, which need more registers), about 64K threads in flight, chunks no shorter than
+//    n1/2 (each chunk re-walks n1 - 1 columns of warm-up).
+//  * column levels: thread = (channel, residue, chunk of window rows); B = 2 (3 for 64-point
+//    trees); about eight row chunks per 32-channel group (sixteen for fused small windows),
+//    more when there are few channel groups, so that the pass has at least four blocks per
+//    SM; every chunk at least 2 n0 rows so warm-up stays under a third.
+inline int default_row_B(int m1) { return m1 >= 6 ? 2 : (m1 < 3 ? m1 : 3); }
+inline int64_t default_row_chunk(int64_t P1, int64_t zrows, int64_t threads_per_row, int n1) {
+    const int64_t t = zrows * threads_per_row;
+    const int64_t nchunk = (64LL << 10) / (t > 1 ? t : 1);
+    const int64_t nc = nchunk > 1 ? nchunk : 1;
+    const int64_t chunk = (P1 + nc - 1) / nc;
+    const int64_t lo = n1 / 2 > 1 ? n1 / 2 : 1;
+    const int64_t c = chunk > lo ? chunk : lo;
+    return c < P1 ? c : P1;
+}
+inline int default_col_B(int m0) { return m0 >= 6 ? 3 : (m0 < 2 ? m0 : 2); }
+inline int default_col_nchunks(int64_t nch, int sm_count, bool fused_small) {
+    const int64_t ch_groups = (nch + 31) / 32;
+    const int64_t want = (4LL * (sm_count > 1 ? sm_count : 1) + ch_groups - 1) / ch_groups;
+    const int64_t base = fused_small ? 16 : 8;
+    const int64_t n = want > base ? want : base;
+    return (int)(n < 65535 ? n : 65535);
+}
+inline int64_t default_col_chunk(int64_t band_rows, int n0, int nchunks) {
+    const int64_t chunk = (band_rows + nchunks - 1) / nchunks;
+    const int64_t c = chunk > 2LL * n0 ? chunk : 2LL * n0;
+    return c < band_rows ? c : band_rows;
+}
+
 // Geometry of one row-level pass (see RowTreeArgs): z[r][q1][k1] for `rows` input rows.
 struct RowGeom {
     const void *x;

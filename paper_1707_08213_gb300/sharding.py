@@ -11,7 +11,7 @@ wanted, is the caller's choice.
 from __future__ import annotations
 
 import heapq
-from typing import List, Sequence, Tuple
+from typing import List, Optional, Sequence, Tuple
 
 
 def band_for_rank(P0: int, rank: int, world: int) -> Tuple[int, int]:
@@ -23,6 +23,13 @@ def band_for_rank(P0: int, rank: int, world: int) -> Tuple[int, int]:
     base, extra = divmod(P0, world)
     begin = rank * base + min(rank, extra)
     return begin, begin + base + (1 if rank < extra else 0)
+
+
+def plan_bands(P0: int, rank: int, world: int) -> Optional[List[Tuple[int, int]]]:
+    """The `bands` argument of a one-array Transform (swdft2d_shape's row_begin/row_end, in
+    window-start coordinates) for this rank's share of one transform: None (every window row)
+    on a single rank, else [band_for_rank(P0, rank, world)]."""
+    return None if world == 1 else [band_for_rank(P0, rank, world)]
 
 
 def input_rows_for_band(begin: int, end: int, n0: int) -> Tuple[int, int]:

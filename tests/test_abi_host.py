@@ -359,3 +359,20 @@ def test_load_tuning_applies_records_of_the_named_gpu(nat, tmp_path):
         with pytest.raises(nat.SwdftError) as e:
             nat.Plan([shp(300, 300, 16, 16)]).load_tuning(str(cache))
         assert e.value.status == -6
+
+
+def test_load_tuning_rejects_chunks_beyond_the_grid_limit(nat, tmp_path):
+    """A record whose row or column chunks would cut this array's pass into more than 65535
+    pieces (the grid's y limit) is not applied: the array keeps its default choice, and the
+    record that fits is applied."""
+    cache = tmp_path / "tune.jsonl"
+    N0, N1 = 70000, 40
+    cache.write_text(
+        _tune_line("G", N0, N1, 2, 2, fused=0, col_chunk=1, col_B=1, row_B=1) +      # 69999 chunks
+        _tune_line("G", 300, 70000, 2, 2, fused=0, row_chunk=1, col_B=1, row_B=1))   # 69999 chunks
+    tall = nat.Plan([shp(N0, N1, 2, 2)])
+    assert tall.load_tuning(str(cache), "G") == 0
+    wide = nat.Plan([shp(300, 70000, 2, 2)])
+    assert wide.load_tuning(str(cache), "G") == 0
+    cache.write_text(_tune_line("G", N0, N1, 2, 2, fused=0, col_chunk=2, col_B=1, row_B=1))
+    assert nat.Plan([shp(N0, N1, 2, 2)]).load_tuning(str(cache), "G") == 1

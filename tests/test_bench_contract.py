@@ -31,3 +31,7 @@ def test_reference_arm_prints_one_contract_line():
                         "d2h_bytes_per_step": 0}
     host = d["cpu_baseline"]["host"]
     assert host["nproc"] >= 1 and host["machine"]
+    # the same workload description as the GPU arm's line (config_dict with the same keys)
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["config"] == bench.config_dict({"algo": "tree_f32", "parallelism": bench.parallelism_for(1)})

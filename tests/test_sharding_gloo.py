@@ -80,6 +80,47 @@ def test_two_rank_band_split_equals_unsplit(tmp_path):
 
 
 
+def _plan_band_worker(rank, world, port, outdir):
+    """Each rank builds the plan a multi-GPU bench run builds for its band (host only: plan
+    creation makes no CUDA call) and records what the library made of the band."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1707_08213_gb300 import _native as nat
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sh = _load_sharding()
+    N0, N1, n0, n1 = 512, 512, 32, 32
+    P0 = N0 - n0 + 1
+    bands = sh.plan_bands(P0, rank, world)
+    assert bands == [sh.band_for_rank(P0, rank, world)]
+    spec = {"N0": N0, "N1": N1, "n0": n0, "n1": n1, "dtype": nat.R32}
+    spec["row_begin"], spec["row_end"] = bands[0]
+    plan = nat.Plan([spec])
+    np.save(os.path.join(outdir, f"plan{rank}.npy"), np.array([*bands[0], *plan.output_shape(0)]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_plans_take_the_ranks_bands(tmp_path):
+    """The bands handed to swdft2d_shape (row_begin/row_end) are band_for_rank's, and the
+    plans' outputs (P0 rows split between the ranks) tile the transform's window rows."""
+    world = 2
+    mp.spawn(_plan_band_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    sh = _load_sharding()
+    rows = []
+    for r in range(world):
+        b, e, p0, p1, k0, k1 = (int(v) for v in np.load(tmp_path / f"plan{r}.npy"))
+        assert (b, e) == sh.band_for_rank(481, r, world)
+        assert (p0, p1, k0, k1) == (e - b, 481, 32, 32)
+        rows.extend(range(b, e))
+    assert rows == list(range(481))
+    assert sh.plan_bands(481, 0, 1) is None
+
+
 def test_image_assignment_covers_and_balances():
     sh = _load_sharding()
     rng = np.random.default_rng(3)
