@@ -8,4 +8,9 @@ SWDFT_ADJ_INSTANTIATE(1)
 SWDFT_ADJ_INSTANTIATE(2)
 SWDFT_ADJ_INSTANTIATE(3)
 
+SWDFT_ADJ_RING_INSTANTIATE(0)
+SWDFT_ADJ_RING_INSTANTIATE(1)
+SWDFT_ADJ_RING_INSTANTIATE(2)
+SWDFT_ADJ_RING_INSTANTIATE(3)
+
 }  // namespace swdft

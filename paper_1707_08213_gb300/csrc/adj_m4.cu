@@ -5,4 +5,6 @@ namespace swdft {
 
 SWDFT_ADJ_INSTANTIATE(4)
 
+SWDFT_ADJ_RING_INSTANTIATE(4)
+
 }  // namespace swdft

@@ -5,4 +5,6 @@ namespace swdft {
 
 SWDFT_ADJ_INSTANTIATE(6)
 
+SWDFT_ADJ_RING_INSTANTIATE(6)
+
 }  // namespace swdft

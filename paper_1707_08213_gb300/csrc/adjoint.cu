@@ -1,6 +1,7 @@
 // Adjoint passes (transposed tree): launchers.  Instantiations live in adj_m*.cu.
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 
 #include "adjoint_kernels.cuh"
 #include "tree_kernels.cuh"
@@ -18,6 +19,17 @@ __global__ void __launch_bounds__(256) adj_fold_kernel(const __grid_constant__ A
         float2 *dst = gz + b * p.chunk * p.nch + (i - (b - 1) * p.per_row);
         *dst = c_add(*dst, side[i]);
     }
+}
+
+// The column adjoint's staging layout for each (n0, n1) = (2^m0, 2^m1), chosen once.
+AdjColLayout adj_col_layout_cached(int m0, int m1) {
+    static std::once_flag once;
+    static AdjColLayout table[kMaxLog2 + 1][kMaxLog2 + 1];
+    std::call_once(once, [] {
+        for (int M = 0; M <= kMaxLog2; ++M)
+            for (int m = 0; m <= kMaxLog2; ++m) table[M][m] = adj_col_layout(M, adj_col_B(M), m);
+    });
+    return table[m0][m1];
 }
 
 int64_t adj_col_chunk(int64_t rows_out, int m0, int64_t requested) {
@@ -45,7 +57,7 @@ cudaError_t launch_adj_col(const AdjColArgs &a, cudaStream_t s) {
     if (a.m0 < 0 || a.m0 > kMaxLog2 || a.m1 < 0 || a.m1 > kMaxLog2 || zrows > INT32_MAX)
         return cudaErrorInvalidValue;
     if (a.nz < 1 || a.nz > kAdjZ) return cudaErrorInvalidValue;
-    AdjColParams p;
+    AdjColRingParams p;
     for (int z = 0; z < kAdjZ; ++z) {
         p.G[z] = a.G[z];
         p.gz[z] = a.gz[z];
@@ -57,8 +69,16 @@ cudaError_t launch_adj_col(const AdjColArgs &a, cudaStream_t s) {
     const int64_t side_elems = adj_side_elems(a.rows_out, a.m0, a.P1, a.m1, a.chunk);
     for (int z = 0; z < a.nz; ++z)
         if (!a.G[z] || !a.gz[z] || (side_elems > 0 && a.side[z] == nullptr)) return cudaErrorInvalidValue;
+    // 8-byte copies need complex64 alignment; 16-byte copies (channel pairs) need n1 >= 2 and
+    // G 16-byte aligned (every pair then starts on an even value in G and in the ring)
+    for (int z = 0; z < a.nz; ++z)
+        if ((uintptr_t)a.G[z] % 8 != 0) return cudaErrorInvalidValue;
+    bool q16 = a.m1 >= 1;
+    for (int z = 0; z < a.nz; ++z) q16 = q16 && (uintptr_t)a.G[z] % 16 == 0;
+    p.q16 = q16 ? 1 : 0;
     p.m1 = a.m1;
     p.scale = a.scale;
+    p.L = adj_col_layout_cached(a.m0, a.m1);
     for (int j = 0; j < kMaxN; ++j) p.om64[j] = a.om64[j];
     const int B = adj_col_B(a.m0);  // the one split built per window side
     const int threads = 128;
@@ -66,10 +86,11 @@ cudaError_t launch_adj_col(const AdjColArgs &a, cudaStream_t s) {
     dim3 grid((unsigned)((nch + per_block - 1) / per_block), (unsigned)((a.rows_out + p.chunk - 1) / p.chunk),
               (unsigned)a.nz);
     if (grid.y > 65535) return cudaErrorInvalidValue;
+    const size_t smem = adj_col_smem(a.m0, p.L.slot);
     switch (a.m0) {
-#define F(M_)                                                                \
-    case M_:                                                                 \
-        adj_col_launch_mb<M_, adj_col_B(M_)>(p, grid, dim3(threads), s);     \
+#define F(M_)                                                                       \
+    case M_:                                                                        \
+        adj_col_ring_launch_mb<M_, adj_col_B(M_)>(p, grid, dim3(threads), smem, s); \
         break;
         F(0) F(1) F(2) F(3) F(4) F(5) F(6)
 #undef F

@@ -41,7 +41,8 @@ def gpu_adjoint(sw, G, N0, N1, cplx, norm="unitary", band=None, pos="start"):
 
 
 SHAPES = [(1, 1, 1, 1), (9, 9, 8, 8), (37, 53, 4, 8), (64, 77, 8, 16), (23, 300, 1, 64),
-          (300, 23, 64, 1), (100, 100, 32, 32), (130, 90, 64, 16), (45, 45, 2, 32), (50, 70, 16, 8)]
+          (300, 23, 64, 1), (100, 100, 32, 32), (130, 90, 64, 16), (45, 45, 2, 32), (50, 70, 16, 8),
+          (80, 120, 32, 64), (130, 100, 64, 64), (60, 70, 16, 16), (40, 33, 16, 1), (33, 40, 2, 1)]
 
 
 @pytest.mark.parametrize("cplx", [False, True])
@@ -200,3 +201,26 @@ def test_adjoint_of_same_shape_arrays_in_grouped_launches(sw, cplx):
             ref = ref.real
         err = workloads.adjoint_error(g.cpu().numpy(), ref, workloads.adjoint_pixel_norms(full, N0, N1))
         assert err <= TOL, f"array {i}: {err:.3e}"
+
+
+@pytest.mark.parametrize("N0,N1,n0,n1", [(60, 70, 16, 16), (100, 100, 32, 32), (130, 90, 64, 16),
+                                         (50, 70, 16, 8), (40, 33, 16, 1), (45, 45, 2, 32)])
+def test_bulk_and_cp_async_staging_agree_bit_for_bit(sw, N0, N1, n0, n1):
+    """The column adjoint stages G by bulk copies when G is 16-byte aligned and by 8-byte
+    cp.async otherwise (a G that starts 8 bytes into a buffer).  Both sum the residues of a
+    channel in the same order, so the two gradients are equal bit for bit; and no bounded
+    wait of the bulk kernel gave up (swdft2d_check_device)."""
+    from paper_1707_08213_gb300 import _native as nat
+    P0, P1 = N0 - n0 + 1, N1 - n1 + 1
+    G = torch.from_numpy(_G(7 * N0 + N1, P0, P1, n0, n1)).cuda()
+    buf = torch.empty(G.numel() + 1, dtype=torch.complex64, device="cuda")
+    Gm = buf[1:].view(G.shape)
+    Gm.copy_(G)
+    assert G.data_ptr() % 16 == 0 and Gm.data_ptr() % 16 == 8
+    t = sw.Transform([(N0, N1, n0, n1, 0)])
+    a = t.adjoint([G])[0].clone()
+    b = t.adjoint([Gm])[0]
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert nat.check_device() == 0
+

@@ -12,8 +12,9 @@ and with the explicit overlap-add of every window's inverse DFT (adjoint).  They
 index arithmetic of the kernels' register schedules without a GPU.
 
 The later tests replay whole passes block by block, with each block's shared-memory staging:
-the two adjoint passes (cp.async staging, chunking of window rows and columns, the side rows
-two column chunks share and the fold that adds them) for every window side they build, and
+the two adjoint passes (cp.async staging of G into a ring in a bank-conflict-free layout,
+chunking of window rows and columns, the side rows two column chunks share and the fold that
+adds them) for every window side they build, and
 the forward passes (row_tile into z; col_tile_impl with its ring of z rows fed by copies of z
 or by the fused form's shuffled row DFTs), and the ternary passes (row_tree3_kernel's staged
 run write-back; col_tree3_kernel's ring and its staged copy-out).
@@ -244,14 +245,73 @@ def adj_col_chunk(rows_out, n, requested):
     return max(1, min(chunk, rows_out))
 
 
-def emulate_adj_col(G, n0, n1, chunk_req):
-    """adj_col_kernel over its grid (channel blocks x window-row chunks), then adj_fold_kernel.
-    G: (rows_out, P1, n0, n1).  Returns gz as (rows_out + n0 - 1, P1 * n1)."""
+# adj_col_ring_kernel (adjoint_kernels.cuh): each step's runs of G are staged in a ring of
+# ADJ_STAGES stages of adj_col_gs(M) steps by all 128 threads (16-byte cp.async pieces, 8-byte
+# when G is not 16-byte aligned or n0 = 1); lanes hold the residue in their high bits; the
+# host picks the staging layout (adj_col_layout, as in adjoint_kernels.cuh).
+
+ADJ_STAGES = 2
+
+
+def adj_col_gs(M):
+    return 2 if M >= 4 else 32 >> M
+
+
+def adj_col_conflicts(M, B, L):
+    """Most distinct 8-byte words one half-warp's read maps to one bank pair (warp 0)."""
+    mode, lw, gs, ks, slot = L
+    R, CPW, n, W = 1 << B, 32 >> B, 1 << M, 1 << lw
+    worst = 1
+    for t in range(n // R):
+        for h in range(2):
+            per_bank = {}
+            for l in range(16):
+                lane = 16 * h + l
+                c, ch = lane // CPW, lane % CPW
+                a = (ch >> lw) * gs + (ch & (W - 1)) + (c + R * t) * ks
+                per_bank.setdefault(a & 15, set()).add(a)
+            worst = max(worst, max(len(v) for v in per_bank.values()))
+    return worst
+
+
+def adj_col_layout(M, B, m1):
+    """(mode, lw, gs, ks, slot): fewest conflicts, then fewest runs per step, then smallest
+    slot; padded q1 groups (mode 1) only when one run would read with more than 2-way conflicts."""
+    n, n1, CH = 1 << M, 1 << m1, 128 >> B
+    best, key = None, None
+
+    def consider(L, runs):  # strict improvement only: the first of equals wins, as in the host code
+        nonlocal best, key
+        k = (adj_col_conflicts(M, B, L), runs, L[4])
+        if key is None or k < key:
+            best, key = L, k
+    if n1 <= CH:
+        consider((0, m1, n * n1, n1, CH * n), 1)
+    if n1 < CH and key[0] > 2:
+        for pad in range(2, 31, 2):
+            consider((1, m1, n * n1 + pad, n1, (CH >> m1) * (n * n1 + pad)), CH >> m1)
+    if n1 >= CH:
+        lw = CH.bit_length() - 1
+        for pad in range(0, 31, 2):
+            consider((2, lw, 0, CH + pad, n * (CH + pad)), n)
+    return best
+
+
+def emulate_adj_col_ring(G, n0, n1, chunk_req, q16=True):
+    """adj_col_ring_kernel over its grid, then adj_fold_kernel: the ring, layout and lanes
+    above, filled by all 128 threads with 16-byte (q16) or 8-byte cp.async pieces.  Every
+    piece is checked to be aligned to its size at both ends, to land inside its step's part of
+    its ring slot and to read inside G; the pieces of a step cover its runs exactly once; a
+    slot is refilled (stage g + ADJ_STAGES - 1, after the block barrier of stage g) only once
+    the stage in it was read; every staged value a thread reads is the G value it stands for."""
     rows_out, P1 = G.shape[0], G.shape[1]
     M, m1 = n0.bit_length() - 1, n1.bit_length() - 1
     B = adj_col_B(M)
-    R, n, CH, GS = 1 << B, n0, 128 >> B, 2
-    STEP = n * CH
+    R, n, CH, CPW = 1 << B, n0, 128 >> B, 32 >> B
+    GS, NS = adj_col_gs(M), ADJ_STAGES
+    mode, lw, gs, ks, slot = adj_col_layout(M, B, m1)
+    q16 = q16 and m1 >= 1  # channel pairs need n1 >= 2
+    assert 128 + 8 * NS * GS * slot <= 227 * 1024
     nch = P1 * n1
     Gf = G.reshape(-1)
     grow = nch * n
@@ -259,53 +319,103 @@ def emulate_adj_col(G, n0, n1, chunk_req):
     nchunks = -(-rows_out // chunk)
     gz = np.full((rows_out + n - 1) * nch, np.nan, complex)
     side = np.full(max(nchunks - 1, 0) * (n - 1) * nch, np.nan, complex)
+    tid = np.arange(128)
+    warp, lane = tid >> 5, tid & 31
+    c_of, chl_of = lane // CPW, warp * CPW + (lane & (CPW - 1))
+    tbase = (chl_of >> lw) * gs + (chl_of & ((1 << lw) - 1)) + c_of * ks
+    tstride = R * ks
     for bx in range(-(-nch // CH)):
         ch0 = bx * CH
+        chv = min(CH, nch - ch0)
+        assert chv % min(n1, CH) == 0
+        gbase = (ch0 >> m1) * n * n1 + (ch0 & (n1 - 1))
+        runs = 1 if mode == 0 else (chv >> m1 if mode == 1 else n)
+        run_vals = chv * n if mode == 0 else (n * n1 if mode == 1 else CH)
+        # copies: thread i owns channel pair cl (one channel with 8-byte pieces) and the
+        # k0 = k0f + KS t of every step
+        qv = 2 if q16 else 1
+        NP = CH // qv
+        KS = 128 // NP
         for by in range(nchunks):
             qa = by * chunk
             qb = min(qa + chunk, rows_out)
             last = qb == rows_out
             p_hi, nwin = qb + n - 2, qb - qa
             steps = nwin + n - 1
-            sg = np.full(2 * GS * STEP, np.nan, complex)
+            ngroups = -(-nwin // GS)
+            ring = np.full(NS * GS * slot, np.nan, complex)
+            in_slot = [None] * NS
+            read = set()
 
-            def fetch(j0, b):
-                for tid in range(128):
-                    cl_f, k0_f = tid & (CH - 1), tid // CH
-                    cg_f = ch0 + cl_f
-                    ok = cg_f < nch
-                    gsrc = ((cg_f >> m1) * n + k0_f) * n1 + (cg_f & (n1 - 1)) if ok else 0
-                    dst = b * GS * STEP + k0_f * CH + cl_f
-                    src = gsrc + (qb - 1 - j0) * grow
-                    for _ in range(min(GS, nwin - j0)):
-                        for t in range(n // R):
-                            sg[dst + t * R * CH] = Gf[src + t * R * n1] if ok else 0
-                        dst += STEP
-                        src -= grow
+            def piece(src, dst, vals, step0):
+                assert (8 * src) % (8 * vals) == 0 and (128 + 8 * dst) % (8 * vals) == 0
+                assert step0 <= dst and dst + vals <= step0 + slot, "piece leaves its step's slot"
+                assert 0 <= src and src + vals <= Gf.size, "piece reads outside G"
+                assert np.isnan(ring[dst:dst + vals]).all(), "piece written twice in one stage"
+                ring[dst:dst + vals] = Gf[src:src + vals]
 
-            if nwin > 0:
-                fetch(0, 0)
-            feeds = [[] for _ in range(R)]
-            lanes = np.arange(CH)
+            def fetch(g):
+                if g >= ngroups:
+                    return
+                sl = g % NS
+                assert in_slot[sl] is None or in_slot[sl] in read, "slot refilled before it was read"
+                in_slot[sl] = g
+                ring[sl * GS * slot:(sl + 1) * GS * slot] = np.nan
+                j0 = g * GS
+                cnt = min(GS, nwin - j0)
+                dst0 = sl * GS * slot
+                for t in range(128):
+                    cl, k0f = (t % NP) * qv, t // NP
+                    if not (cl < chv and k0f < n):
+                        continue
+                    gsrc = gbase + (cl >> m1) * n * n1 + (cl & (n1 - 1)) + k0f * n1
+                    sdst = (cl >> lw) * gs + (cl & ((1 << lw) - 1)) + k0f * ks
+                    for st in range(cnt):
+                        step0 = dst0 + st * slot
+                        src = gsrc + (qb - 1 - (j0 + st)) * grow
+                        for u in range(max(1, -(-(n - k0f) // KS))):
+                            if k0f + KS * u >= n:
+                                break
+                            piece(src + u * KS * n1, step0 + sdst + u * KS * ks, qv, step0)
+                for st in range(cnt):  # the pieces cover exactly each step's runs
+                    step0 = dst0 + st * slot
+                    assert (~np.isnan(ring[step0:step0 + slot])).sum() == runs * run_vals
+
+            for g in range(NS - 1):
+                fetch(g)
+            feeds = {c: [] for c in range(R)}
             for j in range(steps):
-                if j % GS == 0 and j + GS < nwin:
-                    fetch(j + GS, (j // GS + 1) & 1)
+                g = j // GS
+                if j % GS == 0:
+                    if g >= 1:
+                        read.add(g - 1)  # the block barrier: every thread has read stage g - 1
+                    fetch(g + NS - 1)
+                if j < nwin:
+                    assert in_slot[g % NS] == g
+                    base = (g % NS) * GS * slot + (j % GS) * slot
+                    addrs = base + tbase[:, None] + tstride * np.arange(held(B, M))[None, :]
+                    assert (addrs >= base).all() and (addrs < base + slot).all()
+                    u = ring[addrs]
+                    chg = ch0 + chl_of
+                    ok = chg < nch
+                    chc = np.minimum(chg, nch - 1)
+                    k0 = c_of[:, None] + R * np.arange(held(B, M))[None, :]
+                    want = G[qb - 1 - j, (chc >> m1)[:, None], k0, (chc & (n1 - 1))[:, None]]
+                    np.testing.assert_array_equal(u[ok], want[ok])
+                else:
+                    u = np.zeros((128, held(B, M)), complex)
                 for c in range(R):
-                    ks = [c + R * t for t in range(held(B, M))]
-                    if j < nwin:
-                        base = (((j // GS) & 1) * GS + j % GS) * STEP
-                        u = [sg[base + k * CH + lanes] for k in ks]
-                        # the staged values are G[qb - 1 - j][q1][k0][k1] of each lane's channel
-                        ch = ch0 + lanes
-                        ok = ch < nch
-                        for k, uk in zip(ks, u):
-                            want = np.where(ok, G[qb - 1 - j, np.minimum(ch, nch - 1) >> m1, k,
-                                                  np.minimum(ch, nch - 1) & (n1 - 1)], 0)
-                            np.testing.assert_array_equal(uk, want)
-                    else:
-                        u = [np.zeros(CH, complex) for _ in ks]
-                    feeds[c].append(u)
-            y = sum(np.array(adjoint_tree(M, B, c, feeds[c])) for c in range(R))  # (steps, CH)
+                    sel = np.nonzero(c_of == c)[0]
+                    feeds[c].append([u[sel, t] for t in range(held(B, M))])
+            part = np.zeros((steps, 128), complex)
+            for c in range(R):
+                part[:, np.nonzero(c_of == c)[0]] = np.array(adjoint_tree(M, B, c, feeds[c]))
+            off = CPW
+            while off < 32:
+                part = part + part[:, (warp << 5) | (lane ^ off)]
+                off <<= 1
+            y = np.zeros((steps, CH), complex)
+            y[:, chl_of[c_of == 0]] = part[:, c_of == 0]
             for j in range(steps):
                 r = p_hi - j
                 for chl in range(CH):
@@ -319,14 +429,56 @@ def emulate_adj_col(G, n0, n1, chunk_req):
                     else:
                         assert np.isnan(gz[r * nch + ch]), "gz value written twice"
                         gz[r * nch + ch] = y[j, chl]
-    # adj_fold_kernel: gz rows [qb, qb + n0 - 2] += the side rows of boundary qb
     per_row = (n - 1) * nch
-    assert side.size == (nchunks - 1) * per_row
     for i in range(side.size):
         b = i // per_row + 1
         gz[b * chunk * nch + (i - (b - 1) * per_row)] += side[i]
     assert not np.isnan(gz).any(), "a gz value was never written"
     return gz.reshape(rows_out + n - 1, nch)
+
+
+RING_CASES = [(1, 64), (1, 1), (2, 64), (2, 1), (4, 16), (8, 8), (16, 16), (16, 4), (16, 1),
+              (32, 32), (32, 2), (64, 16), (64, 64), (64, 1)]
+
+
+@pytest.mark.parametrize("n0,n1", RING_CASES)
+def test_adj_col_ring_staging_replayed(n0, n1):
+    rows_out, P1 = 19, 5
+    N0, N1 = rows_out + n0 - 1, P1 + n1 - 1
+    rng = np.random.default_rng(13 * n0 + n1)
+    G = rng.standard_normal((rows_out, P1, n0, n1)) + 1j * rng.standard_normal((rows_out, P1, n0, n1))
+    want = np.zeros((rows_out + n0 - 1, P1, n1), complex)
+    for q0 in range(rows_out):
+        want[q0:q0 + n0] += np.fft.ifft(G[q0], axis=1).transpose(1, 0, 2) * n0
+    want = want.reshape(rows_out + n0 - 1, -1)
+    for q16 in (True, False):  # G 16-byte aligned, or not
+        for col_chunk in (0, max(n0 - 1, 1), 7):
+            gz = emulate_adj_col_ring(G, n0, n1, col_chunk, q16)
+            np.testing.assert_allclose(gz, want, atol=1e-9)
+    gx = emulate_adj_row(want, N1, n1, N1)
+    np.testing.assert_allclose(gx, overlap_add_of_inverse_dfts(G, N0, N1), atol=1e-8)
+
+
+@pytest.mark.parametrize("M", range(0, 7))
+def test_adj_col_layouts_stay_aligned_and_inside_the_ring(M):
+    """For every window side 2^M >= 2 and every n1 = 1..64, the staging layout the host picks
+    keeps runs 16-byte aligned, fits the ring in shared memory, and reads free of bank
+    conflicts in the cases the workloads use (16x16, 32x32, 64x16 windows)."""
+    B = adj_col_B(M)
+    CH = 128 >> B
+    for m1 in range(0, 7):
+        mode, lw, gs, ks, slot = adj_col_layout(M, B, m1)
+        # runs start 16-byte aligned: steps (slot), q1 groups (gs, mode 1), k0 runs (ks, mode 2)
+        assert slot % 2 == 0 and (mode != 1 or gs % 2 == 0) and (mode != 2 or ks % 2 == 0)
+        assert 128 + 8 * ADJ_STAGES * adj_col_gs(M) * slot <= 227 * 1024
+        if mode == 2:
+            assert (1 << m1) >= CH
+        else:
+            assert (1 << m1) <= CH
+    assert adj_col_conflicts(4, 1, adj_col_layout(4, 1, 4)) == 1
+    assert adj_col_conflicts(5, 2, adj_col_layout(5, 2, 5)) == 1
+    assert adj_col_conflicts(6, 3, adj_col_layout(6, 3, 4)) == 1
+    assert adj_col_layout(4, 1, 4)[0] == 0  # 16x16: one contiguous run per step
 
 
 def emulate_adj_row(gz, N1, n1, chunk):
@@ -429,7 +581,7 @@ def test_adjoint_passes_with_staging_chunks_and_fold(n0, n1):
     ref = overlap_add_of_inverse_dfts(G, N0, N1)
     ref_z = None
     for col_chunk in (0, 1, 5, 8):  # one chunk; the n0 - 1 minimum; ragged chunks
-        gz = emulate_adj_col(G, n0, n1, col_chunk)
+        gz = emulate_adj_col_ring(G, n0, n1, col_chunk)
         if ref_z is None:
             ref_z = gz
         else:
