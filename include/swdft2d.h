@@ -189,8 +189,9 @@ swdft_status swdft2d_execute_stage(swdft2d_plan_t plan, int32_t stage, const voi
  * dimension 1 / 0 (clamped to [0, min(m, 3)]), row_chunk = window columns per row-pass
  * thread, col_chunk = window rows per column-pass thread (0 = all), col_groups = 32-channel
  * groups per column-pass block, fused = 1: evaluate the row levels inside the column
- * kernel (one launch, z never written to HBM; windows with n1 <= 32 only), 0: two passes,
- * -1: the library's default.  Results do not depend on these values; speed does. */
+ * kernel (one launch, z never written to HBM; windows with n1 <= 32, or n1 = 64 and
+ * n0 <= 32), 0: two passes, -1: the library's default.  Results do not depend on these
+ * values; speed does. */
 swdft_status swdft2d_set_tree_config(swdft2d_plan_t plan, int32_t i, int32_t row_B,
                                      int64_t row_chunk, int32_t col_B, int64_t col_chunk,
                                      int32_t col_groups, int32_t fused);

@@ -58,7 +58,7 @@ int log2_exact(int64_t n) {
 }
 
 struct TreeConfig {
-    bool fused = false;  // n1 <= 32: row levels inside the column kernel (no z in HBM)
+    bool fused = false;  // n1 <= 64: row levels inside the column kernel (no z in HBM)
     int row_B = 2;
     int64_t row_chunk = 0;
     int col_B = 2;
@@ -219,12 +219,12 @@ void default_config(ArrayPlan &a, int sm_count, int conc) {
     // group per block (32 * 2^B threads)
     c.col_B = default_col_B(a.m0);
     c.col_groups = 1;
-    // fused form (row levels inside the column tile, n1 <= 32): it recomputes each z value
+    // fused form (row levels inside the column tile, fused_supported): it recomputes each z value
     // from the input (log2 n1 butterflies) instead of writing and re-reading z, which wins for
     // small windows (z is 1/n0 of the output) and when the z of the arrays in flight would
     // not stay in L2 (measured on 256..1024-square arrays with the 4x4 .. 64x16 windows:
     // fused faster for n0 n1 <= 64 everywhere and for n0 >= 16 once z exceeds ~100 MB)
-    const bool can_fuse = !a.ternary() && a.m1 <= 5 && a.algo == SWDFT_ALGO_TREE_F32;
+    const bool can_fuse = !a.ternary() && fused_supported(a.m0, a.m1) && a.algo == SWDFT_ALGO_TREE_F32;
     const bool small = a.n0 * a.n1 <= 64;
     const double z_live = (double)a.z_bytes(a.band_rows()) * std::max(1, conc);
     c.fused = can_fuse && (small || (a.n0 >= 16 && z_live > 96e6));
@@ -550,7 +550,7 @@ cudaError_t enqueue_forward(const swdft2d_plan_s *plan, const ArrayPlan &a, cons
         c.chunk = a.cfg.col_chunk;
         return launch_col_tree3(c, s);
     }
-    if (a.cfg.fused && a.m1 <= 5) {
+    if (a.cfg.fused && fused_supported(a.m0, a.m1)) {
         // one launch: row levels inside the column tile; stage 0 has nothing to do
         if (!(stages & 2)) return cudaSuccess;
         FusedTreeArgs f;
@@ -699,7 +699,7 @@ bool tune_record_applies(const TuneRecord &r, const char *gpu, const ArrayPlan &
         return false;
     if (r.row_B < 0 || r.row_B > std::min(a.m1, 3) || r.col_B < 0 || r.col_B > std::min(a.m0, 3) ||
         r.row_chunk < 0 || r.col_chunk < 0 || r.col_groups < 1 || r.col_groups > 8 || r.fused < 0 || r.fused > 1 ||
-        (r.fused == 1 && a.m1 > 5))
+        (r.fused == 1 && !fused_supported(a.m0, a.m1)))
         return false;
     // chunks so short that a pass would need more than 65535 of them (the grid's y limit) on
     // this array's band: a stale or hand-edited record, not one the autotuner writes
@@ -935,7 +935,7 @@ swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t 
     int32_t n = 0;
     for (const auto &a : plan->arrays)
         n += adjoint ? 1 + adj_col_launches(a.band_rows(), a.m0, a.adj_chunk(a.band_rows()))
-                     : ((a.algo == SWDFT_ALGO_TREE_F32 && a.cfg.fused && a.m1 <= 5) ? 1 : 2);
+                     : ((a.algo == SWDFT_ALGO_TREE_F32 && a.cfg.fused && fused_supported(a.m0, a.m1)) ? 1 : 2);
     *launches = n;
     return SWDFT_OK;
 }
@@ -1028,7 +1028,7 @@ swdft_status swdft2d_set_tree_config(swdft2d_plan_t plan, int32_t i, int32_t row
         default_config(tmp, plan->sm_count, plan->conc);
         c.fused = tmp.cfg.fused;
     } else {
-        c.fused = fused == 1 && a.m1 <= 5 && !a.ternary();
+        c.fused = fused == 1 && fused_supported(a.m0, a.m1) && !a.ternary();
     }
     c.row_B = std::max(0, std::min(row_B, std::min(a.m1, 3)));
     c.row_chunk = row_chunk;
@@ -1282,9 +1282,9 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
                 }
             }
         }
-        // fused form (n1 <= 32): one kernel, timed as a whole against the two passes
+        // fused form: one kernel, timed as a whole against the two passes
         float best = best_row + best_col;
-        if (ok && a.m1 <= 5) {
+        if (ok && fused_supported(a.m0, a.m1)) {
             for (int nc : {4, 8, 16}) {
                 TreeConfig c = best_c;
                 c.fused = true;

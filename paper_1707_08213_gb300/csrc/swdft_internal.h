@@ -213,7 +213,7 @@ int col_tree_clamp_groups(int m0, int B, int groups);
 int col_tree_blocks_per_sm(int m0, int B, int groups);
 cudaError_t launch_col_tree(const ColTreeArgs &a, cudaStream_t s);
 
-// Fused tree, n1 <= 32: one kernel evaluates the row levels of each z row inside the column
+// Fused tree, n1 <= 64: one kernel evaluates the row levels of each z row inside the column
 // tile (a warp per 32 channels) and the column levels as col_tree does; z never reaches HBM.
 struct FusedTreeArgs {
     const void *x = nullptr;  // first input row of the band
@@ -228,6 +228,9 @@ struct FusedTreeArgs {
     int groups = 1;
 };
 cudaError_t launch_fused_tree(const FusedTreeArgs &a, cudaStream_t s);
+// Window shapes the fused form is built for: n1 <= 32, and n1 = 64 with n0 <= 32 (64 x 64
+// windows would need more registers than the fused kernel's two resident blocks allow).
+inline bool fused_supported(int m0, int m1) { return m1 >= 0 && (m1 <= 5 || (m1 == 6 && m0 <= 5)); }
 
 // Adjoint of the column levels: gz[r][q1][k1] = scale * sum_{j0,k0} G[r-j0][q1][k0][k1] w_{n0}^{+j0 k0}
 // for the rows_out + n0 - 1 z rows of a band (G holds rows_out window rows).

@@ -85,7 +85,7 @@ int fused_col_B(int m0) { return m0 >= 6 ? 3 : std::min(m0, 2); }
 cudaError_t launch_fused_tree(const FusedTreeArgs &a, cudaStream_t s) {
     const int64_t nch = a.P1 << a.m1;
     if (a.rows_out <= 0 || nch <= 0) return cudaSuccess;
-    if (a.m0 < 0 || a.m0 > kMaxLog2 || a.m1 < 0 || a.m1 > 5 || a.rows_out > INT32_MAX || a.P1 > INT32_MAX)
+    if (a.m0 < 0 || a.m0 > kMaxLog2 || !fused_supported(a.m0, a.m1) || a.rows_out > INT32_MAX || a.P1 > INT32_MAX)
         return cudaErrorInvalidValue;
     FusedParams p;
     p.g.z = nullptr;
@@ -99,7 +99,9 @@ cudaError_t launch_fused_tree(const FusedTreeArgs &a, cudaStream_t s) {
     p.g.zslice = 0;
     p.g.oslice = 0;
     const int B = fused_col_B(a.m0);
-    p.g.groups = col_tree_clamp_groups(a.m0, B, a.groups);
+    // n1 = 64: a tile holds whole window columns (an even number of 32-channel groups)
+    p.g.groups = a.m1 == 6 ? std::max(2, col_tree_clamp_groups(a.m0, B, a.groups) & ~1)
+                           : col_tree_clamp_groups(a.m0, B, a.groups);
     p.x = a.x;
     p.ld = a.ld;
     p.zrows = (int)(a.rows_out + (int64_t(1) << a.m0) - 1);

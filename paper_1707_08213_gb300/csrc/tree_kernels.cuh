@@ -124,7 +124,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // z rows for a column tile come from one of two stages:
 //  * ZStageLoad  : cp.async copies of z rows written by the row pass (two-pass form);
 //  * ZStageRowDft: the row levels of Eq. rowfswft2d evaluated in the tile itself (fused
-//                  form, n1 <= 32): z never goes to HBM.
+//                  form): z never goes to HBM.
 // fetch(ring, r_lo, r_hi, CH, ch0, RD) fills ring rows r_lo..r_hi-1; wait() completes it.
 struct ZStageLoad {
     const float2 *z;
@@ -144,61 +144,131 @@ struct ZStageLoad {
 };
 
 // Row levels of one z row for 32 channels, by one warp.  Channels are (q1, k1) with k1
-// fastest, so the warp covers 32 >> M1 window columns q1.  Level t of the tree under the
-// window ending at column p needs level t-1 at p and p - s_t (s_t = 2^(M1-t)); for one
+// fastest, so the warp covers 32 >> M1 window columns q1 (M1 <= 5).  Level t of the tree under
+// the window ending at column p needs level t-1 at p and p - s_t (s_t = 2^(M1-t)); for one
 // window that is 2^(M1-t) positions x 2^t nodes = n1 values per level, one per lane:
 // lane (i, d) holds node i at position p - d.  Each level is two shuffles and one node
 // evaluation T = T_{t-1}(p - d - s_t) + W_t^i T_{t-1}(p - d) per lane; level M1 leaves node
 // k1 = lane on lane k1, in natural order.
+//
+// n1 = 64 (M1 = 6): a warp evaluates one whole window column, both 32-channel halves (the
+// tile then holds an even number of channel groups).  A level has 64 values, two per lane:
+// value e of lane L is flat index l = 2 L + e in the (i, d) layout above.  For levels 1..5, d
+// has at least one bit and its lowest bit is e, so both operands of a value sit in the same
+// register (e) of the lanes holding l_c = (i mod 2^(t-1)) 2^(7-t) + d and l_c + 2^(6-t): one
+// shuffle each.  After level 5 lane L holds node L at p (e = 0) and at p - 1 (e = 1): level
+// 6's nodes L and 32 + L need just those two, in the lane's own registers.  Same nodes,
+// operands and operation order as the row pass's tree, so z is bit for bit the two-pass
+// form's.
 template <int M1, bool CPLX>
 struct ZStageRowDft {
     const void *x;      // first input row of the band
     int64_t ld;
     int zrows;          // z rows that exist (band rows + n0 - 1)
     int P1;
-    float2 w[M1 > 0 ? M1 : 1];  // this lane's twiddle per level
+    // this lane's twiddle per level (M1 <= 5); for M1 = 6, per level 1..5 and value, then
+    // level 6's W^lane and W^(32 + lane)
+    float2 w[M1 == 6 ? 12 : (M1 > 0 ? M1 : 1)];
 
     __device__ __forceinline__ void init(const float2 *om64) {
-        const int l = threadIdx.x & ((1 << M1) - 1);
+        if constexpr (M1 == 6) {
+            const int lane = threadIdx.x & 31;
 #pragma unroll
-        for (int t = 1; t <= M1; ++t) {
-            const int i = l >> (M1 - t);
-            w[t - 1] = om64[i << (6 - t)];
+            for (int t = 1; t <= 5; ++t)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) w[2 * (t - 1) + e] = om64[((2 * lane + e) >> (6 - t)) << (6 - t)];
+            w[10] = om64[lane];
+            w[11] = om64[32 + lane];
+        } else {
+            const int l = threadIdx.x & ((1 << M1) - 1);
+#pragma unroll
+            for (int t = 1; t <= M1; ++t) {
+                const int i = l >> (M1 - t);
+                w[t - 1] = om64[i << (6 - t)];
+            }
+        }
+    }
+
+    __device__ __forceinline__ float2 load(int r, int64_t col) const {
+        if constexpr (CPLX)
+            return __ldg(reinterpret_cast<const float2 *>(x) + (int64_t)r * ld + col);
+        else
+            return make_float2(__ldg(reinterpret_cast<const float *>(x) + (int64_t)r * ld + col), 0.f);
+    }
+
+    // n1 = 64: window column q1 of z row r; lane L returns nodes L (lo) and 32 + L (hi)
+    __device__ __forceinline__ void row_dft64(int r, int64_t q1, float2 &lo, float2 &hi) const {
+        const int lane = threadIdx.x & 31;
+        {
+            float2 v[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            if (r >= 0 && r < zrows && q1 < P1) {  // level 0 at flat index d = 2 L + e: x at p - d
+                const int64_t p = q1 + 63;
+                v[0] = load(r, p - 2 * lane);
+                v[1] = load(r, p - 2 * lane - 1);
+            }
+#pragma unroll
+            for (int t = 1; t <= 5; ++t) {
+                float2 nv[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int l = 2 * lane + e;
+                    const int i = l >> (6 - t), d = l & ((1 << (6 - t)) - 1);
+                    const int lc = ((i & ((1 << (t - 1)) - 1)) << (7 - t)) | d;  // node i mod 2^(t-1), offset d
+                    const float cx = __shfl_sync(0xffffffffu, v[e].x, lc >> 1);
+                    const float cy = __shfl_sync(0xffffffffu, v[e].y, lc >> 1);
+                    const float sx = __shfl_sync(0xffffffffu, v[e].x, (lc >> 1) + (1 << (5 - t)));  // offset d + s_t
+                    const float sy = __shfl_sync(0xffffffffu, v[e].y, (lc >> 1) + (1 << (5 - t)));
+                    nv[e] = c_add(make_float2(sx, sy), c_mul(w[2 * (t - 1) + e], make_float2(cx, cy)));
+                }
+                v[0] = nv[0];
+                v[1] = nv[1];
+            }
+            lo = c_add(v[1], c_mul(w[10], v[0]));
+            hi = c_add(v[1], c_mul(w[11], v[0]));
         }
     }
 
     __device__ __forceinline__ float2 row_dft(int r, int64_t ch0) const {
         const int lane = threadIdx.x & 31;
-        const int l = lane & ((1 << M1) - 1);
-        const int base = lane - l;
-        const int64_t q1 = (ch0 >> M1) + (lane >> M1);
-        float2 v = make_float2(0.f, 0.f);
-        if (r >= 0 && r < zrows && q1 < P1) {
-            const int64_t col = q1 + (1 << M1) - 1 - l;  // level 0 on lane d: x at p - d
-            if constexpr (CPLX)
-                v = __ldg(reinterpret_cast<const float2 *>(x) + (int64_t)r * ld + col);
-            else
-                v = make_float2(__ldg(reinterpret_cast<const float *>(x) + (int64_t)r * ld + col), 0.f);
-        }
+        {
+            const int l = lane & ((1 << M1) - 1);
+            const int base = lane - l;
+            const int64_t q1 = (ch0 >> M1) + (lane >> M1);
+            float2 v = make_float2(0.f, 0.f);
+            if (r >= 0 && r < zrows && q1 < P1) v = load(r, q1 + (1 << M1) - 1 - l);  // level 0 on lane d: x at p - d
 #pragma unroll
-        for (int t = 1; t <= M1; ++t) {
-            const int i = l >> (M1 - t), d = l & ((1 << (M1 - t)) - 1);
-            const int src = base + ((i & ((1 << (t - 1)) - 1)) << (M1 - t + 1)) + d;  // node i mod 2^(t-1), offset d
-            const float cx = __shfl_sync(0xffffffffu, v.x, src);
-            const float cy = __shfl_sync(0xffffffffu, v.y, src);
-            const float sx = __shfl_sync(0xffffffffu, v.x, src + (1 << (M1 - t)));  // offset d + s_t
-            const float sy = __shfl_sync(0xffffffffu, v.y, src + (1 << (M1 - t)));
-            v = c_add(make_float2(sx, sy), c_mul(w[t - 1], make_float2(cx, cy)));
+            for (int t = 1; t <= M1; ++t) {
+                const int i = l >> (M1 - t), d = l & ((1 << (M1 - t)) - 1);
+                const int src = base + ((i & ((1 << (t - 1)) - 1)) << (M1 - t + 1)) + d;  // node i mod 2^(t-1), offset d
+                const float cx = __shfl_sync(0xffffffffu, v.x, src);
+                const float cy = __shfl_sync(0xffffffffu, v.y, src);
+                const float sx = __shfl_sync(0xffffffffu, v.x, src + (1 << (M1 - t)));  // offset d + s_t
+                const float sy = __shfl_sync(0xffffffffu, v.y, src + (1 << (M1 - t)));
+                v = c_add(make_float2(sx, sy), c_mul(w[t - 1], make_float2(cx, cy)));
+            }
+            return v;
         }
-        return v;
     }
 
     __device__ __forceinline__ void fetch(float2 *ring, int r_lo, int r_hi, int CH, int64_t ch0, int RD) {
         const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-        const int groups = CH >> 5;
-        for (int e = warp; e < (r_hi - r_lo) * groups; e += nwarp) {
-            const int rr = r_lo + e / groups, g = e - (e / groups) * groups;
-            ring[(rr & (RD - 1)) * CH + g * 32 + (threadIdx.x & 31)] = row_dft(rr, ch0 + g * 32);
+        const int lane = threadIdx.x & 31;
+        if constexpr (M1 == 6) {
+            const int cols = CH >> 6;  // whole window columns of the tile (CH a multiple of 64)
+            for (int e = warp; e < (r_hi - r_lo) * cols; e += nwarp) {
+                const int rr = r_lo + e / cols, wc = e - (e / cols) * cols;
+                float2 lo, hi;
+                row_dft64(rr, (ch0 >> 6) + wc, lo, hi);
+                float2 *dst = ring + (rr & (RD - 1)) * CH + wc * 64 + lane;
+                dst[0] = lo;
+                dst[32] = hi;
+            }
+        } else {
+            const int groups = CH >> 5;
+            for (int e = warp; e < (r_hi - r_lo) * groups; e += nwarp) {
+                const int rr = r_lo + e / groups, g = e - (e / groups) * groups;
+                ring[(rr & (RD - 1)) * CH + g * 32 + lane] = row_dft(rr, ch0 + g * 32);
+            }
         }
     }
     __device__ __forceinline__ void wait() {}
@@ -289,7 +359,7 @@ __global__ void __launch_bounds__(256, (M >= 6 ? 1 : 2)) col_tree_kernel(const _
     col_tile<M, B>(p.g, blockIdx.x, blockIdx.y, p.om.w, ring, blockIdx.z);
 }
 
-// Fused form: both level groups in one kernel, x in, window DFTs out.
+// Fused form: both level groups in one kernel, x in, window DFTs out (n1 <= 64).
 struct FusedParams {
     ColGeom g;          // g.z unused
     const void *x;      // first input row of the band
@@ -362,6 +432,12 @@ int col_blocks_per_sm(int threads, int groups);
             case 9: fused_tree_kernel<M_, B_, 4, true><<<g, b, smem, s>>>(p); break;             \
             case 10: fused_tree_kernel<M_, B_, 5, false><<<g, b, smem, s>>>(p); break;           \
             case 11: fused_tree_kernel<M_, B_, 5, true><<<g, b, smem, s>>>(p); break;            \
+            case 12:                                                                             \
+                if constexpr (M_ <= 5) fused_tree_kernel<M_, B_, 6, false><<<g, b, smem, s>>>(p); \
+                break;                                                                           \
+            case 13:                                                                             \
+                if constexpr (M_ <= 5) fused_tree_kernel<M_, B_, 6, true><<<g, b, smem, s>>>(p); \
+                break;                                                                           \
             default: break;                                                                      \
         }                                                                                        \
     }

@@ -376,3 +376,14 @@ def test_load_tuning_rejects_chunks_beyond_the_grid_limit(nat, tmp_path):
     assert wide.load_tuning(str(cache), "G") == 0
     cache.write_text(_tune_line("G", N0, N1, 2, 2, fused=0, col_chunk=2, col_B=1, row_B=1))
     assert nat.Plan([shp(N0, N1, 2, 2)]).load_tuning(str(cache), "G") == 1
+
+
+def test_fused_form_covers_n1_64_up_to_n0_32(nat):
+    """The fused form (one launch) is built for n1 <= 32 and for n1 = 64 with n0 <= 32: a plan
+    asked for it on 16x64 or 1x64 windows runs one kernel; on 64x64 windows it keeps two passes."""
+    for (n0, n1), want in (((16, 64), 1), ((1, 64), 1), ((32, 64), 1), ((64, 64), 2), ((64, 32), 1)):
+        p = nat.Plan([shp(200, 200, n0, n1)])
+        p.set_tree_config(0, 2, 0, 2, 0, 1, 1)
+        assert p.launch_count() == want, (n0, n1)
+    # 1024x2048 complex with 16x64 windows: z would be 1 GB, so the default is the fused form
+    assert nat.Plan([shp(1024, 2048, 16, 64, dtype=nat.C64)]).launch_count() == 1

@@ -242,7 +242,9 @@ def test_sinusoids_512_every_coefficient_tree_and_split_bf16(sw):
 
 FUSED_SHAPES = [(41, 67, 8, 16, False), (61, 35, 32, 4, True), (90, 75, 64, 8, False),
                 (70, 100, 16, 32, True), (100, 100, 32, 32, False), (23, 50, 1, 32, False),
-                (50, 23, 32, 1, True), (9, 9, 8, 8, False)]
+                (50, 23, 32, 1, True), (9, 9, 8, 8, False),
+                (60, 130, 16, 64, True), (45, 100, 32, 64, False), (20, 64, 1, 64, True),
+                (33, 200, 8, 64, False)]
 
 
 @pytest.mark.parametrize("chunk", [0, 5])

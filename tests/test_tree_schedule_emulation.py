@@ -685,10 +685,43 @@ class RowDftStage:
             v = v[src + (1 << (M1 - t))] + self.om64[i << (6 - t)] * v[src]
         return v
 
+    def row_dft64(self, r, q1):
+        """n1 = 64: one warp evaluates the whole window column q1; value e of lane L is flat
+        index l = 2 L + e of the (i, d) layout, so levels 1..5 take both operands from register
+        e of the source lanes, and level 6 (nodes L and 32 + L) from the lane's own two
+        registers.  Returns (lo, hi) per lane."""
+        lane = np.arange(32)
+        v = np.zeros((2, 32), complex)
+        if 0 <= r < self.zrows and q1 < self.P1:
+            p = q1 + 63
+            v[0] = self.x[r, p - 2 * lane]
+            v[1] = self.x[r, p - 2 * lane - 1]
+        for t in range(1, 6):
+            nv = np.zeros_like(v)
+            for e in range(2):
+                l = 2 * lane + e
+                i, d = l >> (6 - t), l & ((1 << (6 - t)) - 1)
+                assert ((d & 1) == e).all()  # an operand's register is the value's own
+                lc = ((i & ((1 << (t - 1)) - 1)) << (7 - t)) | d
+                ls = lc + (1 << (6 - t))
+                assert ((lc & 1) == e).all() and ((ls & 1) == e).all()
+                assert ((lc >> 1) + (1 << (5 - t)) == ls >> 1).all()
+                nv[e] = v[e][ls >> 1] + self.om64[i << (6 - t)] * v[e][lc >> 1]
+            v = nv
+        return v[1] + self.om64[lane] * v[0], v[1] + self.om64[32 + lane] * v[0]
+
     def fetch(self, ring, r_lo, r_hi, CH, ch0, RD):
         for rr in range(r_lo, r_hi):
-            for g in range(CH >> 5):
-                ring[(rr & (RD - 1)) * CH + g * 32 + np.arange(32)] = self.row_dft(rr, ch0 + g * 32)
+            if self.n1 == 64:  # whole window columns
+                assert CH % 64 == 0 and ch0 % 64 == 0
+                for wc in range(CH >> 6):
+                    lo, hi = self.row_dft64(rr, (ch0 >> 6) + wc)
+                    base = (rr & (RD - 1)) * CH + wc * 64
+                    ring[base + np.arange(32)] = lo
+                    ring[base + 32 + np.arange(32)] = hi
+            else:
+                for g in range(CH >> 5):
+                    ring[(rr & (RD - 1)) * CH + g * 32 + np.arange(32)] = self.row_dft(rr, ch0 + g * 32)
 
     def check(self, got, zr, ch):  # the n1-point DFT of the window's row (0 outside x)
         q1, k1 = ch >> self.M1, ch & (self.n1 - 1)
@@ -785,13 +818,19 @@ def test_two_pass_forward_with_ring_staging(n0, n1, rows_out, P1, groups, chunks
             np.testing.assert_allclose(out, ref, atol=1e-9)
 
 
-@pytest.mark.parametrize("n0,n1,rows_out,P1,groups,chunks", [c for c in FWD_CASES if c[1] <= 32])
+FUSED64_CASES = [(16, 64, 7, 5, 1, (7, 3)), (1, 64, 4, 6, 2, (4, 3)), (32, 64, 5, 3, 2, (5, 2))]
+
+
+@pytest.mark.parametrize("n0,n1,rows_out,P1,groups,chunks",
+                         [c for c in FWD_CASES if c[1] <= 32] + FUSED64_CASES)
 def test_fused_forward_with_row_dfts_by_shuffles(n0, n1, rows_out, P1, groups, chunks):
     rng = np.random.default_rng(2000 + n0 * 64 + n1)
     N0, N1 = rows_out + n0 - 1, P1 + n1 - 1
     x = rng.standard_normal((N0, N1))
     ref = every_window_dft(x, n0, n1, 1.0)
     m1 = n1.bit_length() - 1
+    if n1 == 64:  # launch_fused_tree: tiles of whole window columns
+        groups = max(2, groups & ~1)
     for chunk in chunks:
         out = emulate_col_pass(RowDftStage(x, n1), n0, col_split(n0.bit_length() - 1), groups, m1,
                                P1, rows_out, chunk, 1.0)
