@@ -46,7 +46,9 @@ FALLBACK_HBM_GBS = 6800.0
 # files whose content defines the column-level kernel (for matching a stored ncu capture)
 COL_KERNEL_SOURCES = ["paper_1707_08213_gb300/csrc/tree_core.cuh",
                       "paper_1707_08213_gb300/csrc/tree_kernels.cuh",
-                      "paper_1707_08213_gb300/csrc/tree_col_m5.cu"]
+                      "paper_1707_08213_gb300/csrc/tree_col_m5.cu",
+                      "paper_1707_08213_gb300/csrc/tree_col.cu",
+                      "paper_1707_08213_gb300/csrc/sm100_ptx.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "col_tree_sinusoids_512.json")
 TC_PROFILE_FILE = os.path.join(ROOT, "profiles", "tc_col_sinusoids_512.json")
 TC_KERNEL_SOURCES = ["paper_1707_08213_gb300/csrc/tc_kernels.cu",
@@ -955,7 +957,7 @@ def run_ours(args):
     except Exception:
         pass
     kname = ("fused_tree_kernel<5,2,5,false> (row levels in the column tile + column levels)"
-             if fused else "col_tree_kernel<5,2> (column levels, Eq. colfswft2d)")
+             if fused else "col_tree_tma_kernel<5,2> (column levels, Eq. colfswft2d; z rows staged by TMA)")
     roofline = {"bound": "hbm", "kernel": kname,
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,

@@ -598,6 +598,8 @@ cudaError_t enqueue_forward(const swdft2d_plan_s *plan, const ArrayPlan &a, cons
     c.B = a.cfg.col_B;
     c.chunk = a.cfg.col_chunk;
     c.groups = a.cfg.col_groups;
+    c.z_full = static_cast<const float2 *>(ws);  // z's padding rows start the workspace
+    c.z_pad = a.z_pad();
     return launch_col_tree(c, s);
 }
 
@@ -1363,10 +1365,11 @@ swdft_status swdft2d_load_tuning(swdft2d_plan_t plan, const char *path, const ch
 }
 
 swdft_status swdft2d_check_device(void) {
-    int status = 0, probe = 0;
-    if (tc_status(&status, true) != cudaSuccess || probe_status(&probe, true) != cudaSuccess)
+    int status = 0, probe = 0, col = 0;
+    if (tc_status(&status, true) != cudaSuccess || probe_status(&probe, true) != cudaSuccess ||
+        col_tma_status(&col, true) != cudaSuccess)
         return SWDFT_ERR_CUDA;
-    return (status || probe) ? SWDFT_ERR_DEVICE_TIMEOUT : SWDFT_OK;
+    return (status || probe || col) ? SWDFT_ERR_DEVICE_TIMEOUT : SWDFT_OK;
 }
 
 swdft_status swdft2d_destroy(swdft2d_plan_t plan) {

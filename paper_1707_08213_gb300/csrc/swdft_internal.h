@@ -201,7 +201,13 @@ struct ColTreeArgs {
     int64_t slices = 1;         // stacks of z rows; slice s reads z + s*z_slice and
     int64_t z_slice = 0;        // writes out + s*out_slice (elements).  Rows before a
     int64_t out_slice = 0;      // slice's first row must be readable (padding / previous slice).
+    // Optional, one stack: z_full = z's first padding row (z = z_full + z_pad * P1 * n1).
+    // Given and 16-byte aligned with P1 * n1 even, the tiles' z rows are loaded by TMA.
+    const float2 *z_full = nullptr;
+    int64_t z_pad = 0;
 };
+// Device word of the TMA-staged column kernels (1 = a bounded wait gave up).
+cudaError_t col_tma_status(int *status, bool reset);
 // Largest m1 a column pass accepts (coefficient blocks of up to 2^18 per window column).
 constexpr int kMaxInnerLog2 = 18;
 

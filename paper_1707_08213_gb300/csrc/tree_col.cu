@@ -1,6 +1,7 @@
 // Column-level pass (Eq. colfswft2d): launcher.  Kernel instantiations live in
 // tree_col_m*.cu so they compile in parallel.
 #include <algorithm>
+#include <cstring>
 
 #include "tree_kernels.cuh"
 
@@ -32,6 +33,46 @@ int col_tree_blocks_per_sm(int m0, int B, int groups) {
     }
 }
 
+cudaError_t col_tma_status(int *status, bool reset) {
+    *status = 0;
+    for (int M = 0; M <= kMaxLog2; ++M) {
+        int st = 0;
+        cudaError_t e = cudaSuccess;
+        switch (M) {
+#define F(M_)                                  \
+    case M_:                                   \
+        e = col_tma_status_mb<M_>(&st, reset); \
+        break;
+            F(0) F(1) F(2) F(3) F(4) F(5) F(6)
+#undef F
+        }
+        if (e != cudaSuccess) return e;
+        if (st) *status = 1;
+    }
+    return cudaSuccess;
+}
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tiled_encoder() {
+    static EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        return cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                           cudaSuccess &&
+                       q == cudaDriverEntryPointSuccess
+                   ? reinterpret_cast<EncodeTiledFn>(p)
+                   : nullptr;
+    }();
+    return fn;
+}
+
+}  // namespace
+
 cudaError_t launch_col_tree(const ColTreeArgs &a, cudaStream_t s) {
     if (a.P1 < 0 || a.m1 < 0 || a.m1 > kMaxInnerLog2 || a.P1 > (INT64_MAX >> kMaxInnerLog2)) return cudaErrorInvalidValue;
     const int64_t nch = a.P1 << a.m1;
@@ -57,6 +98,45 @@ cudaError_t launch_col_tree(const ColTreeArgs &a, cudaStream_t s) {
     const int64_t gy = (a.rows_out + p.g.chunk - 1) / p.g.chunk;
     if (gy > 65535 || gx > INT32_MAX) return cudaErrorInvalidValue;
     dim3 block(32 * (1 << B) * groups);
+    // one stack of z rows given from its first padding row: the tile's z rows come by TMA
+    // (rows 16-byte aligned: nch even, the base aligned; every tile's first channel is even)
+    // (its ring holds one more step group: tiles whose ring would pass the default 48 KB of
+    // dynamic shared memory keep the cp.async stage)
+    const size_t tma_smem = 128 + sizeof(float2) * col_ring_rows(a.m0 < 0 ? 0 : a.m0, kColTmaAhead) * per_block;
+    // (chunks must start on whole step groups)
+    if (a.z_full && a.slices == 1 && nch % 2 == 0 && (uintptr_t)a.z_full % 16 == 0 && a.z_pad >= 0 &&
+        nch <= (int64_t(1) << 32) && a.z == a.z_full + a.z_pad * nch && tma_smem <= 48 * 1024 &&
+        p.g.chunk % col_group(a.m0 < 0 ? 0 : a.m0) == 0) {
+        EncodeTiledFn enc = tiled_encoder();
+        if (enc) {
+            ColTmaParams q;
+            std::memset(&q, 0, sizeof(q));
+            const int64_t rows = a.z_pad + a.rows_out + (int64_t(1) << a.m0) - 1;
+            cuuint64_t dims[2] = {(cuuint64_t)nch, (cuuint64_t)rows};
+            cuuint64_t strides[1] = {(cuuint64_t)nch * sizeof(float2)};
+            cuuint32_t box[2] = {(cuuint32_t)per_block, (cuuint32_t)col_group(a.m0)};
+            cuuint32_t estr[2] = {1, 1};
+            if (enc(&q.zmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<float2 *>(a.z_full), dims, strides, box,
+                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+                q.g = p.g;
+                q.pad = (int)a.z_pad;
+                q.om = p.om;
+                dim3 grid((unsigned)gx, (unsigned)gy, 1);
+                switch (a.m0 * 8 + B) {
+#define F(M_, B_)                                      \
+    case M_ * 8 + B_:                                  \
+        col_tma_launch_mb<M_, B_>(q, grid, block, s);  \
+        break;
+                    SWDFT_MB_CASES(F)
+#undef F
+                    default:
+                        return cudaErrorInvalidValue;
+                }
+                return cudaGetLastError();
+            }
+        }
+    }
     // slices beyond the grid's z limit go out as further launches with shifted bases
     constexpr int64_t kMaxZ = 65535;
     for (int64_t s0 = 0; s0 < a.slices; s0 += kMaxZ) {

@@ -6,5 +6,6 @@ namespace swdft {
 #define F(M_, B_) SWDFT_COL_INSTANTIATE(M_, B_)
 F(5, 0) F(5, 1) F(5, 2) F(5, 3)
 #undef F
+SWDFT_COL_TMA_STATUS(5)
 
 }  // namespace swdft

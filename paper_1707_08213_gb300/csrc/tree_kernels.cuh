@@ -18,6 +18,9 @@
 
 #include <cstdint>
 
+#include <cuda.h>
+
+#include "sm100_ptx.cuh"
 #include "swdft_internal.h"
 #include "tree_core.cuh"
 
@@ -103,10 +106,13 @@ __global__ void __launch_bounds__(128) row_tree_kernel(const __grid_constant__ R
 __host__ __device__ constexpr int col_group(int M) { return tg_period(M) > 8 ? tg_period(M) : 8; }
 
 // Rows of z staged in shared memory per column-pass block: a ring that holds the level-0
-// look-back (n/2 rows) plus two step groups (the group being computed and the one being
-// fetched), rounded up to a power of two.
-__host__ __device__ constexpr int col_ring_rows(int M) {
-    const int need = (M >= 1 ? (1 << (M - 1)) : 0) + 2 * col_group(M);
+// look-back (n/2 rows) plus the group being computed and the `ahead` groups being fetched,
+// rounded up to a power of two.
+__host__ __device__ constexpr int col_ring_rows(int M, int ahead = 1) {
+    const int look = M >= 1 ? (1 << (M - 1)) : 0;
+    // TMA (ahead 2) loads whole groups: its look-back is rounded up to a group
+    const int need = (ahead >= 2 ? (look + col_group(M) - 1) / col_group(M) * col_group(M) : look) +
+                     (1 + ahead) * col_group(M);
     int r = 1;
     while (r < need) r <<= 1;
     return r;
@@ -276,11 +282,11 @@ struct ZStageRowDft {
 
 // Column pass, one block tile.  Thread = (channel ch = q1*n1 + k1, residue c, chunk of
 // window rows).  Warp w of a block takes residue w mod 2^B (uniform per warp) and channel
-// group w / 2^B.  The tile's z rows reach a shared-memory ring one step group ahead of use
-// (copied or computed by the stage); all residue warps read the same staged rows.  One
-// __syncthreads per step group, no spin-waits; the tile ends with a barrier, so the ring is
-// free for the next tile.
-template <int M, int B, class Stage>
+// group w / 2^B.  The tile's z rows reach a shared-memory ring AHEAD step groups ahead of use
+// (copied or computed by the stage; stage.wait() completes the oldest fetch still in flight);
+// all residue warps read the same staged rows.  One __syncthreads per step group; the tile
+// ends with a barrier, so the ring is free for the next tile.
+template <int M, int B, int AHEAD = 1, class Stage>
 __device__ __forceinline__ void col_tile_impl(const ColGeom &p, int64_t ch_block, int chunk_idx,
                                               const float2 *om64, float2 *ring, Stage &stage,
                                               int64_t slice = 0) {
@@ -289,7 +295,7 @@ __device__ __forceinline__ void col_tile_impl(const ColGeom &p, int64_t ch_block
     constexpr int n = 1 << M;
     constexpr int kP = col_group(M);  // steps per staged group, a multiple of Tree::kPeriod
     constexpr int kH = Tree::kHalf;
-    constexpr int RD = col_ring_rows(M);
+    constexpr int RD = col_ring_rows(M, AHEAD);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -316,10 +322,14 @@ __device__ __forceinline__ void col_tile_impl(const ColGeom &p, int64_t ch_block
     Tree tree;
     tree.init(c, om64);
     stage.fetch(ring, qa - kH, min(qa + kP, zr_end), CH, ch0, RD);
+#pragma unroll
+    for (int a = 1; a < AHEAD; ++a)
+        if (a * kP < steps) stage.fetch(ring, qa + a * kP, min(qa + (a + 1) * kP, zr_end), CH, ch0, RD);
     stage.wait();
     __syncthreads();
     for (int jb = 0; jb < steps; jb += kP) {
-        if (jb + kP < steps) stage.fetch(ring, qa + jb + kP, min(qa + jb + 2 * kP, zr_end), CH, ch0, RD);
+        if (jb + AHEAD * kP < steps)
+            stage.fetch(ring, qa + jb + AHEAD * kP, min(qa + jb + (AHEAD + 1) * kP, zr_end), CH, ch0, RD);
         static_for<0, kP>([&](auto JJ) {
             constexpr int J = decltype(JJ)::value;
             const int j = jb + J;
@@ -359,6 +369,72 @@ __global__ void __launch_bounds__(256, (M >= 6 ? 1 : 2)) col_tree_kernel(const _
     col_tile<M, B>(p.g, blockIdx.x, blockIdx.y, p.om.w, ring, blockIdx.z);
 }
 
+// z rows by TMA (two-pass form of a single array): z is described, from its first padding
+// row, as a 2D tensor [rows][nch] of 8-byte elements, and a step group of kP z rows is one
+// tiled load of a box of CH channels x kP rows (channels past nch and rows outside z read as
+// zero), issued by thread 0 and completing on the mbarrier of its fetch.  The tile's chunk
+// starts on a multiple of kP and its look-back is rounded up to whole groups, so every box
+// starts on a multiple of kP and lands in kP consecutive rows of the ring (a multiple of kP
+// rows long); rows a box carries beyond those asked for are never read.  The tile runs two
+// step groups ahead.  Waits are bounded: a wait that gives up records it in g_col_tma_status and the block
+// carries on (its outputs are then wrong; nothing hangs).
+constexpr uint32_t kColTmaPolls = 2000;  // ~1 ms per poll at most
+static __device__ int g_col_tma_status;  // one word per translation unit (no relocatable device code)
+
+// Fetch f completes on barrier f mod kColTmaBars, phase f / kColTmaBars; with the tile
+// kColTmaAhead groups ahead, a barrier is re-armed only after its previous fetch was waited for.
+constexpr int kColTmaAhead = 2;
+constexpr int kColTmaBars = kColTmaAhead + 1;
+template <int kP>
+struct ZStageTma {
+    const CUtensorMap *map;
+    int pad;            // padding rows in front of z (tensor row of z row r = r + pad)
+    uint64_t *bar;      // kColTmaBars mbarriers in shared memory
+    int k = 0;          // fetches issued so far
+    int w = 0;          // fetches waited for so far
+    // rows [r_lo, r_hi) widened to whole groups [floor(r_lo / kP) kP, ceil(r_hi / kP) kP)
+    __device__ __forceinline__ void fetch(float2 *ring, int r_lo, int r_hi, int CH, int64_t ch0, int RD) {
+        if (threadIdx.x == 0) {
+            const int g0 = r_lo >= 0 ? r_lo / kP : -((kP - 1 - r_lo) / kP);
+            const int g1 = (r_hi + kP - 1) / kP;
+            uint64_t *b = &bar[k % kColTmaBars];
+            fence_proxy_async_smem();  // the rows refilled here were last read by generic loads
+            mbar_expect_tx(b, (uint32_t)((g1 - g0) * kP * CH * sizeof(float2)));
+            for (int g = g0; g < g1; ++g)
+                tma_load_2d(ring + ((g * kP) & (RD - 1)) * CH, map, b, (int)ch0, g * kP + pad);
+        }
+        ++k;
+    }
+    // completes the oldest fetch still in flight
+    __device__ __forceinline__ void wait() {
+        if (w >= k) return;
+        const int f = w++;
+        if (!mbar_wait(&bar[f % kColTmaBars], (uint32_t)(f / kColTmaBars) & 1u, kColTmaPolls))
+            atomicExch(&g_col_tma_status, 1);
+    }
+};
+
+struct ColTmaParams {
+    CUtensorMap zmap;   // z from its first padding row: [pad + rows][nch], 8-byte elements
+    ColGeom g;          // g.z unused
+    int pad;
+    Omega64 om;
+};
+
+template <int M, int B>
+__global__ void __launch_bounds__(256, (M >= 6 ? 1 : 2)) col_tree_tma_kernel(const __grid_constant__ ColTmaParams p) {
+    extern __shared__ __align__(128) unsigned char col_smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(col_smem);       // kColTmaBars mbarriers
+    float2 *ring = reinterpret_cast<float2 *>(col_smem + 128);    // col_ring_rows(M, 2) x (32 * groups)
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < kColTmaBars; ++b) mbar_init(&bar[b], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    ZStageTma<col_group(M)> stage{&p.zmap, p.pad, bar};
+    col_tile_impl<M, B, kColTmaAhead>(p.g, blockIdx.x, blockIdx.y, p.om.w, ring, stage);
+}
+
 // Fused form: both level groups in one kernel, x in, window DFTs out (n1 <= 64).
 struct FusedParams {
     ColGeom g;          // g.z unused
@@ -387,6 +463,10 @@ void fused_launch_mb(const FusedParams &p, int m1, int cplx, dim3 g, dim3 b, cud
 template <int M, int B>
 void col_launch_mb(const ColParams &p, dim3 g, dim3 b, cudaStream_t s);
 template <int M, int B>
+void col_tma_launch_mb(const ColTmaParams &p, dim3 g, dim3 b, cudaStream_t s);
+template <int M>
+cudaError_t col_tma_status_mb(int *status, bool reset);  // the g_col_tma_status of M's unit
+template <int M, int B>
 int col_blocks_per_sm(int threads, int groups);
 
 #define SWDFT_ROW_INSTANTIATE(M_, B_)                                                        \
@@ -403,6 +483,11 @@ int col_blocks_per_sm(int threads, int groups);
     void col_launch_mb<M_, B_>(const ColParams &p, dim3 g, dim3 b, cudaStream_t s) {      \
         const size_t smem = sizeof(float2) * col_ring_rows(M_) * 32 * p.g.groups;          \
         col_tree_kernel<M_, B_><<<g, b, smem, s>>>(p);                                    \
+    }                                                                                     \
+    template <>                                                                           \
+    void col_tma_launch_mb<M_, B_>(const ColTmaParams &p, dim3 g, dim3 b, cudaStream_t s) { \
+        const size_t smem = 128 + sizeof(float2) * col_ring_rows(M_, kColTmaAhead) * 32 * p.g.groups; \
+        col_tree_tma_kernel<M_, B_><<<g, b, smem, s>>>(p);                                \
     }                                                                                     \
     template <>                                                                           \
     int col_blocks_per_sm<M_, B_>(int threads, int groups) {                              \
@@ -440,6 +525,18 @@ int col_blocks_per_sm(int threads, int groups);
                 break;                                                                           \
             default: break;                                                                      \
         }                                                                                        \
+    }
+
+// This unit's g_col_tma_status (read and reset by swdft2d_check_device).
+#define SWDFT_COL_TMA_STATUS(M_)                                                          \
+    template <>                                                                           \
+    cudaError_t col_tma_status_mb<M_>(int *status, bool reset) {                          \
+        cudaError_t e = cudaMemcpyFromSymbol(status, g_col_tma_status, sizeof(int));      \
+        if (e == cudaSuccess && reset && *status != 0) {                                  \
+            const int zero = 0;                                                           \
+            e = cudaMemcpyToSymbol(g_col_tma_status, &zero, sizeof(int));                 \
+        }                                                                                 \
+        return e;                                                                         \
     }
 
 // (M, B) pairs built: B <= min(M, 3), and B >= 2 for 64-point trees (fewer threads per tree

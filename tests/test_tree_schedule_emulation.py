@@ -606,8 +606,11 @@ def col_group(M):
     return max(tg_period(M), 8)
 
 
-def col_ring_rows(M):
-    need = ((1 << (M - 1)) if M >= 1 else 0) + 2 * col_group(M)
+def col_ring_rows(M, ahead=1):
+    look = (1 << (M - 1)) if M >= 1 else 0
+    if ahead >= 2:  # TMA: the look-back rounded up to whole groups
+        look = -(-look // col_group(M)) * col_group(M)
+    need = look + (1 + ahead) * col_group(M)
     r = 1
     while r < need:
         r <<= 1
@@ -649,10 +652,66 @@ class LoadStage:
             cc = np.arange(CH)
             ok = ch0 + cc < self.nch
             ring[(rr & (RD - 1)) * CH + cc] = np.where(ok, self.z[self.pad + rr, np.minimum(ch0 + cc, self.nch - 1)], 0)
+        return {rr & (RD - 1) for rr in range(r_lo, r_hi)}
 
     def check(self, got, zr, ch):  # a copy: bit for bit (NaN for padding rows)
         ok = ch < self.nch
         np.testing.assert_array_equal(got, np.where(ok, self.z[self.pad + zr, np.minimum(ch, self.nch - 1)], 0))
+
+    def wait(self):
+        pass
+
+
+class TmaStage(LoadStage):
+    """ZStageTma: thread 0 loads each ring row as one TMA box of CH channels x 1 row of the
+    2D tensor [pad + rows][nch] (8-byte elements; zero past nch and past the last row), the
+    loads of fetch f completing on mbarrier f mod 3 (the tile runs two groups ahead); wait()
+    completes the oldest fetch in flight.  Checks the TMA rules (inner coordinate x 8 bytes a
+    multiple of 16, the box's inner extent a multiple of 16 bytes and at most 256 elements, a
+    non-negative row) and that a barrier is never re-armed before its phase was waited for."""
+    AHEAD = 2
+    NB = AHEAD + 1
+
+    def __init__(self, z, pad, nch):
+        super().__init__(z, pad, nch)
+        self.k, self.w = 0, 0
+        self.armed, self.phase = [False] * self.NB, [0] * self.NB
+
+    def __call__(self, kP):
+        self.kP = kP
+        return self
+
+    def fetch(self, ring, r_lo, r_hi, CH, ch0, RD):
+        kP = self.kP
+        assert (8 * ch0) % 16 == 0 and (8 * CH) % 16 == 0 and CH <= 256 and kP <= 256
+        assert RD % kP == 0
+        b = self.k % self.NB
+        assert not self.armed[b], "barrier re-armed before its phase was waited for"
+        self.armed[b] = True
+        g0, g1 = r_lo // kP, -(-r_hi // kP)  # whole groups (floor, ceil)
+        rows = set()
+        for g in range(g0, g1):  # one box of CH channels x kP rows, zero outside z
+            dst = ((g * kP) & (RD - 1)) * CH
+            assert 0 <= dst and dst + kP * CH <= RD * CH  # inside the ring, no wrap
+            for i in range(kP):
+                y = self.pad + g * kP + i
+                cc = ch0 + np.arange(CH)
+                ok = (cc < self.nch) & (0 <= y) & (y < self.z.shape[0])
+                ring[dst + i * CH:dst + (i + 1) * CH] = np.where(
+                    ok, self.z[min(max(y, 0), self.z.shape[0] - 1), np.minimum(cc, self.nch - 1)], 0)
+                rows.add((g * kP + i) & (RD - 1))
+        self.k += 1
+        return rows
+
+    def wait(self):
+        if self.w >= self.k:
+            return
+        f = self.w
+        self.w += 1
+        b = f % self.NB
+        assert self.armed[b] and self.phase[b] == f // self.NB
+        self.armed[b] = False
+        self.phase[b] += 1
 
 
 class RowDftStage:
@@ -722,6 +781,7 @@ class RowDftStage:
             else:
                 for g in range(CH >> 5):
                     ring[(rr & (RD - 1)) * CH + g * 32 + np.arange(32)] = self.row_dft(rr, ch0 + g * 32)
+        return {rr & (RD - 1) for rr in range(r_lo, r_hi)}
 
     def check(self, got, zr, ch):  # the n1-point DFT of the window's row (0 outside x)
         q1, k1 = ch >> self.M1, ch & (self.n1 - 1)
@@ -731,14 +791,21 @@ class RowDftStage:
                 want[i] = np.fft.fft(self.x[zr, q1[i]:q1[i] + self.n1])[k1[i]]
         np.testing.assert_allclose(got, want, atol=1e-12)
 
+    def wait(self):
+        pass
+
 
 def emulate_col_pass(stage, n0, B, groups, m1, P1, rows_out, chunk, scale):
     """col_tile_impl over (blocks of 32 * groups channels) x (chunks of window rows); returns
     the output (rows_out, P1, n0, n1), every value written exactly once."""
     M = n0.bit_length() - 1
     R, n, n1 = 1 << B, n0, 1 << m1
-    kP, kH, RD = col_group(M), n0 // 2, col_ring_rows(M)
-    assert kP % tg_period(M) == 0 and RD >= kH + 2 * kP
+    AHEAD = getattr(stage, "AHEAD", 1)  # step groups fetched ahead of the one computed
+    kP, kH, RD = col_group(M), n0 // 2, col_ring_rows(M, AHEAD)
+    assert kP % tg_period(M) == 0 and RD >= kH + (AHEAD + 1) * kP
+    if isinstance(stage, TmaStage):
+        stage = stage(kP)
+        assert chunk % kP == 0  # launch_col_tree takes TMA only for chunks of whole groups
     CH, nch = 32 * groups, P1 << m1
     out = np.full((rows_out, P1, n0, n1), np.nan, complex)
     my = np.arange(CH)
@@ -750,18 +817,31 @@ def emulate_col_pass(stage, n0, B, groups, m1, P1, rows_out, chunk, scale):
             steps, zr_end = (qb - qa) + (n - 1), qb + n - 1
             ring = np.full(RD * CH, np.nan, complex)
             stage.fetch(ring, qa - kH, min(qa + kP, zr_end), CH, ch0, RD)
+            inflight = []  # ring rows of each fetch still in flight, oldest first
+            for a in range(1, AHEAD):
+                if a * kP < steps:
+                    lo, hi = qa + a * kP, min(qa + (a + 1) * kP, zr_end)
+                    inflight.append(stage.fetch(ring, lo, hi, CH, ch0, RD))
+            stage.wait()
             feeds = []
             for jb in range(0, steps, kP):
-                if jb + kP < steps:
-                    stage.fetch(ring, qa + jb + kP, min(qa + jb + 2 * kP, zr_end), CH, ch0, RD)
+                if jb + AHEAD * kP < steps:
+                    lo, hi = qa + jb + AHEAD * kP, min(qa + jb + (AHEAD + 1) * kP, zr_end)
+                    inflight.append(stage.fetch(ring, lo, hi, CH, ch0, RD))
+                busy = set().union(*inflight) if inflight else set()
                 for j in range(jb, min(jb + kP, steps)):
                     zr = qa + j
+                    # no row this group reads is one the fetch in flight writes
+                    assert (zr & (RD - 1)) not in busy and ((zr - kH) & (RD - 1)) not in busy
                     xp = ring[(zr & (RD - 1)) * CH + my]
                     xs = ring[((zr - kH) & (RD - 1)) * CH + my] if M >= 1 else 0j
                     stage.check(xp, zr, ch)
                     if M >= 1:
                         stage.check(xs, zr - kH, ch)
                     feeds.append((xp, xs))
+                stage.wait()
+                if inflight:
+                    inflight.pop(0)
             for c in range(R):
                 outs = forward_tree(M, B, c, feeds)
                 for j in range(n - 1, steps):
@@ -801,6 +881,31 @@ FWD_CASES = [  # (n0, n1, rows_out, P1, groups, column chunks)
 ]
 
 
+TMA_CASES = [  # chunks of whole step groups (8 rows; 16 for n0 = 64), ragged last chunks
+    (1, 8, 21, 7, 1, (8, 16)),
+    (4, 16, 19, 3, 1, (8,)),
+    (8, 2, 25, 19, 2, (8, 16)),
+    (16, 4, 20, 9, 1, (8, 16)),
+    (32, 4, 18, 10, 1, (8,)),
+    (64, 2, 40, 6, 1, (16, 32)),
+]
+
+
+@pytest.mark.parametrize("n0,n1,rows_out,P1,groups,chunks", TMA_CASES)
+def test_two_pass_forward_with_tma_boxes(n0, n1, rows_out, P1, groups, chunks):
+    rng = np.random.default_rng(3000 + n0 * 64 + n1)
+    N0, N1 = rows_out + n0 - 1, P1 + n1 - 1
+    x = rng.standard_normal((N0, N1)) + 1j * rng.standard_normal((N0, N1))
+    ref = every_window_dft(x, n0, n1, 1.0)
+    m1 = n1.bit_length() - 1
+    pad = n0 // 2
+    z = emulate_row_pass(x, n1, min(m1, 3), P1, pad)
+    for chunk in chunks:
+        out = emulate_col_pass(TmaStage(z, pad, P1 * n1), n0, col_split(n0.bit_length() - 1),
+                               groups, m1, P1, rows_out, chunk, 1.0)
+        np.testing.assert_allclose(out, ref, atol=1e-9)
+
+
 @pytest.mark.parametrize("n0,n1,rows_out,P1,groups,chunks", FWD_CASES)
 def test_two_pass_forward_with_ring_staging(n0, n1, rows_out, P1, groups, chunks):
     rng = np.random.default_rng(1000 + n0 * 64 + n1)
@@ -813,9 +918,13 @@ def test_two_pass_forward_with_ring_staging(n0, n1, rows_out, P1, groups, chunks
     for row_chunk in (P1, max(1, n1 // 2)):
         z = emulate_row_pass(x, n1, min(m1, 3), row_chunk, pad)
         for chunk in chunks:
-            out = emulate_col_pass(LoadStage(z, pad, P1 * n1), n0, col_split(n0.bit_length() - 1),
-                                   groups, m1, P1, rows_out, chunk, scale)
-            np.testing.assert_allclose(out, ref, atol=1e-9)
+            for Stage in (LoadStage, TmaStage):  # cp.async copies, or TMA boxes
+                # (TMA: z rows of an even number of channels, chunks of whole step groups)
+                if Stage is TmaStage and ((P1 * n1) % 2 or chunk % col_group(n0.bit_length() - 1)):
+                    continue
+                out = emulate_col_pass(Stage(z, pad, P1 * n1), n0, col_split(n0.bit_length() - 1),
+                                       groups, m1, P1, rows_out, chunk, scale)
+                np.testing.assert_allclose(out, ref, atol=1e-9)
 
 
 FUSED64_CASES = [(16, 64, 7, 5, 1, (7, 3)), (1, 64, 4, 6, 2, (4, 3)), (32, 64, 5, 3, 2, (5, 2))]
