@@ -17,6 +17,8 @@ Contents (plain C in ``swdft2d_oracle.c`` / ``swdft2d_tree_ref.c``, loaded throu
 * :func:`treekd` -- the tree of Eq. kdfswft in FP64, with its node-operation count.
 * :func:`tree2d_radix` -- the 2D tree with radix-2 or radix-3 levels per axis (the ternary
   trees Section 5 mentions; recurrence derived in ``swdft_radix_tree.c``), FP64.
+* :func:`tree2d_mixed` -- the same tree with a radix chosen per level (2 or 3, any order),
+  for windows of 2^a 3^b samples along an axis, FP64.
 
 Arrays are numpy; outputs are complex128 with layout [q0][q1][k0][k1], where window q
 covers rows q0..q0+n0-1 and columns q1..q1+n1-1 (the paper's window end p = q + n - 1).
@@ -78,10 +80,11 @@ def _load():
     lib.swo_swdftkd_windows.argtypes = [P, i32, P, P, d, i32, i64, P, i32, P]
     lib.swt_treekd_f64.argtypes = [P, i32, P, P, d, P, P]
     lib.swt_tree2d_radix_f64.argtypes = [P, i64, i64, i32, i32, d, P, P]
+    lib.swt_tree2d_mixed_f64.argtypes = [P, i64, i64, P, i32, P, i32, d, P, P]
     for f in ("swo_swdft2d", "swo_swdft2d_windows", "swo_swdft2d_adjoint",
               "swo_swdft2d_adjoint_pixels", "swt_tree2d_f64", "swt_tree2d_f32",
               "swo_openmp_available", "swo_swdftkd", "swo_swdftkd_windows", "swt_treekd_f64",
-              "swt_tree2d_radix_f64"):
+              "swt_tree2d_radix_f64", "swt_tree2d_mixed_f64"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -277,3 +280,20 @@ def tree2d_radix(x, n0: int, n1: int, norm: str = "unitary"):
     _check(_load().swt_tree2d_radix_f64(_ptr(xs), N0, N1, n0, n1, scale_for(norm, n0, n1),
                                         _ptr(out), ctypes.byref(ops)), "tree2d_radix")
     return out, int(ops.value)
+
+
+def tree2d_mixed(x, radices0: Sequence[int], radices1: Sequence[int], norm: str = "unitary"):
+    """The 2D tree with per-level radices (each 2 or 3, in level order) along each axis: the
+    windows are n0 = prod(radices0) by n1 = prod(radices1), FP64.  Returns (out (P0, P1, n0,
+    n1) complex128, nodes evaluated)."""
+    xs = _as_c128(x)
+    N0, N1 = xs.shape
+    r0 = np.ascontiguousarray(list(radices0) or [0], dtype=np.int32)
+    r1 = np.ascontiguousarray(list(radices1) or [0], dtype=np.int32)
+    n0, n1 = int(np.prod(radices0)) if radices0 else 1, int(np.prod(radices1)) if radices1 else 1
+    out = np.empty((N0 - n0 + 1, N1 - n1 + 1, n0, n1), dtype=np.complex128)
+    ops = ctypes.c_int64(0)
+    _check(_load().swt_tree2d_mixed_f64(_ptr(xs), N0, N1, _ptr(r0), len(radices0), _ptr(r1), len(radices1),
+                                        scale_for(norm, n0, n1), _ptr(out), ctypes.byref(ops)), "tree2d_mixed")
+    return out, int(ops.value)
+

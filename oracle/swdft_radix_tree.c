@@ -153,3 +153,133 @@ int swt_tree2d_radix_f64(const double *x, int64_t N0, int64_t N1, int n0, int n1
     free(om1);
     return 0;
 }
+
+/*
+ * Mixed radices within one axis.  The window of an axis has n = r_1 r_2 ... r_L samples and
+ * level t of its tree uses radix r_t (2 or 3, in any order).  With N_t = r_1 ... r_t and
+ * s_t = n / N_t, level t under position p holds the N_t-point DFT of the samples spaced s_t
+ * apart that end at p.  Those samples interleave r_t sequences of N_(t-1) samples spaced
+ * r_t s_t = s_(t-1) apart; sequence d ends at p - (r_t - 1 - d) s_t (it is level t-1 of the
+ * tree there), so
+ *
+ *   T_t(p)[i] = sum_{d < r_t} w_{N_t}^{-i d} T_(t-1)(p - (r_t - 1 - d) s_t)[i mod N_(t-1)],
+ *
+ * w_{N_t}^{-i d} = Om[(i d s_t) mod n], Om[j] = w_n^{-j}: the same recurrence as above with
+ * the radix chosen per level (a constant radix gives swt_tree2d_radix_f64).  rad0 / rad1
+ * list the radices of dimension 0 / 1 in level order (L0 / L1 entries; L = 0 for n = 1).
+ * Same loop order, buffers, border rule and node count as swt_tree2d_radix_f64.
+ */
+int swt_tree2d_mixed_f64(const double *x, int64_t N0, int64_t N1, const int *rad0, int L0, const int *rad1,
+                         int L1, double c, double *out, int64_t *opcount) {
+    int n0 = 1, n1 = 1;
+    for (int t = 0; t < L0; ++t) {
+        if (rad0[t] != 2 && rad0[t] != 3) return -1;
+        n0 *= rad0[t];
+    }
+    for (int t = 0; t < L1; ++t) {
+        if (rad1[t] != 2 && rad1[t] != 3) return -1;
+        n1 *= rad1[t];
+    }
+    if (N0 < n0 || N1 < n1) return -1;
+    const int64_t nn = (int64_t)n0 * n1, P0 = N0 - n0 + 1, P1 = N1 - n1 + 1;
+    const size_t cells = (size_t)(N0 * N1 * nn);
+    double *prev = (double *)calloc(2 * cells, sizeof(double));
+    double *cur = (double *)calloc(2 * cells, sizeof(double));
+    double *om0 = (double *)malloc(sizeof(double) * 2 * (size_t)n0);
+    double *om1 = (double *)malloc(sizeof(double) * 2 * (size_t)n1);
+    if (!prev || !cur || !om0 || !om1) {
+        free(prev);
+        free(cur);
+        free(om0);
+        free(om1);
+        return -5;
+    }
+    for (int j = 0; j < n0; ++j) {
+        om0[2 * j] = cos(SWR_TWO_PI * j / n0);
+        om0[2 * j + 1] = -sin(SWR_TWO_PI * j / n0);
+    }
+    for (int j = 0; j < n1; ++j) {
+        om1[2 * j] = cos(SWR_TWO_PI * j / n1);
+        om1[2 * j + 1] = -sin(SWR_TWO_PI * j / n1);
+    }
+    for (int64_t p = 0; p < N0 * N1; ++p) {
+        prev[2 * p * nn] = x[2 * p];
+        prev[2 * p * nn + 1] = x[2 * p + 1];
+    }
+    int64_t ops = 0;
+    /* dimension 1: nodes (0, i1), i1 < N_t */
+    int64_t s = n1, size = 1;
+    for (int t = 0; t < L1; ++t) {
+        const int r = rad1[t];
+        s /= r;
+        const int64_t prev_size = size; /* N_(t-1) */
+        size *= r;
+        for (int64_t p0 = 0; p0 < N0; ++p0)
+            for (int64_t p1 = 0; p1 < N1; ++p1) {
+                double *A = cur + 2 * ((p0 * N1 + p1) * nn);
+                for (int64_t i = 0; i < size; ++i) {
+                    double ar = 0.0, ai = 0.0;
+                    for (int d = 0; d < r; ++d) {
+                        const int64_t q = p1 - (int64_t)(r - 1 - d) * s;
+                        if (q < 0) continue; /* incomplete border tree */
+                        const double *T = prev + 2 * ((p0 * N1 + q) * nn + (i % prev_size));
+                        const double *w = om1 + 2 * ((i * d * s) % n1);
+                        ar += w[0] * T[0] - w[1] * T[1];
+                        ai += w[0] * T[1] + w[1] * T[0];
+                    }
+                    A[2 * i] = ar;
+                    A[2 * i + 1] = ai;
+                }
+                ops += size;
+            }
+        double *tmp = prev;
+        prev = cur;
+        cur = tmp;
+    }
+    /* dimension 0: nodes (i0, i1), i0 < N_v, i1 < n1 */
+    s = n0;
+    size = 1;
+    for (int v = 0; v < L0; ++v) {
+        const int r = rad0[v];
+        s /= r;
+        const int64_t prev_size = size;
+        size *= r;
+        for (int64_t p0 = 0; p0 < N0; ++p0)
+            for (int64_t p1 = 0; p1 < N1; ++p1) {
+                double *A = cur + 2 * ((p0 * N1 + p1) * nn);
+                for (int64_t i0 = 0; i0 < size; ++i0)
+                    for (int64_t i1 = 0; i1 < n1; ++i1) {
+                        double ar = 0.0, ai = 0.0;
+                        for (int d = 0; d < r; ++d) {
+                            const int64_t q = p0 - (int64_t)(r - 1 - d) * s;
+                            if (q < 0) continue;
+                            const double *T = prev + 2 * ((q * N1 + p1) * nn + (i0 % prev_size) * n1 + i1);
+                            const double *w = om0 + 2 * ((i0 * d * s) % n0);
+                            ar += w[0] * T[0] - w[1] * T[1];
+                            ai += w[0] * T[1] + w[1] * T[0];
+                        }
+                        A[2 * (i0 * n1 + i1)] = ar;
+                        A[2 * (i0 * n1 + i1) + 1] = ai;
+                    }
+                ops += size * n1;
+            }
+        double *tmp = prev;
+        prev = cur;
+        cur = tmp;
+    }
+    for (int64_t q0 = 0; q0 < P0; ++q0)
+        for (int64_t q1 = 0; q1 < P1; ++q1) {
+            const double *T = prev + 2 * (((q0 + n0 - 1) * N1 + (q1 + n1 - 1)) * nn);
+            double *o = out + 2 * ((q0 * P1 + q1) * nn);
+            for (int64_t k = 0; k < nn; ++k) {
+                o[2 * k] = c * T[2 * k];
+                o[2 * k + 1] = c * T[2 * k + 1];
+            }
+        }
+    if (opcount) *opcount = ops;
+    free(prev);
+    free(cur);
+    free(om0);
+    free(om1);
+    return 0;
+}
