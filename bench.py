@@ -738,13 +738,14 @@ def small_measurement(torch, sw):
 
 
 def radix3_measurement(torch, sw):
-    """Ternary trees: 512x512 float32 N(0,1) (seed 79) with 27x27 and 9x9 windows, and the
-    mixed 9x16 (binary rows, ternary columns)."""
+    """Ternary and mixed-radix trees: 512x512 float32 N(0,1) (seed 79) with 27x27 and 9x9
+    windows, 9x16 (binary rows, ternary columns), and windows of 3^b 2^a samples within an
+    axis: 12x12, 24x24 and 48x24."""
     import workloads
     x = torch.from_numpy(workloads.random_array(79, 512, 512)).cuda()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=x.device)
     res = {"workload": "512x512 float32 N(0,1) (seed 79); L2 flushed before every step"}
-    for a0, a1 in ((27, 27), (9, 9), (9, 16)):
+    for a0, a1 in ((27, 27), (9, 9), (9, 16), (12, 12), (24, 24), (48, 24)):
         t = sw.Transform([(512, 512, a0, a1, sw.R32)])
         out = t.empty_outputs()
         coeffs = out[0].numel()

@@ -5,7 +5,8 @@
  * Transform", arXiv 1707.08213):
  *
  *   Section 4.1, Eq. (2): for an N0 x N1 array x and n0 x n1 windows (n_i = 2^m_i <= 64,
- *   or 3^m_i <= 27 with ternary trees; n_i <= N_i), every window position gets its 2D DFT
+ *   or 3^b_i 2^a_i <= 64 with b_i >= 1 by ternary and mixed-radix trees; n_i <= N_i), every
+ *   window position gets its 2D DFT
  *
  *     a[q0,q1,k0,k1] = c * sum_{j0<n0} sum_{j1<n1} x[q0+j0, q1+j1] w_{n0}^{-j0 k0} w_{n1}^{-j1 k1}
  *
@@ -58,7 +59,8 @@ typedef enum {
     SWDFT_OK = 0,
     SWDFT_ERR_INVALID_ARG = -1,       /* null pointer, bad enum, negative size, bad band */
     SWDFT_ERR_NOT_POW2 = -2,          /* n0 or n1 is neither a power of two (Sec. 4.2's radix-2
-                                       * tree) nor a power of three (ternary trees) */
+                                       * tree) nor 3^b 2^a with b >= 1 (ternary and mixed-radix
+                                       * trees) */
     SWDFT_ERR_WINDOW_TOO_LARGE = -3,  /* n_i > N_i: no window position exists */
     SWDFT_ERR_UNSUPPORTED = -4,       /* valid request the library does not implement */
     SWDFT_ERR_OOM = -5,               /* host or device allocation of plan-owned memory failed */
@@ -103,8 +105,10 @@ enum {
 typedef struct {
     int64_t N0, N1;  /* array rows and columns, >= 1 */
     int64_t ld;      /* input row stride in elements, >= N1; 0 means N1 */
-    int32_t n0, n1;  /* window rows and columns: powers of two (<= 64) or of three (<= 27),
-                      * 1 <= n_i <= N_i; a ternary n1 needs a ternary (or 1) n0 */
+    int32_t n0, n1;  /* window rows and columns: powers of two (<= 64), or 3^b 2^a <= 64
+                      * with b >= 1 (3, 6, 9, 12, 18, 24, 27, 36, 48, 54: ternary and
+                      * mixed-radix trees), 1 <= n_i <= N_i; such an n1 needs an n0 of that
+                      * kind too (or 1) */
     int32_t dtype;   /* swdft_dtype of the input */
     int32_t reserved;
     int64_t row_begin, row_end;
@@ -114,8 +118,8 @@ typedef struct {
  * validates every shape (SWDFT_ERR_NOT_POW2 / WINDOW_TOO_LARGE / INVALID_ARG), builds the
  * twiddle vectors Omega^0, Omega^1 of Section 4.2 in FP64 and rounds them to FP32, and
  * picks kernels.  SWDFT_ERR_UNSUPPORTED for an algorithm or window size the library lacks
- * (tree: n_i <= 64, or 3, 9, 27; tensor-core forms: powers of two with 16 <= n0 <= 64 and
- * 8 <= n1 <= 64, no persistent batch; ternary windows: tree only, no persistent batch, no
+ * (tree: n_i <= 64; tensor-core forms: powers of two with 16 <= n0 <= 64 and 8 <= n1 <= 64,
+ * no persistent batch; ternary and mixed-radix windows: tree only, no persistent batch, no
  * adjoint).  *plan is NULL on any error. */
 swdft_status swdft2d_plan(swdft2d_plan_t *plan, int32_t batch, const swdft2d_shape *shapes,
                           int32_t norm, int32_t pos, int32_t algo, uint32_t flags);
@@ -209,8 +213,8 @@ swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t 
  * window rows whose z fits there.  Arguments as in swdft2d_shape / swdft2d_execute
  * (ld = 0 means N1); output layout as for swdft2d_execute with all P0 window rows.
  * Radix-2 trees only: windows of 2^m <= 64 per side.  Errors: SWDFT_ERR_UNSUPPORTED for
- * windows of 3, 9 or 27 samples on a side (ternary trees, which plans accept) and for sides
- * above 64; SWDFT_ERR_NOT_POW2 for sides that are neither powers of two nor of three;
+ * sides of 3^b 2^a samples with b >= 1 (ternary and mixed-radix trees, which plans accept)
+ * and for sides above 64; SWDFT_ERR_NOT_POW2 for sides of no such form;
  * otherwise as swdft2d_plan for the shape; SWDFT_ERR_WORKSPACE when even a one-row band
  * needs more than 32 MiB, i.e. (3*n0/2) * (N1-n1+1) * n1 * 8 bytes > 32 MiB.
  * The first call on a device looks up the array's address there and the device's SM count

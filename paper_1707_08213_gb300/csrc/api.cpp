@@ -38,16 +38,22 @@ constexpr int kConc = 4;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-// n = 3^m: m, else -1
-int log3_exact(int64_t n) {
-    if (n < 1) return -1;
-    int m = 0;
-    int64_t v = 1;
-    while (v < n) {
-        v *= 3;
-        ++m;
+// n = 3^b 2^a with b >= 1 (a ternary or mixed-radix window side): true, and b, a
+bool mixed_split(int64_t n, int *b, int *a) {
+    if (n < 3) return false;
+    int bb = 0, aa = 0;
+    while (n % 3 == 0) {
+        n /= 3;
+        ++bb;
     }
-    return v == n ? m : -1;
+    while (n % 2 == 0) {
+        n /= 2;
+        ++aa;
+    }
+    if (n != 1 || bb == 0) return false;
+    *b = bb;
+    *a = aa;
+    return true;
 }
 
 int log2_exact(int64_t n) {
@@ -69,7 +75,10 @@ struct TreeConfig {
 struct ArrayPlan {
     int64_t N0 = 0, N1 = 0, ld = 0, P0 = 0, P1 = 0;
     int n0 = 1, n1 = 1, m0 = 0, m1 = 0, dtype = SWDFT_R32;
-    int r0 = 2, r1 = 2;  // radix of each axis's tree: n_i = r_i^m_i (n_i = 1 counts as radix 2)
+    // radix family of each axis's tree: 2 (n_i = 2^m_i; n_i = 1 counts as radix 2) or 3
+    // (n_i = 3^b_i 2^a_i, b_i >= 1: ternary and mixed-radix trees; m_i = b_i)
+    int r0 = 2, r1 = 2;
+    int b0 = 0, a0 = 0, b1 = 0, a1 = 0;
     int64_t q_begin = 0, q_end = 0;  // band of window rows, q coordinates
     TreeConfig cfg;
     bool tuned = false;
@@ -139,7 +148,6 @@ struct swdft2d_plan_s {
     // Omega of length 64 (FP64-evaluated, FP32-rounded): Omega^i of Section 4.2 for every
     // n_i = 2^m_i <= 64 is its strided view, Omega^i[j] = om64[j * 64 / n_i], bit for bit.
     float2 om64[kMaxN];
-    float2 om27[kMaxN3];  // Omega of length 27 for ternary trees (3, 9 and 27 are its strided views)
     bool configured = false;
     bool autotuned = false;  // SWDFT_FLAG_AUTOTUNE: the first execute has tuned the plan
     int sm_count = 152;
@@ -515,9 +523,9 @@ cudaError_t enqueue_forward(const swdft2d_plan_s *plan, const ArrayPlan &a, cons
                 r.r_base = q_lo;
                 r.rows = rows_out + a.n0 - 1;
                 r.P1 = a.P1;
-                r.m1 = a.m1;
+                r.b1 = a.b1;
+                r.a1 = a.a1;
                 r.z = z;
-                r.om27 = plan->om27;
                 r.chunk = a.cfg.row_chunk;
                 e = launch_row_tree3(r, s);
             } else {
@@ -543,10 +551,10 @@ cudaError_t enqueue_forward(const swdft2d_plan_s *plan, const ArrayPlan &a, cons
         c.P1 = a.P1;
         c.rows_out = rows_out;
         c.n1 = a.n1;
-        c.m0 = a.m0;  // n0 = 3^m0, or n0 = 1
+        c.b0 = a.b0;  // n0 = 3^b0 2^a0, or n0 = 1
+        c.a0 = a.a0;
         c.out = static_cast<float2 *>(out);
         c.scale = norm_scale(plan->norm, a.n0, a.n1);
-        c.om27 = plan->om27;
         c.chunk = a.cfg.col_chunk;
         return launch_col_tree3(c, s);
     }
@@ -793,9 +801,15 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
         ArrayPlan &a = arrays[(size_t)i];
         if (s.N0 < 1 || s.N1 < 1 || s.n0 < 1 || s.n1 < 1) return SWDFT_ERR_INVALID_ARG;
         if (s.dtype != SWDFT_R32 && s.dtype != SWDFT_C64) return SWDFT_ERR_INVALID_ARG;
-        int m0 = log2_exact(s.n0), m1 = log2_exact(s.n1), r0 = 2, r1 = 2;
-        if (m0 < 0 && (m0 = log3_exact(s.n0)) >= 0) r0 = 3;
-        if (m1 < 0 && (m1 = log3_exact(s.n1)) >= 0) r1 = 3;
+        int m0 = log2_exact(s.n0), m1 = log2_exact(s.n1), r0 = 2, r1 = 2, b0 = 0, a0 = 0, b1 = 0, a1 = 0;
+        if (m0 < 0 && mixed_split(s.n0, &b0, &a0)) {
+            r0 = 3;
+            m0 = b0;
+        }
+        if (m1 < 0 && mixed_split(s.n1, &b1, &a1)) {
+            r1 = 3;
+            m1 = b1;
+        }
         if (m0 < 0 || m1 < 0) return SWDFT_ERR_NOT_POW2;
         if (s.n0 > s.N0 || s.n1 > s.N1) return SWDFT_ERR_WINDOW_TOO_LARGE;
         const int64_t ld = s.ld == 0 ? s.N1 : s.ld;
@@ -809,6 +823,10 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
         a.m1 = m1;
         a.r0 = r0;
         a.r1 = r1;
+        a.b0 = b0;
+        a.a0 = a0;
+        a.b1 = b1;
+        a.a1 = a1;
         a.dtype = s.dtype;
         a.P0 = s.N0 - s.n0 + 1;
         a.P1 = s.N1 - s.n1 + 1;
@@ -824,7 +842,10 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
             a.q_end = e - shift;
             if (a.q_begin < 0 || a.q_end > a.P0 || a.q_begin >= a.q_end) return SWDFT_ERR_INVALID_ARG;
         }
-        if (m0 > (r0 == 3 ? kMaxLog3 : kMaxLog2) || m1 > (r1 == 3 ? kMaxLog3 : kMaxLog2)) return SWDFT_ERR_UNSUPPORTED;
+        // trees built: 2^m <= 64; 3^b 2^a <= 64 (b <= 3)
+        if ((r0 == 3 ? (s.n0 > kMaxN || b0 > kMaxLog3) : m0 > kMaxLog2) ||
+            (r1 == 3 ? (s.n1 > kMaxN || b1 > kMaxLog3) : m1 > kMaxLog2))
+            return SWDFT_ERR_UNSUPPORTED;
         // a ternary row tree feeds the ternary column kernel (z rows of any length); the
         // binary column kernel needs power-of-two rows
         if (r1 == 3 && r0 == 2 && m0 > 0) return SWDFT_ERR_UNSUPPORTED;
@@ -843,7 +864,6 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
     p->algo = (algo == SWDFT_ALGO_AUTO) ? SWDFT_ALGO_TREE_F32 : algo;
     p->flags = flags;
     make_omega(kMaxN, p->om64);
-    make_omega(kMaxN3, p->om27);
     size_t ws = 0;
     if (flags & SWDFT_FLAG_PERSISTENT) {
         // one launch covers every array, so each array has its own z region; the window

@@ -60,10 +60,11 @@ swdft_status scratch_address(void **out, int *sm_count) {
     return SWDFT_OK;
 }
 
-// n = 3^m (m >= 1)
-bool power_of_three(int64_t n) {
-    if (n < 3) return false;
+// n = 3^b 2^a with b >= 1: a side plans build a ternary or mixed-radix tree for
+bool radix3_family(int64_t n) {
+    if (n < 3 || n % 3 != 0) return false;
     while (n % 3 == 0) n /= 3;
+    while (n % 2 == 0) n /= 2;
     return n == 1;
 }
 
@@ -86,8 +87,8 @@ extern "C" swdft_status swdft2d_execute_static_scratch(const void *d_in, int64_t
     if (dtype != SWDFT_R32 && dtype != SWDFT_C64) return SWDFT_ERR_INVALID_ARG;
     if (norm < SWDFT_NORM_UNITARY || norm > SWDFT_NORM_INV_N) return SWDFT_ERR_INVALID_ARG;
     const int m0 = log2_pow2(n0), m1 = log2_pow2(n1);
-    // radix-2 trees only: windows of 3, 9 or 27 (which plans accept) are not offered here
-    if ((m0 < 0 && power_of_three(n0)) || (m1 < 0 && power_of_three(n1))) return SWDFT_ERR_UNSUPPORTED;
+    // radix-2 trees only: ternary and mixed-radix windows (which plans accept) are not offered here
+    if ((m0 < 0 && radix3_family(n0)) || (m1 < 0 && radix3_family(n1))) return SWDFT_ERR_UNSUPPORTED;
     if (m0 < 0 || m1 < 0) return SWDFT_ERR_NOT_POW2;
     if (n0 > N0 || n1 > N1) return SWDFT_ERR_WINDOW_TOO_LARGE;
     if (m0 > kMaxLog2 || m1 > kMaxLog2) return SWDFT_ERR_UNSUPPORTED;

@@ -18,7 +18,8 @@ bool alloc_fails();
 // for window lengths up to 2^kMaxLog2 along each axis.
 constexpr int kMaxLog2 = 6;
 constexpr int kMaxN = 1 << kMaxLog2;
-// Ternary trees (tree3.cu) are built for window lengths 3^m, m <= kMaxLog3.
+// Ternary and mixed-radix trees (tree3.cu) are built for window lengths 3^b 2^a <= 64 with
+// 1 <= b <= kMaxLog3.
 constexpr int kMaxLog3 = 3;
 constexpr int kMaxN3 = 27;
 
@@ -279,28 +280,27 @@ struct AdjRowArgs {
     int sm_count = 152;  // for chunk = 0
 };
 
-// Ternary trees (tree3.cu): windows of 3^m samples, m <= 3, along an axis.
-// Row levels: z[r][q1][k1] for `rows` input rows (n1 = 3^m1), as RowTreeArgs.
+// Ternary and mixed-radix trees (tree3.cu): windows of n = 3^b 2^a samples along an axis
+// (b >= 1, n <= 64; b = a = 0: one sample), radix-3 levels first.
+// Row levels: z[r][q1][k1] for `rows` input rows (n1 = 3^b1 2^a1), as RowTreeArgs.
 struct Row3Args {
     const void *x = nullptr;
     int64_t ld = 0;
     int cplx = 0;
     int64_t r_base = 0, rows = 0, P1 = 0;
-    int m1 = 0;                     // n1 = 3^m1
+    int b1 = 0, a1 = 0;             // n1 = 3^b1 2^a1
     float2 *z = nullptr;
-    const float2 *om27 = nullptr;   // host table w_27^{-j}, 27 entries
     int64_t chunk = 0;
 };
-// Column levels with a ternary tree (n0 = 3^m0) over z rows of P1 x n1 (n1 any length);
+// Column levels with such a tree (n0 = 3^b0 2^a0) over z rows of P1 x n1 (n1 any length <= 64);
 // z needs 2*n0/3 readable rows in front of its first row.
 struct Col3Args {
     const float2 *z = nullptr;
     int64_t P1 = 0, rows_out = 0;
     int n1 = 1;
-    int m0 = 0;                     // n0 = 3^m0
+    int b0 = 0, a0 = 0;             // n0 = 3^b0 2^a0
     float2 *out = nullptr;
     float scale = 1.f;
-    const float2 *om27 = nullptr;
     int64_t chunk = 0;
 };
 cudaError_t launch_row_tree3(const Row3Args &a, cudaStream_t s);

@@ -53,9 +53,11 @@ def shp(N0, N1, n0, n1, **kw):
 
 
 @pytest.mark.parametrize("shape,status", [
-    (shp(16, 16, 5, 4), -2),           # neither a power of two nor of three
-    (shp(16, 16, 4, 12), -2),
+    (shp(16, 16, 5, 4), -2),           # neither a power of two nor 3^b 2^a
+    (shp(16, 16, 4, 10), -2),
+    (shp(16, 16, 4, 12), -4),          # binary column tree over mixed-radix row DFTs
     (shp(100, 100, 81, 3), -4),        # ternary trees are built up to 27
+    (shp(120, 120, 96, 3), -4),        # mixed-radix trees up to 64
     (shp(40, 40, 16, 9), -4),          # binary column tree over ternary row DFTs
     (shp(40, 40, 8, 3), -4),
     (shp(16, 16, 32, 4), -3),          # window larger than the array
@@ -74,13 +76,18 @@ def test_plan_validation(nat, shape, status):
     assert h is None
 
 
-def test_ternary_windows_are_accepted_by_the_tree_only(nat):
-    for n0, n1 in ((3, 3), (9, 27), (27, 1), (1, 9), (9, 16), (27, 64), (3, 2)):
-        st, h = nat.raw_plan([shp(40, 70, n0, n1)], 0, 0, 1, 0)
+def test_ternary_and_mixed_radix_windows_are_accepted_by_the_tree_only(nat):
+    for n0, n1 in ((3, 3), (9, 27), (27, 1), (1, 9), (9, 16), (27, 64), (3, 2),
+                   (6, 6), (12, 48), (54, 1), (1, 24), (18, 36), (48, 64), (36, 9)):
+        st, h = nat.raw_plan([shp(60, 70, n0, n1)], 0, 0, 1, 0)
         assert st == 0, (n0, n1)
         nat.lib.swdft2d_destroy(h)
     assert nat.raw_plan([shp(40, 40, 27, 27)], 0, 0, 2, 0)[0] == -4   # tensor-core forms
     assert nat.raw_plan([shp(40, 40, 9, 9)], 0, 0, 1, 4)[0] == -4      # persistent batch
+    assert nat.raw_plan([shp(40, 40, 12, 6)], 0, 0, 1, 4)[0] == -4     # (mixed radix too)
+    p = nat.Plan([dict(N0=60, N1=70, n0=24, n1=12)])
+    assert p.output_shape(0) == (37, 59, 24, 12)
+    assert p.workspace_size() >= (16 + 37 + 23) * 59 * 12 * 8  # 2*n0/3 look-back rows
     p = nat.Plan([dict(N0=40, N1=70, n0=9, n1=27)])
     assert p.output_shape(0) == (32, 44, 9, 27)
     # z: 2*n0/3 look-back rows in front, then P0 + n0 - 1 rows of P1 * n1 complex64

@@ -1,8 +1,9 @@
-"""Ternary trees on the GPU (windows of 3, 9 or 27 along an axis; the radix-3 trees Section 5
-mentions) against the FP64 oracle's definition: max over a window's coefficients of
-|a - a_oracle| / ||x_w||_2 <= 1e-5 on the unitary scale, every coefficient of small arrays
-(ragged sizes, both radices mixed across the axes), and the 512x512 array with 27x27
-windows on sampled windows plus per-window Parseval."""
+"""Ternary and mixed-radix trees on the GPU (windows of 3, 9 or 27 along an axis -- the
+radix-3 trees Section 5 mentions -- and of 3^b 2^a samples, radix-3 levels then radix-2
+levels within one axis) against the FP64 oracle's definition: max over a window's
+coefficients of |a - a_oracle| / ||x_w||_2 <= 1e-5 on the unitary scale, every coefficient
+of small arrays (ragged sizes, radices mixed within and across the axes), and 512x512
+arrays with 27x27 and 48x24 windows on sampled windows plus per-window Parseval."""
 import numpy as np
 import pytest
 import torch
@@ -39,7 +40,10 @@ def check(a, x, n0, n1, norm="unitary"):
 
 
 SHAPES = [(3, 3), (9, 9), (27, 27), (27, 1), (1, 27), (9, 3), (3, 27), (9, 16), (27, 64), (3, 2),
-          (1, 3), (27, 8)]
+          (1, 3), (27, 8),
+          # mixed radices within an axis (3^b 2^a): every length to 54
+          (6, 6), (12, 12), (24, 6), (48, 4), (6, 48), (18, 18), (36, 12), (54, 6), (9, 54),
+          (12, 1), (1, 48), (48, 48), (24, 36), (54, 64)]
 
 
 @pytest.mark.parametrize("cplx", [False, True])
@@ -58,6 +62,8 @@ def test_normalisations(sw, norm):
     x = workloads.random_array(77, 60, 90, complex_input=True)
     a, _ = run(sw, x, 9, 27, norm=norm)
     check(a, x, 9, 27, norm=norm)
+    a, _ = run(sw, x, 12, 18, norm=norm)
+    check(a, x, 12, 18, norm=norm)
 
 
 def test_band_graph_and_host_buffers_match(sw):
@@ -89,9 +95,9 @@ def test_adjoint_is_refused(sw):
         t.adjoint([G])
 
 
-def test_512_with_27x27_windows_full_size(sw):
+@pytest.mark.parametrize("n0,n1", [(27, 27), (48, 24)])
+def test_512_full_size(sw, n0, n1):
     x = workloads.random_array(79, 512, 512)
-    n0 = n1 = 27
     a, _ = run(sw, x, n0, n1)
     P0, P1 = a.shape[:2]
     rng = np.random.default_rng(80)

@@ -204,6 +204,100 @@ def ternary_tree(M, c, feeds):
     return outs
 
 
+def mixed_split(n):
+    """n = 3^B3 2^A2: (B3, A2), or None."""
+    b = a = 0
+    while n % 3 == 0:
+        n //= 3
+        b += 1
+    while n % 2 == 0:
+        n //= 2
+        a += 1
+    return (b, a) if n == 1 else None
+
+
+def mixed_period(B3, A2):
+    """The unroll period of SlidingTreeMixed: the depth of level 2's FIFO."""
+    n = 3 ** B3 * 2 ** A2
+    if B3 + A2 < 2:
+        return 1
+    r2 = 3 if B3 >= 2 else 2
+    N2 = 3 * r2
+    return (r2 - 1) * (n // N2)
+
+
+def mixed_tree(B3, A2, c, feeds):
+    """Thread c (< 3) of the mixed-radix tree split by residue mod 3 (tree3_core.cuh,
+    SlidingTreeMixed: B3 radix-3 levels, then A2 radix-2 levels) over the steps j = 0, 1, ..:
+    feeds[j] = (x at p, x at p - s_1, x at p - 2 s_1), s_1 = n / 3; returns its level-L
+    nodes c + 3u, u < n / 3.  FIFO depths, slots (step index modulo the depth, within the
+    unroll period) and twiddle indices as the kernel has them."""
+    n = 3 ** B3 * 2 ** A2
+    L = B3 + A2
+    om = np.exp(-2j * np.pi * np.arange(n) / n)
+
+    def rad(t):
+        return 3 if t <= B3 else 2
+
+    def Nt(t):
+        return 3 ** t if t <= B3 else 3 ** B3 * 2 ** (t - B3)
+
+    def held(t):
+        return 1 if t <= 1 else Nt(t) // 3
+
+    def depth(t):
+        return (rad(t) - 1) * (n // Nt(t))
+
+    period = mixed_period(B3, A2)
+    assert all(period % depth(t) == 0 for t in range(2, L + 1))
+    s1 = n // 3
+    tw1 = (om[(c * s1) % n], om[(2 * c * s1) % n])
+    tw = {t: [[om[((c + 3 * a) * d * (n // Nt(t))) % n] for d in range(1, rad(t))]
+              for a in range(held(t - 1))] for t in range(2, L + 1)}
+    fifos = {t: [[0j] * held(t - 1) for _ in range(depth(t))] for t in range(2, L + 1)}
+    w3 = np.exp(-2j * np.pi / 3)
+    outs = []
+    for j, (xp, xs1, xs2) in enumerate(feeds):
+        J = j % period
+        cur = [xs2 + tw1[0] * xs1 + tw1[1] * xp]  # level 1, node c
+        for t in range(2, L + 1):
+            s, D, hp = n // Nt(t), depth(t), held(t - 1)
+            nxt = [0j] * (rad(t) * hp)
+            for a in range(hp):
+                if rad(t) == 3:
+                    a2, a1, a0 = cur[a], fifos[t][(J + s) % D][a], fifos[t][J % D][a]
+                    fifos[t][J % D][a] = a2
+                    b1, b2 = tw[t][a][0] * a1, tw[t][a][1] * a2
+                    for k in range(3):
+                        nxt[a + k * hp] = a0 + w3 ** k * b1 + w3 ** (2 * k) * b2
+                else:
+                    a1, a0 = cur[a], fifos[t][J % D][a]
+                    fifos[t][J % D][a] = a1
+                    b = tw[t][a][0] * a1
+                    nxt[a], nxt[a + hp] = a0 + b, a0 - b
+            cur = nxt
+        outs.append(cur)
+    return outs
+
+
+MIXED_SHAPES = [(b, a) for b in (1, 2, 3) for a in range(0, 5) if 3 ** b * 2 ** a <= 64]
+
+
+@pytest.mark.parametrize("B3,A2", MIXED_SHAPES)
+def test_mixed_schedule_gives_every_windows_dft(B3, A2):
+    n = 3 ** B3 * 2 ** A2
+    rng = np.random.default_rng(700 + n)
+    x = rng.standard_normal(n + 19) + 1j * rng.standard_normal(n + 19)
+    s1 = n // 3
+    feeds = [(x[p], x[p - s1] if p - s1 >= 0 else 0j, x[p - 2 * s1] if p - 2 * s1 >= 0 else 0j)
+             for p in range(len(x))]
+    for c in range(3):
+        outs = mixed_tree(B3, A2, c, feeds)
+        for p in range(n - 1, len(x)):
+            ref = np.fft.fft(x[p - n + 1:p + 1])
+            np.testing.assert_allclose(outs[p], ref[c::3], atol=1e-9)
+
+
 def ternary_walk(M, c, x):
     """Thread c's level-M nodes at every position p of x (zero before the array)."""
     s1 = 3 ** (M - 1)
@@ -952,13 +1046,29 @@ def test_fused_forward_with_row_dfts_by_shuffles(n0, n1, rows_out, P1, groups, c
 # (look-backs s_1 and 2 s_1 rows up, 2 n0 / 3 padding rows in front of z) and, when n1 is not
 # a multiple of 4, its double-buffered output stage copied out by consecutive threads.
 
+def row3_unr(period):
+    return 6 if period <= 6 and 6 % period == 0 else (8 if period <= 8 and 8 % period == 0 else 12)
+
+
+def col3_group(period):
+    return 8 if period <= 8 and 8 % period == 0 else (6 if period == 6 else 12)
+
+
+def tree3_outs(n, feeds):
+    """Every residue thread's outputs (the mixed tree; n = 1: the data itself)."""
+    B3, A2 = mixed_split(n)
+    if B3 == 0:
+        return {0: [[f[0]] for f in feeds]}
+    return {c: mixed_tree(B3, A2, c, feeds) for c in range(3)}
+
+
 def emulate_row_pass3(x, n1, chunk, pad):
     rows, N1 = x.shape
-    M = {1: 0, 3: 1, 9: 2, 27: 3}[n1]
-    n, R, OUT = n1, (3 if M >= 1 else 1), (3 ** (M - 1) if M >= 1 else 1)
-    S1 = 3 ** (M - 1) if M >= 1 else 0
-    UNR = 6
-    assert M < 2 or UNR % (2 * 3 ** (M - 2)) == 0
+    B3, A2 = mixed_split(n1)
+    n, R, OUT = n1, (3 if B3 >= 1 else 1), (n1 // 3 if B3 >= 1 else 1)
+    S1 = n1 // 3 if B3 >= 1 else 0
+    UNR = row3_unr(mixed_period(B3, A2) if B3 >= 1 else 1)
+    assert B3 == 0 or UNR % mixed_period(B3, A2) == 0
     P1 = N1 - n + 1
     zrow = P1 * n
     z = np.full((pad + rows) * zrow, np.nan, complex)
@@ -974,7 +1084,7 @@ def emulate_row_pass3(x, n1, chunk, pad):
             stage = np.full(32 * UNR * n, np.nan, complex)
             feeds = [(xr[:, qa + j], xr[:, max(qa + j - S1, 0)], xr[:, max(qa + j - 2 * S1, 0)])
                      for j in range(steps)]
-            outs = {c: (ternary_tree(M, c, feeds) if M >= 1 else [[f[0]] for f in feeds]) for c in range(R)}
+            outs = tree3_outs(n, feeds)
             for jb in range(0, steps, UNR):
                 for j in range(jb, min(jb + UNR, steps)):
                     if j >= n - 1:
@@ -995,13 +1105,14 @@ def emulate_row_pass3(x, n1, chunk, pad):
 
 
 def emulate_col_pass3(z, pad, n0, n1, P1, rows_out, chunk, scale):
-    M = {1: 0, 3: 1, 9: 2, 27: 3}[n0]
-    n, R, OUT = n0, (3 if M >= 1 else 1), (3 ** (M - 1) if M >= 1 else 1)
-    S1 = 3 ** (M - 1) if M >= 1 else 0
+    B3, A2 = mixed_split(n0)
+    M = B3  # 0: a window of one row
+    n, R, OUT = n0, (3 if B3 >= 1 else 1), (n0 // 3 if B3 >= 1 else 1)
+    S1 = n0 // 3 if B3 >= 1 else 0
     W = 64
-    G = 6 if M >= 3 else 8
-    assert M < 2 or G % (2 * 3 ** (M - 2)) == 0
-    need = (2 * S1 if M >= 1 else 0) + 2 * G
+    G = col3_group(mixed_period(B3, A2) if B3 >= 1 else 1)
+    assert B3 == 0 or G % mixed_period(B3, A2) == 0
+    need = (2 * S1 if B3 >= 1 else 0) + 2 * G
     RD = 1 << (need - 1).bit_length()
     T = max(1, W // n1)
     CH = T * n1
@@ -1042,7 +1153,7 @@ def emulate_col_pass3(z, pad, n0, n1, P1, rows_out, chunk, scale):
                         if M >= 1 or d == 0:
                             np.testing.assert_array_equal(v[active], z[pad + zr - d, ch[active]])
                     feeds.append(f)
-            outs = {c: (ternary_tree(M, c, feeds) if M >= 1 else [[f[0]] for f in feeds]) for c in range(R)}
+            outs = tree3_outs(n, feeds)
             orow = qa * orow_len + q1_0 * n * n1
             stage = [np.full(W * n, np.nan, complex) for _ in range(2)]
             buf = 0
@@ -1077,6 +1188,16 @@ TERNARY_CASES = [  # (n0, n1, rows_out, P1, column chunks); n1 of 2^k comes from
     (3, 27, 6, 5, (6, 4)),
     (27, 27, 3, 4, (3, 2)),
     (3, 64, 4, 3, (4, 3)),
+    # mixed radices within an axis: 3^b 2^a
+    (6, 6, 6, 11, (6, 4)),
+    (12, 2, 5, 30, (5, 3)),
+    (1, 12, 5, 9, (5, 2)),
+    (24, 8, 4, 6, (4, 3)),
+    (48, 1, 3, 40, (3, 2)),
+    (18, 36, 3, 3, (3, 2)),
+    (54, 3, 3, 5, (3, 2)),
+    (9, 48, 4, 2, (4, 3)),
+    (36, 16, 3, 4, (3, 2)),
 ]
 
 
@@ -1089,7 +1210,7 @@ def test_ternary_passes_with_staging(n0, n1, rows_out, P1, chunks):
     ref = every_window_dft(x, n0, n1, scale)
     pad = 2 * n0 // 3
     for row_chunk in (P1, 4):
-        if n1 in (1, 3, 9, 27):
+        if n1 % 3 == 0 or n1 == 1:
             z = emulate_row_pass3(x, n1, min(row_chunk, P1), pad)
         else:
             m1 = n1.bit_length() - 1

@@ -109,10 +109,12 @@ def test_static_scratch_rejects_oversized_and_bad_args(sw):
     assert st == nat.ERR_WORKSPACE
     assert nat.lib.swdft2d_execute_static_scratch(None, 8, 8, 0, 8, 8, 0, 0,
                                                   ctypes.c_void_p(out.data_ptr()), s) == nat.ERR_INVALID_ARG
-    # ternary windows (which plans accept) are not offered by this radix-2 entry point
+    # ternary and mixed-radix windows (which plans accept) are not offered by this radix-2 entry point
     assert nat.lib.swdft2d_execute_static_scratch(ctypes.c_void_p(x.data_ptr()), 8, 8, 0, 3, 8, 0,
                                                   0, ctypes.c_void_p(out.data_ptr()), s) == nat.ERR_UNSUPPORTED
     assert nat.lib.swdft2d_execute_static_scratch(ctypes.c_void_p(x.data_ptr()), 9, 9, 0, 8, 9, 0,
+                                                  0, ctypes.c_void_p(out.data_ptr()), s) == nat.ERR_UNSUPPORTED
+    assert nat.lib.swdft2d_execute_static_scratch(ctypes.c_void_p(x.data_ptr()), 12, 8, 0, 12, 8, 0,
                                                   0, ctypes.c_void_p(out.data_ptr()), s) == nat.ERR_UNSUPPORTED
     assert nat.lib.swdft2d_execute_static_scratch(ctypes.c_void_p(x.data_ptr()), 8, 8, 0, 5, 8, 0,
                                                   0, ctypes.c_void_p(out.data_ptr()), s) == nat.ERR_NOT_POW2
