@@ -867,6 +867,33 @@ def _fig4_fft(torch, n0, n1):
 
 # ----------------------------------------------------------------------- our arm
 
+def side_summary(line):
+    """The side measurements' headline figures in a few hundred bytes (ms per step, TB/s,
+    errors), placed at the end of the JSON line."""
+    def g(*path):
+        d = line
+        for k in path:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return round(d, 4) if isinstance(d, float) else d
+    out = {"frac_col": g("roofline", "frac"), "step_frac": g("roofline", "step_frac"),
+           "e2e_ms": g("e2e", "ms_per_step")}
+    for algo in ("tc_bf16x3", "tc_bf16", "tc_f16_scaled"):
+        out[f"c2_{algo}"] = [g("tensor_core", algo, "ms_per_step"), g("tensor_core", algo, "error_vs_oracle", "max")]
+    for algo in ("tree", "tc_bf16x3", "tc_bf16", "tc_f16_scaled"):
+        out[f"c3_{algo}"] = [g("complex", algo, "ms_per_step"), g("complex", algo, "error_vs_oracle", "max")]
+    out["batch_ms"] = {k: g("batch", k, "ms_per_step") for k in ("persistent_graph", "per_array_graph",
+                                                                  "per_array_graph_autotuned")}
+    out["adjoint_ms"] = [g("adjoint", "forward", "ms_per_step"), g("adjoint", "adjoint", "ms_per_step")]
+    out["volume_ms"] = g("volume", "ms_per_step")
+    out["radix3_ms"] = {k: v.get("ms_per_step") for k, v in (line.get("radix3") or {}).items() if isinstance(v, dict)}
+    out["stream_graph_us"] = [g("stream", f"rows_per_push_{r}", "graph_us_per_push") for r in (1, 32, 256)]
+    out["static_scratch_ms"] = g("static_scratch", "ms_per_step")
+    out["small_graph_us"] = g("small", "graph_us")
+    return out
+
+
 def run_ours(args):
     rank, world, local_rank = dist_env()
     import numpy as np
@@ -1080,6 +1107,7 @@ def run_ours(args):
                 line["fig4_shapes"]["cpu_tree"] = {"error": str(e)}
     if isinstance(line.get("complex"), dict):
         line["complex"].pop("_samples", None)
+    line["side_summary"] = side_summary(line)  # last key: a log that keeps only the line's end has it
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
