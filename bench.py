@@ -356,8 +356,9 @@ def tc_comparison(torch, sw, xd, flush, tree_ms):
 
 
 def batch_measurement(torch, sw):
-    """The 256-image uneven batch (1.8e10 coefficients) through one persistent launch pair
-    replayed from a CUDA graph, and through per-array launches replayed from a graph."""
+    """The 256-image uneven batch (1.8e10 coefficients) through the persistent kernels (one per
+    window shape) replayed from a CUDA graph, by default and as the autotuner chose per window
+    shape, and through per-array launches replayed from a graph, likewise."""
     import workloads
     wl = workloads.uneven_batch_256()
     shapes = [(x.shape[0], x.shape[1], a, b, 0) for x, (a, b) in zip(wl.images, wl.windows)]
@@ -368,9 +369,12 @@ def batch_measurement(torch, sw):
            "coeffs_per_step": coeffs, "output_bytes_per_step": 8 * coeffs}
     outs = None
     s = torch.cuda.Stream()
-    # the third form: per-array graph after the plan's autotuner chose, per shape, the tree's
-    # launch shapes, two-pass or fused levels, and tree or split-bf16 tensor-core form
+    # persistent: the default split (pipelined kernels for the two-pass arrays, fused kernels
+    # for small windows), then the autotuner's choice per window shape among pipelined, fused,
+    # per-array tree and per-array split-bf16; per-array: default launch shapes, then the
+    # autotuner's choice per shape of launch shapes, two-pass or fused, tree or split-bf16
     for name, flags, algo in (("persistent_graph", sw.FLAG_PERSISTENT | sw.FLAG_GRAPH, "tree"),
+                              ("persistent_graph_autotuned", sw.FLAG_PERSISTENT | sw.FLAG_GRAPH, "auto"),
                               ("per_array_graph", sw.FLAG_GRAPH, "tree"),
                               ("per_array_graph_autotuned", sw.FLAG_GRAPH, "auto")):
         t = sw.Transform(shapes, flags=flags, algo=algo)
@@ -883,7 +887,8 @@ def side_summary(line):
         out[f"c2_{algo}"] = [g("tensor_core", algo, "ms_per_step"), g("tensor_core", algo, "error_vs_oracle", "max")]
     for algo in ("tree", "tc_bf16x3", "tc_bf16", "tc_f16_scaled"):
         out[f"c3_{algo}"] = [g("complex", algo, "ms_per_step"), g("complex", algo, "error_vs_oracle", "max")]
-    out["batch_ms"] = {k: g("batch", k, "ms_per_step") for k in ("persistent_graph", "per_array_graph",
+    out["batch_ms"] = {k: g("batch", k, "ms_per_step") for k in ("persistent_graph", "persistent_graph_autotuned",
+                                                                  "per_array_graph",
                                                                   "per_array_graph_autotuned")}
     out["adjoint_ms"] = [g("adjoint", "forward", "ms_per_step"), g("adjoint", "adjoint", "ms_per_step")]
     out["volume_ms"] = g("volume", "ms_per_step")

@@ -36,9 +36,10 @@
  * Errors: every call returns a swdft_status; nothing aborts, exits or throws across the
  * ABI.  Argument checks happen before any CUDA call.  A CUDA launch or copy failure
  * returns SWDFT_ERR_CUDA; asynchronous faults surface at the next synchronising call.
- * The only device-side waits are the tensor-core kernels' mbarrier waits (and the one of
- * swdft2d_selftest_wait_timeout); each gives up after a bounded number of polls and records
- * it (see swdft2d_check_device).
+ * The only device-side waits are the tensor-core and TMA-staged kernels' mbarrier waits, the
+ * pipelined batch kernels' waits on their row tiles' counters (and the one of
+ * swdft2d_selftest_wait_timeout); each gives up after a bounded number of polls or clock
+ * cycles and records it (see swdft2d_check_device).
  *
  * Threads and streams: a plan is immutable after swdft2d_plan except for its tuning
  * state, graph and staging buffers; do not execute one plan on two streams at once.
@@ -94,7 +95,9 @@ typedef enum {
 enum {
     SWDFT_FLAG_GRAPH = 1u,    /* capture each execute's launch sequence in a CUDA graph, replay after */
     SWDFT_FLAG_HOST_IO = 2u,  /* plan owns device staging so swdft2d_execute_host can run */
-    SWDFT_FLAG_PERSISTENT = 4u, /* batch: one persistent launch over all (image, tile) items */
+    SWDFT_FLAG_PERSISTENT = 4u, /* batch: one persistent kernel per window shape (n0, n1) over all
+                                 * its arrays' tiles -- a pipelined row+column kernel, or a
+                                 * fused one for n0 n1 <= 64 -- run concurrently; radix-2 tree only */
     SWDFT_FLAG_AUTOTUNE = 8u    /* the first swdft2d_execute runs swdft2d_autotune on its own
                                  * buffers first (blocking; skipped if its stream is capturing) */
 };
@@ -227,8 +230,9 @@ swdft_status swdft2d_execute_static_scratch(const void *d_in, int64_t N0, int64_
                                             void *d_out, void *stream);
 
 /* Device-side health of the current device: SWDFT_ERR_DEVICE_TIMEOUT if, since the last
- * call, a tensor-core kernel gave up on one of its bounded waits (its outputs are then
- * incomplete) or swdft2d_selftest_wait_timeout ran; SWDFT_OK otherwise.  Reads and resets
+ * call, a tensor-core kernel, a TMA-staged column kernel or a pipelined batch kernel gave up
+ * on one of its bounded waits (its outputs are then incomplete) or
+ * swdft2d_selftest_wait_timeout ran; SWDFT_OK otherwise.  Reads and resets
  * the library's device status words (synchronous copies).  SWDFT_ERR_CUDA if a read fails. */
 swdft_status swdft2d_check_device(void);
 
@@ -241,10 +245,21 @@ swdft_status swdft2d_check_device(void);
  * any CUDA call). */
 swdft_status swdft2d_selftest_wait_timeout(int32_t polls, void *stream);
 
+/* Test hook for the pipelined persistent batch kernels' bounded waits (a column tile waits,
+ * spinning on a device counter, until the row tiles of the z rows it reads have finished).
+ * budget_cycles: clock64 cycles one column tile may wait before it records a time-out and
+ * every block of the launch stops (0 restores the default, about a second); poison: extra
+ * row tiles, which never run, that the column tiles of the batch's array 0 wait for (0 in
+ * normal use).  A time-out leaves that launch's outputs incomplete and makes the next
+ * swdft2d_check_device return SWDFT_ERR_DEVICE_TIMEOUT; nothing faults and the context stays
+ * usable.  Process-wide; read when a persistent launch is enqueued or captured into a graph.
+ * SWDFT_ERR_INVALID_ARG for negative values. */
+swdft_status swdft2d_debug_batch_wait(int64_t budget_cycles, int32_t poison);
+
 /* Fault injection for tests: the library's next `after` allocations succeed and every later
  * one fails with SWDFT_ERR_OOM, until a call with after < 0 turns injection off (the
  * default).  Counted allocations: plan and stream objects (host), a persistent plan's
- * descriptor tables (pinned host and device) and the device buffers of
+ * descriptor tables (pinned host and device) and tile table (device), and the device buffers of
  * swdft2d_execute_host.  Process-wide (one atomic counter).  A call that fails this way
  * keeps what it did allocate, so repeating it once injection is off completes it.  Always
  * returns SWDFT_OK. */

@@ -40,6 +40,7 @@ EXPORTS = (
     "swdft2d_load_tuning",
     "swdft2d_execute_stage", "swdft2d_set_tree_config", "swdft2d_execute_static_scratch",
     "swdft2d_check_device", "swdft2d_inject_alloc_failure", "swdft2d_selftest_wait_timeout",
+    "swdft2d_debug_batch_wait",
     "swdftkd_plan", "swdftkd_output_shape", "swdftkd_workspace_size", "swdftkd_launch_count",
     "swdftkd_execute", "swdftkd_destroy",
     "swdft2d_stream_create", "swdft2d_stream_state_size", "swdft2d_stream_push",
@@ -90,6 +91,7 @@ def _load() -> ctypes.CDLL:
         "swdft2d_check_device": ([], i32),
         "swdft2d_inject_alloc_failure": ([i64], i32),
         "swdft2d_selftest_wait_timeout": ([i32, P], i32),
+        "swdft2d_debug_batch_wait": ([i64, i32], i32),
         "swdft2d_destroy": ([P], i32),
         "swdft2d_status_string": ([i32], ctypes.c_char_p),
         "swdft2d_version": ([], i32),
@@ -240,6 +242,13 @@ def selftest_wait_timeout(polls: int, stream: int = 0) -> None:
     of about 1 ms); the next check_device() then reports ERR_DEVICE_TIMEOUT."""
     _check(lib.swdft2d_selftest_wait_timeout(int(polls), ctypes.c_void_p(stream or None)),
            "swdft2d_selftest_wait_timeout")
+
+
+def debug_batch_wait(budget_cycles: int, poison: int) -> None:
+    """Set the clock64 budget of the pipelined batch kernels' waits (0: the default, about a
+    second) and the test hook that makes array 0's column tiles wait for `poison` row tiles
+    that never run; used by the next persistent launch enqueued or captured."""
+    _check(lib.swdft2d_debug_batch_wait(int(budget_cycles), int(poison)), "swdft2d_debug_batch_wait")
 
 
 def inject_alloc_failure(after: int) -> None:

@@ -25,6 +25,11 @@ bool alloc_fails() {
         if (g_alloc_budget.compare_exchange_weak(v, v - 1, std::memory_order_relaxed)) return false;
     return v == 0;
 }
+// pipelined batch launches: clock64 cycles a column tile may wait (about a second at the
+// GB300's clock), and the test hook's extra row-tile count (swdft2d_debug_batch_wait)
+constexpr int64_t kPipeBudget = 2000000000LL;
+static std::atomic<int64_t> g_pipe_budget{kPipeBudget};
+static std::atomic<int32_t> g_pipe_poison{0};
 }  // namespace swdft
 
 using namespace swdft;
@@ -84,7 +89,10 @@ struct ArrayPlan {
     bool tuned = false;
     int algo = SWDFT_ALGO_TREE_F32;  // per array: tree or one of the tensor-core forms
     bool algo_auto = false;          // made with SWDFT_ALGO_AUTO: the autotuner may pick a form
-    bool batch_fused = false;        // persistent batch: run in a fused group (no row tiles, no z)
+    // persistent batch: how the array runs -- in the pipelined kernel of its window shape,
+    // in the fused group of its window shape (no row tiles, no z), or on its own through the
+    // per-array launches (tree or tensor-core form) beside the persistent kernels
+    int batch_mode = 0;
     int64_t tc_chunk = 48;           // window rows per tensor-core CTA
 
     int64_t band_rows() const { return q_end - q_begin; }
@@ -132,6 +140,8 @@ struct ArrayPlan {
     }
 };
 
+constexpr int kBatchPipe = 0, kBatchFused = 1, kBatchSolo = 2;
+
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     std::vector<const void *> key;
@@ -165,25 +175,34 @@ struct swdft2d_plan_s {
     // persistent batch (SWDFT_FLAG_PERSISTENT): per-array z offsets in the workspace, the
     // tile descriptors (pinned staging + device copy, allocated at the first execute)
     std::vector<size_t> z_off;
-    // descriptor buffers: BatchImage[n], then the row-group entries, then the column-group
-    // entries (each group contiguous); pinned staging, a direct-execute copy, a graph copy
+    // descriptor buffers: BatchImage[n], then the fused groups' entries (each group
+    // contiguous); pinned staging, a direct-execute copy, a graph copy
     unsigned char *desc_host = nullptr;
     unsigned char *desc_dev = nullptr;
     unsigned char *desc_graph = nullptr;
     size_t desc_bytes = 0;
     cudaEvent_t desc_uploaded = nullptr;
-    // per window exponent m: entries [off, off + n) of the group, its tile count, grid slots
-    int row_off[kMaxLog2 + 1] = {}, row_n[kMaxLog2 + 1] = {};
-    int col_off[kMaxLog2 + 1] = {}, col_n[kMaxLog2 + 1] = {};
-    int64_t row_items[kMaxLog2 + 1] = {}, col_items[kMaxLog2 + 1] = {};
-    int64_t row_slots[kMaxLog2 + 1] = {}, col_slots[kMaxLog2 + 1] = {};
     // fused groups, index m0 * kBatchFusedM1 + m1, on their own side streams
     static constexpr int kFz = (kMaxLog2 + 1) * kBatchFusedM1;
     int fz_off[kFz] = {}, fz_n[kFz] = {};
     int64_t fz_items[kFz] = {}, fz_slots[kFz] = {};
-    bool any_fused = false;
     cudaStream_t fside[kConc] = {};
     cudaEvent_t fjoin_ev[kConc] = {};
+    // pipelined classes (every two-pass array of a persistent plan), index m0 * 7 + m1: the
+    // class's tiles are items [pz_off, pz_off + pz_n) of the plan-constant item table on the
+    // device (pipe_dev).  The workspace ends with the launch's counters: a ticket per class
+    // and the abort word (kPipeHead ints), then a flag per (array, row block, row chunk).
+    static constexpr int kPz = (kMaxLog2 + 1) * (kMaxLog2 + 1);
+    static constexpr int kPipeHead = 64;
+    int pz_off[kPz] = {}, pz_n[kPz] = {};
+    int64_t pz_slots[kPz] = {};
+    int pipe_flags = 0;          // row tiles of all two-pass arrays
+    size_t sync_off = 0;         // counters' offset in the workspace
+    size_t sync_bytes = 0;
+    unsigned char *pipe_dev = nullptr;
+    size_t pipe_dev_bytes = 0;
+    bool pipe_uploaded = false;  // cleared when the arrays' chunks change (autotuning)
+    std::vector<int> pipe_sync;  // per array: its first row-tile flag
     // host-buffer pipeline (SWDFT_FLAG_HOST_IO), allocated at the first execute_host
     bool io_ready = false;
     int64_t io_band = 0;
@@ -241,6 +260,103 @@ void default_config(ArrayPlan &a, int sm_count, int conc) {
     a.cfg = c;
 }
 
+// Tile geometry of a two-pass array in a pipelined persistent launch; the item table built at
+// configure time and the descriptors filled per buffer set both come from here.
+struct PipeGeom {
+    int rpb = 1, row_chunk = 1, row_chunks = 1, row_blocks = 1;
+    int col_chunk = 1, col_chunks = 1, col_blocks = 1;
+};
+PipeGeom pipe_geom(const ArrayPlan &a) {
+    PipeGeom g;
+    const int64_t rows_out = a.band_rows();
+    const int64_t zrows = rows_out + a.n0 - 1;
+    g.rpb = batch_pipe_rows_per_tile(a.m0, a.m1);  // row tiles: independent of the tuning state
+    g.row_chunk = (int)std::min<int64_t>(
+        a.P1, std::max<int64_t>(1, default_row_chunk(a.P1, zrows, int64_t(1) << batch_pipe_row_B(a.m1), a.n1)));
+    g.row_chunks = (int)((a.P1 + g.row_chunk - 1) / g.row_chunk);
+    g.row_blocks = (int)((zrows + g.rpb - 1) / g.rpb);
+    g.col_chunk = (int)std::min<int64_t>(rows_out, std::max<int64_t>(1, a.cfg.col_chunk));
+    g.col_chunks = (int)((rows_out + g.col_chunk - 1) / g.col_chunk);
+    const int64_t per_block = 32LL * batch_col_groups(a.m0);
+    g.col_blocks = (int)((a.P1 * a.n1 + per_block - 1) / per_block);
+    return g;
+}
+
+// The pipelined classes' tiles in ticket order.  A class's arrays (largest first) are cut
+// into stages: per column chunk, the row tiles of the z rows it is the first chunk to read,
+// then its column tiles.  Stages keep their order, but each stage's column tiles are held
+// back until at least `slots` tickets (the blocks the kernel keeps resident) have been issued
+// since its last row tile -- later stages' row tiles, of this array or the next ones, fill
+// the gap -- so that when a block takes a column tile its row tiles have almost surely
+// finished and the wait is a formality.  The next stage's row tiles always precede a stage's
+// column tiles; beyond that at most kPipeZAhead bytes of z are written ahead of their readers,
+// so they are still in L2 when read.
+constexpr int64_t kPipeZAhead = 48LL << 20;
+
+void build_pipe(swdft2d_plan_s *plan, std::vector<BatchPipeItem> &items, std::vector<int> &sync_off) {
+    const size_t n = plan->arrays.size();
+    items.clear();
+    sync_off.assign(n, 0);
+    int off = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const PipeGeom g = pipe_geom(plan->arrays[i]);
+        sync_off[i] = off;
+        off += g.row_blocks * g.row_chunks;
+    }
+    struct Stage {
+        int img, rb0, rb1, ck;
+        int64_t zbytes;
+    };
+    for (int c = 0; c < swdft2d_plan_s::kPz; ++c) {
+        plan->pz_off[c] = (int)items.size();
+        std::vector<size_t> idx;
+        for (size_t i = 0; i < n; ++i) {
+            const ArrayPlan &a = plan->arrays[i];
+            if (a.batch_mode == kBatchPipe && a.m0 * (kMaxLog2 + 1) + a.m1 == c) idx.push_back(i);
+        }
+        std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
+            const ArrayPlan &a = plan->arrays[x], &b = plan->arrays[y];
+            return a.band_rows() * a.out_row_bytes() > b.band_rows() * b.out_row_bytes();
+        });
+        std::vector<Stage> st;
+        for (size_t i : idx) {
+            const ArrayPlan &a = plan->arrays[i];
+            const PipeGeom g = pipe_geom(a);
+            const int zrows = (int)(a.band_rows() + a.n0 - 1);
+            int next_rb = 0;
+            for (int ck = 0; ck < g.col_chunks; ++ck) {
+                int r_lo = 0, r_hi = 0;
+                pipe_col_rows(ck, g.col_chunk, (int)a.band_rows(), a.n0, &r_lo, &r_hi);
+                const int rb1 = std::max(next_rb, (r_hi - 1) / g.rpb + 1);
+                const int64_t rows = std::min(rb1 * g.rpb, zrows) - std::min(next_rb * g.rpb, zrows);
+                st.push_back({(int)i, next_rb, rb1, ck, rows * a.P1 * a.n1 * (int64_t)sizeof(float2)});
+                next_rb = rb1;
+            }
+        }
+        const size_t slots = (size_t)std::max<int64_t>(1, plan->pz_slots[c]);
+        std::vector<size_t> dep_end(st.size(), 0);
+        int64_t z_ahead = 0;
+        size_t r = 0;
+        auto emit_rows = [&](size_t k) {
+            const Stage &e = st[k];
+            const int row_chunks = pipe_geom(plan->arrays[(size_t)e.img]).row_chunks;
+            for (int rb = e.rb0; rb < e.rb1; ++rb)
+                for (int rc = 0; rc < row_chunks; ++rc) items.push_back({e.img, rb * row_chunks + rc});
+            dep_end[k] = items.size();
+            z_ahead += e.zbytes;
+        };
+        for (size_t k = 0; k < st.size(); ++k) {
+            while (r <= k + 1 && r < st.size()) emit_rows(r++);  // the next stage's row tiles always go first
+            while (r < st.size() && items.size() - dep_end[k] < slots && z_ahead + st[r].zbytes <= kPipeZAhead)
+                emit_rows(r++);
+            const int col_blocks = pipe_geom(plan->arrays[(size_t)st[k].img]).col_blocks;
+            for (int cb = 0; cb < col_blocks; ++cb) items.push_back({st[k].img, ~(st[k].ck * col_blocks + cb)});
+            z_ahead -= st[k].zbytes;
+        }
+        plan->pz_n[c] = (int)items.size() - plan->pz_off[c];
+    }
+}
+
 swdft_status configure(swdft2d_plan_t plan) {
     if (plan->configured) return SWDFT_OK;
     int dev = 0, sms = 0;
@@ -264,7 +380,7 @@ swdft_status configure(swdft2d_plan_t plan) {
     }
     if (plan->flags & SWDFT_FLAG_PERSISTENT) {
         const size_t n = plan->arrays.size();
-        plan->desc_bytes = sizeof(BatchImage) * n + 3 * sizeof(BatchClassEntry) * n;
+        plan->desc_bytes = sizeof(BatchImage) * n + sizeof(BatchClassEntry) * n;
         if (!plan->desc_host && (alloc_fails() || cudaHostAlloc((void **)&plan->desc_host, plan->desc_bytes,
                                                                 cudaHostAllocDefault) != cudaSuccess))
             return SWDFT_ERR_OOM;
@@ -275,30 +391,57 @@ swdft_status configure(swdft2d_plan_t plan) {
             return SWDFT_ERR_OOM;
         if (!plan->desc_uploaded && cudaEventCreateWithFlags(&plan->desc_uploaded, cudaEventDisableTiming) != cudaSuccess)
             return SWDFT_ERR_CUDA;
-        for (int m = 0; m <= kMaxLog2; ++m) {
-            int row_bps = 0, col_bps = 0;
-            if (batch_blocks_per_sm(m, &row_bps, &col_bps) != cudaSuccess) return SWDFT_ERR_CUDA;
-            plan->row_slots[m] = (int64_t)plan->sm_count * std::max(1, row_bps);
-            plan->col_slots[m] = (int64_t)plan->sm_count * std::max(1, col_bps);
-        }
-        if (plan->any_fused) {
-            for (const auto &a : plan->arrays) {
-                if (!a.batch_fused) continue;
-                const int f = a.m0 * kBatchFusedM1 + a.m1;
-                if (plan->fz_slots[f] > 0) continue;
+        // grid slots of every kernel an array may run in (the autotuner may move arrays
+        // between the pipelined and fused kernels)
+        for (const auto &a : plan->arrays) {
+            const int c = a.m0 * (kMaxLog2 + 1) + a.m1;
+            if (plan->pz_slots[c] == 0) {
                 int bps = 0;
-                if (batch_fused_blocks_per_sm(a.m0, a.m1, &bps) != cudaSuccess) return SWDFT_ERR_CUDA;
-                plan->fz_slots[f] = (int64_t)plan->sm_count * std::max(1, bps);
+                if (batch_pipe_blocks_per_sm(a.m0, a.m1, &bps) != cudaSuccess) return SWDFT_ERR_CUDA;
+                plan->pz_slots[c] = (int64_t)plan->sm_count * std::max(1, bps);
             }
-            for (int k = 0; k < plan->conc; ++k) {
-                if (!plan->fside[k] && cudaStreamCreateWithFlags(&plan->fside[k], cudaStreamNonBlocking) != cudaSuccess)
-                    return SWDFT_ERR_CUDA;
-                if (!plan->fjoin_ev[k] && cudaEventCreateWithFlags(&plan->fjoin_ev[k], cudaEventDisableTiming) != cudaSuccess)
-                    return SWDFT_ERR_CUDA;
-            }
+            if (a.m1 >= kBatchFusedM1) continue;
+            const int f = a.m0 * kBatchFusedM1 + a.m1;
+            if (plan->fz_slots[f] > 0) continue;
+            int bps = 0;
+            if (batch_fused_blocks_per_sm(a.m0, a.m1, &bps) != cudaSuccess) return SWDFT_ERR_CUDA;
+            plan->fz_slots[f] = (int64_t)plan->sm_count * std::max(1, bps);
+        }
+        for (int k = 0; k < plan->conc; ++k) {
+            if (!plan->fside[k] && cudaStreamCreateWithFlags(&plan->fside[k], cudaStreamNonBlocking) != cudaSuccess)
+                return SWDFT_ERR_CUDA;
+            if (!plan->fjoin_ev[k] && cudaEventCreateWithFlags(&plan->fjoin_ev[k], cudaEventDisableTiming) != cudaSuccess)
+                return SWDFT_ERR_CUDA;
         }
     }
     plan->configured = true;
+    return SWDFT_OK;
+}
+
+// Build and upload the pipelined classes' item table (a plan constant; again after autotuning
+// changed the arrays' chunks).  Synchronous: not while a stream is capturing.
+swdft_status pipe_ready(swdft2d_plan_t plan) {
+    if (plan->pipe_uploaded) return SWDFT_OK;
+    std::vector<BatchPipeItem> items;
+    build_pipe(plan, items, plan->pipe_sync);
+    const size_t bytes = sizeof(BatchPipeItem) * std::max<size_t>(1, items.size());
+    if (bytes > plan->pipe_dev_bytes) {
+        if (plan->pipe_dev) {
+            if (cudaDeviceSynchronize() != cudaSuccess) return SWDFT_ERR_CUDA;  // a graph may still read it
+            cudaFree(plan->pipe_dev);
+            plan->pipe_dev = nullptr;
+            plan->pipe_dev_bytes = 0;
+        }
+        if (alloc_fails() || cudaMalloc((void **)&plan->pipe_dev, bytes) != cudaSuccess) return SWDFT_ERR_OOM;
+        plan->pipe_dev_bytes = bytes;
+    } else if (cudaDeviceSynchronize() != cudaSuccess) {
+        return SWDFT_ERR_CUDA;
+    }
+    if (!items.empty() &&
+        cudaMemcpy(plan->pipe_dev, items.data(), sizeof(BatchPipeItem) * items.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+        return SWDFT_ERR_CUDA;
+    plan->pipe_uploaded = true;
     return SWDFT_OK;
 }
 
@@ -307,9 +450,7 @@ swdft_status configure(swdft2d_plan_t plan) {
 void fill_batch(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out, void *ws) {
     const size_t n = plan->arrays.size();
     BatchImage *imgs = reinterpret_cast<BatchImage *>(plan->desc_host);
-    BatchClassEntry *row_ent = reinterpret_cast<BatchClassEntry *>(imgs + n);
-    BatchClassEntry *col_ent = row_ent + n;
-    BatchClassEntry *fz_ent = col_ent + n;
+    BatchClassEntry *fz_ent = reinterpret_cast<BatchClassEntry *>(imgs + n);
     for (size_t i = 0; i < n; ++i) {
         const ArrayPlan &a = plan->arrays[i];
         BatchImage d;
@@ -322,62 +463,38 @@ void fill_batch(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out
         d.row.zrow = a.P1 * a.n1;
         d.row.rows = (int)zrows;
         d.row.P1 = (int)a.P1;
-        d.row.chunk = (int)std::min<int64_t>(a.P1, std::max<int64_t>(1, a.cfg.row_chunk));
         d.row.z = z;
         d.col.z = z;
         d.col.out = static_cast<float2 *>(d_out[i]);
         d.col.nch = a.P1 * a.n1;
         d.col.orow = a.P1 * a.n1 * a.n0;
         d.col.rows_out = (int)a.band_rows();
-        d.col.chunk = (int)std::min<int64_t>(a.band_rows(), std::max<int64_t>(1, a.cfg.col_chunk));
         d.col.m1 = a.m1;
         d.col.groups = batch_col_groups(a.m0);
         d.col.scale = norm_scale(plan->norm, a.n0, a.n1);
         d.m0 = a.m0;
         d.m1 = a.m1;
         d.cplx = a.dtype == SWDFT_C64;
-        d.fused = a.batch_fused ? 1 : 0;
-        const int rows_per_block = 128 >> batch_row_B(a.m1);
-        d.row_blocks = (int)((zrows + rows_per_block - 1) / rows_per_block);
-        d.row_chunks = (int)((a.P1 + d.row.chunk - 1) / d.row.chunk);
+        d.fused = a.batch_mode == kBatchFused ? 1 : 0;
         const int64_t ch_per_block = 32LL * d.col.groups;
         d.col_blocks = (int)((d.col.nch + ch_per_block - 1) / ch_per_block);
-        d.col_chunks = (int)((a.band_rows() + d.col.chunk - 1) / d.col.chunk);
+        if (a.batch_mode == kBatchFused) {
+            d.col.chunk = (int)std::min<int64_t>(a.band_rows(), std::max<int64_t>(1, a.cfg.col_chunk));
+            d.col_chunks = (int)((a.band_rows() + d.col.chunk - 1) / d.col.chunk);
+        } else {
+            const PipeGeom g = pipe_geom(a);
+            d.row.chunk = g.row_chunk;
+            d.row_blocks = g.row_blocks;
+            d.row_chunks = g.row_chunks;
+            d.col.chunk = g.col_chunk;
+            d.col_chunks = g.col_chunks;
+            d.col_blocks = g.col_blocks;
+            d.sync_off = plan->pipe_sync[i];
+        }
         imgs[i] = d;
     }
-    // group the arrays by window exponent, in array order within a group
-    int pos = 0;
-    for (int m = 0; m <= kMaxLog2; ++m) {
-        plan->row_off[m] = pos;
-        int64_t items = 0;
-        for (size_t i = 0; i < n; ++i)
-            if (imgs[i].m1 == m && !imgs[i].fused) {
-                row_ent[pos].item0 = items;
-                row_ent[pos].img = (int)i;
-                row_ent[pos].pad = 0;
-                items += (int64_t)imgs[i].row_blocks * imgs[i].row_chunks;
-                ++pos;
-            }
-        plan->row_n[m] = pos - plan->row_off[m];
-        plan->row_items[m] = items;
-    }
-    pos = 0;
-    for (int m = 0; m <= kMaxLog2; ++m) {
-        plan->col_off[m] = pos;
-        int64_t items = 0;
-        for (size_t i = 0; i < n; ++i)
-            if (imgs[i].m0 == m && !imgs[i].fused) {
-                col_ent[pos].item0 = items;
-                col_ent[pos].img = (int)i;
-                col_ent[pos].pad = 0;
-                items += (int64_t)imgs[i].col_blocks * imgs[i].col_chunks;
-                ++pos;
-            }
-        plan->col_n[m] = pos - plan->col_off[m];
-        plan->col_items[m] = items;
-    }
     // fused groups: column tiles of the fused arrays, grouped by (m0, m1)
-    pos = 0;
+    int pos = 0;
     for (int f = 0; f < swdft2d_plan_s::kFz; ++f) {
         plan->fz_off[f] = pos;
         int64_t items = 0;
@@ -394,58 +511,71 @@ void fill_batch(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out
     }
 }
 
-// Launch every row group, join, then every column group, join: groups run concurrently on
-// the plan's side streams.  Only event records/waits and kernel launches (capturable).
-swdft_status launch_batch(swdft2d_plan_t plan, const unsigned char *desc, cudaStream_t s) {
+cudaError_t enqueue_forward(const swdft2d_plan_s *plan, const ArrayPlan &a, const void *in, void *out, void *ws,
+                            int64_t q_lo, int64_t q_hi, cudaStream_t s, int stages = 3);
+
+// Zero the pipelined kernels' counters, then run, concurrently on the plan's side streams and
+// joined back into s: the pipelined kernel of every window shape with arrays in that mode, the
+// fused kernel of every window shape with fused arrays, and the per-array launches of the
+// arrays that run on their own.  only >= 0 restricts it all to the arrays of window shape
+// `only` (m0 * 7 + m1; the autotuner's timing runs).  Only memsets, event records/waits and
+// kernel launches (capturable).
+swdft_status launch_batch(swdft2d_plan_t plan, const unsigned char *desc, const void *const *d_in,
+                          void *const *d_out, void *ws, cudaStream_t s, int only = -1) {
     const size_t n = plan->arrays.size();
     const BatchImage *imgs = reinterpret_cast<const BatchImage *>(desc);
-    const BatchClassEntry *row_ent = reinterpret_cast<const BatchClassEntry *>(imgs + n);
-    const BatchClassEntry *col_ent = row_ent + n;
-    const BatchClassEntry *fz_ent = col_ent + n;
+    const BatchClassEntry *fz_ent = reinterpret_cast<const BatchClassEntry *>(imgs + n);
     swdft_status st = SWDFT_OK;
-    // fused groups need no z: they start with the row groups on their own streams and are
-    // joined at the end
-    if (plan->any_fused) {
-        if (cudaEventRecord(plan->fork_ev, s) != cudaSuccess) return SWDFT_ERR_CUDA;
-        int k = 0;
-        for (int j = 0; j < plan->conc; ++j)
-            if (cudaStreamWaitEvent(plan->fside[j], plan->fork_ev, 0) != cudaSuccess) return SWDFT_ERR_CUDA;
-        for (int f = 0; f < swdft2d_plan_s::kFz && st == SWDFT_OK; ++f) {
-            if (plan->fz_n[f] == 0) continue;
-            if (launch_batch_fused_class(f / kBatchFusedM1, f % kBatchFusedM1, imgs, fz_ent + plan->fz_off[f],
-                                         plan->fz_n[f], plan->fz_items[f], plan->om64, plan->fz_slots[f],
-                                         plan->fside[k % plan->conc]) != cudaSuccess)
-                st = SWDFT_ERR_CUDA;
-            ++k;
-        }
+    int *sync = reinterpret_cast<int *>(static_cast<char *>(ws) + plan->sync_off);
+    if (cudaMemsetAsync(sync, 0, plan->sync_bytes, s) != cudaSuccess) return SWDFT_ERR_CUDA;
+    if (cudaEventRecord(plan->fork_ev, s) != cudaSuccess) return SWDFT_ERR_CUDA;
+    for (int j = 0; j < plan->conc; ++j)
+        if (cudaStreamWaitEvent(plan->side[j], plan->fork_ev, 0) != cudaSuccess ||
+            cudaStreamWaitEvent(plan->fside[j], plan->fork_ev, 0) != cudaSuccess)
+            return SWDFT_ERR_CUDA;
+    auto cls = [](const ArrayPlan &a) { return a.m0 * (kMaxLog2 + 1) + a.m1; };
+    int k = 0;
+    BatchPipeArgs pa;
+    pa.imgs = imgs;
+    const BatchPipeItem *items = reinterpret_cast<const BatchPipeItem *>(plan->pipe_dev);
+    pa.abort = sync + swdft2d_plan_s::kPz;
+    pa.done = sync + swdft2d_plan_s::kPipeHead;
+    pa.budget = g_pipe_budget.load(std::memory_order_relaxed);
+    pa.poison = g_pipe_poison.load(std::memory_order_relaxed);
+    pa.om64 = plan->om64;
+    for (int c = 0; c < swdft2d_plan_s::kPz && st == SWDFT_OK; ++c) {
+        if (plan->pz_n[c] == 0 || (only >= 0 && c != only)) continue;
+        pa.items = items + plan->pz_off[c];
+        pa.nitems = plan->pz_n[c];
+        pa.ticket = sync + c;
+        if (launch_batch_pipe(c / (kMaxLog2 + 1), c % (kMaxLog2 + 1), pa, plan->pz_slots[c],
+                              plan->side[k++ % plan->conc]) != cudaSuccess)
+            st = SWDFT_ERR_CUDA;
     }
-    for (int phase = 0; phase < 2 && st == SWDFT_OK; ++phase) {
-        const bool col = phase == 1;
-        if (cudaEventRecord(plan->fork_ev, s) != cudaSuccess) return SWDFT_ERR_CUDA;
-        for (int k = 0; k < plan->conc; ++k)
-            if (cudaStreamWaitEvent(plan->side[k], plan->fork_ev, 0) != cudaSuccess) return SWDFT_ERR_CUDA;
-        int k = 0;
-        for (int m = 0; m <= kMaxLog2 && st == SWDFT_OK; ++m) {
-            const int cnt = col ? plan->col_n[m] : plan->row_n[m];
-            if (cnt == 0) continue;
-            const BatchClassEntry *ent = col ? col_ent + plan->col_off[m] : row_ent + plan->row_off[m];
-            if (launch_batch_class(col, m, imgs, ent, cnt, col ? plan->col_items[m] : plan->row_items[m],
-                                   plan->om64, col ? plan->col_slots[m] : plan->row_slots[m],
-                                   plan->side[k % plan->conc]) != cudaSuccess)
-                st = SWDFT_ERR_CUDA;
-            ++k;
-        }
-        for (int j = 0; j < plan->conc; ++j) {
-            if (cudaEventRecord(plan->join_ev[j], plan->side[j]) != cudaSuccess) st = SWDFT_ERR_CUDA;
-            if (cudaStreamWaitEvent(s, plan->join_ev[j], 0) != cudaSuccess) st = SWDFT_ERR_CUDA;
-        }
+    // fused groups need no z: they run beside the pipelined kernels on their own streams
+    int kf = 0;
+    for (int f = 0; f < swdft2d_plan_s::kFz && st == SWDFT_OK; ++f) {
+        const int m0 = f / kBatchFusedM1, m1 = f % kBatchFusedM1;
+        if (plan->fz_n[f] == 0 || (only >= 0 && m0 * (kMaxLog2 + 1) + m1 != only)) continue;
+        if (launch_batch_fused_class(m0, m1, imgs, fz_ent + plan->fz_off[f], plan->fz_n[f], plan->fz_items[f],
+                                     plan->om64, plan->fz_slots[f], plan->fside[kf++ % plan->conc]) != cudaSuccess)
+            st = SWDFT_ERR_CUDA;
     }
-    // always join the fused streams back (a capture must end with every stream joined)
-    if (plan->any_fused)
-        for (int j = 0; j < plan->conc; ++j) {
-            if (cudaEventRecord(plan->fjoin_ev[j], plan->fside[j]) != cudaSuccess) st = SWDFT_ERR_CUDA;
-            if (cudaStreamWaitEvent(s, plan->fjoin_ev[j], 0) != cudaSuccess) st = SWDFT_ERR_CUDA;
-        }
+    // arrays on their own: their per-array launches (tree or tensor-core form) in their region
+    for (size_t i = 0; i < n && st == SWDFT_OK; ++i) {
+        const ArrayPlan &a = plan->arrays[i];
+        if (a.batch_mode != kBatchSolo || (only >= 0 && cls(a) != only)) continue;
+        if (enqueue_forward(plan, a, d_in[i], d_out[i], static_cast<char *>(ws) + plan->z_off[i], a.q_begin, a.q_end,
+                            plan->side[k++ % plan->conc]) != cudaSuccess)
+            st = SWDFT_ERR_CUDA;
+    }
+    // always join every forked stream back (a capture must end with every stream joined)
+    for (int j = 0; j < plan->conc; ++j) {
+        if (cudaEventRecord(plan->join_ev[j], plan->side[j]) != cudaSuccess) st = SWDFT_ERR_CUDA;
+        if (cudaStreamWaitEvent(s, plan->join_ev[j], 0) != cudaSuccess) st = SWDFT_ERR_CUDA;
+        if (cudaEventRecord(plan->fjoin_ev[j], plan->fside[j]) != cudaSuccess) st = SWDFT_ERR_CUDA;
+        if (cudaStreamWaitEvent(s, plan->fjoin_ev[j], 0) != cudaSuccess) st = SWDFT_ERR_CUDA;
+    }
     return st;
 }
 
@@ -453,19 +583,21 @@ swdft_status launch_batch(swdft2d_plan_t plan, const unsigned char *desc, cudaSt
 // upload it on the stream and launch the two persistent passes.
 swdft_status enqueue_batch(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out,
                            void *ws, cudaStream_t s) {
+    swdft_status st = pipe_ready(plan);
+    if (st != SWDFT_OK) return st;
     if (cudaEventSynchronize(plan->desc_uploaded) != cudaSuccess) return SWDFT_ERR_CUDA;
     fill_batch(plan, d_in, d_out, ws);
     if (cudaMemcpyAsync(plan->desc_dev, plan->desc_host, plan->desc_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return SWDFT_ERR_CUDA;
     if (cudaEventRecord(plan->desc_uploaded, s) != cudaSuccess) return SWDFT_ERR_CUDA;
-    return launch_batch(plan, plan->desc_dev, s);
+    return launch_batch(plan, plan->desc_dev, d_in, d_out, ws, s);
 }
 
 // Enqueue the forward transform of output rows [q_lo, q_hi) of array a.
 // stages: bit 0 = row levels (x -> z), bit 1 = column levels (z -> out).
 cudaError_t enqueue_forward(const swdft2d_plan_s *plan, const ArrayPlan &a, const void *in,
                             void *out, void *ws, int64_t q_lo, int64_t q_hi, cudaStream_t s,
-                            int stages = 3) {
+                            int stages) {
     const int64_t rows_out = q_hi - q_lo;
     if (rows_out <= 0) return cudaSuccess;
     if (a.algo >= SWDFT_ALGO_TC_BF16X3) {
@@ -850,11 +982,10 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
         // binary column kernel needs power-of-two rows
         if (r1 == 3 && r0 == 2 && m0 > 0) return SWDFT_ERR_UNSUPPORTED;
         a.algo = (algo == SWDFT_ALGO_AUTO) ? SWDFT_ALGO_TREE_F32 : algo;
-        a.algo_auto = algo == SWDFT_ALGO_AUTO && !(flags & SWDFT_FLAG_PERSISTENT);
+        a.algo_auto = algo == SWDFT_ALGO_AUTO;
         if (a.algo >= SWDFT_ALGO_TC_BF16X3 && !a.tc_eligible()) return SWDFT_ERR_UNSUPPORTED;
         if (a.ternary() && (flags & SWDFT_FLAG_PERSISTENT)) return SWDFT_ERR_UNSUPPORTED;
     }
-    if (algo >= SWDFT_ALGO_TC_BF16X3 && (flags & SWDFT_FLAG_PERSISTENT)) return SWDFT_ERR_UNSUPPORTED;
 
     swdft2d_plan_s *p = alloc_fails() ? nullptr : new (std::nothrow) swdft2d_plan_s();
     if (!p) return SWDFT_ERR_OOM;
@@ -866,20 +997,28 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
     make_omega(kMaxN, p->om64);
     size_t ws = 0;
     if (flags & SWDFT_FLAG_PERSISTENT) {
-        // one launch covers every array, so each array has its own z region; the window
-        // groups' kernels run on up to four side streams
+        // the batch's kernels run at once, so each array has its own region (its z, or the
+        // tensor-core form's operand planes when that form may run); the kernels run on up to
+        // four side streams
         for (const auto &a : p->arrays) {
             p->z_off.push_back(ws);
-            ws += align_up(a.ws_bytes_for(a.band_rows(), SWDFT_ALGO_TREE_F32));
+            ws += align_up(a.ws_bytes_plan(a.band_rows()));
         }
         p->conc = 4;
-        // small windows (n0 n1 <= 64, where z is 1/n0 >= 1/8 of the output) run in fused
-        // groups; measured on the 256-image batch, fusing larger windows as well was slower
-        // (28.1 ms with every n0 >= 16 fused, 26.9 with none, 26.2 with small windows only)
+        // tensor-core forms run per array beside the persistent kernels; small windows (n0 n1
+        // <= 64, where z is 1/n0 >= 1/8 of the output) in fused groups; every other array in
+        // the pipelined kernel of its (n0, n1).  The autotuner may move arrays between the
+        // three, per window shape.  Every array has row-tile flags, whatever its mode.
         for (auto &a : p->arrays) {
-            a.batch_fused = !a.ternary() && a.m1 < kBatchFusedM1 && a.n0 * a.n1 <= 64;
-            p->any_fused = p->any_fused || a.batch_fused;
+            a.batch_mode = a.algo >= SWDFT_ALGO_TC_BF16X3 ? kBatchSolo
+                           : (a.m1 < kBatchFusedM1 && a.n0 * a.n1 <= 64) ? kBatchFused
+                                                                          : kBatchPipe;
+            const PipeGeom g = pipe_geom(a);
+            p->pipe_flags += g.row_blocks * g.row_chunks;
         }
+        p->sync_off = ws;
+        p->sync_bytes = sizeof(int) * ((size_t)swdft2d_plan_s::kPipeHead + (size_t)p->pipe_flags);
+        ws += align_up(p->sync_bytes);
     } else {
         // up to four arrays run at once (plan-owned streams), each with its own z slot;
         // arrays of one shape run their adjoint passes in groups of up to kAdjZ launches
@@ -930,18 +1069,19 @@ swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t 
     // forward: row + column pass per array, or the two persistent passes for the whole batch;
     // adjoint: column + row adjoint pass per array
     if (!adjoint && (plan->flags & SWDFT_FLAG_PERSISTENT)) {
-        // one persistent kernel per row-window group and per column-window group
-        bool r[kMaxLog2 + 1] = {}, c[kMaxLog2 + 1] = {}, f[swdft2d_plan_s::kFz] = {};
-        for (const auto &a : plan->arrays) {
-            if (a.batch_fused) {
-                f[a.m0 * kBatchFusedM1 + a.m1] = true;
-            } else {
-                r[a.m1] = true;
-                c[a.m0] = true;
-            }
-        }
+        // one pipelined kernel per (n0, n1) of the pipelined arrays, one fused kernel per
+        // (n0, n1) of the fused arrays, and the per-array launches of the arrays on their own
+        bool c[swdft2d_plan_s::kPz] = {}, f[swdft2d_plan_s::kFz] = {};
         int32_t k = 0;
-        for (int m = 0; m <= kMaxLog2; ++m) k += (int)r[m] + (int)c[m];
+        for (const auto &a : plan->arrays) {
+            if (a.batch_mode == kBatchFused)
+                f[a.m0 * kBatchFusedM1 + a.m1] = true;
+            else if (a.batch_mode == kBatchPipe)
+                c[a.m0 * (kMaxLog2 + 1) + a.m1] = true;
+            else
+                k += (a.algo == SWDFT_ALGO_TREE_F32 && a.cfg.fused && fused_supported(a.m0, a.m1)) ? 1 : 2;
+        }
+        for (int j = 0; j < swdft2d_plan_s::kPz; ++j) k += (int)c[j];
         for (int j = 0; j < swdft2d_plan_s::kFz; ++j) k += (int)f[j];
         *launches = k;
         return SWDFT_OK;
@@ -987,7 +1127,7 @@ swdft_status swdft2d_execute(swdft2d_plan_t plan, const void *const *d_in, void 
     // these buffers go to the graph's own device buffer before capture
     auto enqueue = [&]() {
         if (!persistent) return enqueue_all(plan, d_in, d_out, d_workspace, s);
-        return launch_batch(plan, plan->desc_graph, s);
+        return launch_batch(plan, plan->desc_graph, d_in, d_out, d_workspace, s);
     };
 
     // CUDA graph: capture the launch sequence once per (buffers, stream), replay after.
@@ -1004,6 +1144,7 @@ swdft_status swdft2d_execute(swdft2d_plan_t plan, const void *const *d_in, void 
             // an earlier graph of this plan may still be reading the descriptors on any
             // stream: re-capture is rare, so wait for the whole device
             if (cudaDeviceSynchronize() != cudaSuccess) return SWDFT_ERR_CUDA;
+            if ((st = pipe_ready(plan)) != SWDFT_OK) return st;
             fill_batch(plan, d_in, d_out, d_workspace);
             if (cudaMemcpy(plan->desc_graph, plan->desc_host, plan->desc_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
                 return SWDFT_ERR_CUDA;
@@ -1210,6 +1351,81 @@ swdft_status swdft2d_execute_host(swdft2d_plan_t plan, const void *const *h_in,
     return SWDFT_OK;
 }
 
+namespace {
+
+// Persistent plans: per window shape (n0, n1), time its arrays in each form they may take --
+// the pipelined kernel, the fused kernel (n1 <= 32), per-array launches of the tree, and, with
+// SWDFT_ALGO_AUTO where the window allows, per-array launches of the split-bf16 tensor-core
+// form -- each alone (launch_batch restricted to that shape, best of three), and keep the
+// fastest.  Arrays made with a tensor-core algorithm stay on their own.  Synchronous.
+swdft_status autotune_batch(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out, void *ws,
+                            cudaStream_t s) {
+    const size_t n = plan->arrays.size();
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SWDFT_ERR_CUDA;
+    auto cls = [](const ArrayPlan &a) { return a.m0 * (kMaxLog2 + 1) + a.m1; };
+    auto set_form = [&](int c, int mode, int algo) {
+        for (auto &a : plan->arrays)
+            if (cls(a) == c && (a.algo_auto || a.algo == SWDFT_ALGO_TREE_F32)) {
+                a.batch_mode = mode;
+                a.algo = algo;
+            }
+    };
+    // time shape c in its current forms
+    auto time_class = [&](int c, float *ms_out) -> swdft_status {
+        plan->pipe_uploaded = false;
+        swdft_status st = pipe_ready(plan);  // synchronises the device
+        if (st != SWDFT_OK) return st;
+        fill_batch(plan, d_in, d_out, ws);
+        if (cudaMemcpy(plan->desc_dev, plan->desc_host, plan->desc_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+            return SWDFT_ERR_CUDA;
+        float best = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            if (cudaEventRecord(e0, s) != cudaSuccess) return SWDFT_ERR_CUDA;
+            if ((st = launch_batch(plan, plan->desc_dev, d_in, d_out, ws, s, c)) != SWDFT_OK) return st;
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return SWDFT_ERR_CUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) best = std::min(best, ms);  // the first run warms up
+        }
+        *ms_out = best;
+        return SWDFT_OK;
+    };
+    swdft_status st = SWDFT_OK;
+    std::vector<char> done(swdft2d_plan_s::kPz, 0);
+    for (size_t i = 0; i < n && st == SWDFT_OK; ++i) {
+        const ArrayPlan &a0 = plan->arrays[i];
+        const int c = cls(a0);
+        if (done[(size_t)c] || !(a0.algo_auto || a0.algo == SWDFT_ALGO_TREE_F32)) continue;
+        done[(size_t)c] = 1;
+        struct Form {
+            int mode, algo;
+        };
+        std::vector<Form> forms = {{kBatchPipe, SWDFT_ALGO_TREE_F32}, {kBatchSolo, SWDFT_ALGO_TREE_F32}};
+        if (a0.m1 < kBatchFusedM1) forms.push_back({kBatchFused, SWDFT_ALGO_TREE_F32});
+        if (a0.algo_auto && a0.tc_eligible()) forms.push_back({kBatchSolo, SWDFT_ALGO_TC_BF16X3});
+        Form best{kBatchPipe, SWDFT_ALGO_TREE_F32};
+        float best_ms = 1e30f;
+        for (const Form &f : forms) {
+            set_form(c, f.mode, f.algo);
+            float ms = 0.f;
+            if ((st = time_class(c, &ms)) != SWDFT_OK) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = f;
+            }
+        }
+        set_form(c, best.mode, best.algo);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    plan->pipe_uploaded = false;
+    destroy_graph(plan->graph);
+    return st;
+}
+
+}  // namespace
+
 swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out,
                               void *d_workspace, void *stream) {
     if (!plan) return SWDFT_ERR_INVALID_ARG;
@@ -1217,6 +1433,7 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
     if (st != SWDFT_OK) return st;
     if ((st = configure(plan)) != SWDFT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (plan->flags & SWDFT_FLAG_PERSISTENT) return autotune_batch(plan, d_in, d_out, d_workspace, s);
     // arrays with a record in the tuning cache for this GPU take it without timing
     const char *cache = std::getenv("SWDFT_TUNE_CACHE");
     char gpu[256] = "unknown";
@@ -1353,6 +1570,7 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     destroy_graph(plan->graph);
+    plan->pipe_uploaded = false;  // a persistent plan's tiles follow the tuned chunks
     return SWDFT_OK;
 }
 
@@ -1385,11 +1603,18 @@ swdft_status swdft2d_load_tuning(swdft2d_plan_t plan, const char *path, const ch
 }
 
 swdft_status swdft2d_check_device(void) {
-    int status = 0, probe = 0, col = 0;
+    int status = 0, probe = 0, col = 0, pipe = 0;
     if (tc_status(&status, true) != cudaSuccess || probe_status(&probe, true) != cudaSuccess ||
-        col_tma_status(&col, true) != cudaSuccess)
+        col_tma_status(&col, true) != cudaSuccess || batch_pipe_status(&pipe, true) != cudaSuccess)
         return SWDFT_ERR_CUDA;
-    return (status || probe || col) ? SWDFT_ERR_DEVICE_TIMEOUT : SWDFT_OK;
+    return (status || probe || col || pipe) ? SWDFT_ERR_DEVICE_TIMEOUT : SWDFT_OK;
+}
+
+swdft_status swdft2d_debug_batch_wait(int64_t budget_cycles, int32_t poison) {
+    if (budget_cycles < 0 || poison < 0) return SWDFT_ERR_INVALID_ARG;
+    g_pipe_budget.store(budget_cycles == 0 ? kPipeBudget : budget_cycles, std::memory_order_relaxed);
+    g_pipe_poison.store(poison, std::memory_order_relaxed);
+    return SWDFT_OK;
 }
 
 swdft_status swdft2d_destroy(swdft2d_plan_t plan) {
@@ -1409,6 +1634,7 @@ swdft_status swdft2d_destroy(swdft2d_plan_t plan) {
     if (plan->fork_ev) cudaEventDestroy(plan->fork_ev);
     if (plan->desc_dev) cudaFree(plan->desc_dev);
     if (plan->desc_graph) cudaFree(plan->desc_graph);
+    if (plan->pipe_dev) cudaFree(plan->pipe_dev);
     // host-buffer staging, including what a set-up that ran out of memory left behind
     if (plan->io_in) cudaFree(plan->io_in);
     if (plan->io_ws) cudaFree(plan->io_ws);

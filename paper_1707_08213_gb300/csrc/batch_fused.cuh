@@ -9,6 +9,15 @@ namespace swdft {
 
 __host__ __device__ constexpr int bfu_B(int m0) { return m0 >= 6 ? 3 : (m0 < 2 ? m0 : 2); }
 __host__ __device__ constexpr int bfu_threads(int m0) { return m0 >= 6 ? 256 : 128; }
+// Resident blocks the batch kernels are compiled for.  A batch block reads its tile's geometry
+// from the descriptor table, so without a bound the compiler keeps it in up to ~20 more
+// registers than the per-array kernels (whose geometry is a kernel parameter) and fewer
+// blocks fit an SM; these bounds are the largest that compile without spills (n0 = 32: 96
+// registers, 5 blocks; n0 = 16: 64-80; n0 <= 8: 64).
+__host__ __device__ constexpr int bcol_min_blocks(int m0) { return m0 >= 6 ? 2 : (m0 == 5 ? 5 : 8); }
+__host__ __device__ constexpr int bfu_min_blocks(int m0, int m1) {
+    return m0 >= 6 ? 2 : (m0 == 5 ? 5 : (m0 == 4 ? (m1 >= 5 ? 6 : 7) : 8));
+}
 
 __device__ __forceinline__ int bfu_find_entry(const BatchClassEntry *__restrict__ ent, int n, int64_t item) {
     int lo = 0, hi = n - 1;
@@ -35,7 +44,7 @@ __device__ __forceinline__ void bfu_tile(const BatchImage &d, int64_t cb, int ck
 }
 
 template <int M0, int M1>
-__global__ void __launch_bounds__(bfu_threads(M0), M0 >= 6 ? 2 : 4)
+__global__ void __launch_bounds__(bfu_threads(M0), bfu_min_blocks(M0, M1))
     batch_fused_kernel(const BatchImage *__restrict__ imgs, const BatchClassEntry *__restrict__ ent, int nent,
                        int64_t nitems, const __grid_constant__ Omega64 om) {
     extern __shared__ float2 ring[];

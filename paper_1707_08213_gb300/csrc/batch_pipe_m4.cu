@@ -1,0 +1,9 @@
+// Pipelined persistent batch kernels: instantiations for log2(n0) in {4} (split so they
+// compile in parallel).
+#include "batch_pipe.cuh"
+
+namespace swdft {
+
+SWDFT_BPIPE_INSTANTIATE(4)
+
+}  // namespace swdft

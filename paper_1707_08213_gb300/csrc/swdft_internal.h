@@ -96,6 +96,8 @@ struct BatchImage {
     int fused;  // row levels inside the column tile (no row tiles, no z)
     int row_blocks, row_chunks;  // row pass: blocks of (128 >> B) rows x chunks of columns
     int col_blocks, col_chunks;  // column pass: blocks of 32 * groups channels x row chunks
+    int sync_off;                // pipelined launch: first of this array's row-tile flags
+    int pad_;
 };
 
 // Tensor-core column levels: out[q0][q1][k0][k1] = scale * sum_j0 z[q0+j0][ch] F0[j0][k0]
@@ -148,20 +150,46 @@ struct BatchClassEntry {
     int img;
     int pad;
 };
-// Persistent launch over every tile of one group (col = false: row tiles of the arrays with
-// n1 = 2^m; true: column tiles of those with n0 = 2^m).  grid = min(items, slots), slots =
-// SMs x resident blocks (batch_blocks_per_sm).  No CUDA call besides the launch (capturable).
-cudaError_t launch_batch_class(bool col, int m, const BatchImage *d_images, const BatchClassEntry *ent, int nent,
-                               int64_t nitems, const float2 *om64, int64_t slots, cudaStream_t s);
-cudaError_t batch_blocks_per_sm(int m, int *row_bps, int *col_bps);
 // Fused groups (arrays with n0 = 2^m0, n1 = 2^m1, m1 <= 5): column tiles that evaluate their
 // own row levels from the input, as fused_tree_kernel does for one array.
 constexpr int kBatchFusedM1 = 6;  // m1 = 0..5
 cudaError_t launch_batch_fused_class(int m0, int m1, const BatchImage *d_images, const BatchClassEntry *ent,
                                      int nent, int64_t nitems, const float2 *om64, int64_t slots, cudaStream_t s);
 cudaError_t batch_fused_blocks_per_sm(int m0, int m1, int *bps);
+// Pipelined launches (batch_pipe.cuh): one per (n0, n1) = (2^m0, 2^m1) of the two-pass
+// arrays, both passes in one kernel.  Device pointers; the counters are zeroed before the
+// launch.  grid = min(nitems, slots).
+struct BatchPipeItem {
+    int img;   // index into the image table
+    int code;  // >= 0: row tile rb * row_chunks + rc; < 0: column tile ~(ck * col_blocks + cb)
+};
+// z rows [r_lo, r_hi) of the band that column chunk ck reads (its ring starts n0/2 rows before
+// the chunk's first window row, the column tree's look-back; padding rows below 0 are never
+// written and never waited for).
+constexpr void pipe_col_rows(int ck, int chunk, int rows_out, int n0, int *r_lo, int *r_hi) {
+    const int qa = ck * chunk;
+    const int qb = qa + chunk < rows_out ? qa + chunk : rows_out;
+    const int look = n0 >= 2 ? n0 / 2 : 0;
+    *r_lo = qa - look > 0 ? qa - look : 0;
+    *r_hi = qb + n0 - 1;
+}
+struct BatchPipeArgs {
+    const BatchImage *imgs = nullptr;
+    const BatchPipeItem *items = nullptr;  // the class's tiles in ticket order
+    int *ticket = nullptr, *abort = nullptr;
+    int *done = nullptr;        // per (array, row block, row chunk) flags
+    int nitems = 0;
+    int poison = 0;             // test hook (swdft2d_debug_batch_wait)
+    long long budget = 0;       // clock64 cycles a column tile may wait
+    const float2 *om64 = nullptr;
+};
+cudaError_t launch_batch_pipe(int m0, int m1, const BatchPipeArgs &a, int64_t slots, cudaStream_t s);
+cudaError_t batch_pipe_blocks_per_sm(int m0, int m1, int *bps);
+cudaError_t batch_pipe_status(int *status, bool reset);
+// z rows per row tile of a pipelined launch, and the residue split of its row trees
+int batch_pipe_rows_per_tile(int m0, int m1);
+int batch_pipe_row_B(int m1);
 // Launch choices the batch kernels use for a window side of 2^m.
-int batch_row_B(int m1);
 int batch_col_B(int m0);
 int batch_col_groups(int m0);
 

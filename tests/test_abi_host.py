@@ -267,13 +267,13 @@ def test_stream_state_and_push_bookkeeping(nat):
 
 
 def test_persistent_batch_launches_one_kernel_per_window_class(nat):
-    """A persistent plan runs one kernel per row-window exponent, per column-window exponent
-    and per fused (m0, m1) pair, whatever the number of arrays: repeating arrays adds no
-    launch, and the 256-image uneven batch needs at most two per distinct window shape."""
+    """A persistent plan runs one kernel per window shape (n0, n1), pipelined or fused,
+    whatever the number of arrays: repeating arrays adds no launch, and the 256-image uneven
+    batch needs one per distinct window shape."""
     import workloads
     one = [shp(256, 256, 4, 4), shp(512, 128, 32, 32), shp(128, 1024, 64, 16)]
     base = nat.Plan(one, flags=nat.FLAG_PERSISTENT).launch_count()
-    assert 1 <= base <= 5
+    assert base == 3
     for k in (2, 7, 40):
         assert nat.Plan(one * k, flags=nat.FLAG_PERSISTENT).launch_count() == base
     # per-array plans launch once or twice per array instead
@@ -283,9 +283,29 @@ def test_persistent_batch_launches_one_kernel_per_window_class(nat):
               for i in range(len(widx))]
     windows = {workloads.UNEVEN_WINDOWS[int(w)] for w in widx}
     n_pers = nat.Plan(shapes, flags=nat.FLAG_PERSISTENT).launch_count()
-    # at most a row and a column kernel, or one fused kernel, per distinct window shape
-    assert 1 <= n_pers <= 2 * len(windows)
+    assert n_pers == len(windows) == 6
     assert nat.Plan(shapes).launch_count() >= len(shapes)
+
+
+def test_persistent_workspace_holds_z_regions_and_the_pipeline_counters(nat):
+    """A persistent plan's workspace: every array's own region (its z, or its adjoint's gz and
+    side rows), then one block of counters for the pipelined kernels -- 64 words, then a flag
+    per row tile (row block of z rows x row chunk of window columns) of every array (the
+    autotuner may move any array into a pipelined kernel), 256-byte aligned.  So a batch takes
+    its arrays' single-array workspaces less all but one counter block."""
+    r = lambda b: (b + 255) // 256 * 256
+    A, B, C = shp(100, 90, 32, 32), shp(20, 20, 4, 4), shp(70, 130, 16, 64)
+    ws = lambda shapes: nat.Plan(shapes, flags=nat.FLAG_PERSISTENT).workspace_size()
+    # row tiles: ceil(z rows / (128 >> B)) x ceil(P1 / chunk), B = 3 for n1 >= 8 (m1 for
+    # n1 < 8), chunk = max(n1 / 2, P1 over ~64K threads)
+    f = {"A": -(-(69 + 31) // 16) * -(-59 // 16), "B": -(-(17 + 3) // 32) * -(-17 // 2),
+         "C": -(-(55 + 15) // 16) * -(-67 // 32)}
+    shape = {"A": A, "B": B, "C": C}
+    cnt = lambda flags: r(4 * (64 + flags))
+    region = {x: ws([shape[x]]) - cnt(f[x]) for x in "ABC"}
+    for batch in ("ABC", "AA", "BB", "A" * 10 + "C" * 7 + "B" * 3):
+        assert ws([shape[x] for x in batch]) == sum(region[x] for x in batch) + cnt(sum(f[x] for x in batch))
+    assert cnt(10 * f["A"] + 7 * f["C"] + 3 * f["B"]) == 2048  # 64 + 412 words, 256-byte aligned
 
 
 def test_injected_allocation_failures(nat):

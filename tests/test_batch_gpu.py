@@ -1,7 +1,8 @@
 """The persistent batched launch (SWDFT_FLAG_PERSISTENT): many arrays of uneven sizes and
-window shapes in persistent kernels per window group (row, column and fused groups),
-optionally replayed from a CUDA graph, against the FP64 oracle (Section 4.1, Eq. 2;
-per-window error / window norm <= 1e-5)."""
+window shapes in one persistent kernel per window shape (a pipelined row+column kernel for
+the two-pass arrays, a fused kernel for small windows), optionally replayed from a CUDA
+graph, against the FP64 oracle (Section 4.1, Eq. 2; per-window error / window norm <= 1e-5);
+the pipelined kernels' bounded waits made to run out through the test hook."""
 import numpy as np
 import pytest
 import torch
@@ -43,12 +44,12 @@ def test_persistent_batch_of_mixed_shapes(sw, flags):
     xs = _inputs()
     f = sw.FLAG_PERSISTENT | (sw.FLAG_GRAPH if "graph" in flags else 0)
     t = sw.Transform([(N0, N1, n0, n1, int(c)) for (N0, N1, n0, n1, c) in MIXED], flags=f)
-    # one persistent kernel per row-window group and per column-window group of the two-pass
-    # arrays, and one per (n0, n1) group of the fused arrays (small windows, n0 n1 <= 64)
-    fused = [(n0, n1) for _, _, n0, n1, _ in MIXED if n0 * n1 <= 64]
+    # one pipelined kernel per (n0, n1) of the two-pass arrays, one fused kernel per (n0, n1)
+    # of the fused arrays (small windows: n0 n1 <= 64, n1 < 64)
+    fused = [(n0, n1) for _, _, n0, n1, _ in MIXED if n0 * n1 <= 64 and n1 < 64]
     two = [(n0, n1) for _, _, n0, n1, _ in MIXED if (n0, n1) not in fused]
-    assert t.plan.launch_count() == len({b for _, b in two}) + len({a for a, _ in two}) + len(set(fused))
-    assert t.plan.launch_count() == 12
+    assert t.plan.launch_count() == len(set(two)) + len(set(fused))
+    assert t.plan.launch_count() == 9
     xd = [torch.from_numpy(x).cuda() for x in xs]
     outs = t.empty_outputs()
     s = torch.cuda.Stream()
@@ -73,10 +74,92 @@ def test_persistent_matches_per_array_launches(sw):
         assert torch.equal(u, v)
 
 
+def test_persistent_bands_match_per_array_launches(sw):
+    """Bands of window rows (row_begin/row_end) in a persistent plan: the pipelined and fused
+    kernels start at the band's first input row, bit for bit the per-array result."""
+    shapes = [(300, 90, 32, 32, 0), (200, 70, 16, 64, 1), (150, 40, 8, 8, 0), (260, 33, 64, 16, 0)]
+    bands = [(37, 211), (0, 5), (100, 0), (1, 2)]
+    xs = [workloads.random_array(70 + i, s[0], s[1], complex_input=bool(s[4])) for i, s in enumerate(shapes)]
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    a = sw.Transform(shapes, bands=bands).forward(xd)
+    b = sw.Transform(shapes, bands=bands, flags=sw.FLAG_PERSISTENT).forward(xd)
+    torch.cuda.synchronize()
+    assert sw._native.check_device() == 0
+    for u, v in zip(a, b):
+        assert torch.equal(u, v)
+
+
+def test_pipelined_wait_gives_up_then_the_next_launch_is_clean(sw):
+    """The test hook makes array 0's column tiles wait for a row tile that never runs: the
+    bounded wait (about 1 ms of clock64 cycles) gives up, every block of the launch stops,
+    check_device reports the time-out; with the hook off the same plan runs clean and
+    matches the per-array result bit for bit."""
+    nat = sw._native
+    shapes = [(130, 64, 64, 16, 0), (70, 50, 8, 32, 0), (20, 20, 4, 4, 0)]
+    xs = [workloads.random_array(80 + i, s[0], s[1]) for i, s in enumerate(shapes)]
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    want = sw.Transform(shapes).forward(xd)
+    t = sw.Transform(shapes, flags=sw.FLAG_PERSISTENT)
+    torch.cuda.synchronize()
+    assert nat.check_device() == 0
+    try:
+        nat.debug_batch_wait(2_000_000, 1)
+        t.forward(xd)
+        torch.cuda.synchronize()
+        assert nat.check_device() == -7
+    finally:
+        nat.debug_batch_wait(0, 0)
+    got = t.forward(xd)
+    torch.cuda.synchronize()
+    assert nat.check_device() == 0
+    for u, v in zip(want, got):
+        assert torch.equal(u, v)
+
+
+def test_persistent_tensor_core_arrays_match_per_array_launches(sw):
+    """A persistent plan made with the split-bf16 tensor-core form runs each array through the
+    per-array tensor-core launches beside the persistent kernels: bit for bit the per-array
+    plan's result, within the 1e-5 bar of the oracle."""
+    shapes = [(70, 140, 16, 64, 0), (100, 90, 32, 32, 1), (150, 60, 64, 8, 0)]
+    xs = [workloads.random_array(60 + i, s[0], s[1], complex_input=bool(s[4])) for i, s in enumerate(shapes)]
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    a = sw.Transform(shapes, algo="tc_bf16x3").forward(xd)
+    t = sw.Transform(shapes, algo="tc_bf16x3", flags=sw.FLAG_PERSISTENT | sw.FLAG_GRAPH)
+    assert t.plan.launch_count() == 2 * len(shapes)
+    b = t.forward(xd)
+    b = t.forward(xd)  # replayed from the graph
+    torch.cuda.synchronize()
+    assert sw._native.check_device() == 0
+    for u, v, x, s in zip(a, b, xs, shapes):
+        assert torch.equal(u, v)
+        _check(v, x, s[2], s[3])
+
+
+def test_persistent_autotuned_batch_of_mixed_shapes(sw):
+    """algo="auto" with a persistent plan: the autotuner times each window shape's arrays in
+    the pipelined kernel, the fused kernel, per-array tree launches and per-array split-bf16
+    launches, and keeps the fastest per shape; whatever it keeps, every array meets the 1e-5
+    bar, also replayed from a graph."""
+    xs = _inputs()
+    shapes = [(N0, N1, n0, n1, int(c)) for (N0, N1, n0, n1, c) in MIXED]
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    t = sw.Transform(shapes, algo="auto", flags=sw.FLAG_PERSISTENT | sw.FLAG_GRAPH)
+    outs = t.autotune(xd)
+    assert t.plan.launch_count() >= 1
+    for _ in range(2):
+        for o in outs:
+            o.fill_(float("nan"))
+        t.forward(xd, outs)
+    torch.cuda.synchronize()
+    assert sw._native.check_device() == 0
+    for o, x, (N0, N1, n0, n1, c) in zip(outs, xs, MIXED):
+        _check(o, x, n0, n1)
+
+
 def test_uneven_batch_256_full_size(sw):
     """256 float32 images, sides in {128..1024}, windows from six shapes, one persistent
-    launch pair: >= 256 sampled windows per image against the oracle, and per-window
-    Parseval on every window of every image."""
+    kernel per window shape: >= 256 sampled windows per image against the oracle, and
+    per-window Parseval on every window of every image."""
     wl = workloads.uneven_batch_256()
     shapes = [(x.shape[0], x.shape[1], n0, n1, 0) for x, (n0, n1) in zip(wl.images, wl.windows)]
     t = sw.Transform(shapes, flags=sw.FLAG_PERSISTENT | sw.FLAG_GRAPH)

@@ -52,8 +52,9 @@ def test_persistent_plan_fails_at_each_descriptor_table_then_recovers(sw):
     t = sw.Transform(shapes, flags=sw.FLAG_PERSISTENT)
     outs = t.empty_outputs()
     try:
-        # pinned staging, device copy, graph copy: each attempt gets one more of them
-        for after in (0, 1, 1):
+        # pinned staging, device copy, graph copy of the descriptors, then the pipelined
+        # kernels' tile table: each attempt gets one more of them
+        for after in (0, 1, 1, 1):
             nat.inject_alloc_failure(after)
             with pytest.raises(nat.SwdftError) as e:
                 t.forward(xs, outs)
