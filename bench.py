@@ -405,6 +405,9 @@ def batch_measurement(torch, sw):
         if tune_s is not None:
             res[name]["autotune_s"] = round(tune_s, 2)
             res[name]["algo_array0"] = t.plan.algo()
+            # per window shape, the (algorithm, form) its arrays run in
+            res[name]["forms"] = {f"{n0}x{n1}": "/".join(t.plan.form(i))
+                                  for i, (_, _, n0, n1, _) in enumerate(shapes)}
         del t
     del outs, xd
     torch.cuda.empty_cache()

@@ -137,6 +137,14 @@ swdft_status swdft2d_workspace_size(swdft2d_plan_t plan, size_t *bytes);
 /* The algorithm actually used (after AUTO and tuning). */
 swdft_status swdft2d_get_algo(swdft2d_plan_t plan, int32_t *algo);
 
+/* How array i runs, after AUTO and tuning: *algo its algorithm (swdft_algo), *form
+ * SWDFT_FORM_PIPELINED / SWDFT_FORM_FUSED_GROUP (a persistent plan's kernels shared by the
+ * arrays of one window shape) or SWDFT_FORM_PER_ARRAY (its own launches; every array of a
+ * plan without SWDFT_FLAG_PERSISTENT).  Either pointer may be NULL.  SWDFT_ERR_INVALID_ARG
+ * for a bad plan or index. */
+enum { SWDFT_FORM_PIPELINED = 0, SWDFT_FORM_FUSED_GROUP = 1, SWDFT_FORM_PER_ARRAY = 2 };
+swdft_status swdft2d_get_form(swdft2d_plan_t plan, int32_t i, int32_t *algo, int32_t *form);
+
 /* Forward transform, Eq. (2), of every array of the plan, enqueued on `stream`
  * (a cudaStream_t; NULL = legacy default stream).  d_in[i] / d_out[i]: device pointers of
  * array i, layouts above; input 4-byte (R32) or 8-byte (C64) aligned, output 16-byte

@@ -31,10 +31,12 @@ POS = {"start": 0, "end": 1}
 ALGOS = {"auto": 0, "tree": 1, "tc_bf16x3": 2, "tc_bf16": 3, "tc_f16_scaled": 4, "tc_f16": 5}
 ALGO_NAMES = {v: k for k, v in ALGOS.items()}
 FLAG_GRAPH, FLAG_HOST_IO, FLAG_PERSISTENT, FLAG_AUTOTUNE = 1, 2, 4, 8
+FORM_NAMES = {0: "pipelined", 1: "fused_group", 2: "per_array"}
 
 # every symbol include/*.h declare
 EXPORTS = (
     "swdft2d_plan", "swdft2d_output_shape", "swdft2d_workspace_size", "swdft2d_get_algo",
+    "swdft2d_get_form",
     "swdft2d_execute", "swdft2d_execute_adjoint", "swdft2d_execute_host", "swdft2d_autotune",
     "swdft2d_launch_count", "swdft2d_destroy", "swdft2d_status_string", "swdft2d_version",
     "swdft2d_load_tuning",
@@ -79,6 +81,7 @@ def _load() -> ctypes.CDLL:
         "swdft2d_output_shape": ([P, i32, ctypes.POINTER(i64)], i32),
         "swdft2d_workspace_size": ([P, ctypes.POINTER(ctypes.c_size_t)], i32),
         "swdft2d_get_algo": ([P, ctypes.POINTER(i32)], i32),
+        "swdft2d_get_form": ([P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
         "swdft2d_execute": ([P, PP, PP, P, P], i32),
         "swdft2d_execute_adjoint": ([P, PP, PP, P, P], i32),
         "swdft2d_execute_host": ([P, PP, PP, P], i32),
@@ -172,6 +175,13 @@ class Plan:
         v = ctypes.c_int32()
         _check(lib.swdft2d_get_algo(self.handle, ctypes.byref(v)), "swdft2d_get_algo")
         return ALGO_NAMES[int(v.value)]
+
+    def form(self, i: int):
+        """(algorithm name, form name) array i runs in: form "pipelined" / "fused_group" (a
+        persistent plan's shared kernels) or "per_array"."""
+        a, f = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib.swdft2d_get_form(self.handle, int(i), ctypes.byref(a), ctypes.byref(f)), "swdft2d_get_form")
+        return ALGO_NAMES[int(a.value)], FORM_NAMES[int(f.value)]
 
     def launch_count(self, adjoint: bool = False) -> int:
         v = ctypes.c_int32()

@@ -1064,6 +1064,17 @@ swdft_status swdft2d_get_algo(swdft2d_plan_t plan, int32_t *algo) {
     return SWDFT_OK;
 }
 
+swdft_status swdft2d_get_form(swdft2d_plan_t plan, int32_t i, int32_t *algo, int32_t *form) {
+    if (!plan || i < 0 || (size_t)i >= plan->arrays.size()) return SWDFT_ERR_INVALID_ARG;
+    const ArrayPlan &a = plan->arrays[(size_t)i];
+    static_assert(kBatchPipe == SWDFT_FORM_PIPELINED && kBatchFused == SWDFT_FORM_FUSED_GROUP &&
+                      kBatchSolo == SWDFT_FORM_PER_ARRAY,
+                  "batch modes are the public forms");
+    if (algo) *algo = a.algo;
+    if (form) *form = (plan->flags & SWDFT_FLAG_PERSISTENT) ? a.batch_mode : SWDFT_FORM_PER_ARRAY;
+    return SWDFT_OK;
+}
+
 swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t *launches) {
     if (!plan || !launches) return SWDFT_ERR_INVALID_ARG;
     // forward: row + column pass per array, or the two persistent passes for the whole batch;
@@ -1353,23 +1364,27 @@ swdft_status swdft2d_execute_host(swdft2d_plan_t plan, const void *const *h_in,
 
 namespace {
 
-// Persistent plans: per window shape (n0, n1), time its arrays in each form they may take --
-// the pipelined kernel, the fused kernel (n1 <= 32), per-array launches of the tree, and, with
-// SWDFT_ALGO_AUTO where the window allows, per-array launches of the split-bf16 tensor-core
-// form -- each alone (launch_batch restricted to that shape, best of three), and keep the
-// fastest.  Arrays made with a tensor-core algorithm stay on their own.  Synchronous.
+// Persistent plans, after the per-array tuning: per window shape (n0, n1), time its arrays in
+// each form they may take -- the pipelined kernel, the fused kernel (n1 <= 32), and their own
+// launches as just tuned (launch shapes, two-pass or fused, tree or split-bf16) -- each alone
+// (launch_batch restricted to that shape, best of three), and keep the fastest.  Arrays made
+// with a tensor-core algorithm stay on their own.  Synchronous.
 swdft_status autotune_batch(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out, void *ws,
                             cudaStream_t s) {
     const size_t n = plan->arrays.size();
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SWDFT_ERR_CUDA;
     auto cls = [](const ArrayPlan &a) { return a.m0 * (kMaxLog2 + 1) + a.m1; };
-    auto set_form = [&](int c, int mode, int algo) {
-        for (auto &a : plan->arrays)
+    std::vector<int> own_algo(n);  // the per-array tuner's choice
+    for (size_t i = 0; i < n; ++i) own_algo[i] = plan->arrays[i].algo;
+    auto set_form = [&](int c, int mode) {
+        for (size_t i = 0; i < n; ++i) {
+            ArrayPlan &a = plan->arrays[i];
             if (cls(a) == c && (a.algo_auto || a.algo == SWDFT_ALGO_TREE_F32)) {
                 a.batch_mode = mode;
-                a.algo = algo;
+                a.algo = mode == kBatchSolo ? own_algo[i] : SWDFT_ALGO_TREE_F32;
             }
+        }
     };
     // time shape c in its current forms
     auto time_class = [&](int c, float *ms_out) -> swdft_status {
@@ -1398,16 +1413,12 @@ swdft_status autotune_batch(swdft2d_plan_t plan, const void *const *d_in, void *
         const int c = cls(a0);
         if (done[(size_t)c] || !(a0.algo_auto || a0.algo == SWDFT_ALGO_TREE_F32)) continue;
         done[(size_t)c] = 1;
-        struct Form {
-            int mode, algo;
-        };
-        std::vector<Form> forms = {{kBatchPipe, SWDFT_ALGO_TREE_F32}, {kBatchSolo, SWDFT_ALGO_TREE_F32}};
-        if (a0.m1 < kBatchFusedM1) forms.push_back({kBatchFused, SWDFT_ALGO_TREE_F32});
-        if (a0.algo_auto && a0.tc_eligible()) forms.push_back({kBatchSolo, SWDFT_ALGO_TC_BF16X3});
-        Form best{kBatchPipe, SWDFT_ALGO_TREE_F32};
+        std::vector<int> forms = {kBatchPipe, kBatchSolo};
+        if (a0.m1 < kBatchFusedM1) forms.push_back(kBatchFused);
+        int best = kBatchPipe;
         float best_ms = 1e30f;
-        for (const Form &f : forms) {
-            set_form(c, f.mode, f.algo);
+        for (int f : forms) {
+            set_form(c, f);
             float ms = 0.f;
             if ((st = time_class(c, &ms)) != SWDFT_OK) break;
             if (ms < best_ms) {
@@ -1415,7 +1426,7 @@ swdft_status autotune_batch(swdft2d_plan_t plan, const void *const *d_in, void *
                 best = f;
             }
         }
-        set_form(c, best.mode, best.algo);
+        set_form(c, best);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1433,7 +1444,7 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
     if (st != SWDFT_OK) return st;
     if ((st = configure(plan)) != SWDFT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (plan->flags & SWDFT_FLAG_PERSISTENT) return autotune_batch(plan, d_in, d_out, d_workspace, s);
+    const bool persistent = (plan->flags & SWDFT_FLAG_PERSISTENT) != 0;
     // arrays with a record in the tuning cache for this GPU take it without timing
     const char *cache = std::getenv("SWDFT_TUNE_CACHE");
     char gpu[256] = "unknown";
@@ -1481,13 +1492,15 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
             c.row_B = rb;
             cands.push_back(c);
         }
-        // time one pass (stage 1 = row levels, 2 = column levels) of config c, best of 3
+        // time one pass (stage 1 = row levels, 2 = column levels) of config c, best of 3, in
+        // the array's own workspace region (a persistent plan's) or the plan's first slot
+        void *slot = persistent ? static_cast<char *>(d_workspace) + plan->z_off[i] : d_workspace;
         auto time_pass = [&](const TreeConfig &c, int stage, float *ms_out) -> bool {
             a.cfg = c;
             float ms_min = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 cudaEventRecord(e0, s);
-                if (enqueue_forward(plan, a, d_in[i], d_out[i], d_workspace, a.q_begin, a.q_end, s,
+                if (enqueue_forward(plan, a, d_in[i], d_out[i], slot, a.q_begin, a.q_end, s,
                                     stage) != cudaSuccess)
                     return false;
                 cudaEventRecord(e1, s);
@@ -1571,7 +1584,9 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
     cudaEventDestroy(e1);
     destroy_graph(plan->graph);
     plan->pipe_uploaded = false;  // a persistent plan's tiles follow the tuned chunks
-    return SWDFT_OK;
+    // a persistent plan then picks, per window shape, the kernels its arrays share or their
+    // own (just tuned) launches
+    return persistent ? autotune_batch(plan, d_in, d_out, d_workspace, s) : SWDFT_OK;
 }
 
 swdft_status swdft2d_inject_alloc_failure(int64_t after) {

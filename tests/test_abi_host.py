@@ -287,6 +287,24 @@ def test_persistent_batch_launches_one_kernel_per_window_class(nat):
     assert nat.Plan(shapes).launch_count() >= len(shapes)
 
 
+def test_forms_of_a_persistent_plan(nat):
+    """swdft2d_get_form: in a persistent plan, two-pass windows run pipelined, small windows
+    (n0 n1 <= 64, n1 < 64) in fused groups, tensor-core arrays on their own; without the flag
+    every array runs on its own."""
+    shapes = [shp(100, 90, 32, 32), shp(20, 20, 4, 4), shp(70, 130, 1, 64), shp(64, 64, 16, 4)]
+    p = nat.Plan(shapes, flags=nat.FLAG_PERSISTENT)
+    assert [p.form(i) for i in range(4)] == [("tree", "pipelined"), ("tree", "fused_group"),
+                                            ("tree", "pipelined"), ("tree", "fused_group")]
+    q = nat.Plan(shapes)
+    assert [q.form(i)[1] for i in range(4)] == ["per_array"] * 4
+    tc = nat.Plan([shp(100, 90, 32, 32), shp(70, 130, 16, 64)], algo="tc_bf16x3",
+                  flags=nat.FLAG_PERSISTENT)
+    assert [tc.form(i) for i in range(2)] == [("tc_bf16x3", "per_array")] * 2
+    assert tc.launch_count() == 4
+    with pytest.raises(nat.SwdftError):
+        p.form(4)
+
+
 def test_persistent_workspace_holds_z_regions_and_the_pipeline_counters(nat):
     """A persistent plan's workspace: every array's own region (its z, or its adjoint's gz and
     side rows), then one block of counters for the pipelined kernels -- 64 words, then a flag
