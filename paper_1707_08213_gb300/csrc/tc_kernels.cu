@@ -299,10 +299,15 @@ __global__ void __launch_bounds__(TCC_THREADS) tc_col_kernel(const __grid_consta
 //
 // z[r][q1][k1] = sum_j1 x[r][q1 + j1] F1[j1][k1], one product per input row and 128 window
 // positions: D (128 x 2n1) = A (128 x K) * B (K x 2n1), A[m][k] = x[r][q1_0 + m + k] (Re x,
-// then Im x for complex input; K padded with zeros to a multiple of 16), B = realified F1.
-// A is a Hankel matrix -- consecutive positions shift by one element, which no descriptor
-// can express -- so each row's A is written to shared memory (K-major) from the staged input
-// rows.  The epilogue writes z directly as the column pass's operand planes.
+// then Im x for complex input; K padded to a multiple of 16 with rows of B that are zero),
+// B = realified F1.  A is a Hankel matrix: consecutive positions shift by one element.  As an
+// MN-major operand (a core matrix = 8 consecutive positions x 8 consecutive k, one 16-byte
+// row per k) its core matrix (m / 8, k / 8) holds x[8 (m/8 + k/8) + (k mod 8) + 0..7] in row
+// k mod 8: so the staged row is written eight times, shifted by s = 0..7 elements, unit u
+// (16 bytes: x[8u + s .. 8u + s + 7]) of copy s at byte (8u + s) 16, and every core matrix
+// is one 128-byte unit row further along M and along K (both descriptor strides 128 B).
+// Complex input interleaves the Re and Im unit rows (unit row 2u + part).  The epilogue writes
+// z directly as the column pass's operand planes.
 
 constexpr int TCR_ROWS = 8;  // input rows per CTA
 constexpr int TCR_TQ = 2;    // threads per position (TMEM lane): A chunks and epilogue slices
@@ -323,12 +328,20 @@ __host__ __device__ constexpr int tcr_K(int M1, bool cplx) {
     return ((cplx ? 2 : 1) << M1) < 16 ? 16 : ((cplx ? 2 : 1) << M1);
 }
 
+// A's shifted copies: unit rows per part (positions 0..127 plus K per part, in 8-element units)
+// and bytes per operand set
+__host__ __device__ constexpr int tcr_units(int M1, bool cplx) {
+    return TC_CH / 8 + ((cplx ? (1 << M1) : tcr_K(M1, false)) + 7) / 8;
+}
+__host__ __device__ constexpr int tcr_copy_bytes(int M1, bool cplx) { return (cplx ? 2 : 1) * tcr_units(M1, cplx) * 128; }
+
 size_t tc_row_smem_bytes(int m1, bool cplx, int terms) {
     const int n1 = 1 << m1, K = tcr_K(m1, cplx), N = 2 * n1, nb = terms == 3 ? 2 : 1;
     const int W = TC_CH + n1;  // staged columns per row (n1 - 1 look-ahead, rounded)
-    // staged rows, B (nb sets), A (two buffers of nb sets), barriers and TMEM slot, alignment
-    return (size_t)TCR_ROWS * W * (cplx ? 2 : 1) * 4 + (size_t)nb * N * K * 2 + (size_t)2 * nb * TC_CH * K * 2 +
-           64 + 1024 + 8192;
+    // staged rows, B (nb sets), A's copies (two buffers of nb sets), barriers and TMEM slot,
+    // alignment
+    return (size_t)TCR_ROWS * W * (cplx ? 2 : 1) * 4 + (size_t)nb * N * K * 2 +
+           (size_t)2 * nb * tcr_copy_bytes(m1, cplx) + 64 + 1024 + 8192;
 }
 
 // Pipelined over the CTA's rows: while the tensor core multiplies row r (A buffer and TMEM
@@ -345,15 +358,22 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
     constexpr int NB = TERMS == 3 ? 2 : 1;
     constexpr int W = TC_CH + n1;
     constexpr uint32_t TMEM_COLS = 2 * N < 32 ? 32 : 2 * N;  // two accumulators
-    constexpr uint32_t B_BYTES = N * K * 2, A_BYTES = TC_CH * K * 2;
-    constexpr uint32_t IDESC = umma_idesc_f16(TC_CH, N, !F16, /*a_mn=*/false, /*b_mn=*/false);
+    constexpr uint32_t B_BYTES = N * K * 2;
+    constexpr int U = tcr_units(M1, CPLX);                    // unit rows per part
+    constexpr uint32_t A_BYTES = tcr_copy_bytes(M1, CPLX);    // one set of A's copies
+    constexpr uint32_t IDESC = umma_idesc_f16(TC_CH, N, !F16, /*a_mn=*/true, /*b_mn=*/false);
+    // A's descriptor strides: along K and along M one unit row (real), two (complex: Re and Im
+    // interleaved), except a complex n1 = 8, whose one 16-wide k-step covers Re (k < 8) then
+    // Im (k >= 8): its K step goes from the Re unit row to the Im one
+    constexpr uint32_t A_SBO = CPLX ? 256u : 128u;
+    constexpr uint32_t A_LBO = (CPLX && n1 == 8) ? 128u : A_SBO;
     constexpr int SW = N / TCR_TQ < 16 ? 16 : N / TCR_TQ;  // D columns per epilogue slice
     constexpr int NSL = N / SW;                             // slices: 1 (n1 = 8) or TCR_TQ
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char *sB = smem;                                   // NB x B_BYTES
-    unsigned char *sA = sB + NB * B_BYTES;                      // 2 buffers x NB x A_BYTES
+    unsigned char *sA = sB + NB * B_BYTES;                      // 2 buffers x NB x A_BYTES (copies)
     float *sx = reinterpret_cast<float *>(sA + 2 * NB * A_BYTES);  // TCR_ROWS x W (x2 complex)
     uint64_t *bar = reinterpret_cast<uint64_t *>(sx + TCR_ROWS * W * (CPLX ? 2 : 1));  // 2 barriers
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2);
@@ -416,8 +436,8 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
-    const uint32_t lbo = 128u, sbo = (uint32_t)(K / 8) * 128u;  // K-major, both operands
-    const uint64_t a_desc0 = smem_desc(sA0, lbo, sbo), b_desc0 = smem_desc(sB0, lbo, sbo);
+    const uint32_t lbo = 128u, sbo = (uint32_t)(K / 8) * 128u;  // B: K-major
+    const uint64_t a_desc0 = smem_desc(sA0, A_LBO, A_SBO), b_desc0 = smem_desc(sB0, lbo, sbo);
 
     const int pos = q1_0 + m;
     const int64_t nch = (int64_t)p.P1 * n1;
@@ -425,25 +445,24 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
     int issued = 0;  // rows whose UMMAs were committed
     for (int rr = 0; rr <= nrows; ++rr) {
         if (rr < nrows && worker) {
-            // A row m of buffer rr & 1: x[pos + k] (Re, then Im), this thread's half of the
-            // 16-byte chunks.  The buffer's last reader, row rr - 2's UMMAs, completed: every
-            // thread waited for them in row rr - 2's epilogue.
+            // A of buffer rr & 1: the shifted copies of input row rr (Re, then Im), unit (u, s)
+            // per thread, consecutive threads on consecutive 16-byte slots.  Staged columns
+            // past the row (only ever multiplied by B's zero rows, or feeding positions past
+            // P1 that are not stored) read as zero.  The buffer's last reader, row rr - 2's
+            // UMMAs, completed: every thread waited for them in row rr - 2's epilogue.
             unsigned char *a_buf = sA + (rr & 1) * NB * A_BYTES;
-#pragma unroll
-            for (int g = h; g < K / 8; g += TCR_TQ) {
+            for (int e = tid; e < (CPLX ? 2 : 1) * U * 8; e += TCR_TQ * TC_CH) {
+                const int part = CPLX ? e / (U * 8) : 0;
+                const int us = e - part * (U * 8);
+                const int u = us >> 3, sh = us & 7;
                 float v[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int k = 8 * g + e;
-                    v[e] = 0.f;
-                    if (CPLX) {
-                        if (k < n1) v[e] = sx[(rr * W + m + k) * 2];
-                        else if (k < 2 * n1) v[e] = sx[(rr * W + m + k - n1) * 2 + 1];
-                    } else if (k < n1) {
-                        v[e] = sx[rr * W + m + k];
-                    }
+                for (int j = 0; j < 8; ++j) {
+                    const int c = 8 * u + sh + j;
+                    v[j] = 0.f;
+                    if (c < W) v[j] = CPLX ? sx[(rr * W + c) * 2 + part] : sx[rr * W + c];
                 }
-                const uint32_t off = (uint32_t)((m >> 3) * (K / 8) + g) * 128u + (uint32_t)(m & 7) * 16u;
+                const uint32_t off = (uint32_t)((CPLX ? 2 * u + part : u) * 128 + sh * 16);
                 uint4 h4, l4;
                 split_pair<F16>(v[0], v[1], h4.x, l4.x);
                 split_pair<F16>(v[2], v[3], h4.y, l4.y);
@@ -470,9 +489,13 @@ __global__ void __launch_bounds__(TCR_THREADS) tc_row_kernel(const __grid_consta
                 for (int t = 0; t < TERMS; ++t) {
                     const int a_set = (t == 2) ? 1 : 0, b_set = (t == 1) ? 1 : 0;
 #pragma unroll
-                    for (int ks = 0; ks < KS; ++ks)
-                        umma_f16(d_tmem, a_base + (uint64_t)((a_set * A_BYTES + ks * 256) >> 4),
+                    for (int ks = 0; ks < KS; ++ks) {
+                        // k-step ks = k in [16 ks, 16 ks + 16): its first core matrix's unit row
+                        const int k0 = 16 * ks;
+                        const int a_row = CPLX ? (n1 == 8 ? 0 : 2 * ((k0 % n1) / 8) + k0 / n1) : k0 / 8;
+                        umma_f16(d_tmem, a_base + (uint64_t)((a_set * A_BYTES + a_row * 128) >> 4),
                                  b_desc0 + (uint64_t)((b_set * B_BYTES + ks * 256) >> 4), IDESC, (t | ks) != 0);
+                    }
                 }
                 umma_commit(&bar[rr & 1]);
             }
