@@ -121,9 +121,10 @@ typedef struct {
  * validates every shape (SWDFT_ERR_NOT_POW2 / WINDOW_TOO_LARGE / INVALID_ARG), builds the
  * twiddle vectors Omega^0, Omega^1 of Section 4.2 in FP64 and rounds them to FP32, and
  * picks kernels.  SWDFT_ERR_UNSUPPORTED for an algorithm or window size the library lacks
- * (tree: n_i <= 64; tensor-core forms: powers of two with 16 <= n0 <= 64 and 8 <= n1 <= 64,
- * no persistent batch; ternary and mixed-radix windows: tree only, no persistent batch, no
- * adjoint).  *plan is NULL on any error. */
+ * (tree: n_i <= 64; tensor-core forms: powers of two with 16 <= n0 <= 64 and 8 <= n1 <= 64;
+ * ternary and mixed-radix windows: tree only, no adjoint).  With SWDFT_FLAG_PERSISTENT,
+ * tensor-core and ternary or mixed-radix arrays run on their own launches beside the
+ * persistent kernels (swdft2d_get_form).  *plan is NULL on any error. */
 swdft_status swdft2d_plan(swdft2d_plan_t *plan, int32_t batch, const swdft2d_shape *shapes,
                           int32_t norm, int32_t pos, int32_t algo, uint32_t flags);
 

@@ -984,7 +984,6 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
         a.algo = (algo == SWDFT_ALGO_AUTO) ? SWDFT_ALGO_TREE_F32 : algo;
         a.algo_auto = algo == SWDFT_ALGO_AUTO;
         if (a.algo >= SWDFT_ALGO_TC_BF16X3 && !a.tc_eligible()) return SWDFT_ERR_UNSUPPORTED;
-        if (a.ternary() && (flags & SWDFT_FLAG_PERSISTENT)) return SWDFT_ERR_UNSUPPORTED;
     }
 
     swdft2d_plan_s *p = alloc_fails() ? nullptr : new (std::nothrow) swdft2d_plan_s();
@@ -1005,12 +1004,13 @@ swdft_status swdft2d_plan(swdft2d_plan_t *out, int32_t batch, const swdft2d_shap
             ws += align_up(a.ws_bytes_plan(a.band_rows()));
         }
         p->conc = 4;
-        // tensor-core forms run per array beside the persistent kernels; small windows (n0 n1
-        // <= 64, where z is 1/n0 >= 1/8 of the output) in fused groups; every other array in
-        // the pipelined kernel of its (n0, n1).  The autotuner may move arrays between the
-        // three, per window shape.  Every array has row-tile flags, whatever its mode.
+        // tensor-core forms and ternary or mixed-radix windows run per array beside the
+        // persistent kernels; small windows (n0 n1 <= 64, where z is 1/n0 >= 1/8 of the
+        // output) in fused groups; every other array in the pipelined kernel of its (n0, n1).
+        // The autotuner may move radix-2 tree arrays between the three, per window shape.
+        // Every array has row-tile flags, whatever its mode.
         for (auto &a : p->arrays) {
-            a.batch_mode = a.algo >= SWDFT_ALGO_TC_BF16X3 ? kBatchSolo
+            a.batch_mode = (a.algo >= SWDFT_ALGO_TC_BF16X3 || a.ternary()) ? kBatchSolo
                            : (a.m1 < kBatchFusedM1 && a.n0 * a.n1 <= 64) ? kBatchFused
                                                                           : kBatchPipe;
             const PipeGeom g = pipe_geom(a);
@@ -1380,7 +1380,7 @@ swdft_status autotune_batch(swdft2d_plan_t plan, const void *const *d_in, void *
     auto set_form = [&](int c, int mode) {
         for (size_t i = 0; i < n; ++i) {
             ArrayPlan &a = plan->arrays[i];
-            if (cls(a) == c && (a.algo_auto || a.algo == SWDFT_ALGO_TREE_F32)) {
+            if (cls(a) == c && !a.ternary() && (a.algo_auto || a.algo == SWDFT_ALGO_TREE_F32)) {
                 a.batch_mode = mode;
                 a.algo = mode == kBatchSolo ? own_algo[i] : SWDFT_ALGO_TREE_F32;
             }
@@ -1411,7 +1411,7 @@ swdft_status autotune_batch(swdft2d_plan_t plan, const void *const *d_in, void *
     for (size_t i = 0; i < n && st == SWDFT_OK; ++i) {
         const ArrayPlan &a0 = plan->arrays[i];
         const int c = cls(a0);
-        if (done[(size_t)c] || !(a0.algo_auto || a0.algo == SWDFT_ALGO_TREE_F32)) continue;
+        if (a0.ternary() || done[(size_t)c] || !(a0.algo_auto || a0.algo == SWDFT_ALGO_TREE_F32)) continue;
         done[(size_t)c] = 1;
         std::vector<int> forms = {kBatchPipe, kBatchSolo};
         if (a0.m1 < kBatchFusedM1) forms.push_back(kBatchFused);

@@ -83,8 +83,11 @@ def test_ternary_and_mixed_radix_windows_are_accepted_by_the_tree_only(nat):
         assert st == 0, (n0, n1)
         nat.lib.swdft2d_destroy(h)
     assert nat.raw_plan([shp(40, 40, 27, 27)], 0, 0, 2, 0)[0] == -4   # tensor-core forms
-    assert nat.raw_plan([shp(40, 40, 9, 9)], 0, 0, 1, 4)[0] == -4      # persistent batch
-    assert nat.raw_plan([shp(40, 40, 12, 6)], 0, 0, 1, 4)[0] == -4     # (mixed radix too)
+    # a persistent batch runs ternary and mixed-radix arrays on their own launches
+    for n0, n1 in ((9, 9), (12, 6)):
+        st, h = nat.raw_plan([shp(40, 40, n0, n1), shp(40, 40, 8, 8)], 0, 0, 1, 4)
+        assert st == 0
+        nat.lib.swdft2d_destroy(h)
     p = nat.Plan([dict(N0=60, N1=70, n0=24, n1=12)])
     assert p.output_shape(0) == (37, 59, 24, 12)
     assert p.workspace_size() >= (16 + 37 + 23) * 59 * 12 * 8  # 2*n0/3 look-back rows
@@ -303,6 +306,9 @@ def test_forms_of_a_persistent_plan(nat):
     assert tc.launch_count() == 4
     with pytest.raises(nat.SwdftError):
         p.form(4)
+    mixed = nat.Plan([shp(100, 90, 27, 27), shp(100, 90, 12, 16), shp(100, 90, 32, 32)], flags=nat.FLAG_PERSISTENT)
+    assert [mixed.form(i)[1] for i in range(3)] == ["per_array", "per_array", "pipelined"]
+    assert mixed.launch_count() == 2 + 2 + 1
 
 
 def test_persistent_workspace_holds_z_regions_and_the_pipeline_counters(nat):

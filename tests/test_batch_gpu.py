@@ -135,6 +135,33 @@ def test_persistent_tensor_core_arrays_match_per_array_launches(sw):
         _check(v, x, s[2], s[3])
 
 
+def test_persistent_plan_with_ternary_and_mixed_radix_arrays(sw):
+    """Ternary and mixed-radix windows in a persistent plan run on their own launches beside
+    the pipelined and fused kernels: bit for bit the per-array plan's result, also after the
+    autotuner (which leaves them on their own)."""
+    shapes = [(90, 80, 27, 9, 0), (70, 100, 12, 16, 1), (130, 64, 64, 16, 0), (40, 40, 4, 4, 0),
+              (60, 75, 6, 48, 0)]
+    xs = [workloads.random_array(40 + i, s[0], s[1], complex_input=bool(s[4])) for i, s in enumerate(shapes)]
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    want = sw.Transform(shapes).forward(xd)
+    t = sw.Transform(shapes, flags=sw.FLAG_PERSISTENT | sw.FLAG_GRAPH)
+    assert [t.plan.form(i)[1] for i in range(len(shapes))] == ["per_array", "per_array", "pipelined",
+                                                              "fused_group", "per_array"]
+    got = t.forward(xd)
+    got = t.forward(xd)
+    tuned = sw.Transform(shapes, algo="auto", flags=sw.FLAG_PERSISTENT)
+    out_t = tuned.autotune(xd)
+    tuned.forward(xd, out_t)
+    torch.cuda.synchronize()
+    assert sw._native.check_device() == 0
+    for i, (u, v, w) in enumerate(zip(want, got, out_t)):
+        assert torch.equal(u, v)
+        if i in (0, 1, 4):
+            assert tuned.plan.form(i)[1] == "per_array"
+            assert torch.equal(u, w)
+        _check(v, xs[i], shapes[i][2], shapes[i][3])
+
+
 def test_persistent_autotuned_batch_of_mixed_shapes(sw):
     """algo="auto" with a persistent plan: the autotuner times each window shape's arrays in
     the pipelined kernel, the fused kernel, per-array tree launches and per-array split-bf16
