@@ -772,6 +772,22 @@ def radix3_measurement(torch, sw):
         ms /= steps
         res[f"{a0}x{a1}"] = {"ms_per_step": round(ms, 4), "value": coeffs / (ms / 1e3),
                              "output_gbs": round(8 * coeffs / (ms / 1e3) / 1e9, 1)}
+        if (a0, a1) in ((27, 27), (12, 12)):
+            # the adjoint (per-window inverse DFTs overlap-added per axis) of the same output
+            g = t.adjoint(out)
+            for _ in range(2):
+                t.adjoint(out, g)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(10):
+                t.adjoint(out, g)
+            e1.record()
+            torch.cuda.synchronize()
+            ams = e0.elapsed_time(e1) / 10
+            res[f"{a0}x{a1}"]["adjoint_ms"] = round(ams, 4)
+            res[f"{a0}x{a1}"]["adjoint_gbs_of_G"] = round(8 * coeffs / (ams / 1e3) / 1e9, 1)
+            del g
         del t, out
     del flush
     torch.cuda.empty_cache()
@@ -896,6 +912,8 @@ def side_summary(line):
     out["adjoint_ms"] = [g("adjoint", "forward", "ms_per_step"), g("adjoint", "adjoint", "ms_per_step")]
     out["volume_ms"] = g("volume", "ms_per_step")
     out["radix3_ms"] = {k: v.get("ms_per_step") for k, v in (line.get("radix3") or {}).items() if isinstance(v, dict)}
+    out["radix3_adjoint_ms"] = {k: v.get("adjoint_ms") for k, v in (line.get("radix3") or {}).items()
+                                if isinstance(v, dict) and "adjoint_ms" in v}
     out["stream_graph_us"] = [g("stream", f"rows_per_push_{r}", "graph_us_per_push") for r in (1, 32, 256)]
     out["static_scratch_ms"] = g("static_scratch", "ms_per_step")
     out["small_graph_us"] = g("small", "graph_us")

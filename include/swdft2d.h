@@ -122,7 +122,7 @@ typedef struct {
  * twiddle vectors Omega^0, Omega^1 of Section 4.2 in FP64 and rounds them to FP32, and
  * picks kernels.  SWDFT_ERR_UNSUPPORTED for an algorithm or window size the library lacks
  * (tree: n_i <= 64; tensor-core forms: powers of two with 16 <= n0 <= 64 and 8 <= n1 <= 64;
- * ternary and mixed-radix windows: tree only, no adjoint).  With SWDFT_FLAG_PERSISTENT,
+ * ternary and mixed-radix windows: tree only).  With SWDFT_FLAG_PERSISTENT,
  * tensor-core and ternary or mixed-radix arrays run on their own launches beside the
  * persistent kernels (swdft2d_get_form).  *plan is NULL on any error. */
 swdft_status swdft2d_plan(swdft2d_plan_t *plan, int32_t batch, const swdft2d_shape *shapes,
@@ -153,9 +153,12 @@ swdft_status swdft2d_get_form(swdft2d_plan_t plan, int32_t i, int32_t *algo, int
 swdft_status swdft2d_execute(swdft2d_plan_t plan, const void *const *d_in, void *const *d_out,
                              void *d_workspace, void *stream);
 
-/* Adjoint A^H of the forward map (the transpose of the tree, conjugated twiddles):
+/* Adjoint A^H of the forward map:
  *   g[r,c] = sum over windows q containing (r,c) of c * sum_k G[q,k] w_{n0}^{+(r-q0)k0} w_{n1}^{+(c-q1)k1}
- * i.e. the overlap-add of every window's inverse DFT of the upstream gradient G.
+ * i.e. the overlap-add of every window's inverse DFT of the upstream gradient G: for
+ * power-of-two windows the transposed tree (conjugated twiddles), for ternary and
+ * mixed-radix windows dense inverse DFTs of length n per window and axis, overlap-added
+ * (a power-of-two row window still takes the transposed tree).
  * d_grad_out[i]: complex64 G with the forward output layout (band rows only);
  * d_grad_in[i]: N0 x N1 (row stride N1) float32 = Re(A^H G) for R32 inputs, complex64
  * for C64.  Every element of d_grad_in is written (rows outside the band's reach get 0). */

@@ -1,0 +1,257 @@
+// Adjoint for ternary and mixed-radix windows (n = 3^b 2^a along an axis, b >= 1): the
+// overlap-add of every window's inverse DFT (the transpose of Eq. 2's map), evaluated per axis
+// in gather form with dense inverse DFTs of length n:
+//
+//   column pass  gz[r][q1][k1] = c sum_{q0 = r-n0+1..r} sum_k0 G[q0][q1][k0][k1] w_{n0}^{+(r-q0) k0}
+//   row pass     gx[r][p1]     =   sum_{q1 = p1-n1+1..p1} sum_k1 gz[r][q1][k1] w_{n1}^{+(p1-q1) k1}
+//
+// (only windows that exist contribute; gx keeps the real part for real input).  A thread walks
+// its channel (column pass) or its row (row pass) window by window: it computes the window's
+// n inverse-DFT values from the n spectral values it loads (twiddles w_n^{+jk}, indices fixed
+// at compile time, read from the kernel parameters) and adds value j into a ring of n partial
+// outputs in shared memory, one slot per output row (column) still open; after window q the
+// output at q has all its windows and leaves the ring.  Chunks of windows run in parallel:
+// the n - 1 outputs a chunk shares with each neighbour are added atomically into a zeroed
+// buffer, the others stored.  An axis whose window is a power of two uses the transposed
+// radix-2 tree instead (adj_row_kernel).
+#include <algorithm>
+
+#include "tree3_core.cuh"
+
+namespace swdft {
+
+struct Adj3ColParams {
+    const float2 *G;  // [rows_out][P1][n0][n1]
+    float2 *gz;       // [rows_out + n0 - 1][P1][n1], zeroed before the launch
+    int64_t nch;      // P1 * n1
+    int n1;
+    int rows_out;
+    int chunk;        // windows per thread
+    float scale;
+    OmegaN om;        // w_{n0}^{-j}
+};
+
+struct Adj3RowParams {
+    const float2 *gz;  // [zrows][P1][n1]
+    void *gx;          // [zrows][ld_out] float or float2, zeroed before the launch
+    int64_t ld_out;
+    int zrows, N1, P1;
+    int chunk;         // windows (columns q1) per thread
+    int row_blocks;    // blocks along the rows (grid x)
+    OmegaN om;         // w_{n1}^{-j}
+};
+
+constexpr int kAdj3Threads = 128;
+
+__device__ __forceinline__ float2 conj_mul(float2 w, float2 v) {  // conj(w) v
+    return make_float2(w.x * v.x + w.y * v.y, w.x * v.y - w.y * v.x);
+}
+
+__device__ __forceinline__ void atomic_add2(float2 *d, float2 v) {
+    atomicAdd(&d->x, v.x);
+    atomicAdd(&d->y, v.y);
+}
+
+// The window's inverse DFT value j of v[0..N-1] (unnormalised), added into ring slot s + j.
+template <int N>
+__device__ __forceinline__ void idft_into_ring(const float2 (&v)[N], const OmegaN &om, float2 *ring, int slot) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        float2 h = v[0];
+#pragma unroll
+        for (int k = 1; k < N; ++k) {
+            const float2 t = conj_mul(om.w[(j * k) % N], v[k]);
+            h.x += t.x;
+            h.y += t.y;
+        }
+        int sj = slot + j;
+        if (sj >= N) sj -= N;
+        float2 *a = ring + sj * kAdj3Threads;
+        a->x += h.x;
+        a->y += h.y;
+    }
+}
+
+template <int N0>
+__global__ void __launch_bounds__(kAdj3Threads) adj3_col_kernel(const __grid_constant__ Adj3ColParams p) {
+    extern __shared__ float2 adj3_ring[];  // [N0][kAdj3Threads]
+    const int t = threadIdx.x;
+    float2 *ring = adj3_ring + t;
+    const int64_t ch = (int64_t)blockIdx.x * kAdj3Threads + t;
+    const bool active = ch < p.nch;
+    const int qa = blockIdx.y * p.chunk;
+    if (qa >= p.rows_out) return;  // uniform per block
+    const int qb = min(qa + p.chunk, p.rows_out);
+    const int64_t q1 = active ? ch / p.n1 : 0, k1 = active ? ch - q1 * p.n1 : 0;
+    const float2 *g = p.G + q1 * (int64_t)N0 * p.n1 + k1;
+    const int64_t grow = p.nch * N0;  // elements of G per window row
+    float2 *dst = p.gz + ch;
+#pragma unroll
+    for (int j = 0; j < N0; ++j) ring[j * kAdj3Threads] = make_float2(0.f, 0.f);
+    int slot = 0;  // ring slot of output row q0: (q0 - qa) mod N0
+    for (int q0 = qa; q0 < qb; ++q0) {
+        float2 v[N0];
+#pragma unroll
+        for (int k0 = 0; k0 < N0; ++k0)
+            v[k0] = active ? __ldg(g + (int64_t)q0 * grow + (int64_t)k0 * p.n1) : make_float2(0.f, 0.f);
+        idft_into_ring<N0>(v, p.om, ring, slot);
+        // row q0 has all its windows (q0 - N0 + 1 .. q0) from this chunk
+        float2 *a = ring + slot * kAdj3Threads;
+        const float2 o = make_float2(a->x * p.scale, a->y * p.scale);
+        *a = make_float2(0.f, 0.f);
+        if (active) {
+            if (q0 >= qa + N0 - 1)
+                dst[(int64_t)q0 * p.nch] = o;  // no other chunk reaches this row
+            else
+                atomic_add2(dst + (int64_t)q0 * p.nch, o);
+        }
+        if (++slot == N0) slot = 0;
+    }
+    // rows qb .. qb + N0 - 2 also take windows of the next chunk
+    for (int i = 0; i + 1 < N0; ++i) {
+        float2 *a = ring + slot * kAdj3Threads;
+        if (active) atomic_add2(dst + (int64_t)(qb + i) * p.nch, make_float2(a->x * p.scale, a->y * p.scale));
+        if (++slot == N0) slot = 0;
+    }
+}
+
+template <int N1, bool CPLX>
+__global__ void __launch_bounds__(kAdj3Threads) adj3_row_kernel(const __grid_constant__ Adj3RowParams p) {
+    extern __shared__ float2 adj3_ring[];  // [N1][kAdj3Threads]
+    const int t = threadIdx.x;
+    float2 *ring = adj3_ring + t;
+    const int r = blockIdx.x * kAdj3Threads + t;  // z row
+    const bool active = r < p.zrows;
+    const int qa = blockIdx.y * p.chunk;
+    if (qa >= p.P1) return;  // uniform per block
+    const int qb = min(qa + p.chunk, p.P1);
+    const float2 *g = p.gz + (int64_t)(active ? r : 0) * p.P1 * N1;
+#pragma unroll
+    for (int j = 0; j < N1; ++j) ring[j * kAdj3Threads] = make_float2(0.f, 0.f);
+    auto put = [&](int c, float2 o, bool alone) {
+        if (!active) return;
+        if (CPLX) {
+            float2 *d = static_cast<float2 *>(p.gx) + (int64_t)r * p.ld_out + c;
+            if (alone)
+                *d = o;
+            else
+                atomic_add2(d, o);
+        } else {
+            float *d = static_cast<float *>(p.gx) + (int64_t)r * p.ld_out + c;
+            if (alone)
+                *d = o.x;
+            else
+                atomicAdd(d, o.x);
+        }
+    };
+    int slot = 0;  // ring slot of output column c: (c - qa) mod N1
+    for (int q1 = qa; q1 < qb; ++q1) {
+        float2 v[N1];
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) v[k1] = active ? __ldg(g + (int64_t)q1 * N1 + k1) : make_float2(0.f, 0.f);
+        idft_into_ring<N1>(v, p.om, ring, slot);
+        float2 *a = ring + slot * kAdj3Threads;
+        put(q1, *a, q1 >= qa + N1 - 1);
+        *a = make_float2(0.f, 0.f);
+        if (++slot == N1) slot = 0;
+    }
+    for (int i = 0; i + 1 < N1; ++i) {
+        put(qb + i, ring[slot * kAdj3Threads], false);
+        if (++slot == N1) slot = 0;
+    }
+}
+
+// window lengths of the dense passes: 1 and every 3^b 2^a <= 64 with b >= 1
+#define SWDFT_ADJ3_CASES(F) F(1) F(3) F(6) F(9) F(12) F(18) F(24) F(27) F(36) F(48) F(54)
+
+static void fill_omega_adj(OmegaN &om, int n) {
+    make_omega(n, om.w);
+    for (int j = n; j < kMaxN; ++j) om.w[j] = make_float2(0.f, 0.f);
+    om.h = 0.f;
+}
+
+cudaError_t launch_adj3_col(const Adj3ColArgs &a, cudaStream_t s) {
+    if (a.rows_out <= 0 || a.P1 <= 0) return cudaSuccess;
+    if (!a.G || !a.gz || a.n0 < 1 || a.n0 > kMaxN || a.n1 < 1 || a.rows_out > INT32_MAX) return cudaErrorInvalidValue;
+    const int64_t nch = a.P1 * a.n1;
+    const int64_t zrows = a.rows_out + a.n0 - 1;
+    cudaError_t e = cudaMemsetAsync(a.gz, 0, sizeof(float2) * (size_t)(zrows * nch), s);
+    if (e != cudaSuccess) return e;
+    Adj3ColParams p;
+    p.G = a.G;
+    p.gz = a.gz;
+    p.nch = nch;
+    p.n1 = a.n1;
+    p.rows_out = (int)a.rows_out;
+    // about four resident waves of blocks, chunks of at least 4 n0 windows
+    const int64_t cblocks = (nch + kAdj3Threads - 1) / kAdj3Threads;
+    const int64_t want = std::max<int64_t>(1, (4LL * 152 * 4 + cblocks - 1) / cblocks);
+    p.chunk = (int)std::min<int64_t>(a.rows_out, std::max<int64_t>(4LL * a.n0, (a.rows_out + want - 1) / want));
+    p.scale = a.scale;
+    fill_omega_adj(p.om, a.n0);
+    const dim3 grid((unsigned)cblocks, (unsigned)((a.rows_out + p.chunk - 1) / p.chunk));
+    if (grid.y > 65535 || cblocks > INT32_MAX) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(float2) * (size_t)a.n0 * kAdj3Threads;
+    switch (a.n0) {
+#define F(N_)                                                                                            \
+    case N_:                                                                                             \
+        if (smem > 48 * 1024 &&                                                                          \
+            (e = cudaFuncSetAttribute(adj3_col_kernel<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                      (int)smem)) != cudaSuccess)                                        \
+            return e;                                                                                    \
+        adj3_col_kernel<N_><<<grid, kAdj3Threads, smem, s>>>(p);                                         \
+        break;
+        SWDFT_ADJ3_CASES(F)
+#undef F
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj3_row(const Adj3RowArgs &a, cudaStream_t s) {
+    if (a.zrows <= 0 || a.N1 <= 0) return cudaSuccess;
+    if (!a.gz || !a.gx || a.n1 < 1 || a.n1 > a.N1 || a.zrows > INT32_MAX || a.N1 > INT32_MAX)
+        return cudaErrorInvalidValue;
+    if (a.ld_out != a.N1) return cudaErrorInvalidValue;  // gradient rows are contiguous
+    const size_t elem = a.cplx ? sizeof(float2) : sizeof(float);
+    cudaError_t e = cudaMemsetAsync(a.gx, 0, (size_t)(a.zrows * a.N1) * elem, s);
+    if (e != cudaSuccess) return e;
+    Adj3RowParams p;
+    p.gz = a.gz;
+    p.gx = a.gx;
+    p.ld_out = a.ld_out;
+    p.zrows = (int)a.zrows;
+    p.N1 = (int)a.N1;
+    p.P1 = (int)(a.N1 - a.n1 + 1);
+    const int64_t rblocks = (a.zrows + kAdj3Threads - 1) / kAdj3Threads;
+    const int64_t want = std::max<int64_t>(1, (2LL * 152 * 4 + rblocks - 1) / rblocks);
+    p.chunk = (int)std::min<int64_t>(p.P1, std::max<int64_t>(4LL * a.n1, (p.P1 + want - 1) / want));
+    p.row_blocks = (int)rblocks;
+    fill_omega_adj(p.om, a.n1);
+    const dim3 grid((unsigned)rblocks, (unsigned)((p.P1 + p.chunk - 1) / p.chunk));
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(float2) * (size_t)a.n1 * kAdj3Threads;
+    switch (a.n1) {
+#define F(N_)                                                                                                \
+    case N_:                                                                                                 \
+        if (smem > 48 * 1024 &&                                                                              \
+            ((e = cudaFuncSetAttribute(adj3_row_kernel<N_, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                       (int)smem)) != cudaSuccess ||                                         \
+             (e = cudaFuncSetAttribute(adj3_row_kernel<N_, false>,                                           \
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)) \
+            return e;                                                                                        \
+        if (a.cplx)                                                                                          \
+            adj3_row_kernel<N_, true><<<grid, kAdj3Threads, smem, s>>>(p);                                   \
+        else                                                                                                 \
+            adj3_row_kernel<N_, false><<<grid, kAdj3Threads, smem, s>>>(p);                                  \
+        break;
+        SWDFT_ADJ3_CASES(F)
+#undef F
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace swdft

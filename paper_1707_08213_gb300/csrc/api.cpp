@@ -120,7 +120,7 @@ struct ArrayPlan {
         return std::min(rows_out, std::max<int64_t>((rows_out + 7) / 8, 4 * n0));
     }
     size_t adj_side_bytes(int64_t rows_out) const {
-        if (ternary()) return 0;  // no adjoint for ternary trees
+        if (ternary()) return 0;  // the ternary adjoint's chunks share rows through atomics
         return (size_t)adj_side_elems(rows_out, m0, P1, m1, adj_chunk(rows_out)) * sizeof(float2);
     }
     size_t adj_bytes(int64_t rows_out) const { return align_up(z_bytes(rows_out)) + align_up(adj_side_bytes(rows_out)); }
@@ -1107,7 +1107,7 @@ swdft_status swdft2d_launch_count(swdft2d_plan_t plan, int32_t adjoint, int32_t 
     }
     int32_t n = 0;
     for (const auto &a : plan->arrays)
-        n += adjoint ? 1 + adj_col_launches(a.band_rows(), a.m0, a.adj_chunk(a.band_rows()))
+        n += adjoint ? (a.ternary() ? 2 : 1 + adj_col_launches(a.band_rows(), a.m0, a.adj_chunk(a.band_rows())))
                      : ((a.algo == SWDFT_ALGO_TREE_F32 && a.cfg.fused && fused_supported(a.m0, a.m1)) ? 1 : 2);
     *launches = n;
     return SWDFT_OK;
@@ -1218,8 +1218,6 @@ swdft_status swdft2d_set_tree_config(swdft2d_plan_t plan, int32_t i, int32_t row
 swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_grad_out,
                                      void *const *d_grad_in, void *d_workspace, void *stream) {
     if (!plan || !d_grad_out || !d_grad_in) return SWDFT_ERR_INVALID_ARG;
-    for (const auto &a : plan->arrays)
-        if (a.ternary()) return SWDFT_ERR_UNSUPPORTED;  // the transposed tree is built for radix 2
     for (size_t i = 0; i < plan->arrays.size(); ++i) {
         const ArrayPlan &a = plan->arrays[i];
         if (!d_grad_out[i] || !d_grad_in[i]) return SWDFT_ERR_INVALID_ARG;
@@ -1230,9 +1228,59 @@ swdft_status swdft2d_execute_adjoint(swdft2d_plan_t plan, const void *const *d_g
     swdft_status st = configure(plan);
     if (st != SWDFT_OK) return st;
     cudaStream_t s0 = static_cast<cudaStream_t>(stream);
+    // ternary and mixed-radix windows: dense per-window inverse DFTs overlap-added per axis
+    // (adjoint3.cu), the transposed radix-2 tree for a power-of-two row window
+    auto enqueue_mixed = [&](const ArrayPlan &a, const void *G, void *gx_all, void *slot,
+                             cudaStream_t s) -> cudaError_t {
+        const int64_t zrows = a.band_rows() + a.n0 - 1;
+        const size_t row_bytes = (size_t)a.N1 * a.in_elem();
+        char *gx = static_cast<char *>(gx_all);
+        cudaError_t e;
+        if (a.q_begin > 0 && (e = cudaMemsetAsync(gx, 0, (size_t)a.q_begin * row_bytes, s)) != cudaSuccess) return e;
+        const int64_t tail = a.N0 - (a.q_begin + zrows);
+        if (tail > 0 &&
+            (e = cudaMemsetAsync(gx + (size_t)(a.q_begin + zrows) * row_bytes, 0, (size_t)tail * row_bytes, s)) !=
+                cudaSuccess)
+            return e;
+        Adj3ColArgs c;
+        c.G = static_cast<const float2 *>(G);
+        c.gz = static_cast<float2 *>(slot);
+        c.P1 = a.P1;
+        c.rows_out = a.band_rows();
+        c.n0 = a.n0;
+        c.n1 = a.n1;
+        c.scale = norm_scale(plan->norm, a.n0, a.n1);
+        if ((e = launch_adj3_col(c, s)) != cudaSuccess) return e;
+        if (a.r1 == 3) {
+            Adj3RowArgs r;
+            r.gz = c.gz;
+            r.gx = gx + (size_t)a.q_begin * row_bytes;
+            r.ld_out = a.N1;
+            r.zrows = zrows;
+            r.N1 = a.N1;
+            r.n1 = a.n1;
+            r.cplx = a.dtype == SWDFT_C64;
+            return launch_adj3_row(r, s);
+        }
+        AdjRowArgs r;
+        r.gz[0] = c.gz;
+        r.gx[0] = gx + (size_t)a.q_begin * row_bytes;
+        r.nz = 1;
+        r.ld_out = a.N1;
+        r.cplx = a.dtype == SWDFT_C64;
+        r.zrows = zrows;
+        r.N1 = a.N1;
+        r.m1 = a.m1;
+        r.om64 = plan->om64;
+        r.B = 0;
+        r.chunk = 0;
+        r.sm_count = plan->sm_count;
+        return launch_adj_row(r, s);
+    };
     // arrays first..first+nz-1 (one shape) in one launch pair; array k of the group uses slots[k]
     auto enqueue_group = [&](size_t first, int nz, void *const *slots, cudaStream_t s) -> cudaError_t {
         const ArrayPlan &a = plan->arrays[first];
+        if (a.ternary()) return enqueue_mixed(a, d_grad_out[first], d_grad_in[first], slots[0], s);
         const int64_t zrows = a.band_rows() + a.n0 - 1;
         const size_t row_bytes = (size_t)a.N1 * a.in_elem();
         AdjColArgs c;

@@ -308,6 +308,30 @@ struct AdjRowArgs {
     int sm_count = 152;  // for chunk = 0
 };
 
+// Adjoint passes for ternary and mixed-radix windows (adjoint3.cu): dense inverse DFTs of
+// length n per window, overlap-added in gather form.  Column pass: gz[r][q1][k1] = scale *
+// sum over the windows q0 covering row r of sum_k0 G[q0][q1][k0][k1] w_{n0}^{+(r-q0) k0}
+// (gz: rows_out + n0 - 1 rows of P1 n1 complex64; zeroed by the launcher).  Row pass:
+// gx[r][p1] = sum over the windows q1 covering column p1 of sum_k1 gz[r][q1][k1]
+// w_{n1}^{+(p1-q1) k1}, real part for float32 gradients (gx: zrows x N1, zeroed by the
+// launcher).  n0: 1 or 3^b 2^a (b >= 1) <= 64; n1: 3^b 2^a (b >= 1) <= 64.
+struct Adj3ColArgs {
+    const float2 *G = nullptr;
+    float2 *gz = nullptr;
+    int64_t P1 = 0, rows_out = 0;
+    int n0 = 1, n1 = 1;
+    float scale = 1.f;
+};
+struct Adj3RowArgs {
+    const float2 *gz = nullptr;
+    void *gx = nullptr;
+    int64_t ld_out = 0, zrows = 0, N1 = 0;
+    int n1 = 1;
+    int cplx = 0;
+};
+cudaError_t launch_adj3_col(const Adj3ColArgs &a, cudaStream_t s);
+cudaError_t launch_adj3_row(const Adj3RowArgs &a, cudaStream_t s);
+
 // Ternary and mixed-radix trees (tree3.cu): windows of n = 3^b 2^a samples along an axis
 // (b >= 1, n <= 64; b = a = 0: one sample), radix-3 levels first.
 // Row levels: z[r][q1][k1] for `rows` input rows (n1 = 3^b1 2^a1), as RowTreeArgs.

@@ -283,9 +283,11 @@ def test_tree_f32_close_to_definition(oracle_lib):
 
 # ---------------------------------------------------------------- adjoint
 
-@pytest.mark.parametrize("n0,n1", [(4, 8), (8, 4), (1, 4), (4, 1), (2, 2)])
+@pytest.mark.parametrize("n0,n1", [(4, 8), (8, 4), (1, 4), (4, 1), (2, 2), (3, 6), (9, 4), (12, 1), (1, 12),
+                                   (6, 9), (27, 3)])
 def test_adjoint_dot_product(oracle_lib, n0, n1):
-    N0, N1 = 11, 13
+    """<A x, G> = <x, A^H G> for both adjoint methods, power-of-two and mixed-radix windows."""
+    N0, N1 = max(11, n0 + 4), max(13, n1 + 5)
     x = _rand(81, N0, N1)
     rng = np.random.default_rng(82)
     G = rng.standard_normal((N0 - n0 + 1, N1 - n1 + 1, n0, n1)) + 1j * rng.standard_normal(
