@@ -7,8 +7,9 @@
 //
 // (only windows that exist contribute; gx keeps the real part for real input).  A thread walks
 // its channel (column pass) or its row (row pass) window by window: it computes the window's
-// n inverse-DFT values from the n spectral values it loads (twiddles w_n^{+jk}, indices fixed
-// at compile time, read from the kernel parameters) and adds value j into a ring of n partial
+// n inverse-DFT values from the n spectral values it loads (one radix-3 or radix-2 step, then
+// dense inverse DFTs of length n / 3 or n / 2; twiddles w_n^{+jk} with indices fixed at compile
+// time, read from the kernel parameters) and adds value j into a ring of n partial
 // outputs in shared memory, one slot per output row (column) still open; after window q the
 // output at q has all its windows and leaves the ring.  Chunks of windows run in parallel:
 // the n - 1 outputs a chunk shares with each neighbour are added atomically into a zeroed
@@ -42,6 +43,7 @@ struct Adj3RowParams {
 };
 
 constexpr int kAdj3Threads = 128;
+constexpr int64_t kAdj3Blocks = 152 * 8;  // blocks a pass is cut into (about eight per SM)
 
 __device__ __forceinline__ float2 conj_mul(float2 w, float2 v) {  // conj(w) v
     return make_float2(w.x * v.x + w.y * v.y, w.x * v.y - w.y * v.x);
@@ -52,17 +54,54 @@ __device__ __forceinline__ void atomic_add2(float2 *d, float2 v) {
     atomicAdd(&d->y, v.y);
 }
 
-// The window's inverse DFT value j of v[0..N-1] (unnormalised), added into ring slot s + j.
+// The window's inverse DFT value j of v[0..N-1] (unnormalised), X[j] = sum_k v[k] w_N^{+jk},
+// added into ring slot s + j.  One radix step first (R = 3, else 2): with k = R k' + d,
+// X[j] = sum_d w_N^{+jd} S_d[j mod M], S_d = the length-M inverse DFT of v[d], v[R + d], ...
+// (M = N / R), computed densely and stored back over v[d], v[R + d], ...: N (M + R - 1)
+// complex multiply-adds instead of N^2.
 template <int N>
-__device__ __forceinline__ void idft_into_ring(const float2 (&v)[N], const OmegaN &om, float2 *ring, int slot) {
+__device__ __forceinline__ void idft_into_ring(float2 (&v)[N], const OmegaN &om, float2 *ring, int slot) {
+    constexpr int R = (N % 3 == 0 && N > 3) ? 3 : ((N % 2 == 0 && N > 2) ? 2 : 1);
+    constexpr int M = N / R;
+    if constexpr (R > 1) {
+#pragma unroll
+        for (int d = 0; d < R; ++d) {
+            float2 tmp[M];
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                float2 h = v[d];
+#pragma unroll
+                for (int k = 1; k < M; ++k) {
+                    const float2 t = conj_mul(om.w[(R * j * k) % N], v[R * k + d]);
+                    h.x += t.x;
+                    h.y += t.y;
+                }
+                tmp[j] = h;
+            }
+#pragma unroll
+            for (int j = 0; j < M; ++j) v[R * j + d] = tmp[j];
+        }
+    }
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-        float2 h = v[0];
+        float2 h;
+        if constexpr (R > 1) {
+            const int jm = j % M;
+            h = v[R * jm];
 #pragma unroll
-        for (int k = 1; k < N; ++k) {
-            const float2 t = conj_mul(om.w[(j * k) % N], v[k]);
-            h.x += t.x;
-            h.y += t.y;
+            for (int d = 1; d < R; ++d) {
+                const float2 t = conj_mul(om.w[(j * d) % N], v[R * jm + d]);
+                h.x += t.x;
+                h.y += t.y;
+            }
+        } else {
+            h = v[0];
+#pragma unroll
+            for (int k = 1; k < N; ++k) {
+                const float2 t = conj_mul(om.w[(j * k) % N], v[k]);
+                h.x += t.x;
+                h.y += t.y;
+            }
         }
         int sj = slot + j;
         if (sj >= N) sj -= N;
@@ -183,10 +222,11 @@ cudaError_t launch_adj3_col(const Adj3ColArgs &a, cudaStream_t s) {
     p.nch = nch;
     p.n1 = a.n1;
     p.rows_out = (int)a.rows_out;
-    // about four resident waves of blocks, chunks of at least 4 n0 windows
+    // chunks cost nothing but the atomic adds of their n0 - 1 shared rows (no warm-up: every
+    // window is transformed once), so they are cut to give about eight blocks per SM
     const int64_t cblocks = (nch + kAdj3Threads - 1) / kAdj3Threads;
-    const int64_t want = std::max<int64_t>(1, (4LL * 152 * 4 + cblocks - 1) / cblocks);
-    p.chunk = (int)std::min<int64_t>(a.rows_out, std::max<int64_t>(4LL * a.n0, (a.rows_out + want - 1) / want));
+    const int64_t want = std::max<int64_t>(1, (kAdj3Blocks + cblocks - 1) / cblocks);
+    p.chunk = (int)std::min<int64_t>(a.rows_out, std::max<int64_t>(4, (a.rows_out + want - 1) / want));
     p.scale = a.scale;
     fill_omega_adj(p.om, a.n0);
     const dim3 grid((unsigned)cblocks, (unsigned)((a.rows_out + p.chunk - 1) / p.chunk));
@@ -225,8 +265,8 @@ cudaError_t launch_adj3_row(const Adj3RowArgs &a, cudaStream_t s) {
     p.N1 = (int)a.N1;
     p.P1 = (int)(a.N1 - a.n1 + 1);
     const int64_t rblocks = (a.zrows + kAdj3Threads - 1) / kAdj3Threads;
-    const int64_t want = std::max<int64_t>(1, (2LL * 152 * 4 + rblocks - 1) / rblocks);
-    p.chunk = (int)std::min<int64_t>(p.P1, std::max<int64_t>(4LL * a.n1, (p.P1 + want - 1) / want));
+    const int64_t want = std::max<int64_t>(1, (kAdj3Blocks + rblocks - 1) / rblocks);
+    p.chunk = (int)std::min<int64_t>(p.P1, std::max<int64_t>(4, (p.P1 + want - 1) / want));
     p.row_blocks = (int)rblocks;
     fill_omega_adj(p.om, a.n1);
     const dim3 grid((unsigned)rblocks, (unsigned)((p.P1 + p.chunk - 1) / p.chunk));
