@@ -1,15 +1,15 @@
 // Adjoint for ternary and mixed-radix windows (n = 3^b 2^a along an axis, b >= 1): the
 // overlap-add of every window's inverse DFT (the transpose of Eq. 2's map), evaluated per axis
-// in gather form with dense inverse DFTs of length n:
+// in gather form with an inverse FFT of length n per window:
 //
 //   column pass  gz[r][q1][k1] = c sum_{q0 = r-n0+1..r} sum_k0 G[q0][q1][k0][k1] w_{n0}^{+(r-q0) k0}
 //   row pass     gx[r][p1]     =   sum_{q1 = p1-n1+1..p1} sum_k1 gz[r][q1][k1] w_{n1}^{+(p1-q1) k1}
 //
 // (only windows that exist contribute; gx keeps the real part for real input).  A thread walks
 // its channel (column pass) or its row (row pass) window by window: it computes the window's
-// n inverse-DFT values from the n spectral values it loads (one radix-3 or radix-2 step, then
-// dense inverse DFTs of length n / 3 or n / 2; twiddles w_n^{+jk} with indices fixed at compile
-// time, read from the kernel parameters) and adds value j into a ring of n partial
+// n inverse-DFT values from the n spectral values it loads (an in-place mixed-radix inverse
+// FFT in registers, radix 3 and 2 steps, every index fixed at compile time; twiddles from the
+// kernel parameters) and adds value j into a ring of n partial
 // outputs in shared memory, one slot per output row (column) still open; after window q the
 // output at q has all its windows and leaves the ring.  Chunks of windows run in parallel:
 // the n - 1 outputs a chunk shares with each neighbour are added atomically into a zeroed
@@ -54,61 +54,75 @@ __device__ __forceinline__ void atomic_add2(float2 *d, float2 v) {
     atomicAdd(&d->y, v.y);
 }
 
-// The window's inverse DFT value j of v[0..N-1] (unnormalised), X[j] = sum_k v[k] w_N^{+jk},
-// added into ring slot s + j.  One radix step first (R = 3, else 2): with k = R k' + d,
-// X[j] = sum_d w_N^{+jd} S_d[j mod M], S_d = the length-M inverse DFT of v[d], v[R + d], ...
-// (M = N / R), computed densely and stored back over v[d], v[R + d], ...: N (M + R - 1)
-// complex multiply-adds instead of N^2.
+// The window's inverse DFT, X[j] = sum_k v[k] w_N^{+jk} (unnormalised), in place by
+// decimation in time: N = R M (radix R = 3 while N has a factor 3 above 3, then 2), the R
+// interleaved subsequences v[d], v[d + R], ... transformed recursively in place, then per
+// j' < M one R-point butterfly on their outputs twiddled by w_N^{+j' d}, its output a stored
+// back over input d.  Inputs in natural order; X[j] ends at position ifft_pos(N, j) =
+// R ifft_pos(M, j mod M) + j / M (digit-reversed), all indices fixed at compile time;
+// twiddles w_N^{+x} = conj(w_NTOP^{-x NTOP / N}) from the kernel parameters' table for the top
+// length NTOP.  N (sum of the radices) complex multiply-adds per element.
+__host__ __device__ constexpr int ifft_radix(int n) { return (n % 3 == 0 && n > 3) ? 3 : ((n % 2 == 0 && n > 2) ? 2 : n); }
+__host__ __device__ constexpr int ifft_pos(int n, int j) {
+    return n <= 3 ? j : ifft_radix(n) * ifft_pos(n / ifft_radix(n), j % (n / ifft_radix(n))) + j / (n / ifft_radix(n));
+}
+
+template <int NTOP, int N, int STRIDE, int OFF, int NV>
+__device__ __forceinline__ void ifft_rec(float2 (&v)[NV], const OmegaN &om) {
+    if constexpr (N == 2) {
+        const float2 a = v[OFF], b = v[OFF + STRIDE];
+        v[OFF] = make_float2(a.x + b.x, a.y + b.y);
+        v[OFF + STRIDE] = make_float2(a.x - b.x, a.y - b.y);
+    } else if constexpr (N == 3) {
+        const float2 x0 = v[OFF], x1 = v[OFF + STRIDE], x2 = v[OFF + 2 * STRIDE];
+        static_for<0, 3>([&](auto AA) {
+            constexpr int a = decltype(AA)::value;
+            const float2 t1 = conj_mul(om.w[(a * 1 * (NTOP / 3)) % NTOP], x1);
+            const float2 t2 = conj_mul(om.w[(a * 2 * (NTOP / 3)) % NTOP], x2);
+            v[OFF + a * STRIDE] = make_float2(x0.x + t1.x + t2.x, x0.y + t1.y + t2.y);
+        });
+    } else if constexpr (N > 3) {
+        constexpr int R = ifft_radix(N), M = N / R;
+        static_for<0, R>([&](auto DD) {
+            constexpr int d = decltype(DD)::value;
+            ifft_rec<NTOP, M, STRIDE * R, OFF + STRIDE * d>(v, om);
+        });
+        static_for<0, M>([&](auto JJ) {
+            constexpr int jp = decltype(JJ)::value;
+            constexpr int base = OFF + STRIDE * R * ifft_pos(M, jp);
+            float2 t[R];
+            static_for<0, R>([&](auto DD) {
+                constexpr int d = decltype(DD)::value;
+                t[d] = d == 0 ? v[base] : conj_mul(om.w[(jp * d * (NTOP / N)) % NTOP], v[base + STRIDE * d]);
+            });
+            static_for<0, R>([&](auto AA) {
+                constexpr int a = decltype(AA)::value;
+                float2 x = t[0];
+                static_for<1, R>([&](auto DD) {
+                    constexpr int d = decltype(DD)::value;
+                    const float2 u = conj_mul(om.w[(a * d * (NTOP / R)) % NTOP], t[d]);
+                    x.x += u.x;
+                    x.y += u.y;
+                });
+                v[base + STRIDE * a] = x;
+            });
+        });
+    }
+}
+
+// The window's inverse DFT values, value j added into ring slot slot + j (mod N).
 template <int N>
 __device__ __forceinline__ void idft_into_ring(float2 (&v)[N], const OmegaN &om, float2 *ring, int slot) {
-    constexpr int R = (N % 3 == 0 && N > 3) ? 3 : ((N % 2 == 0 && N > 2) ? 2 : 1);
-    constexpr int M = N / R;
-    if constexpr (R > 1) {
-#pragma unroll
-        for (int d = 0; d < R; ++d) {
-            float2 tmp[M];
-#pragma unroll
-            for (int j = 0; j < M; ++j) {
-                float2 h = v[d];
-#pragma unroll
-                for (int k = 1; k < M; ++k) {
-                    const float2 t = conj_mul(om.w[(R * j * k) % N], v[R * k + d]);
-                    h.x += t.x;
-                    h.y += t.y;
-                }
-                tmp[j] = h;
-            }
-#pragma unroll
-            for (int j = 0; j < M; ++j) v[R * j + d] = tmp[j];
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-        float2 h;
-        if constexpr (R > 1) {
-            const int jm = j % M;
-            h = v[R * jm];
-#pragma unroll
-            for (int d = 1; d < R; ++d) {
-                const float2 t = conj_mul(om.w[(j * d) % N], v[R * jm + d]);
-                h.x += t.x;
-                h.y += t.y;
-            }
-        } else {
-            h = v[0];
-#pragma unroll
-            for (int k = 1; k < N; ++k) {
-                const float2 t = conj_mul(om.w[(j * k) % N], v[k]);
-                h.x += t.x;
-                h.y += t.y;
-            }
-        }
+    ifft_rec<N, N, 1, 0>(v, om);
+    static_for<0, N>([&](auto JJ) {
+        constexpr int j = decltype(JJ)::value;
+        const float2 h = v[ifft_pos(N, j)];
         int sj = slot + j;
         if (sj >= N) sj -= N;
         float2 *a = ring + sj * kAdj3Threads;
         a->x += h.x;
         a->y += h.y;
-    }
+    });
 }
 
 template <int N0>
