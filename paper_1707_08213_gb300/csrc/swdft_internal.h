@@ -31,11 +31,13 @@ void make_omega(int n, float2 *out);
 // 1024x2048/16x64 workloads).
 //  * row levels: thread = (row, residue, chunk of window columns); B = 3 (2 for 64-point
 //    trees, which need more registers), about 64K threads in flight, chunks no shorter than
-//    n1/2 (each chunk re-walks n1 - 1 columns of warm-up).
+//    n1/2 (each chunk's walk starts n1/2 columns before its first window: n1/2 - 1 steps of
+//    warm-up).
 //  * column levels: thread = (channel, residue, chunk of window rows); B = 2 (3 for 64-point
 //    trees); about eight row chunks per 32-channel group (sixteen for fused small windows),
 //    more when there are few channel groups, so that the pass has at least four blocks per
-//    SM; every chunk at least 2 n0 rows so warm-up stays under a third.
+//    SM; every chunk at least 2 n0 rows (its walk has n0/2 - 1 steps of warm-up; n0 - 1 for
+//    n0 <= 8, whose walks start on a whole step group of 8 rows).
 inline int default_row_B(int m1) { return m1 >= 6 ? 2 : (m1 < 3 ? m1 : 3); }
 inline int64_t default_row_chunk(int64_t P1, int64_t zrows, int64_t threads_per_row, int n1) {
     const int64_t t = zrows * threads_per_row;

@@ -1,8 +1,8 @@
 // Ternary and mixed-radix tree passes (windows of 3^b 2^a samples along an axis, b >= 1,
 // at most 64; tree3_core.cuh): the row levels along dimension 1 and the column levels along
 // dimension 0, laid out like the binary passes (tree_kernels.cuh).  z layout: z_pad rows in
-// front (2 n0 / 3 for such a column tree: its level-0 look-back reaches 2 s_1 rows up), then
-// rows x P1 x n1 complex64.  Kernels are templated on (B3, A2), n = 3^B3 2^A2; (0, 0) is the
+// front (2 n0 / 3 for such a column tree, the reach of its level-0 look-back; walks that
+// start 2 s_1 steps in, as these do, never read them), then rows x P1 x n1 complex64.  Kernels are templated on (B3, A2), n = 3^B3 2^A2; (0, 0) is the
 // window of one sample (no tree).
 #pragma once
 
@@ -83,7 +83,12 @@ __global__ void __launch_bounds__(96) row_tree3_kernel(const __grid_constant__ R
     using Tree = typename Of::Tree;
     Tree tree;
     if constexpr (Of::kSplit) tree.init(c, p.om);
-    for (int jb = 0; jb < steps; jb += UNR) {
+    // The walk starts at step 2 s_1 (= 2n/3): level 1 reads level 0 s_1 and 2 s_1 back from
+    // memory and the FIFOs of levels 1 .. L-1 hold n - 1 - 2 s_1 steps, so the first stored
+    // output (step n - 1) needs level 1 from step 2 s_1 on.  2 s_1 is a multiple of the unroll
+    // period.
+    static_assert(!Of::kSplit || (2 * S1) % Of::kPeriod == 0, "the walk starts on a whole period");
+    for (int jb = 2 * S1; jb < steps; jb += UNR) {
         static_for<0, UNR>([&](auto JJ) {
             constexpr int J = decltype(JJ)::value;
             const int j = jb + J;
@@ -201,10 +206,12 @@ __global__ void __launch_bounds__(192) col_tree3_kernel(const __grid_constant__ 
     Tree tree;
     if constexpr (Of::kSplit) tree.init(c, p.om);
     int buf = 0;
-    fetch(qa - 2 * S1, min(qa + G, zr_end));
+    // the walk starts at step 2 s_1, as in the row pass: its look-backs start at row qa
+    fetch(qa, min(qa + 2 * S1 + G, zr_end));
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    for (int jb = 0; jb < steps; jb += G) {
+    static_assert(!Of::kSplit || (2 * S1) % Of::kPeriod == 0, "the walk starts on a whole period");
+    for (int jb = 2 * S1; jb < steps; jb += G) {
         if (jb + G < steps) fetch(qa + jb + G, min(qa + jb + 2 * G, zr_end));
         static_for<0, G>([&](auto JJ) {
             constexpr int J = decltype(JJ)::value;

@@ -9,7 +9,8 @@
 //
 // z layout: kZPad(n0) = n0/2 padding rows, then rows x P1 x n1 complex64.  The padding lets
 // the column pass read its level-0 look-back z[r - n0/2] without a bounds clamp (values
-// read there only feed incomplete border trees, which are never stored).
+// read there only feed incomplete border trees, which are never stored; only walks of
+// n0 <= 8 rows, which start a whole step group early, read it).
 //
 // Each column-pass warp covers 32 consecutive channels (q1, k1): its z loads and its
 // output stores move 256 contiguous bytes per k0 (full 32-byte sectors).  Outputs go out
@@ -73,7 +74,13 @@ __device__ __forceinline__ void row_tile(const RowGeom &p, int row_block, int ch
 
     Tree tree;
     tree.init(c, om64);
-    for (int jb = 0; jb < steps; jb += Tree::kPeriod) {
+    // The walk starts n/2 steps before the chunk's first complete window: level 1 reads level 0
+    // n/2 positions back from memory, and the FIFOs of levels 1 .. M-1 hold n/2 - 1 steps, so
+    // the first stored output (step n - 1) needs level 1 from step n/2 on; the zeroed FIFOs only
+    // feed steps before it.  n/2 is a multiple of the unroll period (FIFO slots keep their
+    // step residues).
+    static_assert(Tree::kHalf % Tree::kPeriod == 0, "the walk starts on a whole period");
+    for (int jb = Tree::kHalf; jb < steps; jb += Tree::kPeriod) {
         static_for<0, Tree::kPeriod>([&](auto JJ) {
             constexpr int J = decltype(JJ)::value;
             const int j = jb + J;
@@ -315,19 +322,23 @@ __device__ __forceinline__ void col_tile_impl(const ColGeom &p, int64_t ch_block
     const int64_t q1 = ch >> p.m1;
     const int64_t k1 = ch & (n1 - 1);
     const int kstride = R * n1;  // elements between outputs t and t+1 (k0 step 2^B)
+    // First step of the walk: n/2 (as in row_tile) rounded down to whole step groups, so that
+    // every fetch starts on a group; for n0 >= 16 it is n/2 and no padding row is read.
+    constexpr int kJ0 = (kH / kP) * kP;
     float2 *dst = p.out + slice * p.oslice + (int64_t)qa * p.orow + q1 * ((int64_t)n * n1) +
                   (int64_t)c * n1 + k1;
     const float s = p.scale;
 
     Tree tree;
     tree.init(c, om64);
-    stage.fetch(ring, qa - kH, min(qa + kP, zr_end), CH, ch0, RD);
+    stage.fetch(ring, qa + kJ0 - kH, min(qa + kJ0 + kP, zr_end), CH, ch0, RD);
 #pragma unroll
     for (int a = 1; a < AHEAD; ++a)
-        if (a * kP < steps) stage.fetch(ring, qa + a * kP, min(qa + (a + 1) * kP, zr_end), CH, ch0, RD);
+        if (kJ0 + a * kP < steps)
+            stage.fetch(ring, qa + kJ0 + a * kP, min(qa + kJ0 + (a + 1) * kP, zr_end), CH, ch0, RD);
     stage.wait();
     __syncthreads();
-    for (int jb = 0; jb < steps; jb += kP) {
+    for (int jb = kJ0; jb < steps; jb += kP) {
         if (jb + AHEAD * kP < steps)
             stage.fetch(ring, qa + jb + AHEAD * kP, min(qa + jb + (AHEAD + 1) * kP, zr_end), CH, ch0, RD);
         static_for<0, kP>([&](auto JJ) {

@@ -38,10 +38,11 @@ def tw_offset(B, v):
     return sum(1 if w <= B else held(B, w - 1) for w in range(1, v))
 
 
-def forward_tree(M, B, c, feeds):
-    """Thread c of the sliding tree (tree_core.cuh, SlidingTree) over the steps j = 0, 1, ..:
-    feeds[j] = (x at the window's end position, x n/2 positions earlier), values or arrays over
-    independent lanes; returns the thread's level-M nodes k = c + 2^B t at every step."""
+def forward_tree(M, B, c, feeds, j0=0):
+    """Thread c of the sliding tree (tree_core.cuh, SlidingTree) over the steps j = j0, j0 + 1, ..:
+    feeds[j - j0] = (x at the window's end position, x n/2 positions earlier), values or arrays
+    over independent lanes; returns the thread's level-M nodes k = c + 2^B t at every step.
+    The FIFOs start at zero, as the kernels' do."""
     n = 1 << M
     om = np.exp(-2j * np.pi * np.arange(n) / n)
     tw = [0j] * max(1, tw_offset(B, M + 1))
@@ -56,8 +57,8 @@ def forward_tree(M, B, c, feeds):
     fifos = {u: [[0j] * held(B, u) for _ in range(fifo_depth(M, u))] for u in range(1, M)}
     period = 1 << (M - 2) if M >= 2 else 1  # the kernels' unroll period
     outs = []
-    for j, (xp, xs) in enumerate(feeds):
-        J = j % period
+    for i, (xp, xs) in enumerate(feeds):
+        J = (j0 + i) % period
         cur = [xp] + [0j] * (held(B, M) - 1)
         for v in range(1, M + 1):
             hp = held(B, v - 1)
@@ -152,6 +153,53 @@ def test_forward_schedule_gives_every_windows_dft(M, B):
             np.testing.assert_allclose(outs[p], ref[ks], atol=1e-9)
 
 
+def row_walk_start(M):
+    """First step of a row-pass chunk's walk (row_tile): level 1 reads level 0 n/2 positions back
+    from memory, so the output at step n - 1 needs level 1 from step n - 1 - (n/2 - 1) = n/2 on
+    (the FIFO depths of levels 1 .. M-1 add up to n/2 - 1); steps before it are never needed."""
+    return (1 << M) // 2
+
+
+def col_walk_start(M):
+    """First step of a column tile's walk (col_tile_impl): n/2 rounded down to whole step groups,
+    so that every fetch still starts on a group (TMA boxes)."""
+    return ((1 << M) // 2 // col_group(M)) * col_group(M)
+
+
+def late_walk(M, B, c, x, j0):
+    n = 1 << M
+    feeds = [(x[p], x[p - n // 2] if M >= 1 else 0j) for p in range(j0, len(x))]
+    return forward_tree(M, B, c, feeds, j0)
+
+
+@pytest.mark.parametrize("M,B", SPLITS)
+def test_walk_started_at_half_a_window_gives_every_windows_dft(M, B):
+    """Zeroed FIFOs and a walk that starts at the row or column pass's first step: every
+    complete window (end position >= n - 1) is still exact."""
+    n = 1 << M
+    rng = np.random.default_rng(900 + 10 * M + B)
+    x = rng.standard_normal(n + 21) + 1j * rng.standard_normal(n + 21)
+    for j0 in sorted({row_walk_start(M), col_walk_start(M)}):
+        assert j0 % (1 << (M - 2) if M >= 2 else 1) == 0  # FIFO slots keep their step residues
+        for c in range(1 << B):
+            outs = late_walk(M, B, c, x, j0)
+            ks = [(c & ((1 << B) - 1)) + (t << B) for t in range(held(B, M))]
+            for p in range(n - 1, len(x)):
+                np.testing.assert_allclose(outs[p - j0], np.fft.fft(x[p - n + 1:p + 1])[ks], atol=1e-9)
+
+
+@pytest.mark.parametrize("M", [2, 3, 4, 5, 6])
+def test_walk_started_one_period_too_late_is_caught(M):
+    """Planted mistake: a walk that starts one unroll period after n/2 leaves a zero in a FIFO
+    that the first complete window reads."""
+    n, period = 1 << M, 1 << (M - 2)
+    rng = np.random.default_rng(950 + M)
+    x = rng.standard_normal(n + 5) + 1j * rng.standard_normal(n + 5)
+    j0 = n // 2 + period
+    first = np.array(late_walk(M, 0, 0, x, j0)[n - 1 - j0])
+    assert np.abs(first - np.fft.fft(x[:n])).max() > 1e-3
+
+
 @pytest.mark.parametrize("M,B", SPLITS)
 def test_adjoint_schedule_gives_the_overlap_add_of_inverse_dfts(M, B):
     n = 1 << M
@@ -166,9 +214,9 @@ def test_adjoint_schedule_gives_the_overlap_add_of_inverse_dfts(M, B):
     np.testing.assert_allclose(y, ref, atol=1e-9)
 
 
-def ternary_tree(M, c, feeds):
+def ternary_tree(M, c, feeds, j0=0):
     """Thread c (< 3) of the ternary tree split by residue mod 3 (tree3_core.cuh) over the
-    steps j = 0, 1, ..: feeds[j] = (x at the window end p, x at p - s_1, x at p - 2 s_1),
+    steps j = j0, j0 + 1, ..: feeds[j - j0] = (x at the window end p, x at p - s_1, x at p - 2 s_1),
     s_1 = 3^(M-1), values or lane arrays; returns its level-M nodes c + 3u, u < 3^(M-1)."""
     w27 = np.exp(-2j * np.pi * np.arange(27) / 27)
 
@@ -182,8 +230,8 @@ def ternary_tree(M, c, feeds):
     period = 2 * 3 ** (M - 2) if M >= 2 else 1
     w3 = np.exp(-2j * np.pi / 3)
     outs = []
-    for j, (xp, xs1, xs2) in enumerate(feeds):
-        J = j % period
+    for i, (xp, xs1, xs2) in enumerate(feeds):
+        J = (j0 + i) % period
         cur = [xs2 + w3 ** c * xs1 + w3 ** (2 * c) * xp]  # level 1, node c
         for t in range(2, M + 1):
             s = 3 ** (M - t)
@@ -226,10 +274,10 @@ def mixed_period(B3, A2):
     return (r2 - 1) * (n // N2)
 
 
-def mixed_tree(B3, A2, c, feeds):
+def mixed_tree(B3, A2, c, feeds, j0=0):
     """Thread c (< 3) of the mixed-radix tree split by residue mod 3 (tree3_core.cuh,
-    SlidingTreeMixed: B3 radix-3 levels, then A2 radix-2 levels) over the steps j = 0, 1, ..:
-    feeds[j] = (x at p, x at p - s_1, x at p - 2 s_1), s_1 = n / 3; returns its level-L
+    SlidingTreeMixed: B3 radix-3 levels, then A2 radix-2 levels) over the steps j = j0, j0 + 1, ..:
+    feeds[j - j0] = (x at p, x at p - s_1, x at p - 2 s_1), s_1 = n / 3; returns its level-L
     nodes c + 3u, u < n / 3.  FIFO depths, slots (step index modulo the depth, within the
     unroll period) and twiddle indices as the kernel has them."""
     n = 3 ** B3 * 2 ** A2
@@ -257,8 +305,8 @@ def mixed_tree(B3, A2, c, feeds):
     fifos = {t: [[0j] * held(t - 1) for _ in range(depth(t))] for t in range(2, L + 1)}
     w3 = np.exp(-2j * np.pi / 3)
     outs = []
-    for j, (xp, xs1, xs2) in enumerate(feeds):
-        J = j % period
+    for i, (xp, xs1, xs2) in enumerate(feeds):
+        J = (j0 + i) % period
         cur = [xs2 + tw1[0] * xs1 + tw1[1] * xp]  # level 1, node c
         for t in range(2, L + 1):
             s, D, hp = n // Nt(t), depth(t), held(t - 1)
@@ -296,6 +344,33 @@ def test_mixed_schedule_gives_every_windows_dft(B3, A2):
         for p in range(n - 1, len(x)):
             ref = np.fft.fft(x[p - n + 1:p + 1])
             np.testing.assert_allclose(outs[p], ref[c::3], atol=1e-9)
+
+
+def walk3_start(n):
+    """First step of a ternary or mixed chunk's walk (row_tree3_kernel, col_tree3_kernel): level 1
+    reads level 0 s_1 and 2 s_1 back from memory, and the FIFO depths of levels 1 .. L-1 add up
+    to n - 1 - 2 s_1, so the output at step n - 1 needs level 1 from step 2 s_1 = 2n/3 on."""
+    return 2 * (n // 3) if n % 3 == 0 else 0
+
+
+@pytest.mark.parametrize("B3,A2", MIXED_SHAPES)
+def test_mixed_walk_started_at_two_thirds_gives_every_windows_dft(B3, A2):
+    n = 3 ** B3 * 2 ** A2
+    s1, period, j0 = n // 3, mixed_period(B3, A2), walk3_start(n)
+    assert j0 % period == 0
+    rng = np.random.default_rng(760 + n)
+    x = rng.standard_normal(n + 19) + 1j * rng.standard_normal(n + 19)
+    feeds = [(x[p], x[p - s1], x[p - 2 * s1]) for p in range(j0, len(x))]
+    for c in range(3):
+        outs = mixed_tree(B3, A2, c, feeds, j0)
+        for p in range(n - 1, len(x)):
+            np.testing.assert_allclose(outs[p - j0], np.fft.fft(x[p - n + 1:p + 1])[c::3], atol=1e-9)
+    # planted mistake: one period later, the first complete window reads a zeroed FIFO slot
+    if B3 + A2 >= 2:
+        late = [(x[p], x[p - s1], x[p - 2 * s1]) for p in range(j0 + period, len(x))]
+        bad = max(np.abs(np.array(mixed_tree(B3, A2, c, late, j0 + period)[n - 1 - j0 - period]) -
+                         np.fft.fft(x[:n])[c::3]).max() for c in range(3))
+        assert bad > 1e-3
 
 
 def ternary_walk(M, c, x):
@@ -722,12 +797,14 @@ def emulate_row_pass(x, n1, B, chunk, pad):
         qb = min(qa + chunk, P1)
         steps = (qb - qa) + (n1 - 1)
         assert qb + n1 - 2 <= N1 - 1  # last column read
-        feeds = [(x[:, qa + j], x[:, max(qa + j - n1 // 2, 0)] if M >= 1 else 0j) for j in range(steps)]
+        j0 = row_walk_start(M)
+        assert qa + j0 - n1 // 2 >= qa  # no look-back before the chunk's first window
+        feeds = [(x[:, qa + j], x[:, max(qa + j - n1 // 2, 0)] if M >= 1 else 0j) for j in range(j0, steps)]
         for c in range(R):
-            outs = forward_tree(M, B, c, feeds)
+            outs = forward_tree(M, B, c, feeds, j0)
             for j in range(n1 - 1, steps):
                 q1 = qa + j - (n1 - 1)
-                for t, o in enumerate(outs[j]):
+                for t, o in enumerate(outs[j - j0]):
                     col = q1 * n1 + c + (t << B)
                     assert np.isnan(z[pad:, col]).all(), "z value written twice"
                     z[pad:, col] = o
@@ -909,16 +986,17 @@ def emulate_col_pass(stage, n0, B, groups, m1, P1, rows_out, chunk, scale):
         for qa in range(0, rows_out, chunk):
             qb = min(qa + chunk, rows_out)
             steps, zr_end = (qb - qa) + (n - 1), qb + n - 1
+            j0 = col_walk_start(M)
             ring = np.full(RD * CH, np.nan, complex)
-            stage.fetch(ring, qa - kH, min(qa + kP, zr_end), CH, ch0, RD)
+            stage.fetch(ring, qa + j0 - kH, min(qa + j0 + kP, zr_end), CH, ch0, RD)
             inflight = []  # ring rows of each fetch still in flight, oldest first
             for a in range(1, AHEAD):
-                if a * kP < steps:
-                    lo, hi = qa + a * kP, min(qa + (a + 1) * kP, zr_end)
+                if j0 + a * kP < steps:
+                    lo, hi = qa + j0 + a * kP, min(qa + j0 + (a + 1) * kP, zr_end)
                     inflight.append(stage.fetch(ring, lo, hi, CH, ch0, RD))
             stage.wait()
             feeds = []
-            for jb in range(0, steps, kP):
+            for jb in range(j0, steps, kP):
                 if jb + AHEAD * kP < steps:
                     lo, hi = qa + jb + AHEAD * kP, min(qa + jb + (AHEAD + 1) * kP, zr_end)
                     inflight.append(stage.fetch(ring, lo, hi, CH, ch0, RD))
@@ -927,6 +1005,7 @@ def emulate_col_pass(stage, n0, B, groups, m1, P1, rows_out, chunk, scale):
                     zr = qa + j
                     # no row this group reads is one the fetch in flight writes
                     assert (zr & (RD - 1)) not in busy and ((zr - kH) & (RD - 1)) not in busy
+                    assert j0 < kH or zr - kH >= qa  # a walk from n/2 reads no padding row
                     xp = ring[(zr & (RD - 1)) * CH + my]
                     xs = ring[((zr - kH) & (RD - 1)) * CH + my] if M >= 1 else 0j
                     stage.check(xp, zr, ch)
@@ -937,10 +1016,10 @@ def emulate_col_pass(stage, n0, B, groups, m1, P1, rows_out, chunk, scale):
                 if inflight:
                     inflight.pop(0)
             for c in range(R):
-                outs = forward_tree(M, B, c, feeds)
+                outs = forward_tree(M, B, c, feeds, j0)
                 for j in range(n - 1, steps):
                     q0 = qa + j - (n - 1)
-                    for t, o in enumerate(outs[j]):
+                    for t, o in enumerate(outs[j - j0]):
                         k0 = c + R * t
                         for i in np.nonzero(active)[0]:
                             q1, k1 = ch[i] >> m1, ch[i] & (n1 - 1)
@@ -1054,12 +1133,12 @@ def col3_group(period):
     return 8 if period <= 8 and 8 % period == 0 else (6 if period == 6 else 12)
 
 
-def tree3_outs(n, feeds):
-    """Every residue thread's outputs (the mixed tree; n = 1: the data itself)."""
+def tree3_outs(n, feeds, j0=0):
+    """Every residue thread's outputs from step j0 on (the mixed tree; n = 1: the data itself)."""
     B3, A2 = mixed_split(n)
     if B3 == 0:
         return {0: [[f[0]] for f in feeds]}
-    return {c: mixed_tree(B3, A2, c, feeds) for c in range(3)}
+    return {c: mixed_tree(B3, A2, c, feeds, j0) for c in range(3)}
 
 
 def emulate_row_pass3(x, n1, chunk, pad):
@@ -1082,15 +1161,17 @@ def emulate_row_pass3(x, n1, chunk, pad):
             qb = min(qa + chunk, P1)
             steps = (qb - qa) + (n - 1)
             stage = np.full(32 * UNR * n, np.nan, complex)
+            w0 = walk3_start(n)
+            assert w0 - 2 * S1 >= 0  # no look-back before the chunk's first window
             feeds = [(xr[:, qa + j], xr[:, max(qa + j - S1, 0)], xr[:, max(qa + j - 2 * S1, 0)])
-                     for j in range(steps)]
-            outs = tree3_outs(n, feeds)
-            for jb in range(0, steps, UNR):
+                     for j in range(w0, steps)]
+            outs = tree3_outs(n, feeds, w0)
+            for jb in range(w0, steps, UNR):
                 for j in range(jb, min(jb + UNR, steps)):
                     if j >= n - 1:
                         for c in range(R):
                             for u in range(OUT):
-                                stage[(lanes * UNR + (j - jb)) * n + c + 3 * u] = outs[c][j][u]
+                                stage[(lanes * UNR + (j - jb)) * n + c + 3 * u] = outs[c][j - w0][u]
                 j0, j1 = max(jb, n - 1), min(jb + UNR, steps)
                 if j1 > j0:
                     run, q, sofs = (j1 - j0) * n, qa + j0 - (n - 1), (j0 - jb) * n
@@ -1141,19 +1222,21 @@ def emulate_col_pass3(z, pad, n0, n1, P1, rows_out, chunk, scale):
                     ok = ch0 + cc < nch
                     ring[(rr & (RD - 1)) * W + cc] = np.where(ok, z[pad + rr, np.minimum(ch0 + cc, nch - 1)], 0)
 
-            fetch(qa - 2 * S1, min(qa + G, zr_end))
+            w0 = walk3_start(n)
+            fetch(qa + w0 - 2 * S1, min(qa + w0 + G, zr_end))
             feeds = []
-            for jb in range(0, steps, G):
+            for jb in range(w0, steps, G):
                 if jb + G < steps:
                     fetch(qa + jb + G, min(qa + jb + 2 * G, zr_end))
                 for j in range(jb, min(jb + G, steps)):
                     zr = qa + j
+                    assert zr - 2 * S1 >= qa  # the shortened walk reads no padding row
                     f = tuple(ring[((zr - d) & (RD - 1)) * W + my] for d in (0, S1, 2 * S1))
                     for d, v in zip((0, S1, 2 * S1), f):  # the live lanes read z rows zr - d
                         if M >= 1 or d == 0:
                             np.testing.assert_array_equal(v[active], z[pad + zr - d, ch[active]])
                     feeds.append(f)
-            outs = tree3_outs(n, feeds)
+            outs = tree3_outs(n, feeds, w0)
             orow = qa * orow_len + q1_0 * n * n1
             stage = [np.full(W * n, np.nan, complex) for _ in range(2)]
             buf = 0
@@ -1163,7 +1246,7 @@ def emulate_col_pass3(z, pad, n0, n1, P1, rows_out, chunk, scale):
                     for c in range(R):
                         for u in range(OUT):
                             idx = q1l * n * n1 + c * n1 + k1 + 3 * u * n1
-                            st[idx[my < CH]] = scale * outs[c][j][u][my < CH]
+                            st[idx[my < CH]] = scale * outs[c][j - w0][u][my < CH]
                     e = np.arange(tile_elems)
                     out[orow + e] = st[e]
                     written[orow + e] += 1
@@ -1172,7 +1255,7 @@ def emulate_col_pass3(z, pad, n0, n1, P1, rows_out, chunk, scale):
                     for c in range(R):
                         for u in range(OUT):
                             idx = orow + q1l * n * n1 + c * n1 + k1 + 3 * u * n1
-                            out[idx[active]] = scale * outs[c][j][u][active]
+                            out[idx[active]] = scale * outs[c][j - w0][u][active]
                             written[idx[active]] += 1
                 orow += orow_len
     assert (written == 1).all(), "output not written exactly once"
