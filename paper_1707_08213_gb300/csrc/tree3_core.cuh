@@ -37,16 +37,16 @@ struct OmegaN {
 };
 
 // Y0 = B0 + B1 + B2, Y1 = B0 + w3^-1 B1 + w3^-2 B2, Y2 = B0 + w3^-2 B1 + w3^-1 B2,
-// w3^-1 = -1/2 - i h, w3^-2 = -1/2 + i h.
+// w3^-1 = -1/2 - i h, w3^-2 = -1/2 + i h: with s = B1 + B2, d = B1 - B2 and t = B0 - s/2,
+// Y1 = t - i h d and Y2 = t + i h d, each component one fused multiply-add.
 __device__ __forceinline__ void bfly3(float2 b0, float2 b1, float2 b2, float h, float2 &y0, float2 &y1,
                                       float2 &y2) {
     const float2 s = c_add(b1, b2);
     const float2 d = c_sub(b1, b2);
     const float2 t = make_float2(fmaf(-0.5f, s.x, b0.x), fmaf(-0.5f, s.y, b0.y));
-    const float2 u = make_float2(h * d.y, -h * d.x);  // -i h d
     y0 = c_add(b0, s);
-    y1 = c_add(t, u);
-    y2 = c_sub(t, u);
+    y1 = make_float2(fmaf(h, d.y, t.x), fmaf(-h, d.x, t.y));
+    y2 = make_float2(fmaf(-h, d.y, t.x), fmaf(h, d.x, t.y));
 }
 
 // Window lengths n = 3^B3 2^A2 (B3 >= 1): B3 radix-3 levels first, then A2 radix-2 levels.
@@ -103,9 +103,12 @@ struct SlidingTreeMixed {
     float2 fifo[kFifo > 0 ? kFifo : 1];
     float2 tw[kTw];
 
-    __device__ __forceinline__ void init(int c, const OmegaN &om) {
-        tw[0] = om.w[(c * kS1) % kN];
-        tw[1] = om.w[(2 * c * kS1) % kN];
+    // scale: a factor applied to every output, folded into level 1 (its twiddles, and one
+    // FMA for the untwiddled term); the levels after it are linear.  1 leaves the tree's
+    // arithmetic as it is (fmaf(1, a, b) is a + b).
+    __device__ __forceinline__ void init(int c, const OmegaN &om, float scale = 1.f) {
+        tw[0] = c_scale(scale, om.w[(c * kS1) % kN]);
+        tw[1] = c_scale(scale, om.w[(2 * c * kS1) % kN]);
         static_for<2, L + 1>([&](auto TT) {
             constexpr int t = decltype(TT)::value;
             static_for<0, held(t - 1)>([&](auto AA) {
@@ -121,12 +124,15 @@ struct SlidingTreeMixed {
         for (int i = 0; i < (kFifo > 0 ? kFifo : 1); ++i) fifo[i] = make_float2(0.f, 0.f);
     }
 
-    // out[u] = level-L node c + 3 u at p; x_p, x_s1, x_s2 = the data at p, p - s_1, p - 2 s_1.
+    // out[u] = level-L node c + 3 u at p, times the scale given to init (the same scale here);
+    // x_p, x_s1, x_s2 = the data at p, p - s_1, p - 2 s_1.
     template <int J>
-    __device__ __forceinline__ void step(float h, float2 x_p, float2 x_s1, float2 x_s2, float2 (&out)[kOut]) {
-        // level 1, node c: x(p - 2 s1) + w_3^{-c} x(p - s1) + w_3^{-2c} x(p)
+    __device__ __forceinline__ void step(float h, float scale, float2 x_p, float2 x_s1, float2 x_s2,
+                                         float2 (&out)[kOut]) {
+        // level 1, node c: x(p - 2 s1) + w_3^{-c} x(p - s1) + w_3^{-2c} x(p), scaled
         float2 cur[kOut];
-        cur[0] = c_add(x_s2, c_add(c_mul(tw[0], x_s1), c_mul(tw[1], x_p)));
+        const float2 y = c_add(c_mul(tw[0], x_s1), c_mul(tw[1], x_p));
+        cur[0] = make_float2(fmaf(scale, x_s2.x, y.x), fmaf(scale, x_s2.y, y.y));
         level<J, 2>(h, cur);
 #pragma unroll
         for (int u = 0; u < kOut; ++u) out[u] = cur[u];

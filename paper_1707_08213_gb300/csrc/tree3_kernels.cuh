@@ -8,6 +8,7 @@
 
 #include <algorithm>
 
+#include "sm100_ptx.cuh"
 #include "swdft_internal.h"
 #include "tree3_core.cuh"
 
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(96) row_tree3_kernel(const __grid_constant__ R
                 } else {
                     const float2 x1 = load_x3<CPLX>(xrow, max(p1 - S1, 0));
                     const float2 x2 = load_x3<CPLX>(xrow, max(p1 - 2 * S1, 0));
-                    tree.template step<J % Tree::kPeriod>(p.om.h, xp, x1, x2, o);
+                    tree.template step<J % Tree::kPeriod>(p.om.h, 1.f, xp, x1, x2, o);
                 }
                 if (j >= n - 1) {
 #pragma unroll
@@ -152,6 +153,21 @@ __host__ __device__ constexpr size_t col3_smem(int n, int period) {
     return sizeof(float2) * ((size_t)col3_ring_rows(n, period) * kCol3Ch + 2 * (size_t)kCol3Ch * n);
 }
 
+// Bulk copy of `bytes` (a multiple of 16) from shared to global memory (both 16-byte aligned),
+// issued by one thread, with an evict-first L2 policy (the output is written once and should
+// not push z out of L2); read_wait() returns once every copy this thread issued has finished
+// reading shared memory, all_wait() once they are complete.
+__device__ __forceinline__ void bulk_store_evict_first(void *gmem, const void *smem, uint32_t bytes) {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;\n" ::"l"(gmem),
+                 "r"(smem_u32(smem)), "r"(bytes), "l"(pol)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_store_read_wait() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_store_all_wait() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
 __device__ __forceinline__ void cp_async3_8(void *smem, const void *gmem, bool valid) {
     const unsigned dst = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(gmem), "r"(valid ? 8 : 0)
@@ -191,6 +207,12 @@ __global__ void __launch_bounds__(192) col_tree3_kernel(const __grid_constant__ 
     const int sbase = q1l * n * p.n1 + c * p.n1 + k1;  // this thread's first staged output
     float2 *orow = p.out + (int64_t)qa * p.orow + q1_0 * n * p.n1;
     const float s = p.scale;
+    // The staged run of a window row goes out as one bulk copy when it starts 16-byte aligned
+    // and holds an even number of values (output rows of an even length, an even first value):
+    // the stage buffers start on 16 bytes (ring and buffers are multiples of 64 values).
+    // Otherwise every thread copies its share of the run.
+    const bool bulk = STAGED && p.orow % 2 == 0 && (q1_0 * n * p.n1) % 2 == 0 && tile_elems % 2 == 0 &&
+                      reinterpret_cast<uintptr_t>(p.out) % 16 == 0;
 
     auto fetch = [&](int r_lo, int r_hi) {
         const int total = (r_hi - r_lo) * CH;
@@ -203,8 +225,9 @@ __global__ void __launch_bounds__(192) col_tree3_kernel(const __grid_constant__ 
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
 
+    // the scale is folded into the tree's level 1 (an n0 = 1 window, with no tree, scales here)
     Tree tree;
-    if constexpr (Of::kSplit) tree.init(c, p.om);
+    if constexpr (Of::kSplit) tree.init(c, p.om, s);
     int buf = 0;
     // the walk starts at step 2 s_1, as in the row pass: its look-backs start at row qa
     fetch(qa, min(qa + 2 * S1 + G, zr_end));
@@ -221,32 +244,43 @@ __global__ void __launch_bounds__(192) col_tree3_kernel(const __grid_constant__ 
                 const float2 xp = ring[(zr & (RD - 1)) * W + my];
                 float2 o[OUT];
                 if constexpr (!Of::kSplit) {
-                    o[0] = xp;
+                    o[0] = c_scale(s, xp);
                 } else {
                     const float2 x1 = ring[((zr - S1) & (RD - 1)) * W + my];
                     const float2 x2 = ring[((zr - 2 * S1) & (RD - 1)) * W + my];
-                    tree.template step<J % Tree::kPeriod>(p.om.h, xp, x1, x2, o);
+                    tree.template step<J % Tree::kPeriod>(p.om.h, s, xp, x1, x2, o);
                 }
                 if (j >= n - 1) {
                     if constexpr (STAGED) {
                         float2 *st = stage + buf * (W * n);
                         if (my < CH) {
 #pragma unroll
-                            for (int u = 0; u < OUT; ++u) st[sbase + 3 * u * p.n1] = c_scale(s, o[u]);
+                            for (int u = 0; u < OUT; ++u) st[sbase + 3 * u * p.n1] = o[u];
+                        }
+                        if (bulk) {
+                            // this thread's stores are made visible to the bulk copy; thread 0
+                            // waits until the previous row's copy has read the other buffer
+                            // (the one the next row writes) before the barrier publishes it
+                            fence_proxy_async_smem();
+                            if (threadIdx.x == 0) bulk_store_read_wait();
                         }
                         __syncthreads();
                         constexpr int NT = R * W;                 // threads per block
-                        constexpr int PER = (W * n + NT - 1) / NT;  // copies per thread
+                        if (bulk) {
+                            if (threadIdx.x == 0) bulk_store_evict_first(orow, st, (uint32_t)tile_elems * 8u);
+                        } else {
+                            constexpr int PER = (W * n + NT - 1) / NT;  // copies per thread
 #pragma unroll
-                        for (int i = 0; i < PER; ++i) {
-                            const int e = threadIdx.x + i * NT;
-                            if (e < tile_elems) __stcs(orow + e, st[e]);
+                            for (int i = 0; i < PER; ++i) {
+                                const int e = threadIdx.x + i * NT;
+                                if (e < tile_elems) __stcs(orow + e, st[e]);
+                            }
                         }
                         buf ^= 1;
                     } else if (active) {
                         // whole 32-byte sectors per window column already (n1 a multiple of 4)
 #pragma unroll
-                        for (int u = 0; u < OUT; ++u) __stcs(orow + sbase + 3 * u * p.n1, c_scale(s, o[u]));
+                        for (int u = 0; u < OUT; ++u) __stcs(orow + sbase + 3 * u * p.n1, o[u]);
                     }
                     orow += p.orow;
                 }
@@ -255,6 +289,7 @@ __global__ void __launch_bounds__(192) col_tree3_kernel(const __grid_constant__ 
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
     }
+    if (bulk && threadIdx.x == 0) bulk_store_all_wait();  // the stage stays valid until read
     (void)active;
 }
 

@@ -274,12 +274,13 @@ def mixed_period(B3, A2):
     return (r2 - 1) * (n // N2)
 
 
-def mixed_tree(B3, A2, c, feeds, j0=0):
+def mixed_tree(B3, A2, c, feeds, j0=0, scale=1.0):
     """Thread c (< 3) of the mixed-radix tree split by residue mod 3 (tree3_core.cuh,
     SlidingTreeMixed: B3 radix-3 levels, then A2 radix-2 levels) over the steps j = j0, j0 + 1, ..:
     feeds[j - j0] = (x at p, x at p - s_1, x at p - 2 s_1), s_1 = n / 3; returns its level-L
     nodes c + 3u, u < n / 3.  FIFO depths, slots (step index modulo the depth, within the
-    unroll period) and twiddle indices as the kernel has them."""
+    unroll period) and twiddle indices as the kernel has them; `scale` multiplies every output,
+    folded into level 1 as the column kernel folds it."""
     n = 3 ** B3 * 2 ** A2
     L = B3 + A2
     om = np.exp(-2j * np.pi * np.arange(n) / n)
@@ -299,7 +300,7 @@ def mixed_tree(B3, A2, c, feeds, j0=0):
     period = mixed_period(B3, A2)
     assert all(period % depth(t) == 0 for t in range(2, L + 1))
     s1 = n // 3
-    tw1 = (om[(c * s1) % n], om[(2 * c * s1) % n])
+    tw1 = (scale * om[(c * s1) % n], scale * om[(2 * c * s1) % n])
     tw = {t: [[om[((c + 3 * a) * d * (n // Nt(t))) % n] for d in range(1, rad(t))]
               for a in range(held(t - 1))] for t in range(2, L + 1)}
     fifos = {t: [[0j] * held(t - 1) for _ in range(depth(t))] for t in range(2, L + 1)}
@@ -307,7 +308,7 @@ def mixed_tree(B3, A2, c, feeds, j0=0):
     outs = []
     for i, (xp, xs1, xs2) in enumerate(feeds):
         J = (j0 + i) % period
-        cur = [xs2 + tw1[0] * xs1 + tw1[1] * xp]  # level 1, node c
+        cur = [scale * xs2 + tw1[0] * xs1 + tw1[1] * xp]  # level 1, node c
         for t in range(2, L + 1):
             s, D, hp = n // Nt(t), depth(t), held(t - 1)
             nxt = [0j] * (rad(t) * hp)
@@ -1133,12 +1134,13 @@ def col3_group(period):
     return 8 if period <= 8 and 8 % period == 0 else (6 if period == 6 else 12)
 
 
-def tree3_outs(n, feeds, j0=0):
-    """Every residue thread's outputs from step j0 on (the mixed tree; n = 1: the data itself)."""
+def tree3_outs(n, feeds, j0=0, scale=1.0):
+    """Every residue thread's outputs from step j0 on, scaled (the mixed tree; n = 1: the data
+    itself)."""
     B3, A2 = mixed_split(n)
     if B3 == 0:
-        return {0: [[f[0]] for f in feeds]}
-    return {c: mixed_tree(B3, A2, c, feeds, j0) for c in range(3)}
+        return {0: [[scale * f[0]] for f in feeds]}
+    return {c: mixed_tree(B3, A2, c, feeds, j0, scale) for c in range(3)}
 
 
 def emulate_row_pass3(x, n1, chunk, pad):
@@ -1236,7 +1238,7 @@ def emulate_col_pass3(z, pad, n0, n1, P1, rows_out, chunk, scale):
                         if M >= 1 or d == 0:
                             np.testing.assert_array_equal(v[active], z[pad + zr - d, ch[active]])
                     feeds.append(f)
-            outs = tree3_outs(n, feeds, w0)
+            outs = tree3_outs(n, feeds, w0, scale)  # the scale folded into level 1
             orow = qa * orow_len + q1_0 * n * n1
             stage = [np.full(W * n, np.nan, complex) for _ in range(2)]
             buf = 0
@@ -1246,8 +1248,13 @@ def emulate_col_pass3(z, pad, n0, n1, P1, rows_out, chunk, scale):
                     for c in range(R):
                         for u in range(OUT):
                             idx = q1l * n * n1 + c * n1 + k1 + 3 * u * n1
-                            st[idx[my < CH]] = scale * outs[c][j - w0][u][my < CH]
+                            st[idx[my < CH]] = outs[c][j - w0][u][my < CH]
                     e = np.arange(tile_elems)
+                    # one bulk copy (16-byte aligned ends, a multiple of 16 bytes) where the run
+                    # allows it, else per-thread copies: the same values either way
+                    bulk = orow_len % 2 == 0 and (q1_0 * n * n1) % 2 == 0 and tile_elems % 2 == 0
+                    if bulk:
+                        assert orow % 2 == 0 and (RD * W + buf * W * n) % 2 == 0 and (8 * tile_elems) % 16 == 0
                     out[orow + e] = st[e]
                     written[orow + e] += 1
                     buf ^= 1
@@ -1255,7 +1262,7 @@ def emulate_col_pass3(z, pad, n0, n1, P1, rows_out, chunk, scale):
                     for c in range(R):
                         for u in range(OUT):
                             idx = orow + q1l * n * n1 + c * n1 + k1 + 3 * u * n1
-                            out[idx[active]] = scale * outs[c][j - w0][u][active]
+                            out[idx[active]] = outs[c][j - w0][u][active]
                             written[idx[active]] += 1
                 orow += orow_len
     assert (written == 1).all(), "output not written exactly once"
