@@ -78,6 +78,16 @@ struct SlidingTreeAdjoint {
         return u[0];
     }
 
+    // Step J's partial of y(p) when this thread's level-1 node at p is zero: the level-1 FIFO
+    // slot alone (U_1(p + s_1)'s pair sum, or below the split this thread's own partial), with
+    // no level evaluated.  That holds at the last n/2 positions of a walk whose inputs stop
+    // n - 1 steps before its end: U_1(p) depends on the inputs at p .. p + n/2 - 1 only.
+    template <int J>
+    __device__ __forceinline__ float2 tail() const {
+        static_assert(M >= 1, "a window of one sample has no tree");
+        return ring[ta_off(M, B, 1) + (J % (1 << (M - 1))) * ta_slots(B, 1)];
+    }
+
   private:
     template <int J, int V>
     __device__ __forceinline__ void level(float2 (&cur)[kIn]) {

@@ -200,6 +200,10 @@ __global__ void __launch_bounds__(128, (M <= 4 ? 5 : (M == 5 ? 3 : 1))) adj_col_
     constexpr int GS = kAdjGS(M);
     constexpr int NS = kAdjStages;
     constexpr int UNR = Tree::kPeriod > GS ? Tree::kPeriod : GS;  // both powers of two
+    // The last n/2 drain steps read the level-1 FIFO alone (SlidingTreeAdjoint::tail) for
+    // n0 = 16 and 64, where that measured faster (512x512 64x16: 0.97 -> 0.50 ms, 16x16 and
+    // 16x64 2-3%); n0 = 32 measured 4% slower with it and n0 <= 8 has at most 4 such steps.
+    constexpr bool kTail = M == 4 || M == 6;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2 *ring = reinterpret_cast<float2 *>(smem_raw + 128);  // [NS][GS][slot]
 
@@ -287,16 +291,22 @@ __global__ void __launch_bounds__(128, (M <= 4 ? 5 : (M == 5 ? 3 : 1))) adj_col_
             }
             if (j < steps) {
                 const int r = p_hi - j;  // z row (window end row) of this step
-                float2 u[Tree::kIn];
-                if (j < nwin) {
-                    const float2 *src = ring + ((size_t)(g % NS) * GS + (J % GS)) * slot + tbase;
-#pragma unroll
-                    for (int t = 0; t < Tree::kIn; ++t) u[t] = src[t * tstride];
+                float2 y;
+                if (kTail && j >= nwin + n / 2 - 1) {
+                    // the last n/2 rows: no window of the chunk reaches them through level 1
+                    if constexpr (kTail) y = tree.template tail<J>();
                 } else {
+                    float2 u[Tree::kIn];
+                    if (j < nwin) {
+                        const float2 *src = ring + ((size_t)(g % NS) * GS + (J % GS)) * slot + tbase;
 #pragma unroll
-                    for (int t = 0; t < Tree::kIn; ++t) u[t] = make_float2(0.f, 0.f);
+                        for (int t = 0; t < Tree::kIn; ++t) u[t] = src[t * tstride];
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < Tree::kIn; ++t) u[t] = make_float2(0.f, 0.f);
+                    }
+                    y = tree.template step<J>(u);
                 }
-                float2 y = tree.template step<J>(u);
 #pragma unroll
                 for (int off = CPW; off < 32; off <<= 1) {  // the residues of one channel
                     y.x += __shfl_xor_sync(0xffffffffu, y.x, off);

@@ -87,10 +87,12 @@ def forward_walk(M, B, c, x):
     return forward_tree(M, B, c, feeds)
 
 
-def adjoint_tree(M, B, c, feeds):
+def adjoint_tree(M, B, c, feeds, tail_from=None):
     """Thread c of the transposed tree (adjoint_core.cuh, SlidingTreeAdjoint) over the steps
     j = 0, 1, ..: feeds[j] = its held level-M inputs (k = c + 2^B t) at step j, each a value
-    or an array over independent lanes; returns the thread's partial output at every step."""
+    or an array over independent lanes; returns the thread's partial output at every step.
+    From step tail_from on the output is the level-1 FIFO slot alone (SlidingTreeAdjoint::tail),
+    with no tree evaluated."""
     n = 1 << M
     om = np.exp(-2j * np.pi * np.arange(n) / n)
     cb = c & ((1 << B) - 1)
@@ -106,6 +108,9 @@ def adjoint_tree(M, B, c, feeds):
     outs = []
     for j, feed in enumerate(feeds):
         J = j % period
+        if tail_from is not None and j >= tail_from:
+            outs.append(rings[1][J % (1 << (M - 1))][0])
+            continue
         cur = list(feed)
         for v in range(M, 0, -1):
             slot = J % (1 << (M - v))
@@ -212,6 +217,27 @@ def test_adjoint_schedule_gives_the_overlap_add_of_inverse_dfts(M, B):
         ref[q:q + n] += np.fft.ifft(G[q]) * n  # sum_k G[q][k] w^{+jk}
     y = sum(adjoint_walk(M, B, c, G, N) for c in range(1 << B))
     np.testing.assert_allclose(y, ref, atol=1e-9)
+
+
+@pytest.mark.parametrize("M,B", [(M, B) for (M, B) in SPLITS if M >= 1])
+def test_adjoint_walk_ends_with_level_one_fifo_readout(M, B):
+    """A chunk's walk ends with n - 1 steps past its last window (zero inputs).  In the last
+    n/2 of them no window reaches the position through level 1 (its support is n/2 - 1 steps
+    deep), so every thread's partial is its level-1 FIFO slot: the walk with that readout equals
+    the full walk at every step.  Planted mistake: starting the readout one step earlier loses
+    the level-1 node of the first readout step."""
+    n = 1 << M
+    nwin = n + 5
+    rng = np.random.default_rng(1200 + 10 * M + B)
+    G = rng.standard_normal((nwin, n)) + 1j * rng.standard_normal((nwin, n))
+    cb = lambda c: c & ((1 << B) - 1)
+    feeds = {c: [[G[j][cb(c) + (t << B)] for t in range(held(B, M))] if j < nwin else [0j] * held(B, M)
+                 for j in range(nwin + n - 1)] for c in range(1 << B)}
+    full = sum(np.array(adjoint_tree(M, B, c, feeds[c])) for c in range(1 << B))
+    tail = sum(np.array(adjoint_tree(M, B, c, feeds[c], nwin + n // 2 - 1)) for c in range(1 << B))
+    np.testing.assert_allclose(tail, full, atol=1e-12)
+    early = sum(np.array(adjoint_tree(M, B, c, feeds[c], nwin + n // 2 - 2)) for c in range(1 << B))
+    assert np.abs(early - full).max() > 1e-6
 
 
 def ternary_tree(M, c, feeds, j0=0):
@@ -578,8 +604,11 @@ def emulate_adj_col_ring(G, n0, n1, chunk_req, q16=True):
                     sel = np.nonzero(c_of == c)[0]
                     feeds[c].append([u[sel, t] for t in range(held(B, M))])
             part = np.zeros((steps, 128), complex)
+            # for n0 = 16 and 64 the last n/2 steps read the level-1 FIFO alone (no window
+            # reaches them through level 1)
+            tail = nwin + n // 2 - 1 if M in (4, 6) else None
             for c in range(R):
-                part[:, np.nonzero(c_of == c)[0]] = np.array(adjoint_tree(M, B, c, feeds[c]))
+                part[:, np.nonzero(c_of == c)[0]] = np.array(adjoint_tree(M, B, c, feeds[c], tail))
             off = CPW
             while off < 32:
                 part = part + part[:, (warp << 5) | (lane ^ off)]
