@@ -57,30 +57,36 @@ __device__ __forceinline__ void atomic_add2(float2 *d, float2 v) {
 // The window's inverse DFT, X[j] = sum_k v[k] w_N^{+jk} (unnormalised), in place by
 // decimation in time: N = R M (radix R = 3 while N has a factor 3 above 3, then 2), the R
 // interleaved subsequences v[d], v[d + R], ... transformed recursively in place, then per
-// j' < M one R-point butterfly on their outputs twiddled by w_N^{+j' d}, its output a stored
-// back over input d.  Inputs in natural order; X[j] ends at position ifft_pos(N, j) =
-// R ifft_pos(M, j mod M) + j / M (digit-reversed), all indices fixed at compile time;
-// twiddles w_N^{+x} = conj(w_NTOP^{-x NTOP / N}) from the kernel parameters' table for the top
-// length NTOP.  N (sum of the radices) complex multiply-adds per element.
+// j' < M one R-point butterfly on their outputs twiddled by w_N^{+j' d} (no twiddle for
+// j' = 0), its output a stored back over input d.  Inputs in natural order; X[j] ends at
+// position ifft_pos(N, j) = R ifft_pos(M, j mod M) + j / M (digit-reversed), all indices fixed
+// at compile time; twiddles w_N^{+x} = conj(w_NTOP^{-x NTOP / N}) from the kernel parameters'
+// table for the top length NTOP.  The 2-point butterfly is a sum and a difference; the
+// 3-point one, with s = t1 + t2, d = t1 - t2 and m = t0 - s/2, is X0 = t0 + s,
+// X1 = m + i h d, X2 = m - i h d (w_3^{+1} = -1/2 + i h, h = sin(pi/3)), each component of
+// X1 and X2 one fused multiply-add.
 __host__ __device__ constexpr int ifft_radix(int n) { return (n % 3 == 0 && n > 3) ? 3 : ((n % 2 == 0 && n > 2) ? 2 : n); }
 __host__ __device__ constexpr int ifft_pos(int n, int j) {
     return n <= 3 ? j : ifft_radix(n) * ifft_pos(n / ifft_radix(n), j % (n / ifft_radix(n))) + j / (n / ifft_radix(n));
+}
+
+__device__ __forceinline__ void ibfly3(float2 t0, float2 t1, float2 t2, float h, float2 &x0, float2 &x1, float2 &x2) {
+    const float2 s = c_add(t1, t2);
+    const float2 d = c_sub(t1, t2);
+    const float2 m = make_float2(fmaf(-0.5f, s.x, t0.x), fmaf(-0.5f, s.y, t0.y));
+    x0 = c_add(t0, s);
+    x1 = make_float2(fmaf(-h, d.y, m.x), fmaf(h, d.x, m.y));
+    x2 = make_float2(fmaf(h, d.y, m.x), fmaf(-h, d.x, m.y));
 }
 
 template <int NTOP, int N, int STRIDE, int OFF, int NV>
 __device__ __forceinline__ void ifft_rec(float2 (&v)[NV], const OmegaN &om) {
     if constexpr (N == 2) {
         const float2 a = v[OFF], b = v[OFF + STRIDE];
-        v[OFF] = make_float2(a.x + b.x, a.y + b.y);
-        v[OFF + STRIDE] = make_float2(a.x - b.x, a.y - b.y);
+        v[OFF] = c_add(a, b);
+        v[OFF + STRIDE] = c_sub(a, b);
     } else if constexpr (N == 3) {
-        const float2 x0 = v[OFF], x1 = v[OFF + STRIDE], x2 = v[OFF + 2 * STRIDE];
-        static_for<0, 3>([&](auto AA) {
-            constexpr int a = decltype(AA)::value;
-            const float2 t1 = conj_mul(om.w[(a * 1 * (NTOP / 3)) % NTOP], x1);
-            const float2 t2 = conj_mul(om.w[(a * 2 * (NTOP / 3)) % NTOP], x2);
-            v[OFF + a * STRIDE] = make_float2(x0.x + t1.x + t2.x, x0.y + t1.y + t2.y);
-        });
+        ibfly3(v[OFF], v[OFF + STRIDE], v[OFF + 2 * STRIDE], om.h, v[OFF], v[OFF + STRIDE], v[OFF + 2 * STRIDE]);
     } else if constexpr (N > 3) {
         constexpr int R = ifft_radix(N), M = N / R;
         static_for<0, R>([&](auto DD) {
@@ -93,19 +99,17 @@ __device__ __forceinline__ void ifft_rec(float2 (&v)[NV], const OmegaN &om) {
             float2 t[R];
             static_for<0, R>([&](auto DD) {
                 constexpr int d = decltype(DD)::value;
-                t[d] = d == 0 ? v[base] : conj_mul(om.w[(jp * d * (NTOP / N)) % NTOP], v[base + STRIDE * d]);
+                if constexpr (d == 0 || jp == 0)
+                    t[d] = v[base + STRIDE * d];
+                else
+                    t[d] = conj_mul(om.w[(jp * d * (NTOP / N)) % NTOP], v[base + STRIDE * d]);
             });
-            static_for<0, R>([&](auto AA) {
-                constexpr int a = decltype(AA)::value;
-                float2 x = t[0];
-                static_for<1, R>([&](auto DD) {
-                    constexpr int d = decltype(DD)::value;
-                    const float2 u = conj_mul(om.w[(a * d * (NTOP / R)) % NTOP], t[d]);
-                    x.x += u.x;
-                    x.y += u.y;
-                });
-                v[base + STRIDE * a] = x;
-            });
+            if constexpr (R == 3) {
+                ibfly3(t[0], t[1], t[2], om.h, v[base], v[base + STRIDE], v[base + 2 * STRIDE]);
+            } else {
+                v[base] = c_add(t[0], t[1]);
+                v[base + STRIDE] = c_sub(t[0], t[1]);
+            }
         });
     }
 }
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(kAdj3Threads) adj3_row_kernel(const __grid_con
 static void fill_omega_adj(OmegaN &om, int n) {
     make_omega(n, om.w);
     for (int j = n; j < kMaxN; ++j) om.w[j] = make_float2(0.f, 0.f);
-    om.h = 0.f;
+    om.h = n % 3 == 0 ? -om.w[n / 3].y : 0.f;  // sin(pi/3) from the same table
 }
 
 cudaError_t launch_adj3_col(const Adj3ColArgs &a, cudaStream_t s) {
