@@ -9,15 +9,24 @@
 namespace swdft {
 
 // gz[qb + o][ch] += side[b - 1][o][ch] for every chunk boundary qb = b * chunk (b >= 1) and
-// o < n0 - 1: the rows two adj_col chunks share.  Grid z = array.
+// o < n0 - 1: the rows two adj_col chunks share.  Grid y = boundary b - 1, z = array; each
+// boundary's rows are one contiguous run in gz and in side, added two values (16 bytes) at a
+// time when both runs allow it (pairs), else one.
 __global__ void __launch_bounds__(256) adj_fold_kernel(const __grid_constant__ AdjFoldParams p) {
-    float2 *gz = p.gz[blockIdx.z];
-    const float2 *side = p.side[blockIdx.z];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = i / p.per_row + 1;  // boundary
-        float2 *dst = gz + b * p.chunk * p.nch + (i - (b - 1) * p.per_row);
-        *dst = c_add(*dst, side[i]);
+    const int64_t b = (int64_t)blockIdx.y + 1;
+    float2 *dst = p.gz[blockIdx.z] + b * p.chunk * p.nch;
+    const float2 *src = p.side[blockIdx.z] + (b - 1) * p.per_row;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (p.pairs) {
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+        const float4 *s4 = reinterpret_cast<const float4 *>(src);
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.per_row / 2; i += stride) {
+            const float4 a = d4[i], v = s4[i];
+            d4[i] = make_float4(a.x + v.x, a.y + v.y, a.z + v.z, a.w + v.w);
+        }
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.per_row; i += stride)
+            dst[i] = c_add(dst[i], src[i]);
     }
 }
 
@@ -109,8 +118,16 @@ cudaError_t launch_adj_col(const AdjColArgs &a, cudaStream_t s) {
     f.per_row = ((int64_t(1) << a.m0) - 1) * nch;
     f.total = side_elems;
     f.chunk = p.chunk;
-    const int64_t fb = std::min<int64_t>((side_elems + 255) / 256, 4096);
-    adj_fold_kernel<<<dim3((unsigned)fb, 1, (unsigned)a.nz), 256, 0, s>>>(f);
+    // 16-byte pieces: gz and side 16-byte aligned, and every boundary's run (per_row values,
+    // starting chunk * nch values into gz) of an even length at an even offset
+    f.pairs = nch % 2 == 0 ? 1 : 0;
+    for (int z = 0; z < a.nz; ++z)
+        if ((uintptr_t)a.gz[z] % 16 != 0 || (uintptr_t)a.side[z] % 16 != 0) f.pairs = 0;
+    const int64_t nb = side_elems / f.per_row;  // chunk boundaries
+    if (nb > 65535) return cudaErrorInvalidValue;
+    const int64_t pieces = f.pairs ? f.per_row / 2 : f.per_row;
+    const int64_t fb = std::max<int64_t>(1, std::min<int64_t>((pieces + 255) / 256, 1024));
+    adj_fold_kernel<<<dim3((unsigned)fb, (unsigned)nb, (unsigned)a.nz), 256, 0, s>>>(f);
     return cudaGetLastError();
 }
 

@@ -48,6 +48,7 @@ struct AdjFoldParams {
     int64_t per_row;   // (n0 - 1) * nch: side values per chunk boundary
     int64_t total;     // (chunks - 1) * per_row
     int chunk;         // window rows per adj_col chunk
+    int pairs;         // add 16-byte pieces (nch even, gz and side 16-byte aligned)
 };
 
 template <int R>
