@@ -221,6 +221,43 @@ __global__ void __launch_bounds__(kAdj3Threads) adj3_row_kernel(const __grid_con
 // window lengths of the dense passes: 1 and every 3^b 2^a <= 64 with b >= 1
 #define SWDFT_ADJ3_CASES(F) F(1) F(3) F(6) F(9) F(12) F(18) F(24) F(27) F(36) F(48) F(54)
 
+// Resident blocks per SM of one instantiation (occupancy API; 1 if the query fails).
+template <class K>
+static int adj3_bps(K kernel, size_t smem) {
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, kAdj3Threads, smem) != cudaSuccess || bps < 1)
+        bps = 1;
+    return bps;
+}
+
+// Windows per block along the chunked dimension: `blocks` blocks across it, `units` windows
+// along it, `slots` blocks resident at once.  Chunks cost nothing but the atomic adds of
+// their n - 1 shared outputs (no warm-up: every window is transformed once), so the count is
+// the one that minimises whole waves x windows per block (a last wave that is mostly empty
+// leaves most SMs idle), with at least 4 windows per block.
+static int adj3_chunk(int64_t units, int64_t blocks, int64_t slots) {
+    int64_t best = units, best_cost = INT64_MAX;
+    for (int64_t nc = 1; nc <= std::min<int64_t>(units, 256); ++nc) {
+        const int64_t chunk = (units + nc - 1) / nc;
+        if (chunk < 4 && nc > 1) break;
+        const int64_t waves = (blocks * ((units + chunk - 1) / chunk) + slots - 1) / slots;
+        const int64_t cost = waves * chunk;
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = chunk;
+        }
+    }
+    return (int)best;
+}
+
+static int sm_count_now() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1)
+        sms = 152;
+    return sms;
+}
+
 static void fill_omega_adj(OmegaN &om, int n) {
     make_omega(n, om.w);
     for (int j = n; j < kMaxN; ++j) om.w[j] = make_float2(0.f, 0.f);
@@ -240,25 +277,26 @@ cudaError_t launch_adj3_col(const Adj3ColArgs &a, cudaStream_t s) {
     p.nch = nch;
     p.n1 = a.n1;
     p.rows_out = (int)a.rows_out;
-    // chunks cost nothing but the atomic adds of their n0 - 1 shared rows (no warm-up: every
-    // window is transformed once), so they are cut to give about eight blocks per SM
     const int64_t cblocks = (nch + kAdj3Threads - 1) / kAdj3Threads;
-    const int64_t want = std::max<int64_t>(1, (kAdj3Blocks + cblocks - 1) / cblocks);
-    p.chunk = (int)std::min<int64_t>(a.rows_out, std::max<int64_t>(4, (a.rows_out + want - 1) / want));
     p.scale = a.scale;
     fill_omega_adj(p.om, a.n0);
-    const dim3 grid((unsigned)cblocks, (unsigned)((a.rows_out + p.chunk - 1) / p.chunk));
-    if (grid.y > 65535 || cblocks > INT32_MAX) return cudaErrorInvalidValue;
+    if (cblocks > INT32_MAX) return cudaErrorInvalidValue;
     const size_t smem = sizeof(float2) * (size_t)a.n0 * kAdj3Threads;
+    const int64_t sms = sm_count_now();
     switch (a.n0) {
 #define F(N_)                                                                                            \
-    case N_:                                                                                             \
+    case N_: {                                                                                           \
         if (smem > 48 * 1024 &&                                                                          \
             (e = cudaFuncSetAttribute(adj3_col_kernel<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                       (int)smem)) != cudaSuccess)                                        \
             return e;                                                                                    \
+        static const int bps = adj3_bps(adj3_col_kernel<N_>, smem);                                      \
+        p.chunk = adj3_chunk(a.rows_out, cblocks, sms * bps);                                            \
+        const dim3 grid((unsigned)cblocks, (unsigned)((a.rows_out + p.chunk - 1) / p.chunk));            \
+        if (grid.y > 65535) return cudaErrorInvalidValue;                                                \
         adj3_col_kernel<N_><<<grid, kAdj3Threads, smem, s>>>(p);                                         \
-        break;
+        break;                                                                                           \
+    }
         SWDFT_ADJ3_CASES(F)
 #undef F
         default:
