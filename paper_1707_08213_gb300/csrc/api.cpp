@@ -94,6 +94,9 @@ struct ArrayPlan {
     // per-array launches (tree or tensor-core form) beside the persistent kernels
     int batch_mode = 0;
     int64_t tc_chunk = 48;           // window rows per tensor-core CTA
+    // column tiles of the pipelined persistent kernel when cfg is the fused form (whose own
+    // chunks are cut for recomputing z): the two-pass rule's chunk
+    int64_t pipe_col_chunk = 0;
 
     int64_t band_rows() const { return q_end - q_begin; }
     size_t in_elem() const { return dtype == SWDFT_C64 ? sizeof(float2) : sizeof(float); }
@@ -255,8 +258,17 @@ void default_config(ArrayPlan &a, int sm_count, int conc) {
     const bool small = a.n0 * a.n1 <= 64;
     const double z_live = (double)a.z_bytes(a.band_rows()) * std::max(1, conc);
     c.fused = can_fuse && (small || (a.n0 >= 16 && z_live > 96e6));
-    // chunks of window rows (col_nchunks); col_chunk_for keeps every chunk at 2 n0 rows or more
-    c.col_chunk = col_chunk_for(a, col_nchunks(a, sm_count, c.fused && small));
+    // chunks of window rows (col_nchunks); col_chunk_for keeps every chunk at 2 n0 rows or more.
+    // The fused form of larger windows recomputes its n0 - 1 warm-up z rows per chunk by row
+    // DFTs, so it takes two chunks, more only where few 32-channel groups need them for four
+    // blocks per SM (1024x2048 complex, 16x64 windows: 2.585 ms at eight chunks, 2.53 at two).
+    int nchunks = col_nchunks(a, sm_count, c.fused && small);
+    if (c.fused && !small) {
+        const int64_t groups = (a.P1 * a.n1 + 31) / 32;
+        nchunks = (int)std::min<int64_t>(nchunks, std::max<int64_t>(2, (4LL * sm_count + groups - 1) / groups));
+    }
+    c.col_chunk = col_chunk_for(a, nchunks);
+    a.pipe_col_chunk = col_chunk_for(a, col_nchunks(a, sm_count, false));
     a.cfg = c;
 }
 
@@ -275,7 +287,8 @@ PipeGeom pipe_geom(const ArrayPlan &a) {
         a.P1, std::max<int64_t>(1, default_row_chunk(a.P1, zrows, int64_t(1) << batch_pipe_row_B(a.m1), a.n1)));
     g.row_chunks = (int)((a.P1 + g.row_chunk - 1) / g.row_chunk);
     g.row_blocks = (int)((zrows + g.rpb - 1) / g.rpb);
-    g.col_chunk = (int)std::min<int64_t>(rows_out, std::max<int64_t>(1, a.cfg.col_chunk));
+    const int64_t cc = a.cfg.fused && a.pipe_col_chunk > 0 ? a.pipe_col_chunk : a.cfg.col_chunk;
+    g.col_chunk = (int)std::min<int64_t>(rows_out, std::max<int64_t>(1, cc));
     g.col_chunks = (int)((rows_out + g.col_chunk - 1) / g.col_chunk);
     const int64_t per_block = 32LL * batch_col_groups(a.m0);
     g.col_blocks = (int)((a.P1 * a.n1 + per_block - 1) / per_block);
