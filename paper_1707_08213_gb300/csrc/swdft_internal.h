@@ -34,7 +34,8 @@ void make_omega(int n, float2 *out);
 //    n1/2 (each chunk's walk starts n1/2 columns before its first window: n1/2 - 1 steps of
 //    warm-up).
 //  * column levels: thread = (channel, residue, chunk of window rows); B = 2 (3 for 64-point
-//    trees); about eight row chunks per 32-channel group (sixteen for fused small windows),
+//    trees); about eight row chunks per 32-channel group (sixteen for fused small windows;
+//    the plans give the fused form of larger windows two),
 //    more when there are few channel groups, so that the pass has at least four blocks per
 //    SM; every chunk at least 2 n0 rows (its walk has n0/2 - 1 steps of warm-up; n0 - 1 for
 //    n0 <= 8, whose walks start on a whole step group of 8 rows).
