@@ -42,7 +42,8 @@ def gpu_adjoint(sw, G, N0, N1, cplx, norm="unitary", band=None, pos="start"):
 
 SHAPES = [(1, 1, 1, 1), (9, 9, 8, 8), (37, 53, 4, 8), (64, 77, 8, 16), (23, 300, 1, 64),
           (300, 23, 64, 1), (100, 100, 32, 32), (130, 90, 64, 16), (45, 45, 2, 32), (50, 70, 16, 8),
-          (80, 120, 32, 64), (130, 100, 64, 64), (60, 70, 16, 16), (40, 33, 16, 1), (33, 40, 2, 1)]
+          (80, 120, 32, 64), (130, 100, 64, 64), (60, 70, 16, 16), (40, 33, 16, 1), (33, 40, 2, 1),
+          (100, 33, 4, 1)]  # seven column chunks over an odd number of channels: the fold's one-value path
 
 
 @pytest.mark.parametrize("cplx", [False, True])
