@@ -1536,7 +1536,9 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
         if (a.algo_auto) a.algo = SWDFT_ALGO_TREE_F32;  // the tree is tuned first, then compared
         default_config(a, plan->sm_count, plan->conc);
         if (a.ternary()) continue;  // one launch shape per ternary kernel: nothing to choose
-        const TreeConfig base = a.cfg;
+        const TreeConfig dflt = a.cfg;  // the default, fused or not: timed against the winner below
+        TreeConfig base = dflt;
+        base.fused = false;  // launch shapes are searched on the two-pass form (its row pass fills z)
         std::vector<TreeConfig> cands;
         for (int cb = std::max(0, std::min(a.m0, 3) - 2); cb <= std::min(a.m0, 3); ++cb)
             for (int groups : {1, 2})
@@ -1598,7 +1600,7 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
         // fused form: one kernel, timed as a whole against the two passes
         float best = best_row + best_col;
         if (ok && fused_supported(a.m0, a.m1)) {
-            for (int nc : {4, 8, 16}) {
+            for (int nc : {2, 4, 8, 16}) {
                 TreeConfig c = best_c;
                 c.fused = true;
                 c.col_groups = 1;
@@ -1612,8 +1614,17 @@ swdft_status swdft2d_autotune(swdft2d_plan_t plan, const void *const *d_in, void
                 }
             }
         }
+        // the winner against the default, each timed as a whole forward: the search sums
+        // separately timed passes, so it keeps its choice only where the whole is faster too
+        if (ok && (best_c.fused != dflt.fused || best_c.col_B != dflt.col_B || best_c.col_groups != dflt.col_groups ||
+                   best_c.col_chunk != dflt.col_chunk || best_c.row_B != dflt.row_B || best_c.row_chunk != dflt.row_chunk)) {
+            float t_best = 0.f, t_dflt = 0.f;
+            ok = time_pass(best_c, 3, &t_best) && time_pass(dflt, 3, &t_dflt);
+            if (ok && t_dflt <= t_best) best_c = dflt;
+            if (ok) best = std::min(t_best, t_dflt);
+        }
         if (!ok) {
-            a.cfg = base;
+            a.cfg = dflt;
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             return SWDFT_ERR_CUDA;
