@@ -114,12 +114,12 @@ def test_plan_validation_enums(nat):
 
 def test_adjoint_workspace_holds_z_and_the_chunk_side_rows(nat):
     """256x256 with 16x16 windows: the column adjoint splits 241 window rows into chunks of
-    max(ceil(241/8), 4 n0) = 64 rows (4 chunks); each of the 3 boundaries keeps n0 - 1 side
+    max(ceil(241/8), 6 n0) = 96 rows (3 chunks); each of the 2 boundaries keeps n0 - 1 side
     rows of P1*n1 complex64 after gz, which is z's size (n0/2 + 241 + n0 - 1 rows)."""
     p = nat.Plan([shp(256, 256, 16, 16)])
     r = lambda v: (v + 255) // 256 * 256
     z = (8 + 241 + 15) * 241 * 16 * 8
-    side = 3 * 15 * 241 * 16 * 8
+    side = 2 * 15 * 241 * 16 * 8
     assert p.workspace_size() == r(z) + r(side)
     assert p.launch_count(adjoint=True) == 3  # column pass, fold of the side rows, row pass
 

@@ -182,8 +182,8 @@ def test_adjoint_of_persistent_batch_plan(sw):
 def test_adjoint_of_same_shape_arrays_in_grouped_launches(sw, cplx):
     """Eleven arrays of one shape: the adjoint runs them as a group of eight and a group of
     three per launch; each result equals its one-array plan's bit for bit and the oracle's."""
-    N0, N1, n0, n1 = 70, 45, 8, 8  # two column chunks: the fold launch runs too
-    band = (5, 49)
+    N0, N1, n0, n1 = 120, 45, 8, 8  # two column chunks of at most 6 n0 rows: the fold launch runs too
+    band = (5, 99)
     P1 = N1 - n1 + 1
     Gs = [_G(200 + i, band[1] - band[0], P1, n0, n1) for i in range(11)]
     Gd = [torch.from_numpy(G).cuda() for G in Gs]
