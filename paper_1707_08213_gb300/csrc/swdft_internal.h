@@ -38,7 +38,7 @@ void make_omega(int n, float2 *out);
 //    the plans give the fused form of larger windows two),
 //    more when there are few channel groups, so that the pass has at least four blocks per
 //    SM; every chunk at least 2 n0 rows (its walk has n0/2 - 1 steps of warm-up; n0 - 1 for
-//    n0 <= 8, whose walks start on a whole step group of 8 rows).
+//    TMA-staged walks of n0 <= 8, which start on a whole step group of 8 rows).
 inline int default_row_B(int m1) { return m1 >= 6 ? 2 : (m1 < 3 ? m1 : 3); }
 inline int64_t default_row_chunk(int64_t P1, int64_t zrows, int64_t threads_per_row, int n1) {
     const int64_t t = zrows * threads_per_row;

@@ -9,8 +9,8 @@
 //
 // z layout: kZPad(n0) = n0/2 padding rows, then rows x P1 x n1 complex64.  The padding lets
 // the column pass read its level-0 look-back z[r - n0/2] without a bounds clamp (values
-// read there only feed incomplete border trees, which are never stored; only walks of
-// n0 <= 8 rows, which start a whole step group early, read it).
+// read there only feed incomplete border trees, which are never stored; only TMA-staged
+// walks of n0 <= 8 rows, which start a whole step group early, read it).
 //
 // Each column-pass warp covers 32 consecutive channels (q1, k1): its z loads and its
 // output stores move 256 contiguous bytes per k0 (full 32-byte sectors).  Outputs go out
@@ -140,6 +140,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 //                  form): z never goes to HBM.
 // fetch(ring, r_lo, r_hi, CH, ch0, RD) fills ring rows r_lo..r_hi-1; wait() completes it.
 struct ZStageLoad {
+    static constexpr bool kGroupAligned = false;  // fetches may start on any row
     const float2 *z;
     int64_t nch;
     __device__ __forceinline__ void fetch(float2 *ring, int r_lo, int r_hi, int CH, int64_t ch0, int RD) {
@@ -175,6 +176,7 @@ struct ZStageLoad {
 // form's.
 template <int M1, bool CPLX>
 struct ZStageRowDft {
+    static constexpr bool kGroupAligned = false;  // fetches may start on any row
     const void *x;      // first input row of the band
     int64_t ld;
     int zrows;          // z rows that exist (band rows + n0 - 1)
@@ -322,9 +324,10 @@ __device__ __forceinline__ void col_tile_impl(const ColGeom &p, int64_t ch_block
     const int64_t q1 = ch >> p.m1;
     const int64_t k1 = ch & (n1 - 1);
     const int kstride = R * n1;  // elements between outputs t and t+1 (k0 step 2^B)
-    // First step of the walk: n/2 (as in row_tile) rounded down to whole step groups, so that
-    // every fetch starts on a group; for n0 >= 16 it is n/2 and no padding row is read.
-    constexpr int kJ0 = (kH / kP) * kP;
+    // First step of the walk: n/2 (as in row_tile), rounded down to whole step groups for a
+    // stage whose every fetch must start on a group (TMA boxes; n/2 for n0 >= 16 anyway).  n/2
+    // is a multiple of the unroll period, so FIFO slots keep their step residues.
+    constexpr int kJ0 = Stage::kGroupAligned ? (kH / kP) * kP : kH;
     float2 *dst = p.out + slice * p.oslice + (int64_t)qa * p.orow + q1 * ((int64_t)n * n1) +
                   (int64_t)c * n1 + k1;
     const float s = p.scale;
@@ -398,6 +401,7 @@ constexpr int kColTmaAhead = 2;
 constexpr int kColTmaBars = kColTmaAhead + 1;
 template <int kP>
 struct ZStageTma {
+    static constexpr bool kGroupAligned = true;  // every box starts on a whole step group
     const CUtensorMap *map;
     int pad;            // padding rows in front of z (tensor row of z row r = r + pad)
     uint64_t *bar;      // kColTmaBars mbarriers in shared memory

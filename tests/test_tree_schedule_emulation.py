@@ -165,10 +165,11 @@ def row_walk_start(M):
     return (1 << M) // 2
 
 
-def col_walk_start(M):
-    """First step of a column tile's walk (col_tile_impl): n/2 rounded down to whole step groups,
-    so that every fetch still starts on a group (TMA boxes)."""
-    return ((1 << M) // 2 // col_group(M)) * col_group(M)
+def col_walk_start(M, group_aligned=True):
+    """First step of a column tile's walk (col_tile_impl): n/2, rounded down to whole step groups
+    for the TMA stage, whose every fetch must start on a group."""
+    half = (1 << M) // 2
+    return (half // col_group(M)) * col_group(M) if group_aligned else half
 
 
 def late_walk(M, B, c, x, j0):
@@ -1016,7 +1017,7 @@ def emulate_col_pass(stage, n0, B, groups, m1, P1, rows_out, chunk, scale):
         for qa in range(0, rows_out, chunk):
             qb = min(qa + chunk, rows_out)
             steps, zr_end = (qb - qa) + (n - 1), qb + n - 1
-            j0 = col_walk_start(M)
+            j0 = col_walk_start(M, isinstance(stage, TmaStage))
             ring = np.full(RD * CH, np.nan, complex)
             stage.fetch(ring, qa + j0 - kH, min(qa + j0 + kP, zr_end), CH, ch0, RD)
             inflight = []  # ring rows of each fetch still in flight, oldest first
